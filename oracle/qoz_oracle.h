@@ -1,0 +1,177 @@
+/*
+ * QoZ oracle: plain, slow, single-threaded CPU restatement of the QoZ method
+ * (arXiv 2310.14133, "Dynamic Quality Metric Oriented Error-bounded Lossy
+ * Compression for Scientific Datasets").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link or
+ * call this code: only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark use it.  It shares no code with the CUDA library.
+ *
+ * Conventions
+ *   - dims are slowest-first: 2D (ny, nx), 3D (nz, ny, nx); x is contiguous.
+ *   - all floating-point arithmetic on field values is IEEE binary32 with
+ *     contraction disabled (-ffp-contract=off) and a fixed evaluation order.
+ *   - interpolator type: 0 = linear, 1 = cubic.
+ *   - dimension order: index into the lexicographic list of permutations of
+ *     the axes (3D: 012,021,102,120,201,210; 2D: 01,10), Sec. 5.2.2.
+ *   - quant code 0 marks an unpredictable (or anchor) point; otherwise
+ *     code = q + 32768 with |q| <= 32767.
+ */
+#ifndef QOZ_ORACLE_H
+#define QOZ_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_MAX_LEVELS 8
+#define ORC_RADIUS 32768
+
+typedef struct {
+  int32_t anchor_stride;               /* power of two; levels L = log2(stride) */
+  uint8_t interp[ORC_MAX_LEVELS];      /* interp[l-1] for level l */
+  uint8_t order[ORC_MAX_LEVELS];       /* order[l-1] for level l */
+  double alpha, beta;                  /* Eq. (ebl) */
+} orc_params;
+
+/* Per-level statistics of one predictor run (used by Algorithm 1). */
+typedef struct {
+  double l1[ORC_MAX_LEVELS];           /* sum over level-l points of |x - pred| */
+  int64_t cnt[ORC_MAX_LEVELS];         /* number of level-l points */
+} orc_level_stats;
+
+/* Value range over the finite values of x (Sec. 7.1.4: e = eps * vrange).
+ * Returns the number of finite values; min = max = 0 when there is none. */
+int64_t orc_value_range(const float* x, int64_t n, float* out_min, float* out_max);
+
+/* Level-wise error bounds, Eq. (ebl): e_l = e / min(alpha^(l-1), beta),
+ * l = 1..L, written to el[l-1].  alpha^(l-1) by repeated multiplication. */
+void orc_level_bounds(double e, double alpha, double beta, int L, double* el);
+
+/* Permutation table entry: axes of order index `ord` for ndims axes. */
+void orc_order_axes(int ndims, int ord, int* axes);
+
+/* Multi-level interpolation predictor + linear-scale quantizer (Sec. 5).
+ * x[N] input; codes[N], recon[N] outputs (recon may be NULL); anchors gets
+ * the losslessly stored anchor values in array order (may be NULL).
+ * Unpredictable points are returned sorted by linear index; at most `cap` are
+ * written, the full count is returned in *n_unpred.
+ * stop_level: levels below it are not processed (1 = whole field).
+ * stats may be NULL.  Returns 0 on success, nonzero on invalid arguments. */
+int orc_compress(const float* x, int ndims, const int64_t* dims, double e,
+                 const orc_params* p, int stop_level,
+                 uint16_t* codes, float* recon, float* anchors, int64_t* n_anchors,
+                 int64_t* unpred_idx, float* unpred_val, int64_t cap, int64_t* n_unpred,
+                 orc_level_stats* stats);
+
+/* Mirror of orc_compress: rebuilds the field from codes, anchors and the
+ * sorted unpredictable list. */
+int orc_decompress(const uint16_t* codes, int ndims, const int64_t* dims, double e,
+                   const orc_params* p, const float* anchors,
+                   const int64_t* unpred_idx, const float* unpred_val, int64_t n_unpred,
+                   float* out);
+
+/* Number of anchor points (all coordinates multiples of the stride). */
+int64_t orc_anchor_count(int ndims, const int64_t* dims, int anchor_stride);
+
+/* 65536-bin histogram of the quant codes of non-anchor points. */
+void orc_histogram(const uint16_t* codes, int ndims, const int64_t* dims,
+                   int anchor_stride, uint64_t* hist);
+
+/* Total length in bits of an optimal (Huffman) prefix code for the symbol
+ * counts hist[0..K-1]; a single used symbol costs 1 bit per occurrence. */
+uint64_t orc_huffman_bits(const uint64_t* hist, int K);
+
+/* Rate estimate: Huffman bits of the codes + 32 bits per unpredictable value
+ * + 32 bits per anchor. */
+double orc_estimate_bits(const uint64_t* hist, int64_t n_unpred, int64_t n_anchors);
+
+/* Metrics, Sec. 3 */
+double orc_max_abs_err(const float* a, const float* b, int64_t n);
+double orc_mse(const float* a, const float* b, int64_t n);
+double orc_psnr(const float* a, const float* b, int64_t n, double vrange);
+/* Mean SSIM over all box windows of edge `win` placed every `step` points
+ * that lie fully inside the array; c1 = (0.01 vrange)^2, c2 = (0.03 vrange)^2.
+ * Returns the number of windows in *n_windows and the SUM of window SSIMs in
+ * *sum (either may be NULL); the return value is the mean (NaN if none). */
+double orc_ssim(const float* a, const float* b, int ndims, const int64_t* dims,
+                int win, int step, double vrange, int64_t* n_windows, double* sum);
+
+
+/* ------------------------------------------------------------------------
+ * Online tuning, Sec. 6
+ * ---------------------------------------------------------------------- */
+
+#define ORC_METRIC_MAXERR 0
+#define ORC_METRIC_PSNR 1
+#define ORC_METRIC_SSIM 2
+
+typedef struct {
+  int32_t block;          /* sample block size b (power of two); blocks hold b+1 points per axis */
+  double rate;            /* sampling rate r; stride S = round(b * r^(-1/d)) */
+  int32_t n_orders;       /* 2: increasing/decreasing axis order only; 6: all (3D) */
+  int32_t n_alpha;
+  double alphas[8];
+  int32_t n_beta;
+  double betas[8];
+  int32_t ssim_win, ssim_step;
+  int32_t anchor_stride;  /* of the full field */
+} orc_tune_opts;
+
+/* Result of one trial compression of all sampled blocks. */
+typedef struct {
+  double bits;            /* Huffman bits of the aggregated codes + 32 U + 32 A */
+  double B;               /* bits per sampled point */
+  int64_t npts, n_unpred, n_anchors;
+  double max_err, sse;    /* over the sampled points */
+  double ssim_sum;
+  int64_t ssim_n;
+  orc_level_stats stats;  /* summed over blocks */
+} orc_trial;
+
+typedef struct {
+  orc_params params;
+  double e;               /* absolute bound to compress with */
+  double B, M;            /* sampled bit rate and metric of the chosen setting */
+  int32_t n_trials;
+  int32_t n_blocks;
+  int64_t n_sampled_points;
+  double alg1_score[ORC_MAX_LEVELS];
+} orc_tune_result;
+
+/* Uniform block sampling, Sec. 6.1.  Writes block origins (3 per block,
+ * slowest-first, unused axes 0) and the common block extent; returns the
+ * number of blocks (at most cap are written). */
+int64_t orc_sample_blocks(int ndims, const int64_t* dims, int b, double rate,
+                          int64_t* origins, int64_t cap, int64_t* block_dims, int64_t* stride);
+
+/* Trial compression of the sampled blocks with params p (anchor stride of
+ * the blocks = p->anchor_stride) at absolute bound e, down to stop_level. */
+int orc_block_trial(const float* x, int ndims, const int64_t* dims,
+                    const int64_t* origins, int64_t nblocks, const int64_t* block_dims,
+                    const orc_params* p, double e, int stop_level, int ssim_win, int ssim_step,
+                    double vrange, orc_trial* out);
+
+/* Metric value of a trial, higher is better: PSNR (dB), SSIM, or -max error. */
+double orc_trial_metric(const orc_trial* t, int metric, double vrange);
+
+/* Table I comparison of the incumbent I = (b1, m1) with the challenger
+ * II = (b2, m2), both at bound e (metric m higher-is-better).
+ * Returns 0 (keep I), 1 (II replaces I), or -1 when the case needs one more
+ * trial of II: then *second_scale is set to 0.8 (case 3) or 1.2 (case 4) and
+ * the caller runs II at second_scale * e and calls again with (b2p, m2p).
+ * On the first call pass b2p = m2p = NaN. */
+int orc_table1(double b1, double m1, double b2, double m2, double b2p, double m2p,
+               double* second_scale);
+
+/* Whole tuner.  metric: ORC_METRIC_*; target NaN selects the paper's
+ * fixed-bound mode (max-error metric: maximise compression ratio; PSNR / SSIM:
+ * Table I comparisons at e); a finite target selects the target mode. */
+int orc_tune(const float* x, int ndims, const int64_t* dims, double e_user, double vrange,
+             int metric, double target, const orc_tune_opts* o, orc_tune_result* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
