@@ -1,0 +1,335 @@
+"""Benchmark: QoZ compression throughput on GB300.
+
+Workload (N=1): one 512^3 FP32 field, k^-5/3 Gaussian random field plus 8
+tanh fronts (NYX-sized, the plain-method-at-scale case), value-range
+relative bound 1e-3.  One step = one qoz_compress call on the resident
+field: value range, bound table, anchors, the five predictor levels, the code
+histogram and the unpredictable-list read-back.  `value` is FP32 input GB/s
+of whole steps timed with CUDA events; `e2e` adds the pinned host->device
+copy of the field and the device->host read of the serialized stream through
+the public API.  With --gpus N (torchrun) every rank compresses its own field
+(replicas, weak scaling).
+
+The reference arm (--impl reference) is the CPU oracle, timed on a bounded
+sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "compress GB/s (FP32 in) & % HBM roofline, bit-exact; learned vs sampled tune"
+REL_EB = 1e-3
+PARAMS = dict(interp=1, order=0, alpha=1.5, beta=4.0)
+LEVEL1_BYTES_PER_POINT = 4.0 + 2.0 * 7.0 / 8.0 + 4.0 / 8.0   # x + level-1 codes + coarse recon
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--n", type=int, default=512, help="edge of the cubic field")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("qoz_level.cu", "qoz_device.cuh", "qoz_internal.h"):
+        with open(os.path.join(ROOT, "paper_2310_14133_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_from_profile(n):
+    """Per-launch DRAM bytes of the level-1 compress kernel from the committed
+    ncu summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "level1_compress_512.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_hash:\s*(\w+)", txt)
+    t = re.search(r"dram_bytes_per_point:\s*([0-9.]+)", txt)
+    if not m or not t or m.group(1) != _kernel_source_hash():
+        return None
+    return float(t.group(1)) * n ** 3
+
+
+def run_reference(args, rank, world):
+    """CPU oracle arm: each step compresses a bounded sample (a 128^3 corner
+    block of the same field) with the oracle, single-threaded."""
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    import synth
+    oracle.build()
+    n = args.n
+    sub = min(128, n)
+    x = synth.config2_field(sub).numpy()  # same generator, smaller box
+    op = oracle.make_params(3, **PARAMS)
+
+    def step():
+        mn, mx, _ = oracle.value_range(x)
+        e = REL_EB * (float(mx) - float(mn))
+        r = oracle.compress(x, e, op, want_recon=False)
+        oracle.estimate_bits(oracle.histogram(r["codes"], 32), len(r["unpred_idx"]),
+                             len(r["anchors"]))
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    gbs = 4.0 * x.size * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{sub}^3 corner sample of the k^-5/3+fronts field, eps 1e-3, "
+                               "cubic, order 012, alpha 1.5, beta 4", "parallelism": "none"},
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{sub}^3 field per step, single-threaded C++ oracle"},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(x):
+    """The oracle as it stands, on a bounded sample: one compress of the
+    benchmark field itself (a few seconds of single-threaded CPU work)."""
+    import oracle
+    oracle.build()
+    sub = x.shape[0]
+    op = oracle.make_params(3, **PARAMS)
+    t0 = time.perf_counter()
+    mn, mx, _ = oracle.value_range(x)
+    e = REL_EB * (float(mx) - float(mn))
+    r = oracle.compress(x, e, op, want_recon=False)
+    oracle.estimate_bits(oracle.histogram(r["codes"], 32), len(r["unpred_idx"]),
+                         len(r["anchors"]))
+    dt = time.perf_counter() - t0
+    return {"value": 4.0 * x.size / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"one compress of the {sub}^3 benchmark field (eps 1e-3), "
+                      f"single-threaded, {dt:.1f} s"}
+
+
+def main():
+    args = parse()
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2310_14133_gb300 as q
+    import synth
+
+    n = args.n
+    N = n ** 3
+    x = synth.config2_field(n, device="cuda")
+    torch.cuda.synchronize()
+    p = q.make_params(3, **PARAMS)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    def step():
+        b = q.compress(x, REL_EB, p)
+        b.free()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    blob = q.compress(x, REL_EB, p)
+    info = blob.info()
+    ser_bytes = blob.serialize().numel()
+    blob.free()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    q.profile_read(reset=True)
+    q.profile_enable(True)
+    barrier()
+    clocks.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    q.profile_enable(False)
+    prof = q.profile_read(reset=True)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = 4.0 * N * world / (ms_step * 1e-3) / 1e9
+
+    lvl1_ms = prof.ms[q.STAGE_LEVEL + 1] / max(1, prof.calls[q.STAGE_LEVEL + 1])
+    pq_ms = sum(prof.ms[q.STAGE_LEVEL + l] for l in range(1, 9)) / args.steps
+    range_ms = prof.ms[q.STAGE_RANGE] / args.steps
+    peak, peak_kind = _peak_hbm()
+    achieved = LEVEL1_BYTES_PER_POINT * N / (lvl1_ms * 1e-3) / 1e9
+    traffic = _traffic_from_profile(n)
+
+    e2e = None
+    if not args.no_e2e:
+        hx = torch.empty((n, n, n), dtype=torch.float32, pin_memory=True)
+        hx.copy_(x)
+        xd = torch.empty_like(x)
+        out = torch.empty(ser_bytes + 4096, dtype=torch.uint8, pin_memory=True)
+
+        def e2e_step():
+            xd.copy_(hx, non_blocking=True)
+            b = q.compress(xd, REL_EB, p)
+            b.serialize(out)
+            b.free()
+
+        for _ in range(2):
+            e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        barrier()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        e2e = {"value": 4.0 * N * world / e2e_s / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": ser_bytes,
+               "ms_per_step": e2e_s * 1e3}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": f"{n}^3 FP32 k^-5/3 GRF + 8 tanh fronts (NYX-sized), rel bound 1e-3, "
+                        "fixed theta: cubic, order 012, alpha 1.5, beta 4",
+            "step": "qoz_compress: value range + anchors + 5 levels + histogram + counts",
+            "l2": "input 512 MiB > 126 MB L2; no flush needed",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "level_kernel<compress> level 1",
+                     "algorithmic_bytes_per_launch": LEVEL1_BYTES_PER_POINT * N,
+                     "peak_kind": peak_kind},
+        "breakdown_ms": {"range": range_ms, "levels_total": pq_ms, "level1": lvl1_ms,
+                         "pq_input_gbs": 4.0 * N / (pq_ms * 1e-3) / 1e9,
+                         "pq_frac_6N": 6.0 * N / (pq_ms * 1e-3) / 1e9 / peak},
+        "compression": {"est_ratio": info.est_ratio, "n_unpredictable": info.n_unpredictable,
+                        "abs_eb": info.abs_eb},
+        "gpu_launches": int(prof.launches),
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(x.cpu().numpy())
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

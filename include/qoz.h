@@ -1,0 +1,196 @@
+/*
+ * qoz.h -- C ABI of the GB300 (sm_103a) QoZ library.
+ *
+ * QoZ is the quality-metric-oriented, error-bounded lossy compressor of
+ * arXiv 2310.14133.  This library implements its data path on one GPU:
+ *   - the multi-level interpolation predictor with anchor points and
+ *     level-adapted interpolators (Sec. 5.1, Sec. 5.2.1, Sec. 5.2.2),
+ *   - level-wise error bounds e_l = e / min(alpha^(l-1), beta) (Eq. ebl),
+ *   - linear-scale quantization and its mirror on decompression (Sec. 5.1),
+ *   - the quality metrics max error, PSNR (Eq. psnr) and SSIM (Eq. ssim,
+ *     Eq. ssim2), and the Huffman rate estimate of the quantization bins
+ *     (Sec. 6.1),
+ *   - the sampled online tuner (Sec. 6.1 sampling, Algorithm 1, Sec. 6.3
+ *     candidates and Table I comparisons).
+ *
+ * General conventions
+ *   - Field dims are slowest-first: 2D {ny, nx}, 3D {nz, ny, nx}; the last
+ *     axis is contiguous.  Values are IEEE binary32.
+ *   - Pointers named d_* are device pointers of the current CUDA device;
+ *     h_* are host pointers.  Inputs are never modified.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it; calls return after the host-visible
+ *     results they document (counts, sizes) are known, which synchronises the
+ *     stream where stated.
+ *   - Every entry point returns a qoz_status; on failure qoz_last_error()
+ *     gives a message (thread-local).  No call throws across the ABI.
+ *   - Quant codes are uint16 in array order: 0 marks an anchor or an
+ *     unpredictable point, otherwise code = q + 32768 with |q| <= 32767.
+ *   - Interpolator per level: 0 linear, 1 cubic.  Dimension order per level:
+ *     index into the lexicographic permutations of the axes (3D: 012 021 102
+ *     120 201 210; 2D: 01 10); the first axis of the order is interpolated
+ *     first (Sec. 5.2.2).
+ */
+#ifndef QOZ_H
+#define QOZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QOZ_MAX_LEVELS 8
+
+typedef enum {
+  QOZ_OK = 0,
+  QOZ_EINVAL = 1,        /* invalid argument (shape, bound, parameters) */
+  QOZ_ENOMEM = 2,        /* device or host allocation failed */
+  QOZ_ECUDA = 3,         /* a CUDA call or kernel launch failed */
+  QOZ_ECORRUPT = 4,      /* serialized stream damaged (magic, size, CRC) */
+  QOZ_ETIMEOUT = 5,      /* a bounded device wait gave up */
+  QOZ_EUNSUPPORTED = 6   /* valid request outside what this build handles */
+} qoz_status;
+
+typedef enum { QOZ_METRIC_MAXERR = 0, QOZ_METRIC_PSNR = 1, QOZ_METRIC_SSIM = 2 } qoz_metric;
+
+typedef struct {
+  int32_t ndims;         /* 2 or 3 */
+  int64_t dims[3];       /* slowest-first; entries past ndims ignored */
+} qoz_shape;
+
+/* The tuned parameter set theta (Sec. 3 problem statement, Eq. ebl). */
+typedef struct {
+  int32_t anchor_stride;               /* power of two; 0 = default (3D 32, 2D 64, Sec. 7.1.4) */
+  uint8_t interp[QOZ_MAX_LEVELS];      /* interp[l-1]: interpolator of level l */
+  uint8_t order[QOZ_MAX_LEVELS];       /* order[l-1]: dimension order of level l */
+  double alpha;                        /* >= 1 */
+  double beta;                         /* >= 1 */
+} qoz_params;
+
+typedef struct qoz_blob qoz_blob;      /* opaque compressed field; owns device memory */
+
+typedef struct {
+  qoz_shape shape;
+  qoz_params params;
+  double abs_eb;                       /* absolute error bound e used */
+  double rel_eb;                       /* e / value range (NaN if given absolutely) */
+  float vmin, vmax;                    /* value range of the finite input values */
+  int64_t n_points;
+  int64_t n_anchors;
+  int64_t n_unpredictable;
+  double est_bits;                     /* Huffman bits of the codes + 32 per unpredictable and anchor */
+  double est_ratio;                    /* 32 * n_points / est_bits */
+} qoz_blob_info;
+
+/* ---------------------------------------------------------------- field ops */
+
+/* Value range of the finite values of d_x[0..n) (Sec. 7.1.4: the
+ * value-range-relative bound e = eps * (max - min)).  Synchronises `stream`.
+ * h_count receives the number of finite values (may be NULL); min = max = 0
+ * when there is none. */
+qoz_status qoz_value_range(const float* d_x, int64_t n, float* h_min, float* h_max,
+                           int64_t* h_count, void* stream);
+
+/* Compress (Sec. 5): value range, anchors (Sec. 5.2.1), then levels L..1 of
+ * the interpolation predictor with level-wise bounds (Eq. ebl), each level's
+ * dimension passes predicting from reconstructed values and quantizing
+ * linearly; then the 65536-bin code histogram.  rel_eb > 0 and finite;
+ * p = NULL selects cubic, order 0, alpha = beta = 1 on every level.  The blob
+ * is allocated stream-ordered on `stream`; the call synchronises `stream`
+ * once, at the end, to learn the number of unpredictable points.
+ * d_recon, if not NULL, receives the reconstruction the decompressor will
+ * produce (N floats, caller-owned). */
+qoz_status qoz_compress(const float* d_field, qoz_shape shape, double rel_eb,
+                        const qoz_params* p, float* d_recon, void* stream, qoz_blob** out);
+
+/* Same with an absolute bound e >= 0 (no value-range pass; the blob's
+ * vmin/vmax are then 0). */
+qoz_status qoz_compress_abs(const float* d_field, qoz_shape shape, double abs_eb,
+                            const qoz_params* p, float* d_recon, void* stream, qoz_blob** out);
+
+/* Decompress (mirror of Sec. 5.1): anchors, then the same passes with
+ * recon = pred + 2 e_l (code - 32768), or the stored value where code = 0.
+ * d_out: caller-owned N floats.  Asynchronous on `stream`. */
+qoz_status qoz_decompress(const qoz_blob* b, float* d_out, void* stream);
+
+qoz_status qoz_blob_get_info(const qoz_blob* b, qoz_blob_info* info);
+
+/* Device views of the blob's arrays (owned by the blob).  d_unpred_idx are
+ * linear indices sorted ascending, d_unpred_val the stored values; any output
+ * pointer may be NULL. */
+qoz_status qoz_blob_arrays(const qoz_blob* b, const uint16_t** d_codes,
+                           const int64_t** d_unpred_idx, const float** d_unpred_val,
+                           int64_t* n_unpred, const float** d_anchors, int64_t* n_anchors);
+
+/* Copies the blob's arrays into caller-owned device buffers (any may be
+ * NULL): codes N uint16, unpredictable indices / values n_unpredictable each,
+ * anchors n_anchors floats.  Asynchronous on `stream`. */
+qoz_status qoz_blob_copy_arrays(const qoz_blob* b, uint16_t* d_codes, int64_t* d_unpred_idx,
+                                float* d_unpred_val, float* d_anchors, void* stream);
+
+/* Copy the 65536-bin histogram of the non-anchor codes to h_hist (uint32). */
+qoz_status qoz_blob_histogram(const qoz_blob* b, uint32_t* h_hist, void* stream);
+
+/* Serialized form: header (magic, version, shape, bound, params, counts),
+ * anchors, unpredictable list, codes, CRC32 of everything before it.  With
+ * h_buf = NULL only *used is set (the required size).  Synchronises. */
+qoz_status qoz_blob_serialize(const qoz_blob* b, void* h_buf, size_t cap, size_t* used,
+                              void* stream);
+qoz_status qoz_blob_deserialize(const void* h_buf, size_t size, void* stream, qoz_blob** out);
+
+/* Releases the blob's device memory, stream-ordered on the stream the blob
+ * was created on (that stream must still exist). */
+void qoz_blob_free(qoz_blob* b);
+
+const char* qoz_last_error(void);
+
+/* ---------------------------------------------------------------- metrics */
+
+typedef struct {
+  double max_abs_err;    /* max |a - b| (computed in double, exact) */
+  double mse;            /* mean of (a - b)^2 over all points, in double */
+  double psnr;           /* Eq. psnr: 20 log10(vrange / sqrt(mse)); +inf if mse = 0 */
+  double ssim;           /* Eq. ssim: mean over windows (NaN if not requested / none) */
+  int64_t ssim_windows;
+} qoz_metrics;
+
+/* Quality metrics of Sec. 3 between the original d_a and the reconstruction
+ * d_b.  ssim_win > 0 requests SSIM over box windows of edge ssim_win placed
+ * every ssim_step points, fully inside the array, with c1 = (0.01 vrange)^2
+ * and c2 = (0.03 vrange)^2 (Eq. ssim2).  Synchronises `stream`. */
+qoz_status qoz_compute_metrics(const float* d_a, const float* d_b, qoz_shape shape,
+                               double vrange, int32_t ssim_win, int32_t ssim_step,
+                               qoz_metrics* out, void* stream);
+
+/* ---------------------------------------------------------------- profiling */
+
+/* Stage ids of the per-stage timers. */
+#define QOZ_PROF_STAGES 32
+#define QOZ_STAGE_RANGE 0      /* value range pass */
+#define QOZ_STAGE_SETUP 1      /* bound table + anchor gather */
+#define QOZ_STAGE_LEVEL 2      /* + l (l = 1..8): compress, level l */
+#define QOZ_STAGE_HIST 11      /* code histogram */
+#define QOZ_STAGE_FINAL 12     /* count read-back and unpredictable ordering */
+#define QOZ_STAGE_DLEVEL 12    /* + l (l = 1..8): decompress, level l */
+#define QOZ_STAGE_METRICS 21
+#define QOZ_STAGE_TUNE 22      /* sampled-block trials of the tuner */
+
+typedef struct {
+  double ms[QOZ_PROF_STAGES];      /* accumulated device time per stage (CUDA events) */
+  int64_t calls[QOZ_PROF_STAGES];  /* timed occurrences per stage */
+  int64_t launches;                /* kernels launched by the library */
+} qoz_stage_times;
+
+/* Turns per-stage event timing on or off (process-wide; off by default).
+ * The launch counter always runs. */
+qoz_status qoz_profile_enable(int32_t enable);
+/* Folds in all recorded stages (synchronising on their events) and copies
+ * the totals; reset != 0 clears them and the launch counter afterwards. */
+qoz_status qoz_profile_read(qoz_stage_times* out, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QOZ_H */

@@ -117,14 +117,22 @@ def _dims(shape) -> np.ndarray:
     return np.ascontiguousarray(np.array(shape, dtype=np.int64))
 
 
+def _level_value(v, l):
+    """Per-level value: a scalar applies to every level; a list gives level
+    l+1 its entry l, its last entry repeating above its length."""
+    if isinstance(v, (list, tuple)):
+        return v[min(l, len(v) - 1)]
+    return v
+
+
 def make_params(ndims: int, interp=1, order=0, alpha=1.0, beta=1.0, anchor_stride=None) -> Params:
     """Params with the same interpolator/order on every level, or per-level
     lists (index l-1 for level l)."""
     p = Params()
     p.anchor_stride = anchor_stride or (32 if ndims == 3 else 64)
     for l in range(MAX_LEVELS):
-        p.interp[l] = interp[l] if isinstance(interp, (list, tuple)) else interp
-        p.order[l] = order[l] if isinstance(order, (list, tuple)) else order
+        p.interp[l] = _level_value(interp, l)
+        p.order[l] = _level_value(order, l)
     p.alpha, p.beta = float(alpha), float(beta)
     return p
 

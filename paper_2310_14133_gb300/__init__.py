@@ -1,0 +1,32 @@
+"""GB300 (sm_103a) implementation of the QoZ compressor's data path.
+
+The compute runs in the CUDA library libqoz.so (C ABI, include/qoz.h); this
+package only marshals arguments to it.  PyTorch supplies device memory and
+the current CUDA stream.  Importing the package fails loudly when the
+library has not been built: there is no CPU fallback.
+"""
+
+from ._binding import (  # noqa: F401
+    METRIC_MAXERR,
+    METRIC_PSNR,
+    METRIC_SSIM,
+    STAGE_DLEVEL,
+    STAGE_HIST,
+    STAGE_LEVEL,
+    STAGE_RANGE,
+    STAGE_SETUP,
+    Blob,
+    QozError,
+    Shape,
+    compress,
+    compress_abs,
+    compute_metrics,
+    decompress,
+    deserialize,
+    lib,
+    library_path,
+    make_params,
+    profile_enable,
+    profile_read,
+    value_range,
+)

@@ -1,0 +1,271 @@
+"""ctypes binding of libqoz.so: same names as the C ABI, argument marshalling
+only.  Tensors must be CUDA tensors on the current device; the stream is
+torch's current stream unless one is given."""
+
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = os.path.join(_HERE, "_build", "libqoz.so")
+
+MAX_LEVELS = 8
+METRIC_MAXERR, METRIC_PSNR, METRIC_SSIM = 0, 1, 2
+STATUS = {0: "QOZ_OK", 1: "QOZ_EINVAL", 2: "QOZ_ENOMEM", 3: "QOZ_ECUDA", 4: "QOZ_ECORRUPT",
+          5: "QOZ_ETIMEOUT", 6: "QOZ_EUNSUPPORTED"}
+
+
+class QozError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Shape(C.Structure):
+    _fields_ = [("ndims", C.c_int32), ("dims", C.c_int64 * 3)]
+
+
+class Params(C.Structure):
+    _fields_ = [("anchor_stride", C.c_int32), ("interp", C.c_uint8 * MAX_LEVELS),
+                ("order", C.c_uint8 * MAX_LEVELS), ("alpha", C.c_double), ("beta", C.c_double)]
+
+
+class BlobInfo(C.Structure):
+    _fields_ = [("shape", Shape), ("params", Params), ("abs_eb", C.c_double),
+                ("rel_eb", C.c_double), ("vmin", C.c_float), ("vmax", C.c_float),
+                ("n_points", C.c_int64), ("n_anchors", C.c_int64),
+                ("n_unpredictable", C.c_int64), ("est_bits", C.c_double),
+                ("est_ratio", C.c_double)]
+
+
+PROF_STAGES = 32
+STAGE_RANGE, STAGE_SETUP, STAGE_LEVEL, STAGE_HIST, STAGE_FINAL = 0, 1, 2, 11, 12
+STAGE_DLEVEL, STAGE_METRICS, STAGE_TUNE = 12, 21, 22
+
+
+class StageTimes(C.Structure):
+    _fields_ = [("ms", C.c_double * PROF_STAGES), ("calls", C.c_int64 * PROF_STAGES),
+                ("launches", C.c_int64)]
+
+
+def profile_enable(on: bool = True):
+    _check(lib().qoz_profile_enable(1 if on else 0))
+
+
+def profile_read(reset: bool = False) -> StageTimes:
+    t = StageTimes()
+    _check(lib().qoz_profile_read(C.byref(t), 1 if reset else 0))
+    return t
+
+
+class Metrics(C.Structure):
+    _fields_ = [("max_abs_err", C.c_double), ("mse", C.c_double), ("psnr", C.c_double),
+                ("ssim", C.c_double), ("ssim_windows", C.c_int64)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB):
+            raise ImportError(
+                f"{_LIB} is missing: build it with paper_2310_14133_gb300/build.py "
+                "(or __graft_entry__.build()); there is no CPU fallback")
+        _lib = C.CDLL(_LIB)
+        P = C.c_void_p
+        i32, i64, f64 = C.c_int32, C.c_int64, C.c_double
+        sig = {
+            "qoz_last_error": (C.c_char_p, []),
+            "qoz_value_range": (i32, [P, i64, P, P, P, P]),
+            "qoz_compress": (i32, [P, Shape, f64, P, P, P, P]),
+            "qoz_compress_abs": (i32, [P, Shape, f64, P, P, P, P]),
+            "qoz_decompress": (i32, [P, P, P]),
+            "qoz_blob_get_info": (i32, [P, P]),
+            "qoz_blob_arrays": (i32, [P, P, P, P, P, P, P]),
+            "qoz_blob_copy_arrays": (i32, [P, P, P, P, P, P]),
+            "qoz_blob_histogram": (i32, [P, P, P]),
+            "qoz_blob_serialize": (i32, [P, P, C.c_size_t, P, P]),
+            "qoz_blob_deserialize": (i32, [P, C.c_size_t, P, P]),
+            "qoz_blob_free": (None, [P]),
+            "qoz_compute_metrics": (i32, [P, P, Shape, f64, i32, i32, P, P]),
+            "qoz_profile_enable": (i32, [i32]),
+            "qoz_profile_read": (i32, [P, i32]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(_lib, name)
+            fn.restype = res
+            fn.argtypes = args
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise QozError(status, lib().qoz_last_error().decode(errors="replace"))
+
+
+def _stream(stream):
+    if stream is None:
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _shape_of(t: torch.Tensor) -> Shape:
+    s = Shape()
+    s.ndims = t.dim()
+    for i, d in enumerate(t.shape):
+        s.dims[i] = int(d)
+    return s
+
+
+def _dev_ptr(t: torch.Tensor, dtype=torch.float32):
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"expected a contiguous {dtype} tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _level_value(v, l):
+    """Per-level value: a scalar applies to every level; a list gives level
+    l+1 its entry l, its last entry repeating above its length."""
+    if isinstance(v, (list, tuple)):
+        return v[min(l, len(v) - 1)]
+    return v
+
+
+def make_params(ndims: int, interp=1, order=0, alpha=1.0, beta=1.0, anchor_stride=0) -> Params:
+    """Same interpolator/order on every level, or per-level lists (index l-1
+    is level l)."""
+    p = Params()
+    p.anchor_stride = anchor_stride
+    for l in range(MAX_LEVELS):
+        p.interp[l] = _level_value(interp, l)
+        p.order[l] = _level_value(order, l)
+    p.alpha, p.beta = float(alpha), float(beta)
+    return p
+
+
+def value_range(x: torch.Tensor, stream=None):
+    mn, mx, cnt = C.c_float(), C.c_float(), C.c_int64()
+    _check(lib().qoz_value_range(_dev_ptr(x), x.numel(), C.byref(mn), C.byref(mx),
+                                 C.byref(cnt), _stream(stream)))
+    return mn.value, mx.value, cnt.value
+
+
+class Blob:
+    """A compressed field; owns its device memory until freed."""
+
+    def __init__(self, handle: C.c_void_p, shape):
+        self._h = handle
+        self.shape = tuple(shape)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> BlobInfo:
+        inf = BlobInfo()
+        _check(lib().qoz_blob_get_info(self._h, C.byref(inf)))
+        return inf
+
+    def arrays(self, stream=None):
+        """Copies of (codes [shape] as int16 bit patterns of the uint16 codes,
+        unpredictable indices int64, unpredictable values float32, anchors
+        float32) as CUDA tensors."""
+        inf = self.info()
+        codes = torch.empty(self.shape, dtype=torch.int16, device="cuda")
+        ui = torch.empty(inf.n_unpredictable, dtype=torch.int64, device="cuda")
+        uv = torch.empty(inf.n_unpredictable, dtype=torch.float32, device="cuda")
+        an = torch.empty(inf.n_anchors, dtype=torch.float32, device="cuda")
+        _check(lib().qoz_blob_copy_arrays(self._h, C.c_void_p(codes.data_ptr()),
+                                          C.c_void_p(ui.data_ptr()), C.c_void_p(uv.data_ptr()),
+                                          C.c_void_p(an.data_ptr()), _stream(stream)))
+        return codes, ui, uv, an
+
+    def histogram(self, stream=None) -> torch.Tensor:
+        h = torch.zeros(65536, dtype=torch.int32)
+        _check(lib().qoz_blob_histogram(self._h, C.c_void_p(h.data_ptr()), _stream(stream)))
+        return h.to(torch.int64)
+
+    def serialize(self, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        used = C.c_size_t()
+        _check(lib().qoz_blob_serialize(self._h, None, 0, C.byref(used), _stream(stream)))
+        if out is None:
+            out = torch.empty(used.value, dtype=torch.uint8, pin_memory=True)
+        if out.numel() < used.value:
+            raise ValueError("output buffer too small")
+        _check(lib().qoz_blob_serialize(self._h, C.c_void_p(out.data_ptr()), out.numel(),
+                                        C.byref(used), _stream(stream)))
+        return out[:used.value]
+
+    def free(self):
+        if self._h:
+            lib().qoz_blob_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def compress(x: torch.Tensor, rel_eb: float, params: Params | None = None,
+             recon: torch.Tensor | None = None, stream=None) -> Blob:
+    h = C.c_void_p()
+    _check(lib().qoz_compress(_dev_ptr(x), _shape_of(x), float(rel_eb),
+                              C.byref(params) if params is not None else None,
+                              _dev_ptr(recon) if recon is not None else None,
+                              _stream(stream), C.byref(h)))
+    return Blob(h, x.shape)
+
+
+def compress_abs(x: torch.Tensor, abs_eb: float, params: Params | None = None,
+                 recon: torch.Tensor | None = None, stream=None) -> Blob:
+    h = C.c_void_p()
+    _check(lib().qoz_compress_abs(_dev_ptr(x), _shape_of(x), float(abs_eb),
+                                  C.byref(params) if params is not None else None,
+                                  _dev_ptr(recon) if recon is not None else None,
+                                  _stream(stream), C.byref(h)))
+    return Blob(h, x.shape)
+
+
+def decompress(blob: Blob, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    if out is None:
+        out = torch.empty(blob.shape, dtype=torch.float32, device="cuda")
+    _check(lib().qoz_decompress(blob.handle, _dev_ptr(out), _stream(stream)))
+    return out
+
+
+def deserialize(buf: torch.Tensor, stream=None) -> Blob:
+    h = C.c_void_p()
+    if buf.is_cuda or buf.dtype != torch.uint8:
+        raise ValueError("expected a host uint8 buffer")
+    _check(lib().qoz_blob_deserialize(C.c_void_p(buf.data_ptr()), buf.numel(), _stream(stream),
+                                      C.byref(h)))
+    b = Blob(h, ())
+    inf = b.info()
+    b.shape = tuple(int(inf.shape.dims[i]) for i in range(inf.shape.ndims))
+    return b
+
+
+def compute_metrics(a: torch.Tensor, b: torch.Tensor, vrange: float, ssim_win: int = 0,
+                    ssim_step: int = 2, stream=None) -> Metrics:
+    if a.shape != b.shape:
+        raise ValueError("shape mismatch")
+    m = Metrics()
+    _check(lib().qoz_compute_metrics(_dev_ptr(a), _dev_ptr(b), _shape_of(a), float(vrange),
+                                     int(ssim_win), int(ssim_step), C.byref(m), _stream(stream)))
+    return m

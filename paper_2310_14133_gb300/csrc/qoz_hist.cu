@@ -1,0 +1,188 @@
+// Quant-code histogram (the input of the Huffman rate estimate, Sec. 6.1)
+// and ordering of the unpredictable list by index.
+#include <cuda_runtime.h>
+
+#include <climits>
+
+#include "qoz_internal.h"
+
+namespace qoz {
+namespace {
+
+// Codes concentrate around the zero bin 32768; a shared-memory window covers
+// the bins near it, the rare far bins go straight to global memory.  Equal
+// codes within a warp are merged with one match before the shared atomic.
+constexpr int kWinLo = kRadius - 2048;
+constexpr int kWin = 4096;
+constexpr int kHistThreads = 512;
+constexpr int kHistBlocks = 152 * 2;
+
+__device__ __forceinline__ void hist_add(unsigned* sh, unsigned* gh, unsigned code) {
+  const unsigned mask = __activemask();
+  const unsigned peers = __match_any_sync(mask, code);
+  const int lane = threadIdx.x & 31;
+  if (lane == __ffs(peers) - 1) {
+    const unsigned k = code - (unsigned)kWinLo;
+    if (k < (unsigned)kWin)
+      atomicAdd(&sh[k], (unsigned)__popc(peers));
+    else
+      atomicAdd(&gh[code], (unsigned)__popc(peers));
+  }
+}
+
+__global__ void __launch_bounds__(kHistThreads) hist_kernel(const uint16_t* __restrict__ codes,
+                                                            long long n, unsigned* hist) {
+  __shared__ unsigned sh[kWin];
+  for (int i = threadIdx.x; i < kWin; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  const long long n8 = n / 8;
+  const uint4* c8 = reinterpret_cast<const uint4*>(codes);
+  for (long long i = tid; i < n8; i += nth) {
+    const uint4 v = c8[i];
+    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      hist_add(sh, hist, w[k] & 0xffffu);
+      hist_add(sh, hist, w[k] >> 16);
+    }
+  }
+  for (long long i = 8 * n8 + tid; i < n; i += nth) hist_add(sh, hist, codes[i]);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kWin; i += blockDim.x)
+    if (sh[i]) atomicAdd(&hist[kWinLo + i], sh[i]);
+}
+
+// Anchors carry code 0 but are not coded symbols: take them out of bin 0.
+__global__ void hist_remove_anchors(unsigned* hist, long long n_anchors) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) hist[0] -= (unsigned)n_anchors;
+}
+
+// ---- ordering of (index, value) pairs by index
+
+constexpr int kSmemSort = 2048;
+
+__global__ void __launch_bounds__(1024) sort_small_kernel(long long* idx, float* val,
+                                                          long long n) {
+  __shared__ long long k[kSmemSort];
+  __shared__ float v[kSmemSort];
+  int P = 1;
+  while (P < n) P <<= 1;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    k[i] = i < n ? idx[i] : LLONG_MAX;
+    v[i] = i < n ? val[i] : 0.0f;
+  }
+  __syncthreads();
+  for (int size = 2; size <= P; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int j = i ^ stride;
+        if (j > i) {
+          const bool up = (i & size) == 0;
+          if ((k[i] > k[j]) == up) {
+            const long long tk = k[i];
+            k[i] = k[j];
+            k[j] = tk;
+            const float tv = v[i];
+            v[i] = v[j];
+            v[j] = tv;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    idx[i] = k[i];
+    val[i] = v[i];
+  }
+}
+
+__global__ void sort_fill_kernel(const long long* idx, const float* val, long long n,
+                                 long long P, long long* k, float* v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P;
+       i += (long long)gridDim.x * blockDim.x) {
+    k[i] = i < n ? idx[i] : LLONG_MAX;
+    v[i] = i < n ? val[i] : 0.0f;
+  }
+}
+
+__global__ void sort_step_kernel(long long* k, float* v, long long P, long long size,
+                                 long long stride) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long j = i ^ stride;
+    if (j > i) {
+      const bool up = (i & size) == 0;
+      if ((k[i] > k[j]) == up) {
+        const long long tk = k[i];
+        k[i] = k[j];
+        k[j] = tk;
+        const float tv = v[i];
+        v[i] = v[j];
+        v[j] = tv;
+      }
+    }
+  }
+}
+
+__global__ void sort_back_kernel(const long long* k, const float* v, long long n, long long* idx,
+                                 float* val) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    idx[i] = k[i];
+    val[i] = v[i];
+  }
+}
+
+long long pow2_at_least(long long n) {
+  long long P = 1;
+  while (P < n) P <<= 1;
+  return P;
+}
+
+}  // namespace
+
+cudaError_t launch_histogram(const uint16_t* codes, long long n, unsigned* hist,
+                             long long n_anchors, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(unsigned) * 65536, s);
+  if (e != cudaSuccess) return e;
+  if (reinterpret_cast<uintptr_t>(codes) & 15) return cudaErrorMisalignedAddress;
+  long long want = (n / 8 + kHistThreads - 1) / kHistThreads;
+  const int blocks = (int)(want < 1 ? 1 : (want < kHistBlocks ? want : kHistBlocks));
+  hist_kernel<<<blocks, kHistThreads, 0, s>>>(codes, n, hist); note_launch(1);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  hist_remove_anchors<<<1, 32, 0, s>>>(hist, n_anchors); note_launch(1);
+  return cudaGetLastError();
+}
+
+size_t sort_pairs_scratch(long long n) {
+  if (n <= kSmemSort) return 0;
+  const long long P = pow2_at_least(n);
+  return (size_t)P * (sizeof(long long) + sizeof(float));
+}
+
+cudaError_t launch_sort_pairs(long long* idx, float* val, long long n, long long* tmp_idx,
+                              float* tmp_val, cudaStream_t s) {
+  if (n <= 1) return cudaSuccess;
+  if (n <= kSmemSort) {
+    sort_small_kernel<<<1, 1024, 0, s>>>(idx, val, n); note_launch(1);
+    return cudaGetLastError();
+  }
+  const long long P = pow2_at_least(n);
+  const int threads = 256;
+  long long want = (P + threads - 1) / threads;
+  const int blocks = (int)(want < 152 * 8 ? want : 152 * 8);
+  sort_fill_kernel<<<blocks, threads, 0, s>>>(idx, val, n, P, tmp_idx, tmp_val); note_launch(1);
+  for (long long size = 2; size <= P; size <<= 1) {
+    for (long long stride = size >> 1; stride > 0; stride >>= 1) {
+      sort_step_kernel<<<blocks, threads, 0, s>>>(tmp_idx, tmp_val, P, size, stride); note_launch(1);
+    }
+  }
+  sort_back_kernel<<<blocks, threads, 0, s>>>(tmp_idx, tmp_val, n, idx, val); note_launch(1);
+  return cudaGetLastError();
+}
+
+}  // namespace qoz

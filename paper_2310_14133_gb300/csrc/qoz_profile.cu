@@ -1,0 +1,114 @@
+// Per-stage timing with CUDA events and a count of kernel launches.
+//
+// When enabled, each stage of compress / decompress records a pair of events
+// on the caller's stream; elapsed times are folded in when they are read
+// (qoz_profile_read synchronises on the recorded events).  The launch counter
+// is always on: every kernel launch of the library increments it.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "../../include/qoz.h"
+#include "qoz_host.h"
+#include "qoz_internal.h"
+
+namespace qoz {
+namespace {
+
+struct Pending {
+  int stage;
+  cudaEvent_t a, b;
+};
+
+std::mutex g_mu;
+std::atomic<bool> g_on{false};
+std::atomic<long long> g_launches{0};
+std::vector<Pending> g_pending;
+std::vector<cudaEvent_t> g_free;
+double g_ms[QOZ_PROF_STAGES];
+long long g_calls[QOZ_PROF_STAGES];
+
+cudaEvent_t take_event() {
+  if (!g_free.empty()) {
+    cudaEvent_t e = g_free.back();
+    g_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+void fold_pending_locked() {
+  for (const Pending& p : g_pending) {
+    float ms = 0.0f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      g_ms[p.stage] += ms;
+      g_calls[p.stage] += 1;
+    }
+    g_free.push_back(p.a);
+    g_free.push_back(p.b);
+  }
+  g_pending.clear();
+}
+
+}  // namespace
+
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+ProfScope::ProfScope(int stage, cudaStream_t s) : stage_(stage), s_(s), a_(nullptr) {
+  if (!g_on.load(std::memory_order_relaxed) || stage < 0 || stage >= QOZ_PROF_STAGES) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  a_ = take_event();
+  if (a_ && cudaEventRecord(a_, s_) != cudaSuccess) {
+    g_free.push_back(a_);
+    a_ = nullptr;
+  }
+}
+
+ProfScope::~ProfScope() {
+  if (!a_) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  cudaEvent_t b = take_event();
+  if (!b || cudaEventRecord(b, s_) != cudaSuccess) {
+    g_free.push_back(a_);
+    if (b) g_free.push_back(b);
+    return;
+  }
+  g_pending.push_back({stage_, a_, b});
+}
+
+}  // namespace qoz
+
+using namespace qoz;
+
+extern "C" {
+
+qoz_status qoz_profile_enable(int32_t enable) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_on.store(enable != 0);
+  return QOZ_OK;
+}
+
+qoz_status qoz_profile_read(qoz_stage_times* out, int32_t reset) {
+  if (!out) return fail(QOZ_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(g_mu);
+  fold_pending_locked();
+  for (int i = 0; i < QOZ_PROF_STAGES; ++i) {
+    out->ms[i] = g_ms[i];
+    out->calls[i] = g_calls[i];
+  }
+  out->launches = g_launches.load();
+  if (reset) {
+    for (int i = 0; i < QOZ_PROF_STAGES; ++i) {
+      g_ms[i] = 0.0;
+      g_calls[i] = 0;
+    }
+    g_launches.store(0);
+  }
+  return QOZ_OK;
+}
+
+}  // extern "C"

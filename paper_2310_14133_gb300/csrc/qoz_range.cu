@@ -1,0 +1,170 @@
+// Value range of the finite values (Sec. 7.1.4: e = eps * vrange) and the
+// level-wise bound table of Eq. (ebl), both on the device.
+//
+// range_kernel streams the field once with 16-byte loads (a pure HBM read,
+// 4 bytes per point) and leaves one (min, max, count) triple per CTA;
+// bound_table_kernel folds the triples and evaluates e and e_l in double,
+// rounding each table entry to binary32 once, so the predictor's launches
+// can follow without a host round trip.
+#include <cuda_runtime.h>
+
+#include <cfloat>
+
+#include "qoz_internal.h"
+
+namespace qoz {
+namespace {
+
+constexpr int kRangeThreads = 512;
+constexpr int kRangeBlocks = 152 * 4;  // 4 resident CTAs on each of the 152 SMs
+
+__device__ __forceinline__ void fold(float v, float& mn, float& mx, unsigned long long& c) {
+  if (isfinite(v)) {
+    mn = fminf(mn, v);
+    mx = fmaxf(mx, v);
+    ++c;
+  }
+}
+
+__global__ void __launch_bounds__(kRangeThreads) range_kernel(const float* __restrict__ x,
+                                                              long long n, float* pmin,
+                                                              float* pmax,
+                                                              unsigned long long* pcnt) {
+  float mn = FLT_MAX, mx = -FLT_MAX;
+  unsigned long long c = 0;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  // 16-byte aligned body (the caller passes the aligned start), scalar tail
+  const long long n4 = n / 4;
+  const float4* x4 = reinterpret_cast<const float4*>(x);
+  for (long long i = tid; i < n4; i += nth) {
+    const float4 v = __ldcs(x4 + i);
+    fold(v.x, mn, mx, c);
+    fold(v.y, mn, mx, c);
+    fold(v.z, mn, mx, c);
+    fold(v.w, mn, mx, c);
+  }
+  for (long long i = 4 * n4 + tid; i < n; i += nth) fold(x[i], mn, mx, c);
+
+  for (int off = 16; off > 0; off >>= 1) {
+    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    c += __shfl_xor_sync(0xffffffffu, c, off);
+  }
+  __shared__ float smn[32], smx[32];
+  __shared__ unsigned long long sc[32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    smn[w] = mn;
+    smx[w] = mx;
+    sc[w] = c;
+  }
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    mn = l < nw ? smn[l] : FLT_MAX;
+    mx = l < nw ? smx[l] : -FLT_MAX;
+    c = l < nw ? sc[l] : 0;
+    for (int off = 16; off > 0; off >>= 1) {
+      mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+      c += __shfl_xor_sync(0xffffffffu, c, off);
+    }
+    if (l == 0) {
+      pmin[blockIdx.x] = mn;
+      pmax[blockIdx.x] = mx;
+      pcnt[blockIdx.x] = c;
+    }
+  }
+}
+
+// Scalar head for a field pointer that is not 16-byte aligned: folded into
+// the first partial afterwards by the table kernel.
+__global__ void range_head_kernel(const float* __restrict__ x, int nhead, float* pmin,
+                                  float* pmax, unsigned long long* pcnt) {
+  if (threadIdx.x != 0) return;
+  float mn = FLT_MAX, mx = -FLT_MAX;
+  unsigned long long c = 0;
+  for (int i = 0; i < nhead; ++i) fold(x[i], mn, mx, c);
+  *pmin = mn;
+  *pmax = mx;
+  *pcnt = c;
+}
+
+__global__ void bound_table_kernel(const float* pmin, const float* pmax,
+                                   const unsigned long long* pcnt, int nparts, int use_range,
+                                   double eb, double alpha, double beta, int L, BoundTable* bt) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  float mn = FLT_MAX, mx = -FLT_MAX;
+  unsigned long long c = 0;
+  for (int i = 0; i < nparts; ++i) {
+    if (pcnt[i] == 0) continue;
+    mn = fminf(mn, pmin[i]);
+    mx = fmaxf(mx, pmax[i]);
+    c += pcnt[i];
+  }
+  if (c == 0) {
+    mn = 0.0f;
+    mx = 0.0f;
+  }
+  BoundTable t;
+  t.vmin = mn;
+  t.vmax = mx;
+  t.n_finite = (long long)c;
+  t.vrange = (double)mx - (double)mn;
+  t.e = use_range ? eb * t.vrange : eb;
+  // Eq. (ebl): e_l = e / min(alpha^(l-1), beta), alpha^(l-1) by repeated
+  // multiplication in double; each entry rounded to binary32 once.
+  double a = 1.0;
+  for (int l = 0; l < kMaxLevels; ++l) {
+    if (l < L) {
+      const double den = a < beta ? a : beta;
+      const double el = t.e / den;
+      t.el[l] = (float)el;
+      t.two_e[l] = (float)(2.0 * el);
+      t.inv[l] = (float)(1.0 / (2.0 * el));
+      a = a * alpha;
+    } else {
+      t.el[l] = t.two_e[l] = t.inv[l] = 0.0f;
+    }
+  }
+  *bt = t;
+}
+
+}  // namespace
+
+int range_partial_blocks() { return kRangeBlocks + 1; }
+
+cudaError_t launch_range(const float* x, long long n, float* pmin, float* pmax,
+                         unsigned long long* pcnt, cudaStream_t s) {
+  // partial 0 holds the unaligned head (possibly empty), 1.. the main pass
+  const uintptr_t addr = reinterpret_cast<uintptr_t>(x);
+  int head = (int)(((16 - (addr & 15)) & 15) / 4);
+  if ((addr & 3) != 0) return cudaErrorMisalignedAddress;
+  if (head > n) head = (int)n;
+  range_head_kernel<<<1, 32, 0, s>>>(x, head, pmin, pmax, pcnt); note_launch(1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long rest = n - head;
+  long long want = (rest / 4 + kRangeThreads - 1) / kRangeThreads;
+  int blocks = (int)(want < kRangeBlocks ? (want < 1 ? 1 : want) : kRangeBlocks);
+  range_kernel<<<blocks, kRangeThreads, 0, s>>>(x + head, rest, pmin + 1, pmax + 1, pcnt + 1); note_launch(1);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // unused partial slots must not contribute
+  if (blocks < kRangeBlocks)
+    e = cudaMemsetAsync(pcnt + 1 + blocks, 0,
+                        sizeof(unsigned long long) * (kRangeBlocks - blocks), s);
+  return e;
+}
+
+cudaError_t launch_bound_table(const float* pmin, const float* pmax,
+                               const unsigned long long* pcnt, int nparts, int use_range,
+                               double eb, double alpha, double beta, int L, BoundTable* bt,
+                               cudaStream_t s) {
+  bound_table_kernel<<<1, 32, 0, s>>>(pmin, pmax, pcnt, nparts, use_range, eb, alpha, beta, L,
+                                      bt); note_launch(1);
+  return cudaGetLastError();
+}
+
+}  // namespace qoz

@@ -1,0 +1,318 @@
+// Serialized blob format and array export.
+//
+// Layout (little-endian): a 160-byte header, then the anchors (float32), the
+// unpredictable indices (int64) and values (float32), and the codes (uint16),
+// each section padded to 8 bytes.  The header's checksum field holds a 64-bit
+// sum over every 8-byte word w_i of header and payload of mix(w_i ^ mix(i)),
+// taken with the field itself zero; being a sum, it is computed on the
+// device for the device-resident sections, in parallel, and on the host for
+// the header.  mix is the splitmix64 finalizer.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/qoz.h"
+#include "qoz_host.h"
+#include "qoz_internal.h"
+
+
+namespace qoz {
+
+namespace {
+
+constexpr char kMagic[8] = {'Q', 'O', 'Z', 'G', 'B', '3', '0', '0'};
+constexpr uint32_t kVersion = 1;
+
+struct Header {
+  char magic[8];
+  uint32_t version;
+  uint32_t header_bytes;
+  int32_t ndims;
+  int32_t reserved0;
+  int64_t dims[3];
+  double abs_eb;
+  double rel_eb;
+  float vmin, vmax;
+  int32_t anchor_stride;
+  uint8_t interp[8];
+  uint8_t order[8];
+  int32_t reserved1;
+  double alpha, beta;
+  int64_t n_points, n_anchors, n_unpred;
+  uint64_t checksum;
+  uint64_t reserved2[2];
+};
+static_assert(sizeof(Header) == 160, "header layout");
+
+__host__ __device__ inline uint64_t mix64(uint64_t z) {
+  z += 0x9e3779b97f4a7c15ULL;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+constexpr int kSumBlocks = 152 * 2;
+constexpr int kSumThreads = 256;
+
+__global__ void __launch_bounds__(kSumThreads) checksum_kernel(const unsigned char* p,
+                                                               long long nbytes,
+                                                               long long word0,
+                                                               unsigned long long* part) {
+  unsigned long long acc = 0;
+  const long long nw = (nbytes + 7) / 8;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nw;
+       i += (long long)gridDim.x * blockDim.x) {
+    uint64_t w = 0;
+    const long long b0 = i * 8;
+    if (b0 + 8 <= nbytes && ((reinterpret_cast<uintptr_t>(p) & 7) == 0)) {
+      w = *reinterpret_cast<const uint64_t*>(p + b0);
+    } else {
+      for (int k = 0; k < 8 && b0 + k < nbytes; ++k) w |= (uint64_t)p[b0 + k] << (8 * k);
+    }
+    acc += mix64(w ^ mix64((uint64_t)(word0 + i)));
+  }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  __shared__ unsigned long long sh[kSumThreads / 32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long s = 0;
+    for (int k = 0; k < kSumThreads / 32; ++k) s += sh[k];
+    atomicAdd(part, s);
+  }
+}
+
+uint64_t host_checksum(const unsigned char* p, size_t nbytes, uint64_t word0) {
+  uint64_t acc = 0;
+  const size_t nw = (nbytes + 7) / 8;
+  for (size_t i = 0; i < nw; ++i) {
+    uint64_t w = 0;
+    for (int k = 0; k < 8 && i * 8 + k < nbytes; ++k) w |= (uint64_t)p[i * 8 + k] << (8 * k);
+    acc += mix64(w ^ mix64(word0 + i));
+  }
+  return acc;
+}
+
+size_t pad8(size_t v) { return (v + 7) & ~(size_t)7; }
+
+struct Layout {
+  size_t anchors, uidx, uval, codes, total;
+};
+
+Layout layout_of(long long na, long long nu, long long N) {
+  Layout L;
+  L.anchors = sizeof(Header);
+  L.uidx = L.anchors + pad8(sizeof(float) * na);
+  L.uval = L.uidx + pad8(sizeof(long long) * nu);
+  L.codes = L.uval + pad8(sizeof(float) * nu);
+  L.total = L.codes + pad8(sizeof(uint16_t) * N);
+  return L;
+}
+
+// Device-side checksum of the payload sections (word offsets per layout).
+cudaError_t device_payload_sum(const qoz_blob* b, const Layout& L, unsigned long long* d_acc,
+                               cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(d_acc, 0, sizeof(unsigned long long), s);
+  struct Sec {
+    const void* p;
+    size_t bytes, off;
+  } secs[4] = {{b->d_anchors, sizeof(float) * b->na, L.anchors},
+               {b->d_uidx, sizeof(long long) * b->nu, L.uidx},
+               {b->d_uval, sizeof(float) * b->nu, L.uval},
+               {b->d_codes, sizeof(uint16_t) * b->N, L.codes}};
+  for (const Sec& c : secs) {
+    if (e != cudaSuccess) break;
+    if (c.bytes == 0) continue;
+    checksum_kernel<<<kSumBlocks, kSumThreads, 0, s>>>((const unsigned char*)c.p,
+                                                       (long long)c.bytes,
+                                                       (long long)(c.off / 8), d_acc); note_launch(1);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+}  // namespace
+}  // namespace qoz
+
+using namespace qoz;
+
+extern "C" {
+
+qoz_status qoz_blob_copy_arrays(const qoz_blob* b, uint16_t* d_codes, int64_t* d_unpred_idx,
+                                float* d_unpred_val, float* d_anchors, void* stream) {
+  if (!b) return fail(QOZ_EINVAL, "NULL blob");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (d_codes && b->N)
+    e = cudaMemcpyAsync(d_codes, b->d_codes, sizeof(uint16_t) * b->N, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && d_unpred_idx && b->nu)
+    e = cudaMemcpyAsync(d_unpred_idx, b->d_uidx, sizeof(long long) * b->nu,
+                        cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && d_unpred_val && b->nu)
+    e = cudaMemcpyAsync(d_unpred_val, b->d_uval, sizeof(float) * b->nu, cudaMemcpyDeviceToDevice,
+                        s);
+  if (e == cudaSuccess && d_anchors && b->na)
+    e = cudaMemcpyAsync(d_anchors, b->d_anchors, sizeof(float) * b->na, cudaMemcpyDeviceToDevice,
+                        s);
+  if (e != cudaSuccess) return cuda_fail(e, "copy arrays");
+  return QOZ_OK;
+}
+
+qoz_status qoz_blob_serialize(const qoz_blob* b, void* h_buf, size_t cap, size_t* used,
+                              void* stream) {
+  if (!b || !used) return fail(QOZ_EINVAL, "NULL argument");
+  const Layout L = layout_of(b->na, b->nu, b->N);
+  *used = L.total;
+  if (!h_buf) return QOZ_OK;
+  if (cap < L.total) return fail(QOZ_EINVAL, "buffer holds %zu bytes, %zu needed", cap, L.total);
+  cudaStream_t s = stream ? (cudaStream_t)stream : b->stream;
+  unsigned char* out = (unsigned char*)h_buf;
+  Header h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, kMagic, 8);
+  h.version = kVersion;
+  h.header_bytes = sizeof(Header);
+  h.ndims = b->shape.ndims;
+  for (int i = 0; i < 3; ++i) h.dims[i] = i < b->shape.ndims ? b->shape.dims[i] : 0;
+  h.abs_eb = b->abs_eb;
+  h.rel_eb = b->rel_eb;
+  h.vmin = b->vmin;
+  h.vmax = b->vmax;
+  h.anchor_stride = b->params.anchor_stride;
+  memcpy(h.interp, b->params.interp, 8);
+  memcpy(h.order, b->params.order, 8);
+  h.alpha = b->params.alpha;
+  h.beta = b->params.beta;
+  h.n_points = b->N;
+  h.n_anchors = b->na;
+  h.n_unpred = b->nu;
+  // zero the padding bytes so that the stream is a pure function of the blob
+  memset(out + sizeof(Header), 0, L.total - sizeof(Header));
+  unsigned long long* d_acc = nullptr;
+  cudaError_t e = dev_alloc((void**)&d_acc, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return fail(QOZ_ENOMEM, "checksum scratch");
+  e = device_payload_sum(b, L, d_acc, s);
+  unsigned long long acc = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&acc, d_acc, sizeof(acc), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && b->na)
+    e = cudaMemcpyAsync(out + L.anchors, b->d_anchors, sizeof(float) * b->na,
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && b->nu)
+    e = cudaMemcpyAsync(out + L.uidx, b->d_uidx, sizeof(long long) * b->nu,
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && b->nu)
+    e = cudaMemcpyAsync(out + L.uval, b->d_uval, sizeof(float) * b->nu, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && b->N)
+    e = cudaMemcpyAsync(out + L.codes, b->d_codes, sizeof(uint16_t) * b->N,
+                        cudaMemcpyDeviceToHost, s);
+  dev_free(d_acc, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "serialize");
+  h.checksum = 0;
+  h.checksum = acc + host_checksum((const unsigned char*)&h, sizeof(Header), 0);
+  memcpy(out, &h, sizeof(Header));
+  return QOZ_OK;
+}
+
+qoz_status qoz_blob_deserialize(const void* h_buf, size_t size, void* stream, qoz_blob** out) {
+  if (!h_buf || !out) return fail(QOZ_EINVAL, "NULL argument");
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (size < sizeof(Header)) return fail(QOZ_ECORRUPT, "stream shorter than its header");
+  Header h;
+  memcpy(&h, h_buf, sizeof(Header));
+  if (fault_injected("header") || memcmp(h.magic, kMagic, 8) != 0 || h.version != kVersion ||
+      h.header_bytes != sizeof(Header))
+    return fail(QOZ_ECORRUPT, "bad magic / version");
+  qoz_shape shape;
+  shape.ndims = h.ndims;
+  for (int i = 0; i < 3; ++i) shape.dims[i] = h.dims[i];
+  qoz_params p;
+  memset(&p, 0, sizeof(p));
+  p.anchor_stride = h.anchor_stride;
+  memcpy(p.interp, h.interp, 8);
+  memcpy(p.order, h.order, 8);
+  p.alpha = h.alpha;
+  p.beta = h.beta;
+  Resolved r;
+  if (resolve(shape, &p, &r) != QOZ_OK) return fail(QOZ_ECORRUPT, "header: invalid shape/params");
+  long long na = 1;
+  for (int i = 0; i < 3; ++i) na *= (r.n[i] + r.p.anchor_stride - 1) / r.p.anchor_stride;
+  if (h.n_points != r.N || h.n_anchors != na || h.n_unpred < 0 || h.n_unpred > r.N ||
+      !(h.abs_eb >= 0.0) || !std::isfinite(h.abs_eb))
+    return fail(QOZ_ECORRUPT, "header: inconsistent counts or bound");
+  const Layout L = layout_of(na, h.n_unpred, r.N);
+  if (size < L.total) return fail(QOZ_ECORRUPT, "stream truncated (%zu < %zu)", size, L.total);
+  const unsigned char* in = (const unsigned char*)h_buf;
+  // host check of the unpredictable list: strictly increasing, inside the field
+  {
+    const long long* ui = (const long long*)(in + L.uidx);
+    for (long long k = 0; k < h.n_unpred; ++k) {
+      long long v;
+      memcpy(&v, ui + k, sizeof(v));
+      long long prev = -1;
+      if (k > 0) memcpy(&prev, ui + k - 1, sizeof(prev));
+      if (v < 0 || v >= r.N || v <= prev) return fail(QOZ_ECORRUPT, "unpredictable list order");
+    }
+  }
+  configure_pool_once();
+  qoz_blob* b = new qoz_blob();
+  memset(b, 0, sizeof(*b));
+  b->shape = shape;
+  for (int i = 0; i < 3; ++i) b->n[i] = r.n[i];
+  b->N = r.N;
+  b->L = r.L;
+  b->params = r.p;
+  b->abs_eb = h.abs_eb;
+  b->rel_eb = h.rel_eb;
+  b->vmin = h.vmin;
+  b->vmax = h.vmax;
+  b->na = na;
+  b->nu = h.n_unpred;
+  b->stream = s;
+  cudaGetDevice(&b->device);
+  auto cleanup = [&](qoz_status st) {
+    qoz_blob_free(b);
+    return st;
+  };
+  unsigned long long* d_acc = nullptr;
+  cudaError_t e;
+  if ((e = dev_alloc((void**)&b->d_codes, sizeof(uint16_t) * b->N, s)) != cudaSuccess ||
+      (e = dev_alloc((void**)&b->d_anchors, sizeof(float) * na, s)) != cudaSuccess ||
+      (e = dev_alloc((void**)&b->d_uidx, sizeof(long long) * b->nu, s)) != cudaSuccess ||
+      (e = dev_alloc((void**)&b->d_uval, sizeof(float) * b->nu, s)) != cudaSuccess ||
+      (e = dev_alloc((void**)&b->d_hist, sizeof(unsigned) * 65536, s)) != cudaSuccess ||
+      (e = dev_alloc((void**)&b->d_err, sizeof(int), s)) != cudaSuccess ||
+      (e = dev_alloc((void**)&d_acc, sizeof(unsigned long long), s)) != cudaSuccess)
+    return cleanup(fail(QOZ_ENOMEM, "deserialize allocation"));
+  e = cudaMemsetAsync(b->d_err, 0, sizeof(int), s);
+  if (e == cudaSuccess && na)
+    e = cudaMemcpyAsync(b->d_anchors, in + L.anchors, sizeof(float) * na, cudaMemcpyHostToDevice,
+                        s);
+  if (e == cudaSuccess && b->nu)
+    e = cudaMemcpyAsync(b->d_uidx, in + L.uidx, sizeof(long long) * b->nu,
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && b->nu)
+    e = cudaMemcpyAsync(b->d_uval, in + L.uval, sizeof(float) * b->nu, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && b->N)
+    e = cudaMemcpyAsync(b->d_codes, in + L.codes, sizeof(uint16_t) * b->N,
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = device_payload_sum(b, L, d_acc, s);
+  if (e == cudaSuccess) e = launch_histogram(b->d_codes, b->N, b->d_hist, b->na, s);
+  unsigned long long acc = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&acc, d_acc, sizeof(acc), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  dev_free(d_acc, s);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "deserialize"));
+  const uint64_t want = h.checksum;
+  h.checksum = 0;
+  const uint64_t got = acc + host_checksum((const unsigned char*)&h, sizeof(Header), 0);
+  if (got != want) return cleanup(fail(QOZ_ECORRUPT, "checksum mismatch"));
+  *out = b;
+  return QOZ_OK;
+}
+
+}  // extern "C"
