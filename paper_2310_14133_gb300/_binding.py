@@ -122,6 +122,8 @@ def _stream(stream):
 
 
 def _shape_of(t: torch.Tensor) -> Shape:
+    if t.dim() not in (2, 3):
+        raise QozError(1, f"fields must be 2D or 3D (got {t.dim()} dimensions)")
     s = Shape()
     s.ndims = t.dim()
     for i, d in enumerate(t.shape):

@@ -150,66 +150,32 @@ void grid_dims(const Resolved& r, int k, long long g[3]) {
   for (int p = 0; p < 3; ++p) g[p] = ceil_div(r.n[p], 1LL << k);
 }
 
-int even_up(long long v) { return (int)(v + (v & 1)); }
+// Compact per-grid scratch of the hierarchy: for k = 1..L-1 the
+// reconstruction (float) and, when compressing, the codes (uint16) of the
+// field subsampled by 2^k.
+struct Coarse {
+  size_t roff[QOZ_MAX_LEVELS + 1];
+  size_t coff[QOZ_MAX_LEVELS + 1];
+  size_t bytes;
+};
 
-LevelGeom level_geom(const Resolved& r, int l, const int tile_phys[3]) {
-  LevelGeom G;
-  long long g[3], gc[3];
-  grid_dims(r, l - 1, g);
-  grid_dims(r, l, gc);
-  const long long f = 1LL << (l - 1);
-  const long long fst[3] = {r.n[1] * r.n[2], r.n[2], 1};
-  const long long cst[3] = {gc[1] * gc[2], gc[2], 1};
-  const long long ost[3] = {g[1] * g[2], g[2], 1};
-  int Tp[3];
-  for (int p = 0; p < 3; ++p) {
-    long long t = tile_phys[p];
-    if (t > even_up(g[p])) t = even_up(g[p]);
-    Tp[p] = (int)t;
-  }
-  const int a0 = r.axes[l - 1][0];
-  if (g[a0] == 1) Tp[a0] = 1;  // the first pass has no targets (2D, or a unit axis)
-  for (int k = 0; k < 3; ++k) {
-    const int p = r.axes[l - 1][k];
-    G.phys_of[k] = p;
-    G.ord_of[p] = k;
-    G.g[k] = g[p];
-    G.xs[k] = f * fst[p];
-    G.cs[k] = cst[p];
-    G.os[k] = ost[p];
-    G.T[k] = Tp[p];
-  }
-  for (int p = 0; p < 3; ++p) G.nt[p] = ceil_div(g[p], Tp[p]);
-  G.level = l;
-  G.interp = r.p.interp[l - 1];
-  return G;
-}
-
-// Default tile shape: the contiguous axis gets 64 points, the first-pass
-// axis (no halo) a short extent, the remaining axis 16; 2D tiles are 32 x 128.
-void default_tile(const Resolved& r, int l, int tile[3]) {
-  if (r.n[0] == 1 && r.ndims == 2) {
-    tile[0] = 1;
-    tile[1] = 32;
-    tile[2] = 128;
-    return;
-  }
-  const int a0 = r.axes[l - 1][0];
-  for (int p = 0; p < 3; ++p) tile[p] = 16;
-  tile[2] = a0 == 2 ? 32 : 64;
-  if (a0 != 2) tile[a0] = 8;
-}
-
-// Compact reconstruction buffers of the grids subsampled by 2^k, k = 1..L-1.
-size_t coarse_bytes(const Resolved& r, size_t offs[QOZ_MAX_LEVELS + 1]) {
+Coarse coarse_layout(const Resolved& r, bool with_codes) {
+  Coarse c;
+  memset(&c, 0, sizeof(c));
   size_t tot = 0;
   for (int k = 1; k < r.L; ++k) {
     long long g[3];
     grid_dims(r, k, g);
-    offs[k] = tot;
-    tot += ((size_t)(g[0] * g[1] * g[2]) * sizeof(float) + 255) & ~(size_t)255;
+    const size_t n = (size_t)(g[0] * g[1] * g[2]);
+    c.roff[k] = tot;
+    tot += (n * sizeof(float) + 255) & ~(size_t)255;
+    if (with_codes) {
+      c.coff[k] = tot;
+      tot += (n * sizeof(uint16_t) + 255) & ~(size_t)255;
+    }
   }
-  return tot;
+  c.bytes = tot;
+  return c;
 }
 
 long long anchor_dims(const Resolved& r, long long na[3]) {
@@ -217,24 +183,58 @@ long long anchor_dims(const Resolved& r, long long na[3]) {
   return na[0] * na[1] * na[2];
 }
 
+// Geometry of level l: G = field subsampled by 2^(l-1), coarse = by 2^l.
+void level_geometry(const Resolved& r, int l, LevelLaunch* L) {
+  long long g[3], gc[3];
+  grid_dims(r, l - 1, g);
+  grid_dims(r, l, gc);
+  const long long f = 1LL << (l - 1);
+  const long long fst[3] = {r.n[1] * r.n[2], r.n[2], 1};
+  for (int p = 0; p < 3; ++p) {
+    L->g[p] = g[p];
+    L->xs[p] = f * fst[p];
+  }
+  L->cs[0] = gc[1] * gc[2];
+  L->cs[1] = gc[2];
+  L->cs[2] = 1;
+  L->os[0] = g[1] * g[2];
+  L->os[1] = g[2];
+  L->os[2] = 1;
+  L->is2d = r.ndims == 2;
+  L->order3 = r.ndims == 3 ? r.p.order[l - 1] : (r.p.order[l - 1] == 0 ? 0 : 1);
+  L->level = l;
+  L->interp = r.p.interp[l - 1];
+}
+
 // Runs levels L..1 (compress or decompress) over the grid hierarchy.
 cudaError_t run_levels(bool decompress, const Resolved& r, const float* x, uint16_t* codes,
-                       const float* anchors, float* coarse_base, const size_t* offs,
+                       const float* anchors, char* coarse_base, const Coarse& cl,
                        float* final_out, const BoundTable* bt, UnpredList ul,
                        const long long* uidx, const float* uval, long long nu, int* err,
-                       cudaStream_t s, const TileOverride* tiles) {
+                       unsigned* hist, cudaStream_t s) {
   for (int l = r.L; l >= 1; --l) {
-    int tile[3];
-    if (tiles && tiles->set)
-      for (int p = 0; p < 3; ++p) tile[p] = tiles->t[p];
-    else
-      default_tile(r, l, tile);
-    const LevelGeom G = level_geom(r, l, tile);
-    const float* rc = l == r.L ? anchors : coarse_base + offs[l] / sizeof(float);
-    float* rout = l > 1 ? coarse_base + offs[l - 1] / sizeof(float) : final_out;
+    LevelLaunch L;
+    memset(&L, 0, sizeof(L));
+    level_geometry(r, l, &L);
+    L.decompress = decompress;
+    L.rc = l == r.L ? anchors : (const float*)(coarse_base + cl.roff[l]);
+    L.rout = l > 1 ? (float*)(coarse_base + cl.roff[l - 1]) : final_out;
+    L.bt = bt;
+    if (decompress) {
+      L.cin = codes;
+      L.uidx = uidx;
+      L.uval = uval;
+      L.nu = nu;
+      L.err = err;
+    } else {
+      L.x = x;
+      L.cin = l == r.L ? nullptr : (const uint16_t*)(coarse_base + cl.coff[l]);
+      L.cout = l > 1 ? (uint16_t*)(coarse_base + cl.coff[l - 1]) : codes;
+      L.ul = ul;
+      L.hist = l == 1 ? hist : nullptr;
+    }
     ProfScope ps(decompress ? QOZ_STAGE_DLEVEL + l : QOZ_STAGE_LEVEL + l, s);
-    cudaError_t e = launch_check(
-        launch_level(decompress, G, x, codes, rc, rout, bt, ul, uidx, uval, nu, err, s));
+    cudaError_t e = launch_check(launch_level(L, s));
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -255,8 +255,7 @@ HostStage* host_stage() {
 }
 
 qoz_status compress_impl(const float* d_field, const qoz_shape& shape, bool rel, double eb,
-                         const qoz_params* p, float* d_recon, cudaStream_t s, qoz_blob** out,
-                         const TileOverride* tiles) {
+                         const qoz_params* p, float* d_recon, cudaStream_t s, qoz_blob** out) {
   if (!out) return fail(QOZ_EINVAL, "out is NULL");
   *out = nullptr;
   if (!d_field) return fail(QOZ_EINVAL, "d_field is NULL");
@@ -287,8 +286,8 @@ qoz_status compress_impl(const float* d_field, const qoz_shape& shape, bool rel,
 
   cudaError_t e;
   void* scratch = nullptr;
-  size_t offs[QOZ_MAX_LEVELS + 1] = {0};
-  const size_t cb = coarse_bytes(r, offs);
+  const Coarse cl = coarse_layout(r, true);
+  const size_t cb = cl.bytes;
   const int nparts = range_partial_blocks();
   long long cap = r.N / 1024;
   if (cap < 65536) cap = 65536;
@@ -337,9 +336,10 @@ qoz_status compress_impl(const float* d_field, const qoz_shape& shape, bool rel,
     unsigned long long* d_count = (unsigned long long*)(base + o_cnt);
     long long* uidx = (long long*)(base + o_uidx);
     float* uval = (float*)(base + o_uval);
-    float* coarse = (float*)(base + o_coarse);
+    char* coarse = base + o_coarse;
 
     e = cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_hist, 0, sizeof(unsigned) * 65536, s);
     if (e == cudaSuccess && rel) {
       ProfScope ps(QOZ_STAGE_RANGE, s);
       e = launch_check(launch_range(d_field, r.N, pmin, pmax, pcnt, s));
@@ -350,16 +350,16 @@ qoz_status compress_impl(const float* d_field, const qoz_shape& shape, bool rel,
       e = launch_check(launch_bound_table(pmin, pmax, pcnt, rel ? nparts : 0, rel ? 1 : 0, eb,
                                           r.p.alpha, r.p.beta, r.L, d_bt, s));
       if (e == cudaSuccess)
-        e = launch_check(launch_anchor_gather(d_field, b->d_codes, b->d_anchors, na3, fst,
-                                              r.p.anchor_stride, s));
+        e = launch_check(
+            launch_anchor_gather(d_field, b->d_anchors, na3, fst, r.p.anchor_stride, s));
     }
     UnpredList ul{uidx, uval, d_count, cap};
     if (e == cudaSuccess)
-      e = run_levels(false, r, d_field, b->d_codes, b->d_anchors, coarse, offs, d_recon, d_bt, ul,
-                     nullptr, nullptr, 0, nullptr, s, tiles);
+      e = run_levels(false, r, d_field, b->d_codes, b->d_anchors, coarse, cl, d_recon, d_bt, ul,
+                     nullptr, nullptr, 0, nullptr, b->d_hist, s);
     if (e == cudaSuccess) {
       ProfScope ps(QOZ_STAGE_HIST, s);
-      e = launch_check(launch_histogram(b->d_codes, r.N, b->d_hist, b->na, s));
+      e = launch_check(launch_hist_remove_anchors(b->d_hist, b->na, s));
     }
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(&hs->count, d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
@@ -401,26 +401,24 @@ qoz_status compress_impl(const float* d_field, const qoz_shape& shape, bool rel,
   return cleanup(fail(QOZ_ECUDA, "unpredictable list did not converge"));
 }
 
-qoz_status decompress_impl(const qoz_blob* b, float* d_out, cudaStream_t s,
-                           const TileOverride* tiles) {
+qoz_status decompress_impl(const qoz_blob* b, float* d_out, cudaStream_t s) {
   if (!b || !d_out) return fail(QOZ_EINVAL, "NULL argument");
   Resolved r;
   qoz_status st = resolve(b->shape, &b->params, &r);
   if (st != QOZ_OK) return st;
   configure_pool_once();
-  size_t offs[QOZ_MAX_LEVELS + 1] = {0};
-  const size_t cb = coarse_bytes(r, offs);
+  const Coarse cl = coarse_layout(r, false);
   void* scratch = nullptr;
-  cudaError_t e = dev_alloc(&scratch, 256 + cb, s);
+  cudaError_t e = dev_alloc(&scratch, 256 + cl.bytes, s);
   if (e != cudaSuccess) return fail(QOZ_ENOMEM, "decompress scratch: %s", cudaGetErrorString(e));
   BoundTable* d_bt = (BoundTable*)scratch;
-  float* coarse = (float*)((char*)scratch + 256);
+  char* coarse = (char*)scratch + 256;
   e = launch_check(launch_bound_table(nullptr, nullptr, nullptr, 0, 0, b->abs_eb, r.p.alpha,
                                       r.p.beta, r.L, d_bt, s));
   UnpredList ul{nullptr, nullptr, nullptr, 0};
   if (e == cudaSuccess)
-    e = run_levels(true, r, nullptr, b->d_codes, b->d_anchors, coarse, offs, d_out, d_bt, ul,
-                   b->d_uidx, b->d_uval, b->nu, b->d_err, s, tiles);
+    e = run_levels(true, r, nullptr, b->d_codes, b->d_anchors, coarse, cl, d_out, d_bt, ul,
+                   b->d_uidx, b->d_uval, b->nu, b->d_err, nullptr, s);
   dev_free(scratch, s);
   if (e != cudaSuccess) return cuda_fail(e, "decompress");
   return QOZ_OK;
@@ -467,18 +465,16 @@ qoz_status qoz_value_range(const float* d_x, int64_t n, float* h_min, float* h_m
 
 qoz_status qoz_compress(const float* d_field, qoz_shape shape, double rel_eb, const qoz_params* p,
                         float* d_recon, void* stream, qoz_blob** out) {
-  return compress_impl(d_field, shape, true, rel_eb, p, d_recon, (cudaStream_t)stream, out,
-                       nullptr);
+  return compress_impl(d_field, shape, true, rel_eb, p, d_recon, (cudaStream_t)stream, out);
 }
 
 qoz_status qoz_compress_abs(const float* d_field, qoz_shape shape, double abs_eb,
                             const qoz_params* p, float* d_recon, void* stream, qoz_blob** out) {
-  return compress_impl(d_field, shape, false, abs_eb, p, d_recon, (cudaStream_t)stream, out,
-                       nullptr);
+  return compress_impl(d_field, shape, false, abs_eb, p, d_recon, (cudaStream_t)stream, out);
 }
 
 qoz_status qoz_decompress(const qoz_blob* b, float* d_out, void* stream) {
-  return decompress_impl(b, d_out, (cudaStream_t)stream, nullptr);
+  return decompress_impl(b, d_out, (cudaStream_t)stream);
 }
 
 qoz_status qoz_blob_get_info(const qoz_blob* b, qoz_blob_info* info) {

@@ -17,11 +17,13 @@ constexpr int kWin = 4096;
 constexpr int kHistThreads = 512;
 constexpr int kHistBlocks = 152 * 2;
 
+// Adds one code per lane; all 32 lanes of the warp call it together, lanes
+// without a code pass kNoCode.
+constexpr unsigned kNoCode = 0xffffffffu;
 __device__ __forceinline__ void hist_add(unsigned* sh, unsigned* gh, unsigned code) {
-  const unsigned mask = __activemask();
-  const unsigned peers = __match_any_sync(mask, code);
+  const unsigned peers = __match_any_sync(0xffffffffu, code);
   const int lane = threadIdx.x & 31;
-  if (lane == __ffs(peers) - 1) {
+  if (code != kNoCode && lane == __ffs(peers) - 1) {
     const unsigned k = code - (unsigned)kWinLo;
     if (k < (unsigned)kWin)
       atomicAdd(&sh[k], (unsigned)__popc(peers));
@@ -35,20 +37,28 @@ __global__ void __launch_bounds__(kHistThreads) hist_kernel(const uint16_t* __re
   __shared__ unsigned sh[kWin];
   for (int i = threadIdx.x; i < kWin; i += blockDim.x) sh[i] = 0;
   __syncthreads();
-  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
   const long long n8 = n / 8;
   const uint4* c8 = reinterpret_cast<const uint4*>(codes);
-  for (long long i = tid; i < n8; i += nth) {
-    const uint4 v = c8[i];
+  // warp-uniform trip counts: every lane of a warp runs every iteration
+  const long long wbase = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31);
+  const int lane = threadIdx.x & 31;
+  for (long long i0 = wbase; i0 < n8; i0 += nth) {
+    const long long i = i0 + lane;
+    const bool ok = i < n8;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (ok) v = c8[i];
     const unsigned w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      hist_add(sh, hist, w[k] & 0xffffu);
-      hist_add(sh, hist, w[k] >> 16);
+      hist_add(sh, hist, ok ? (w[k] & 0xffffu) : kNoCode);
+      hist_add(sh, hist, ok ? (w[k] >> 16) : kNoCode);
     }
   }
-  for (long long i = 8 * n8 + tid; i < n; i += nth) hist_add(sh, hist, codes[i]);
+  for (long long i0 = 8 * n8 + wbase; i0 < n; i0 += nth) {
+    const long long i = i0 + lane;
+    hist_add(sh, hist, i < n ? (unsigned)codes[i] : kNoCode);
+  }
   __syncthreads();
   for (int i = threadIdx.x; i < kWin; i += blockDim.x)
     if (sh[i]) atomicAdd(&hist[kWinLo + i], sh[i]);
@@ -154,6 +164,10 @@ cudaError_t launch_histogram(const uint16_t* codes, long long n, unsigned* hist,
   hist_kernel<<<blocks, kHistThreads, 0, s>>>(codes, n, hist); note_launch(1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  return launch_hist_remove_anchors(hist, n_anchors, s);
+}
+
+cudaError_t launch_hist_remove_anchors(unsigned* hist, long long n_anchors, cudaStream_t s) {
   hist_remove_anchors<<<1, 32, 0, s>>>(hist, n_anchors); note_launch(1);
   return cudaGetLastError();
 }

@@ -43,12 +43,6 @@ struct Resolved {
   int axes[QOZ_MAX_LEVELS][3];
 };
 
-// Optional tile shape (physical z, y, x extents) for the level kernels.
-struct TileOverride {
-  bool set;
-  int t[3];
-};
-
 qoz_status fail(qoz_status st, const char* fmt, ...);
 qoz_status cuda_fail(cudaError_t e, const char* what);
 qoz_status resolve(const qoz_shape& shape, const qoz_params* p, Resolved* r);

@@ -11,38 +11,41 @@ namespace qoz {
 // Adds n to the library's kernel-launch counter (qoz_profile.cu).
 void note_launch(int n);
 
-// Geometry of one level launch.  The level-l targets of the full field are
-// exactly the finest-level targets of the grid G = the full field subsampled
-// by f = 2^(l-1) (its points whose coordinates are all multiples of f):
-// along each axis a target has an odd G coordinate, its neighbours at
-// +-h, +-3h are at +-1, +-3 in G, and the points with all G coordinates even
-// (the coarse grid) were reconstructed by the levels above.  A launch
-// therefore always works at half-stride 1 on G, whatever the level.
-//
-// All per-axis arrays are in ORDER space: index 0 is the axis interpolated
-// first in this level (u), 1 the second (v), 2 the third (w).
-struct LevelGeom {
-  long long g[3];    // extent of G
-  long long xs[3];   // element stride of the full-resolution arrays (x, codes)
-  long long cs[3];   // stride of the compact coarse reconstruction (G subsampled by 2)
-  long long os[3];   // stride of the compact reconstruction of G (output)
-  int T[3];          // tile extent (even; T[0] may be 1 when g[0] == 1)
-  int phys_of[3];    // physical axis (0 slowest .. 2 contiguous) of order axis k
-  int ord_of[3];     // order axis of physical axis p
-  long long nt[3];   // number of tiles per PHYSICAL axis
-  int level;         // 1-based level, index into the bound table
-  int interp;        // 0 linear, 1 cubic
+// One level launch.  The level-l points of the field are the points of the
+// grid G = field subsampled by 2^(l-1) (all coordinates multiples of
+// 2^(l-1)) that have an odd coordinate in G; their neighbours at +-h, +-3h
+// are at +-1, +-3 in G, and the points of G with all coordinates even (the
+// coarse grid) were reconstructed by the levels above.  A launch therefore
+// always works at half-stride 1 on G, whatever the level.  Per-axis arrays
+// are physical (0 = slowest z, 2 = contiguous x).
+struct LevelLaunch {
+  bool decompress;
+  bool is2d;          // field embedded as (1, ny, nx)
+  int order3;         // 3D order index (2D: 0 = (y, x), 1 = (x, y))
+  int level;          // 1-based, index into the bound table
+  int interp;         // 0 linear, 1 cubic
+  long long g[3];     // extent of G
+  long long xs[3];    // strides of G inside the full-resolution arrays (field, codes)
+  long long cs[3];    // strides of the compact coarse arrays (G subsampled by 2)
+  long long os[3];    // strides of the compact arrays of G (outputs)
+  const float* x;     // compress: the field
+  const uint16_t* cin;  // compress: compact coarse codes (NULL: all 0); decompress: codes
+  const float* rc;    // compact coarse reconstruction
+  float* rout;        // compact reconstruction of G (optional)
+  uint16_t* cout;     // compress: compact codes of G
+  const BoundTable* bt;
+  UnpredList ul;      // compress: unpredictable points of this level
+  const long long* uidx;  // decompress: sorted unpredictable list
+  const float* uval;
+  long long nu;
+  int* err;           // decompress: set to 1 if a code-0 point has no list entry
+  unsigned* hist;     // compress, level 1: 65536-bin code histogram (optional)
 };
 
 // Launch wrappers (qoz_level.cu)
-cudaError_t launch_level(bool decompress, const LevelGeom& G, const float* x, uint16_t* codes,
-                         const float* rc, float* rout, const BoundTable* bt, UnpredList ul,
-                         const long long* uidx, const float* uval, long long nu, int* err,
-                         cudaStream_t s);
-cudaError_t launch_anchor_gather(const float* x, uint16_t* codes, float* anchors,
-                                 const long long na[3], const long long fst[3], long long stride,
-                                 cudaStream_t s);
-size_t level_smem_bytes(const LevelGeom& G);
+cudaError_t launch_level(const LevelLaunch& L, cudaStream_t s);
+cudaError_t launch_anchor_gather(const float* x, float* anchors, const long long na[3],
+                                 const long long fst[3], long long stride, cudaStream_t s);
 
 // Value range and bound table (qoz_range.cu)
 int range_partial_blocks();
@@ -56,6 +59,7 @@ cudaError_t launch_bound_table(const float* pmin, const float* pmax,
 // Histogram and unpredictable ordering (qoz_hist.cu)
 cudaError_t launch_histogram(const uint16_t* codes, long long n, unsigned* hist,
                              long long n_anchors, cudaStream_t s);
+cudaError_t launch_hist_remove_anchors(unsigned* hist, long long n_anchors, cudaStream_t s);
 cudaError_t launch_sort_pairs(long long* idx, float* val, long long n, long long* tmp_idx,
                               float* tmp_val, cudaStream_t s);
 size_t sort_pairs_scratch(long long n);

@@ -91,17 +91,44 @@ __global__ void range_head_kernel(const float* __restrict__ x, int nhead, float*
   *pcnt = c;
 }
 
-__global__ void bound_table_kernel(const float* pmin, const float* pmax,
-                                   const unsigned long long* pcnt, int nparts, int use_range,
-                                   double eb, double alpha, double beta, int L, BoundTable* bt) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// One block folds the per-CTA partials (a tree over the threads), then one
+// thread evaluates Eq. (ebl).
+constexpr int kTableThreads = 1024;
+
+__global__ void __launch_bounds__(kTableThreads)
+    bound_table_kernel(const float* pmin, const float* pmax, const unsigned long long* pcnt,
+                       int nparts, int use_range, double eb, double alpha, double beta, int L,
+                       BoundTable* bt) {
   float mn = FLT_MAX, mx = -FLT_MAX;
   unsigned long long c = 0;
-  for (int i = 0; i < nparts; ++i) {
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
     if (pcnt[i] == 0) continue;
     mn = fminf(mn, pmin[i]);
     mx = fmaxf(mx, pmax[i]);
     c += pcnt[i];
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    c += __shfl_xor_sync(0xffffffffu, c, off);
+  }
+  __shared__ float smn[32], smx[32];
+  __shared__ unsigned long long sc[32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    smn[w] = mn;
+    smx[w] = mx;
+    sc[w] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  mn = FLT_MAX;
+  mx = -FLT_MAX;
+  c = 0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+    mn = fminf(mn, smn[i]);
+    mx = fmaxf(mx, smx[i]);
+    c += sc[i];
   }
   if (c == 0) {
     mn = 0.0f;
@@ -162,8 +189,9 @@ cudaError_t launch_bound_table(const float* pmin, const float* pmax,
                                const unsigned long long* pcnt, int nparts, int use_range,
                                double eb, double alpha, double beta, int L, BoundTable* bt,
                                cudaStream_t s) {
-  bound_table_kernel<<<1, 32, 0, s>>>(pmin, pmax, pcnt, nparts, use_range, eb, alpha, beta, L,
-                                      bt); note_launch(1);
+  bound_table_kernel<<<1, kTableThreads, 0, s>>>(pmin, pmax, pcnt, nparts, use_range, eb, alpha,
+                                                  beta, L, bt);
+  note_launch(1);
   return cudaGetLastError();
 }
 
