@@ -2,9 +2,11 @@
 
 Workload (N=1): one 512^3 FP32 field, k^-5/3 Gaussian random field plus 8
 tanh fronts (NYX-sized, the plain-method-at-scale case), value-range
-relative bound 1e-3.  One step = one qoz_compress call on the resident
-field: value range, bound table, anchors, the five predictor levels, the code
-histogram and the unpredictable-list read-back.  `value` is FP32 input GB/s
+relative bound 1e-3.  One step = the sampled tuner (0.5 % of the field in
+33^3 blocks, 12 interpolators by Algorithm 1, alpha in {1..2} x beta in
+{2, 3, 4}, maximum compression ratio under the bound) followed by the
+compression with the tuned parameters: value range, anchors, the five
+predictor levels, the code histogram and the unpredictable-list read-back.  `value` is FP32 input GB/s
 of whole steps timed with CUDA events; `e2e` adds the pinned host->device
 copy of the field and the device->host read of the serialized stream through
 the public API.  With --gpus N (torchrun) every rank compresses its own field
@@ -31,7 +33,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "compress GB/s (FP32 in) & % HBM roofline, bit-exact; learned vs sampled tune"
 REL_EB = 1e-3
-PARAMS = dict(interp=1, order=0, alpha=1.5, beta=4.0)
+TUNE = dict(block=32, rate=0.005, n_orders=6, alphas=[1.0, 1.25, 1.5, 1.75, 2.0],
+            betas=[2.0, 3.0, 4.0])
 LEVEL1_BYTES_PER_POINT = 4.0 + 2.0 * 7.0 / 8.0 + 4.0 / 8.0   # x + level-1 codes + coarse recon
 
 
@@ -140,32 +143,47 @@ def _traffic_from_profile(n):
     return float(t.group(1)) * n ** 3
 
 
+def _oracle_step(oracle, x):
+    """The oracle as it stands: sampled tuner (max-CR mode), then compression
+    with the tuned parameters, value range and rate estimate included."""
+    mn, mx, _ = oracle.value_range(x)
+    vr = float(mx) - float(mn)
+    oo = oracle.make_tune_opts(3, block=TUNE["block"], rate=TUNE["rate"],
+                               n_orders=TUNE["n_orders"], alphas=TUNE["alphas"],
+                               betas=TUNE["betas"])
+    rep = oracle.tune(x, REL_EB * vr, vr, oracle.METRIC_MAXERR, float("nan"), oo)
+    r = oracle.compress(x, rep.e, rep.params, want_recon=False)
+    oracle.estimate_bits(oracle.histogram(r["codes"], 32), len(r["unpred_idx"]),
+                         len(r["anchors"]))
+
+
+def _workload_host(n, sub):
+    import synth
+    try:
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+    except ImportError:
+        dev = "cpu"
+    if dev == "cpu" and n > 256:
+        n = sub  # generating the full field on the host would dominate
+    x = synth.config2_field(n, device=dev)[:sub, :sub, :sub].contiguous()
+    return x.cpu().numpy()
+
+
 def run_reference(args, rank, world):
-    """CPU oracle arm: each step compresses a bounded sample (a 128^3 corner
-    block of the same field) with the oracle, single-threaded."""
+    """CPU oracle arm: each step runs the oracle's tune + compress on a
+    bounded sample, the 256^3 corner of the benchmark field, single-threaded."""
     if rank != 0:
         return
-    import numpy as np
     import oracle
-    import synth
     oracle.build()
-    n = args.n
-    sub = min(128, n)
-    x = synth.config2_field(sub).numpy()  # same generator, smaller box
-    op = oracle.make_params(3, **PARAMS)
-
-    def step():
-        mn, mx, _ = oracle.value_range(x)
-        e = REL_EB * (float(mx) - float(mn))
-        r = oracle.compress(x, e, op, want_recon=False)
-        oracle.estimate_bits(oracle.histogram(r["codes"], 32), len(r["unpred_idx"]),
-                             len(r["anchors"]))
-
+    sub = min(256, args.n)
+    x = _workload_host(args.n, sub)
     for _ in range(args.warmup):
-        step()
+        _oracle_step(oracle, x)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        step()
+        _oracle_step(oracle, x)
     dt = time.perf_counter() - t0
     gbs = 4.0 * x.size * args.steps / dt / 1e9
     line = {
@@ -173,32 +191,27 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": f"{sub}^3 corner sample of the k^-5/3+fronts field, eps 1e-3, "
-                               "cubic, order 012, alpha 1.5, beta 4", "parallelism": "none"},
+        "config": {"workload": f"{sub}^3 corner sample of the {args.n}^3 k^-5/3+fronts field, "
+                               "rel bound 1e-3, max-CR mode: oracle tune + compress",
+                   "parallelism": "none"},
         "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{sub}^3 field per step, single-threaded C++ oracle"},
+                         "sample": f"{sub}^3 sample per step, single-threaded C++ oracle"},
         "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 def cpu_baseline(x):
-    """The oracle as it stands, on a bounded sample: one compress of the
-    benchmark field itself (a few seconds of single-threaded CPU work)."""
+    """The oracle as it stands, on a bounded sample: one tune + compress of
+    the benchmark field itself (several seconds of single-threaded work)."""
     import oracle
     oracle.build()
-    sub = x.shape[0]
-    op = oracle.make_params(3, **PARAMS)
     t0 = time.perf_counter()
-    mn, mx, _ = oracle.value_range(x)
-    e = REL_EB * (float(mx) - float(mn))
-    r = oracle.compress(x, e, op, want_recon=False)
-    oracle.estimate_bits(oracle.histogram(r["codes"], 32), len(r["unpred_idx"]),
-                         len(r["anchors"]))
+    _oracle_step(oracle, x)
     dt = time.perf_counter() - t0
     return {"value": 4.0 * x.size / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"one compress of the {sub}^3 benchmark field (eps 1e-3), "
-                      f"single-threaded, {dt:.1f} s"}
+            "sample": f"one tune + compress of the {x.shape[0]}^3 benchmark field "
+                      f"(rel bound 1e-3, max-CR mode), single-threaded, {dt:.1f} s"}
 
 
 def main():
@@ -223,7 +236,7 @@ def main():
     N = n ** 3
     x = synth.config2_field(n, device="cuda")
     torch.cuda.synchronize()
-    p = q.make_params(3, **PARAMS)
+    topts = q.make_tune_opts(**TUNE)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -231,13 +244,14 @@ def main():
         if dist:
             dist.barrier()
 
-    def step():
-        b = q.compress(x, REL_EB, p)
-        b.free()
+    def step(field=None):
+        field = x if field is None else field
+        rep = q.tune(field, REL_EB, q.METRIC_MAXERR, float("nan"), topts)
+        return q.compress_abs(field, rep.abs_eb, rep.params), rep
 
     for _ in range(max(3, args.warmup)):
-        step()
-    blob = q.compress(x, REL_EB, p)
+        step()[0].free()
+    blob, rep = step()
     info = blob.info()
     ser_bytes = blob.serialize().numel()
     blob.free()
@@ -252,7 +266,7 @@ def main():
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        step()
+        step()[0].free()
     ev1.record(stream)
     barrier()
     ms = ev0.elapsed_time(ev1)
@@ -269,6 +283,7 @@ def main():
     lvl1_ms = prof.ms[q.STAGE_LEVEL + 1] / max(1, prof.calls[q.STAGE_LEVEL + 1])
     pq_ms = sum(prof.ms[q.STAGE_LEVEL + l] for l in range(1, 9)) / args.steps
     range_ms = prof.ms[q.STAGE_RANGE] / args.steps
+    tune_ms = prof.ms[22] / args.steps
     peak, peak_kind = _peak_hbm()
     achieved = LEVEL1_BYTES_PER_POINT * N / (lvl1_ms * 1e-3) / 1e9
     traffic = _traffic_from_profile(n)
@@ -282,7 +297,7 @@ def main():
 
         def e2e_step():
             xd.copy_(hx, non_blocking=True)
-            b = q.compress(xd, REL_EB, p)
+            b, _ = step(xd)
             b.serialize(out)
             b.free()
 
@@ -305,8 +320,11 @@ def main():
         "data": "synthetic",
         "config": {
             "workload": f"{n}^3 FP32 k^-5/3 GRF + 8 tanh fronts (NYX-sized), rel bound 1e-3, "
-                        "fixed theta: cubic, order 012, alpha 1.5, beta 4",
-            "step": "qoz_compress: value range + anchors + 5 levels + histogram + counts",
+                        "max-CR mode",
+            "step": "qoz_tune (0.5% sampled 33^3 blocks, 12 interpolators, alpha 5 x beta 3) "
+                    "+ qoz_compress_abs with the tuned theta",
+            "theta": {"interp": list(rep.params.interp[:5]), "order": list(rep.params.order[:5]),
+                      "alpha": rep.params.alpha, "beta": rep.params.beta},
             "l2": "input 512 MiB > 126 MB L2; no flush needed",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -314,7 +332,8 @@ def main():
                      "kernel": "level_kernel<compress> level 1",
                      "algorithmic_bytes_per_launch": LEVEL1_BYTES_PER_POINT * N,
                      "peak_kind": peak_kind},
-        "breakdown_ms": {"range": range_ms, "levels_total": pq_ms, "level1": lvl1_ms,
+        "breakdown_ms": {"tune_trials": tune_ms, "range": range_ms, "levels_total": pq_ms,
+                         "level1": lvl1_ms,
                          "pq_input_gbs": 4.0 * N / (pq_ms * 1e-3) / 1e9,
                          "pq_frac_6N": 6.0 * N / (pq_ms * 1e-3) / 1e9 / peak},
         "compression": {"est_ratio": info.est_ratio, "n_unpredictable": info.n_unpredictable,

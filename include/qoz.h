@@ -164,6 +164,52 @@ qoz_status qoz_compute_metrics(const float* d_a, const float* d_b, qoz_shape sha
                                double vrange, int32_t ssim_win, int32_t ssim_step,
                                qoz_metrics* out, void* stream);
 
+/* ---------------------------------------------------------------- tuning */
+
+/* Options of the sampled online tuner (Sec. 6).  Zero / empty fields take
+ * the paper's defaults (Sec. 7.1.4, Sec. 6.3.1): 3D block 16, rate 0.5 %;
+ * 2D block 64, rate 1 %; alpha {1, 1.25, 1.5, 1.75, 2}; beta {1.5, 2, 3, 4};
+ * two dimension orders (increasing and decreasing); SSIM windows 7, step 2. */
+typedef struct {
+  int32_t block;          /* sample block size b (power of two); blocks hold b+1 points per axis */
+  double rate;            /* sampling rate r: block stride S = round(b r^(-1/d)) */
+  int32_t n_orders;       /* 2: increasing/decreasing axis order; 6: all six (3D) */
+  int32_t n_alpha;
+  double alphas[8];
+  int32_t n_beta;
+  double betas[8];
+  int32_t ssim_win, ssim_step;
+  int32_t anchor_stride;  /* of the full field (0: 3D 32, 2D 64) */
+} qoz_tune_opts;
+
+typedef struct {
+  qoz_params params;      /* chosen interpolators / orders per level, alpha, beta */
+  double abs_eb;          /* bound to compress with (target mode may lower it) */
+  double vmin, vmax;      /* value range of the field */
+  double B;               /* sampled bit rate of the chosen setting (bits per point) */
+  double M;               /* sampled metric (PSNR dB, SSIM, or -max error) */
+  int32_t n_trials;       /* trial compressions of the sampled blocks that ran */
+  int32_t n_blocks;
+  int64_t n_sampled_points;
+  double alg1_score[QOZ_MAX_LEVELS];  /* mean |x - pred| of the chosen interpolator per level */
+} qoz_tune_report;
+
+/* Sampled online tuning, Sec. 6: uniform block sampling (Sec. 6.1),
+ * level-adapted interpolator selection (Algorithm 1, greedy from the top
+ * level down, each level scored by the mean absolute prediction error at
+ * bound e), then the (alpha, beta) candidates (Sec. 6.3.1) compared by the
+ * sampled bit rate (Huffman cost of the pooled codes, Sec. 6.1) and metric:
+ *   metric MAXERR, target NaN: minimum bit rate under the bound (the
+ *     maximise-compression-ratio mode);
+ *   metric PSNR / SSIM, target NaN: Table I comparisons at the bound e;
+ *   finite target (PSNR dB or SSIM): each (alpha, beta) is scored by the bit
+ *     rate interpolated at the target between two sampled bounds, then a
+ *     short secant on log e picks the bound (capped at rel_eb * vrange).
+ * Synchronises `stream` several times. */
+qoz_status qoz_tune(const float* d_field, qoz_shape shape, double rel_eb, qoz_metric metric,
+                    double target, const qoz_tune_opts* opts, void* stream,
+                    qoz_tune_report* out);
+
 /* ---------------------------------------------------------------- profiling */
 
 /* Stage ids of the per-stage timers. */

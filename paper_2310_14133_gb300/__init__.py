@@ -26,7 +26,9 @@ from ._binding import (  # noqa: F401
     lib,
     library_path,
     make_params,
+    make_tune_opts,
     profile_enable,
     profile_read,
+    tune,
     value_range,
 )

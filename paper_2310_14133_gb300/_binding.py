@@ -62,6 +62,45 @@ def profile_read(reset: bool = False) -> StageTimes:
     return t
 
 
+class TuneOpts(C.Structure):
+    _fields_ = [("block", C.c_int32), ("rate", C.c_double), ("n_orders", C.c_int32),
+                ("n_alpha", C.c_int32), ("alphas", C.c_double * 8),
+                ("n_beta", C.c_int32), ("betas", C.c_double * 8),
+                ("ssim_win", C.c_int32), ("ssim_step", C.c_int32),
+                ("anchor_stride", C.c_int32)]
+
+
+class TuneReport(C.Structure):
+    _fields_ = [("params", Params), ("abs_eb", C.c_double), ("vmin", C.c_double),
+                ("vmax", C.c_double), ("B", C.c_double), ("M", C.c_double),
+                ("n_trials", C.c_int32), ("n_blocks", C.c_int32),
+                ("n_sampled_points", C.c_int64), ("alg1_score", C.c_double * MAX_LEVELS)]
+
+
+def make_tune_opts(block=0, rate=0.0, n_orders=0, alphas=None, betas=None, ssim_win=0,
+                   ssim_step=0, anchor_stride=0) -> TuneOpts:
+    """Zero / None fields take the library's defaults (the paper's)."""
+    o = TuneOpts()
+    o.block, o.rate, o.n_orders = block, rate, n_orders
+    for i, v in enumerate(alphas or []):
+        o.alphas[i] = v
+    o.n_alpha = len(alphas or [])
+    for i, v in enumerate(betas or []):
+        o.betas[i] = v
+    o.n_beta = len(betas or [])
+    o.ssim_win, o.ssim_step, o.anchor_stride = ssim_win, ssim_step, anchor_stride
+    return o
+
+
+def tune(x: torch.Tensor, rel_eb: float, metric: int = 0, target: float = float("nan"),
+         opts: TuneOpts | None = None, stream=None) -> TuneReport:
+    rep = TuneReport()
+    _check(lib().qoz_tune(_dev_ptr(x), _shape_of(x), float(rel_eb), int(metric), float(target),
+                          C.byref(opts) if opts is not None else None, _stream(stream),
+                          C.byref(rep)))
+    return rep
+
+
 class Metrics(C.Structure):
     _fields_ = [("max_abs_err", C.c_double), ("mse", C.c_double), ("psnr", C.c_double),
                 ("ssim", C.c_double), ("ssim_windows", C.c_int64)]
@@ -99,6 +138,7 @@ def lib():
             "qoz_blob_free": (None, [P]),
             "qoz_compute_metrics": (i32, [P, P, Shape, f64, i32, i32, P, P]),
             "qoz_profile_enable": (i32, [i32]),
+            "qoz_tune": (i32, [P, Shape, f64, i32, f64, P, P, P]),
             "qoz_profile_read": (i32, [P, i32]),
         }
         for name, (res, args) in sig.items():

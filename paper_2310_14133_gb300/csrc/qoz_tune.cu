@@ -1,0 +1,728 @@
+// Sampled online tuner (Sec. 6): uniform block sampling (Sec. 6.1),
+// Algorithm 1 (level-adapted interpolator selection, Sec. 6.2) and the
+// alpha / beta search with the Table I comparisons (Sec. 6.3).
+//
+// Every trial compression of the sampled blocks runs on the GPU: one CTA per
+// (candidate, block) copies its block into shared memory and runs the whole
+// multi-level predictor on it as an independent small field (anchors at the
+// block corners, log2 min(b, s) levels), accumulating the mean absolute
+// prediction error of the scored level, the code histogram (pooled over the
+// candidate's blocks), the unpredictable count, the squared and maximum
+// error and the SSIM window sums.  The host mirrors the method's sequential
+// decisions; trials whose outcome does not depend on an earlier decision are
+// batched into one launch (all candidates of an Algorithm 1 level; all
+// (alpha, beta) at e and at the 0.8 e / 1.2 e that Table I may ask for).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/qoz.h"
+#include "qoz_host.h"
+#include "qoz_internal.h"
+
+namespace qoz {
+namespace {
+
+constexpr int kTrialThreads = 512;
+constexpr int kTHistLo = kRadius - 2048;
+constexpr int kTHistWin = 4096;
+constexpr int kOutStride = 8;  // per (candidate, block): l1, l1_cnt, unpred, sse, maxerr, ssim_sum, ssim_n, pad
+
+struct TrialCand {
+  unsigned char interp[kMaxLevels];
+  unsigned char axes[kMaxLevels][3];  // physical axes of each level's order
+  float el[kMaxLevels], two_e[kMaxLevels], inv[kMaxLevels];
+};
+
+struct TrialArgs {
+  const float* x;
+  long long st0, st1;      // element strides of the embedded field (z, y)
+  const int* origins;      // 3 per block (embedded z, y, x)
+  int nblocks;
+  int bd[3];               // block extent (embedded)
+  int Ls;                  // levels of the block predictor
+  int stop_level;          // lowest level run
+  int score_level;         // level whose |x - pred| is summed (0: none)
+  const TrialCand* cands;
+  unsigned* hist;          // [ncand][65536] or null
+  double* out;             // [ncand][nblocks][kOutStride]
+  int metrics;             // accumulate sse / max error / SSIM after the last level
+  int ssim_win, ssim_step, is3d;
+  double c1, c2;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+  return v;
+}
+
+__global__ void __launch_bounds__(kTrialThreads, 1) trial_kernel(const TrialArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n0 = a.bd[0], n1 = a.bd[1], n2 = a.bd[2];
+  const int npts = n0 * n1 * n2;
+  float* S = reinterpret_cast<float*>(smem);
+  unsigned* SH = reinterpret_cast<unsigned*>(smem + ((sizeof(float) * npts + 15) & ~size_t(15)));
+  __shared__ double red[kTrialThreads / 32][6];
+
+  const int cand = blockIdx.x / a.nblocks;
+  const int blk = blockIdx.x % a.nblocks;
+  const TrialCand& C = a.cands[cand];
+  const int oz = a.origins[3 * blk + 0], oy = a.origins[3 * blk + 1], ox = a.origins[3 * blk + 2];
+  const float* xb = a.x + (long long)oz * a.st0 + (long long)oy * a.st1 + ox;
+  auto gidx = [&](int z, int y, int xx) { return (long long)z * a.st0 + (long long)y * a.st1 + xx; };
+
+  for (int i = threadIdx.x; i < npts; i += blockDim.x) {
+    const int xx = i % n2;
+    const int r = i / n2;
+    S[i] = xb[gidx(r / n1, r % n1, xx)];
+  }
+  if (a.hist)
+    for (int i = threadIdx.x; i < kTHistWin; i += blockDim.x) SH[i] = 0;
+  __syncthreads();
+
+  double l1 = 0.0, l1n = 0.0, unp = 0.0;
+  const int nd[3] = {n0, n1, n2};
+  const int st[3] = {n1 * n2, n2, 1};
+  for (int l = a.Ls; l >= a.stop_level; --l) {
+    const int h = 1 << (l - 1);
+    const float el = C.el[l - 1], two_e = C.two_e[l - 1], inv = C.inv[l - 1];
+    const int interp = C.interp[l - 1];
+    for (int k = 0; k < 3; ++k) {
+      const int ax = C.axes[l - 1][k];
+      int start[3], step[3], cnt[3];
+      for (int j = 0; j < 3; ++j) {
+        const int p = C.axes[l - 1][j];
+        if (j < k) {
+          start[p] = 0;
+          step[p] = h;
+        } else if (j == k) {
+          start[p] = h;
+          step[p] = 2 * h;
+        } else {
+          start[p] = 0;
+          step[p] = 2 * h;
+        }
+        cnt[p] = nd[p] - 1 >= start[p] ? (nd[p] - 1 - start[p]) / step[p] + 1 : 0;
+      }
+      const int total = cnt[0] * cnt[1] * cnt[2];
+      for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        const int i2 = i % cnt[2];
+        const int r = i / cnt[2];
+        const int i1 = r % cnt[1];
+        const int i0 = r / cnt[1];
+        const int c[3] = {start[0] + i0 * step[0], start[1] + i1 * step[1],
+                          start[2] + i2 * step[2]};
+        const int li = c[0] * st[0] + c[1] * st[1] + c[2];
+        const int sa = st[ax], ca = c[ax], na = nd[ax];
+        const bool hb1 = ca + h < na, ha3 = ca >= 3 * h, hb3 = ca + 3 * h < na;
+        const float a1 = S[li - h * sa];
+        const float b1 = hb1 ? S[li + h * sa] : 0.0f;
+        const float a3 = ha3 ? S[li - 3 * h * sa] : 0.0f;
+        const float b3 = hb3 ? S[li + 3 * h * sa] : 0.0f;
+        const float pred = predict(a3, a1, b1, b3, ha3, hb1, hb3, interp);
+        const float xv = xb[gidx(c[0], c[1], c[2])];
+        if (l == a.score_level) {
+          const double ad = fabs((double)xv - (double)pred);
+          if (isfinite(ad)) {
+            l1 += ad;
+            l1n += 1.0;
+          }
+        }
+        uint16_t code;
+        float rec;
+        if (quantize(xv, pred, el, two_e, inv, &code, &rec)) {
+          S[li] = rec;
+        } else {
+          code = 0;
+          S[li] = xv;
+          unp += 1.0;
+        }
+        if (a.hist) {
+          const unsigned kk = (unsigned)code - (unsigned)kTHistLo;
+          if (kk < (unsigned)kTHistWin)
+            atomicAdd(&SH[kk], 1u);
+          else
+            atomicAdd(&a.hist[(size_t)cand * 65536 + code], 1u);
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  double sse = 0.0, mx = 0.0, ss = 0.0, sn = 0.0;
+  if (a.metrics) {
+    for (int i = threadIdx.x; i < npts; i += blockDim.x) {
+      const int xx = i % n2;
+      const int r = i / n2;
+      const double d = (double)xb[gidx(r / n1, r % n1, xx)] - (double)S[i];
+      sse += d * d;
+      const double ad = fabs(d);
+      if (ad != ad || ad > mx) mx = ad;
+    }
+    if (a.ssim_win > 0) {
+      const int w = a.ssim_win, sp = a.ssim_step;
+      const int wz = a.is3d ? w : 1;
+      auto cntw = [&](int n) { return n >= w ? (n - w) / sp + 1 : 0; };
+      const int c0 = a.is3d ? cntw(n0) : 1, c1n = cntw(n1), c2n = cntw(n2);
+      const int nw = c0 * c1n * c2n;
+      const double np = (double)w * w * wz;
+      for (int wi = threadIdx.x; wi < nw; wi += blockDim.x) {
+        const int w2 = wi % c2n;
+        const int r = wi / c2n;
+        const int w1 = r % c1n;
+        const int w0 = r / c1n;
+        double sx = 0, sy = 0, sxx = 0, syy = 0, sxy = 0;
+        for (int i = 0; i < wz; ++i)
+          for (int j = 0; j < w; ++j)
+            for (int k = 0; k < w; ++k) {
+              const int z = w0 * sp + i, y = w1 * sp + j, xx = w2 * sp + k;
+              const double xv = xb[gidx(z, y, xx)];
+              const double yv = S[(z * n1 + y) * n2 + xx];
+              sx += xv;
+              sy += yv;
+              sxx += xv * xv;
+              syy += yv * yv;
+              sxy += xv * yv;
+            }
+        const double mxx = sx / np, myy = sy / np;
+        const double vx = sxx / np - mxx * mxx, vy = syy / np - myy * myy;
+        const double cxy = sxy / np - mxx * myy;
+        ss += ((2.0 * mxx * myy + a.c1) * (2.0 * cxy + a.c2)) /
+              ((mxx * mxx + myy * myy + a.c1) * (vx + vy + a.c2));
+        sn += 1.0;
+      }
+    }
+  }
+  if (a.hist) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kTHistWin; i += blockDim.x)
+      if (SH[i]) atomicAdd(&a.hist[(size_t)cand * 65536 + kTHistLo + i], SH[i]);
+  }
+  // fixed-order block reduction
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double v[6] = {warp_sum(l1), warp_sum(l1n), warp_sum(unp), warp_sum(sse), warp_max(mx),
+                 warp_sum(ss)};
+  const double snw = warp_sum(sn);
+  if (lane == 0)
+    for (int k = 0; k < 6; ++k) red[wid][k] = v[k];
+  __shared__ double sn_red[kTrialThreads / 32];
+  if (lane == 0) sn_red[wid] = snw;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) {
+      t[0] += red[wv][0];
+      t[1] += red[wv][1];
+      t[2] += red[wv][2];
+      t[3] += red[wv][3];
+      if (red[wv][4] != red[wv][4] || red[wv][4] > t[4]) t[4] = red[wv][4];
+      t[5] += red[wv][5];
+      t[6] += sn_red[wv];
+    }
+    double* o = a.out + ((size_t)cand * a.nblocks + blk) * kOutStride;
+    for (int k = 0; k < 7; ++k) o[k] = t[k];
+    o[7] = 0.0;
+  }
+}
+
+// ------------------------------------------------------------- host side
+
+struct Sampling {
+  std::vector<int> origins;  // 3 per block (embedded)
+  int nb = 0;
+  int bd[3] = {1, 1, 1};
+  long long npts = 0;
+  int Ls = 0;
+  long long anchors = 0;     // anchors over all blocks
+};
+
+int floor_log2(long long v) {
+  int l = 0;
+  while ((2LL << l) <= v) ++l;
+  return l;
+}
+
+// Uniform block sampling, Sec. 6.1: blocks of b+1 points per axis placed
+// every S = round(b r^(-1/d)) points while they fit; an axis shorter than a
+// block is taken whole.
+Sampling sample_blocks(const Resolved& r, int b, double rate, int s) {
+  Sampling sm;
+  const int d = r.ndims;
+  long long S = std::llround((double)b * std::pow(rate, -1.0 / (double)d));
+  if (S < 1) S = 1;
+  std::vector<long long> starts[3];
+  for (int p = 0; p < 3; ++p) {
+    const bool active = !(d == 2 && p == 0);
+    if (!active) {
+      starts[p].push_back(0);
+      sm.bd[p] = 1;
+      continue;
+    }
+    for (long long o = 0; o + b <= r.n[p] - 1; o += S) starts[p].push_back(o);
+    if (starts[p].empty()) {
+      starts[p].push_back(0);
+      sm.bd[p] = (int)r.n[p];
+    } else {
+      sm.bd[p] = b + 1;
+    }
+  }
+  for (long long o0 : starts[0])
+    for (long long o1 : starts[1])
+      for (long long o2 : starts[2]) {
+        sm.origins.push_back((int)o0);
+        sm.origins.push_back((int)o1);
+        sm.origins.push_back((int)o2);
+      }
+  sm.nb = (int)(sm.origins.size() / 3);
+  sm.npts = (long long)sm.nb * sm.bd[0] * sm.bd[1] * sm.bd[2];
+  sm.Ls = floor_log2(b < s ? b : s);
+  const long long sb = 1LL << sm.Ls;
+  long long apb = 1;
+  for (int p = 0; p < 3; ++p) apb *= (sm.bd[p] + sb - 1) / sb;
+  sm.anchors = apb * sm.nb;
+  return sm;
+}
+
+// Level bounds of Eq. (ebl) in double, each rounded to binary32 once.
+void fill_bounds(TrialCand* c, double e, double alpha, double beta, int L) {
+  double a = 1.0;
+  for (int l = 0; l < kMaxLevels; ++l) {
+    if (l < L) {
+      const double den = a < beta ? a : beta;
+      const double el = e / den;
+      c->el[l] = (float)el;
+      c->two_e[l] = (float)(2.0 * el);
+      c->inv[l] = (float)(1.0 / (2.0 * el));
+      a = a * alpha;
+    } else {
+      c->el[l] = c->two_e[l] = c->inv[l] = 0.0f;
+    }
+  }
+}
+
+const int kPerm3T[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+void set_axes(TrialCand* c, int level, int ndims, int order) {
+  const int o3 = ndims == 3 ? order : (order == 0 ? 0 : 1);
+  for (int k = 0; k < 3; ++k) c->axes[level - 1][k] = (unsigned char)kPerm3T[o3][k];
+}
+
+struct TrialResult {
+  double B, M;             // bit rate, metric (higher is better)
+  double l1_mean;
+};
+
+class Tuner {
+ public:
+  Tuner(const float* x, const Resolved& r, const Sampling& sm, cudaStream_t s, int metric,
+        int ssim_win, int ssim_step, double vrange)
+      : x_(x), r_(r), sm_(sm), s_(s), metric_(metric), win_(ssim_win), step_(ssim_step),
+        vr_(vrange) {}
+  ~Tuner() {
+    dev_free(d_orig_, s_);
+    dev_free(d_cands_, s_);
+    dev_free(d_out_, s_);
+    dev_free(d_hist_, s_);
+  }
+
+  qoz_status init() {
+    if (dev_alloc((void**)&d_orig_, sizeof(int) * sm_.origins.size(), s_) != cudaSuccess)
+      return fail(QOZ_ENOMEM, "tuner allocation");
+    cudaMemcpyAsync(d_orig_, sm_.origins.data(), sizeof(int) * sm_.origins.size(),
+                    cudaMemcpyHostToDevice, s_);
+    return QOZ_OK;
+  }
+
+  // Runs the given candidates; fills per-candidate results.  hist/metrics
+  // only when stop_level == 1.
+  qoz_status run(const std::vector<TrialCand>& cands, int stop_level, int score_level,
+                 bool full, std::vector<TrialResult>* res) {
+    const int nc = (int)cands.size();
+    if (nc == 0) return QOZ_OK;
+    if (nc > cap_c_) {
+      dev_free(d_cands_, s_);
+      dev_free(d_out_, s_);
+      dev_free(d_hist_, s_);
+      cap_c_ = nc;
+      if (dev_alloc((void**)&d_cands_, sizeof(TrialCand) * nc, s_) != cudaSuccess ||
+          dev_alloc((void**)&d_out_, sizeof(double) * kOutStride * nc * sm_.nb, s_) !=
+              cudaSuccess ||
+          dev_alloc((void**)&d_hist_, sizeof(unsigned) * 65536 * (size_t)nc, s_) != cudaSuccess)
+        return fail(QOZ_ENOMEM, "tuner allocation");
+    }
+    cudaError_t e = cudaMemcpyAsync(d_cands_, cands.data(), sizeof(TrialCand) * nc,
+                                    cudaMemcpyHostToDevice, s_);
+    if (e == cudaSuccess && full)
+      e = cudaMemsetAsync(d_hist_, 0, sizeof(unsigned) * 65536 * (size_t)nc, s_);
+    TrialArgs a;
+    memset(&a, 0, sizeof(a));
+    a.x = x_;
+    a.st0 = r_.n[1] * r_.n[2];
+    a.st1 = r_.n[2];
+    a.origins = d_orig_;
+    a.nblocks = sm_.nb;
+    for (int p = 0; p < 3; ++p) a.bd[p] = sm_.bd[p];
+    a.Ls = sm_.Ls;
+    a.stop_level = stop_level;
+    a.score_level = score_level;
+    a.cands = d_cands_;
+    a.hist = full ? d_hist_ : nullptr;
+    a.out = d_out_;
+    a.metrics = full ? 1 : 0;
+    a.ssim_win = (full && metric_ == QOZ_METRIC_SSIM) ? win_ : 0;
+    a.ssim_step = step_;
+    a.is3d = r_.ndims == 3;
+    a.c1 = (0.01 * vr_) * (0.01 * vr_);
+    a.c2 = (0.03 * vr_) * (0.03 * vr_);
+    const int npb = sm_.bd[0] * sm_.bd[1] * sm_.bd[2];
+    const size_t smem = ((sizeof(float) * npb + 15) & ~size_t(15)) + sizeof(unsigned) * kTHistWin;
+    if (smem > 220 * 1024) return fail(QOZ_EUNSUPPORTED, "sample block too large (%d points)", npb);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute((const void*)trial_kernel,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+      ProfScope ps(QOZ_STAGE_TUNE, s_);
+      trial_kernel<<<nc * sm_.nb, kTrialThreads, smem, s_>>>(a);
+      note_launch(1);
+      e = launch_check(cudaGetLastError());
+    }
+    trials_ += nc;
+    std::vector<double> out((size_t)kOutStride * nc * sm_.nb);
+    std::vector<unsigned> hist;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out.data(), d_out_, sizeof(double) * out.size(), cudaMemcpyDeviceToHost,
+                          s_);
+    if (e == cudaSuccess && full) {
+      hist.resize((size_t)65536 * nc);
+      e = cudaMemcpyAsync(hist.data(), d_hist_, sizeof(unsigned) * hist.size(),
+                          cudaMemcpyDeviceToHost, s_);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s_);
+    if (e != cudaSuccess) return cuda_fail(e, "tuner trial");
+    res->assign(nc, TrialResult{0, 0, 0});
+    for (int c = 0; c < nc; ++c) {
+      double l1 = 0, l1n = 0, unp = 0, sse = 0, mx = 0, ss = 0, sn = 0;
+      for (int b = 0; b < sm_.nb; ++b) {
+        const double* o = &out[((size_t)c * sm_.nb + b) * kOutStride];
+        l1 += o[0];
+        l1n += o[1];
+        unp += o[2];
+        sse += o[3];
+        if (o[4] != o[4] || o[4] > mx) mx = o[4];
+        ss += o[5];
+        sn += o[6];
+      }
+      TrialResult& t = (*res)[c];
+      t.l1_mean = l1n > 0 ? l1 / l1n : 0.0;
+      if (full) {
+        const double bits = (double)huffman_bits_u32(&hist[(size_t)c * 65536], 65536) +
+                            32.0 * unp + 32.0 * (double)sm_.anchors;
+        t.B = bits / (double)sm_.npts;
+        if (metric_ == QOZ_METRIC_PSNR) {
+          const double mse = sse / (double)sm_.npts;
+          t.M = mse == 0.0 ? INFINITY : 20.0 * std::log10(vr_ / std::sqrt(mse));
+        } else if (metric_ == QOZ_METRIC_SSIM) {
+          t.M = sn > 0 ? ss / sn : NAN;
+        } else {
+          t.M = -mx;
+        }
+      }
+    }
+    return QOZ_OK;
+  }
+
+  int trials() const { return trials_; }
+
+ private:
+  const float* x_;
+  const Resolved& r_;
+  const Sampling& sm_;
+  cudaStream_t s_;
+  int metric_, win_, step_;
+  double vr_;
+  int* d_orig_ = nullptr;
+  TrialCand* d_cands_ = nullptr;
+  double* d_out_ = nullptr;
+  unsigned* d_hist_ = nullptr;
+  int cap_c_ = 0;
+  int trials_ = 0;
+};
+
+// Table I: 0 keeps the incumbent I, 1 takes II, -1 asks for II at
+// *scale * e (0.8 in case 3, 1.2 in case 4); pass b2p = NaN first.
+int table1(double b1, double m1, double b2, double m2, double b2p, double m2p, double* scale) {
+  if (b1 <= b2 && m1 >= m2) return 0;
+  if (b1 >= b2 && m1 <= m2) return 1;
+  const bool case3 = b1 > b2 && m1 > m2;
+  if (std::isnan(b2p)) {
+    *scale = case3 ? 0.8 : 1.2;
+    return -1;
+  }
+  double m_line;
+  if (b2p == b2)
+    m_line = m2 > m2p ? m2 : m2p;
+  else
+    m_line = m2 + (m2p - m2) * (b1 - b2) / (b2p - b2);
+  return m1 >= m_line ? 0 : 1;
+}
+
+}  // namespace
+
+qoz_status tune_impl(const float* d_field, const qoz_shape& shape, double rel_eb, int metric,
+                     double target, const qoz_tune_opts* opts_in, cudaStream_t s,
+                     qoz_tune_report* out) {
+  if (!d_field || !out) return fail(QOZ_EINVAL, "NULL argument");
+  if (!(rel_eb > 0.0 && std::isfinite(rel_eb))) return fail(QOZ_EINVAL, "rel_eb must be > 0");
+  if (metric < QOZ_METRIC_MAXERR || metric > QOZ_METRIC_SSIM)
+    return fail(QOZ_EINVAL, "unknown metric %d", metric);
+  const bool target_mode = !std::isnan(target);
+  if (target_mode && metric == QOZ_METRIC_MAXERR)
+    return fail(QOZ_EINVAL, "a target needs the PSNR or SSIM metric");
+  Resolved r;
+  qoz_status st = resolve(shape, nullptr, &r);
+  if (st != QOZ_OK) return st;
+  qoz_tune_opts o;
+  memset(&o, 0, sizeof(o));
+  if (opts_in) o = *opts_in;
+  const int d = r.ndims;
+  if (o.block == 0) o.block = d == 3 ? 16 : 64;
+  if (!(o.rate > 0.0)) o.rate = d == 3 ? 0.005 : 0.01;
+  if (o.n_orders == 0) o.n_orders = 2;
+  if (o.n_alpha == 0) {
+    const double al[5] = {1.0, 1.25, 1.5, 1.75, 2.0};
+    o.n_alpha = 5;
+    for (int i = 0; i < 5; ++i) o.alphas[i] = al[i];
+  }
+  if (o.n_beta == 0) {
+    const double be[4] = {1.5, 2.0, 3.0, 4.0};
+    o.n_beta = 4;
+    for (int i = 0; i < 4; ++i) o.betas[i] = be[i];
+  }
+  if (o.ssim_win == 0) o.ssim_win = 7;
+  if (o.ssim_step == 0) o.ssim_step = 2;
+  if (o.anchor_stride == 0) o.anchor_stride = d == 3 ? 32 : 64;
+  if (o.block < 2 || (o.block & (o.block - 1)) != 0)
+    return fail(QOZ_EINVAL, "block must be a power of two >= 2");
+  if (o.n_alpha < 1 || o.n_alpha > 8 || o.n_beta < 1 || o.n_beta > 8)
+    return fail(QOZ_EINVAL, "1..8 alpha and beta candidates");
+  for (int i = 0; i < o.n_alpha; ++i)
+    if (!(o.alphas[i] >= 1.0)) return fail(QOZ_EINVAL, "alpha < 1");
+  for (int i = 0; i < o.n_beta; ++i)
+    if (!(o.betas[i] >= 1.0)) return fail(QOZ_EINVAL, "beta < 1");
+  {
+    qoz_params chk;
+    memset(&chk, 0, sizeof(chk));
+    chk.anchor_stride = o.anchor_stride;
+    chk.alpha = chk.beta = 1.0;
+    Resolved rr;
+    if (resolve(shape, &chk, &rr) != QOZ_OK) return fail(QOZ_EINVAL, "invalid anchor stride");
+  }
+  int L = 0;
+  while ((1 << L) < o.anchor_stride) ++L;
+
+  float vmin, vmax;
+  int64_t cnt;
+  st = qoz_value_range(d_field, r.N, &vmin, &vmax, &cnt, s);
+  if (st != QOZ_OK) return st;
+  const double vr = (double)vmax - (double)vmin;
+  const double e_user = rel_eb * vr;
+
+  Sampling sm = sample_blocks(r, o.block, o.rate, o.anchor_stride);
+  Tuner T(d_field, r, sm, s, metric, o.ssim_win, o.ssim_step, vr);
+  if ((st = T.init()) != QOZ_OK) return st;
+
+  double e0 = e_user;
+  if (target_mode && metric == QOZ_METRIC_PSNR) {
+    e0 = vr * std::sqrt(3.0) * std::pow(10.0, -target / 20.0);
+    if (e0 > e_user) e0 = e_user;
+  }
+
+  // candidate interpolators: linear before cubic, then the orders
+  std::vector<std::pair<int, int>> cands;
+  {
+    std::vector<int> orders;
+    if (d == 2)
+      orders = {0, 1};
+    else if (o.n_orders >= 6)
+      orders = {0, 1, 2, 3, 4, 5};
+    else
+      orders = {0, 5};
+    for (int t = 0; t < 2; ++t)
+      for (int od : orders) cands.push_back({t, od});
+  }
+
+  memset(out, 0, sizeof(*out));
+  TrialCand base;
+  memset(&base, 0, sizeof(base));
+  for (int l = 1; l <= kMaxLevels; ++l) set_axes(&base, l, d, 0);
+  unsigned char ch_interp[kMaxLevels] = {0}, ch_order[kMaxLevels] = {0};
+  fill_bounds(&base, e0, 1.0, 1.0, sm.Ls);
+
+  // ---- Algorithm 1, from the top sampled level down
+  std::vector<TrialResult> res;
+  for (int l = sm.Ls; l >= 1; --l) {
+    std::vector<TrialCand> tc;
+    for (auto& cd : cands) {
+      TrialCand c = base;
+      for (int ll = l + 1; ll <= sm.Ls; ++ll) {
+        c.interp[ll - 1] = ch_interp[ll - 1];
+        set_axes(&c, ll, d, ch_order[ll - 1]);
+      }
+      c.interp[l - 1] = (unsigned char)cd.first;
+      set_axes(&c, l, d, cd.second);
+      tc.push_back(c);
+    }
+    if ((st = T.run(tc, l, l, false, &res)) != QOZ_OK) return st;
+    double best = INFINITY;
+    int bi = 0;
+    for (size_t c = 0; c < res.size(); ++c) {
+      const double cur = res[c].l1_mean;
+      if (c == 0 || cur < best - 1e-12 * best) {
+        best = cur;
+        bi = (int)c;
+      }
+    }
+    ch_interp[l - 1] = (unsigned char)cands[bi].first;
+    ch_order[l - 1] = (unsigned char)cands[bi].second;
+    out->alg1_score[l - 1] = best;
+  }
+  qoz_params fp;
+  memset(&fp, 0, sizeof(fp));
+  fp.anchor_stride = o.anchor_stride;
+  for (int l = 1; l <= L; ++l) {
+    const int src = l <= sm.Ls ? l : sm.Ls;
+    fp.interp[l - 1] = ch_interp[src - 1];
+    fp.order[l - 1] = ch_order[src - 1];
+  }
+
+  // ---- alpha / beta candidates at e0 and, batched, at 0.8 e0 and 1.2 e0
+  TrialCand chosen = base;
+  for (int l = 1; l <= sm.Ls; ++l) {
+    chosen.interp[l - 1] = ch_interp[l - 1];
+    set_axes(&chosen, l, d, ch_order[l - 1]);
+  }
+  const int nab = o.n_alpha * o.n_beta;
+  const bool need_scaled = metric != QOZ_METRIC_MAXERR;
+  std::vector<TrialCand> tc;
+  const double scales[3] = {1.0, 0.8, 1.2};
+  for (int si = 0; si < (need_scaled ? 3 : 1); ++si)
+    for (int ia = 0; ia < o.n_alpha; ++ia)
+      for (int ib = 0; ib < o.n_beta; ++ib) {
+        TrialCand c = chosen;
+        fill_bounds(&c, scales[si] * e0, o.alphas[ia], o.betas[ib], sm.Ls);
+        tc.push_back(c);
+      }
+  if ((st = T.run(tc, 1, 0, true, &res)) != QOZ_OK) return st;
+  auto at = [&](int si, int k) -> const TrialResult& { return res[(size_t)si * nab + k]; };
+
+  int best_k = 0;
+  double best_B = 0, best_M = 0, best_score = INFINITY, best_e = e0;
+  bool have = false;
+  struct TP {
+    double e, B, M;
+  };
+  std::vector<TP> pts;
+  for (int k = 0; k < nab; ++k) {
+    const TrialResult& t = at(0, k);
+    if (!target_mode) {
+      bool replace;
+      if (!have) {
+        replace = true;
+      } else if (metric == QOZ_METRIC_MAXERR) {
+        replace = t.B < best_B;
+      } else {
+        double scale = 0.0;
+        int dec = table1(best_B, best_M, t.B, t.M, NAN, NAN, &scale);
+        if (dec < 0) {
+          const TrialResult& t2 = at(scale < 1.0 ? 1 : 2, k);
+          dec = table1(best_B, best_M, t.B, t.M, t2.B, t2.M, &scale);
+        }
+        replace = dec == 1;
+      }
+      if (replace) {
+        have = true;
+        best_k = k;
+        best_B = t.B;
+        best_M = t.M;
+      }
+    } else {
+      const double sc = t.M >= target ? 1.2 : 0.8;
+      const TrialResult& t2 = at(sc > 1.0 ? 2 : 1, k);
+      double Bstar;
+      if (t2.M == t.M)
+        Bstar = t.M >= target ? (t.B < t2.B ? t.B : t2.B) : INFINITY;
+      else
+        Bstar = t.B + (target - t.M) * (t2.B - t.B) / (t2.M - t.M);
+      if (!have || Bstar < best_score) {
+        have = true;
+        best_score = Bstar;
+        best_k = k;
+        pts = {{e0, t.B, t.M}, {sc * e0, t2.B, t2.M}};
+      }
+    }
+  }
+  fp.alpha = o.alphas[best_k / o.n_beta];
+  fp.beta = o.betas[best_k % o.n_beta];
+
+  if (target_mode) {
+    // secant on (log e, M) for the chosen setting, at most four more trials
+    for (int it = 0; it < 4; ++it) {
+      const TP pa = pts[pts.size() - 2];
+      const TP pb = pts[pts.size() - 1];
+      if (pa.M == pb.M) break;
+      const double le =
+          std::log(pb.e) + (target - pb.M) * (std::log(pa.e) - std::log(pb.e)) / (pa.M - pb.M);
+      double en = std::exp(le);
+      if (en > e_user) en = e_user;
+      if (en < e0 / 16.0) en = e0 / 16.0;
+      if (en == pb.e) break;
+      TrialCand c = chosen;
+      fill_bounds(&c, en, fp.alpha, fp.beta, sm.Ls);
+      std::vector<TrialResult> r1;
+      if ((st = T.run({c}, 1, 0, true, &r1)) != QOZ_OK) return st;
+      pts.push_back({en, r1[0].B, r1[0].M});
+    }
+    int pick = -1;
+    for (size_t k = 0; k < pts.size(); ++k)
+      if (pts[k].M >= target && pts[k].e <= e_user && (pick < 0 || pts[k].e > pts[pick].e))
+        pick = (int)k;
+    if (pick < 0) {
+      pick = 0;
+      for (size_t k = 1; k < pts.size(); ++k)
+        if (pts[k].e < pts[pick].e) pick = (int)k;
+    }
+    best_e = pts[pick].e;
+    if (best_e > e_user) best_e = e_user;
+    best_B = pts[pick].B;
+    best_M = pts[pick].M;
+  } else {
+    best_e = e_user;
+  }
+
+  out->params = fp;
+  out->abs_eb = best_e;
+  out->vmin = vmin;
+  out->vmax = vmax;
+  out->B = best_B;
+  out->M = best_M;
+  out->n_trials = T.trials();
+  out->n_blocks = sm.nb;
+  out->n_sampled_points = sm.npts;
+  return QOZ_OK;
+}
+
+}  // namespace qoz
+
+extern "C" qoz_status qoz_tune(const float* d_field, qoz_shape shape, double rel_eb,
+                               qoz_metric metric, double target, const qoz_tune_opts* opts,
+                               void* stream, qoz_tune_report* out) {
+  return qoz::tune_impl(d_field, shape, rel_eb, (int)metric, target, opts, (cudaStream_t)stream,
+                        out);
+}

@@ -1,0 +1,104 @@
+"""GPU sampled tuner (Sec. 6) against the oracle's tuner on the same fields:
+the chosen interpolators, orders, alpha and beta must be identical; the
+sampled bit rate is exact (integer histograms), the metric and the
+Algorithm 1 scores agree to rounding."""
+
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2310_14133_gb300 import build
+    build.build()
+    import paper_2310_14133_gb300 as q
+    return q
+
+
+def _field(n=64, seed=21, nd=3):
+    import synth
+    if nd == 3:
+        f = synth.grf((n, n, n), 5.0 / 3.0, seed=seed, n_modes=128).numpy()
+        f += synth.fronts((n, n, n), 2000, count=4).numpy()
+    else:
+        f = (synth.zonal_bands(n, 2 * n, seed) + synth.grf((n, 2 * n), 3.0, seed=seed,
+                                                          sigma=1.0)).numpy()
+    return f
+
+
+def _compare(q, orc, x, rel, metric, target, block, rate, n_orders, alphas, betas, m_rel=1e-9):
+    xd = torch.from_numpy(x).cuda()
+    qo = q.make_tune_opts(block=block, rate=rate, n_orders=n_orders, alphas=alphas, betas=betas)
+    rep = q.tune(xd, rel, metric, target, qo)
+    mn, mx, _ = orc.value_range(x)
+    vr = float(mx) - float(mn)
+    oo = orc.make_tune_opts(x.ndim, block=block, rate=rate, n_orders=n_orders, alphas=alphas,
+                            betas=betas)
+    ref = orc.tune(x, rel * vr, vr, metric, target, oo)
+    L = int(math.log2(ref.params.anchor_stride))
+    assert list(rep.params.interp[:L]) == list(ref.params.interp[:L])
+    assert list(rep.params.order[:L]) == list(ref.params.order[:L])
+    assert (rep.params.alpha, rep.params.beta) == (ref.params.alpha, ref.params.beta)
+    assert rep.n_blocks == ref.n_blocks and rep.n_sampled_points == ref.n_sampled_points
+    for l in range(L):
+        assert rep.alg1_score[l] == pytest.approx(ref.alg1_score[l], rel=1e-12, abs=0)
+    assert rep.abs_eb == pytest.approx(ref.e, rel=1e-9)
+    assert rep.B == pytest.approx(ref.B, rel=1e-9)
+    if metric != 0:
+        assert rep.M == pytest.approx(ref.M, rel=m_rel)
+    return rep, ref
+
+
+@pytest.mark.parametrize("n_orders", [2, 6])
+def test_bound_mode(q, orc, n_orders):
+    x = _field(64, 21)
+    rep, ref = _compare(q, orc, x, 1e-3, 0, float("nan"), 16, 0.05, n_orders,
+                        [1.0, 1.25, 1.5, 1.75, 2.0], [2.0, 3.0, 4.0])
+    assert rep.B == ref.B           # exact: pooled histograms are integers
+
+
+def test_psnr_table1_mode(q, orc):
+    x = _field(64, 22)
+    _compare(q, orc, x, 1e-3, 1, float("nan"), 16, 0.05, 2, None, None)
+
+
+def test_ssim_table1_mode(q, orc):
+    x = _field(48, 23)
+    _compare(q, orc, x, 1e-2, 2, float("nan"), 16, 0.2, 2, [1.0, 1.5, 2.0], [2.0, 4.0])
+
+
+@pytest.mark.parametrize("target", [60.0, 80.0])
+def test_psnr_target_mode(q, orc, target):
+    x = _field(64, 24)
+    rep, ref = _compare(q, orc, x, 1e-2, 1, target, 16, 0.05, 2, None, None)
+    assert rep.M >= target
+
+
+def test_ssim_target_mode(q, orc):
+    x = _field(48, 25)
+    _compare(q, orc, x, 2e-2, 2, 0.99, 16, 0.2, 2, [1.0, 1.5, 2.0], [2.0, 4.0])
+
+
+def test_2d_bound_mode(q, orc):
+    x = _field(300, 26, nd=2)
+    _compare(q, orc, x, 1e-3, 0, float("nan"), 64, 0.05, 2, None, None)
+
+
+def test_full_size_512_sampled_tuner(q, orc):
+    """The plain-method-at-scale workload: 512^3 field with fronts, 0.5 %
+    sampled 33^3 blocks, 12 interpolators, alpha 5 x beta 3, max-CR mode."""
+    import synth
+    xg = synth.config2_field(512, device="cuda")
+    x = xg.cpu().numpy()
+    del xg
+    rep, ref = _compare(q, orc, x, 1e-3, 0, float("nan"), 32, 0.005, 6,
+                        [1.0, 1.25, 1.5, 1.75, 2.0], [2.0, 3.0, 4.0])
+    assert rep.n_blocks == 27
