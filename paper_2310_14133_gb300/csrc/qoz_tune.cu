@@ -54,6 +54,20 @@ struct TrialArgs {
   double c1, c2;
 };
 
+// Compensated (Kahan) binary32 accumulator for per-target sums: double
+// arithmetic runs at a small fraction of the binary32 rate on this part, so
+// per-point work stays in binary32 and only per-thread totals widen.
+struct KSum {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = __fsub_rn(v, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 __device__ __forceinline__ double warp_sum(double v) {
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   return v;
@@ -63,137 +77,170 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
+// The block is held in shared memory subsampled by f = 2^(stop_level - 1):
+// the levels that run (stop_level and above) only ever touch those points,
+// and level l of the block is level l - stop_level + 1 of the subsampled
+// grid (half-stride 2^(l - stop_level)).  x becomes the reconstruction in
+// place, target by target.
 __global__ void __launch_bounds__(kTrialThreads, 1) trial_kernel(const TrialArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int n0 = a.bd[0], n1 = a.bd[1], n2 = a.bd[2];
-  const int npts = n0 * n1 * n2;
+  const int f = 1 << (a.stop_level - 1);
+  const int m0 = (a.bd[0] - 1) / f + 1, m1 = (a.bd[1] - 1) / f + 1, m2 = (a.bd[2] - 1) / f + 1;
+  const int mt = m0 * m1 * m2;
   float* S = reinterpret_cast<float*>(smem);
-  unsigned* SH = reinterpret_cast<unsigned*>(smem + ((sizeof(float) * npts + 15) & ~size_t(15)));
-  __shared__ double red[kTrialThreads / 32][6];
+  unsigned* SH = reinterpret_cast<unsigned*>(smem + ((sizeof(float) * mt + 15) & ~size_t(15)));
+  __shared__ double red[kTrialThreads / 32][7];
 
   const int cand = blockIdx.x / a.nblocks;
   const int blk = blockIdx.x % a.nblocks;
   const TrialCand& C = a.cands[cand];
   const int oz = a.origins[3 * blk + 0], oy = a.origins[3 * blk + 1], ox = a.origins[3 * blk + 2];
   const float* xb = a.x + (long long)oz * a.st0 + (long long)oy * a.st1 + ox;
-  auto gidx = [&](int z, int y, int xx) { return (long long)z * a.st0 + (long long)y * a.st1 + xx; };
+  const long long fs0 = (long long)f * a.st0, fs1 = (long long)f * a.st1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
 
-  for (int i = threadIdx.x; i < npts; i += blockDim.x) {
-    const int xx = i % n2;
-    const int r = i / n2;
-    S[i] = xb[gidx(r / n1, r % n1, xx)];
+  for (int row = warp; row < m0 * m1; row += nw) {
+    const int z = row / m1, y = row - (row / m1) * m1;
+    const float* src = xb + z * fs0 + y * fs1;
+    float* dst = S + row * m2;
+    for (int xx = lane; xx < m2; xx += 32) {
+      const unsigned d = (unsigned)__cvta_generic_to_shared(dst + xx);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src + xx * f)
+                   : "memory");
+    }
   }
   if (a.hist)
     for (int i = threadIdx.x; i < kTHistWin; i += blockDim.x) SH[i] = 0;
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
 
-  double l1 = 0.0, l1n = 0.0, unp = 0.0;
-  const int nd[3] = {n0, n1, n2};
-  const int st[3] = {n1 * n2, n2, 1};
+  KSum l1;
+  int l1n = 0, unp = 0;
+  const int st1 = m2, st0 = m1 * m2;
   for (int l = a.Ls; l >= a.stop_level; --l) {
-    const int h = 1 << (l - 1);
+    const int h = 1 << (l - a.stop_level);
     const float el = C.el[l - 1], two_e = C.two_e[l - 1], inv = C.inv[l - 1];
     const int interp = C.interp[l - 1];
+    const int ax0 = C.axes[l - 1][0], ax1 = C.axes[l - 1][1], ax2 = C.axes[l - 1][2];
     for (int k = 0; k < 3; ++k) {
-      const int ax = C.axes[l - 1][k];
-      int start[3], step[3], cnt[3];
-      for (int j = 0; j < 3; ++j) {
-        const int p = C.axes[l - 1][j];
-        if (j < k) {
-          start[p] = 0;
-          step[p] = h;
-        } else if (j == k) {
-          start[p] = h;
-          step[p] = 2 * h;
-        } else {
-          start[p] = 0;
-          step[p] = 2 * h;
-        }
-        cnt[p] = nd[p] - 1 >= start[p] ? (nd[p] - 1 - start[p]) / step[p] + 1 : 0;
-      }
-      const int total = cnt[0] * cnt[1] * cnt[2];
-      for (int i = threadIdx.x; i < total; i += blockDim.x) {
-        const int i2 = i % cnt[2];
-        const int r = i / cnt[2];
-        const int i1 = r % cnt[1];
-        const int i0 = r / cnt[1];
-        const int c[3] = {start[0] + i0 * step[0], start[1] + i1 * step[1],
-                          start[2] + i2 * step[2]};
-        const int li = c[0] * st[0] + c[1] * st[1] + c[2];
-        const int sa = st[ax], ca = c[ax], na = nd[ax];
-        const bool hb1 = ca + h < na, ha3 = ca >= 3 * h, hb3 = ca + 3 * h < na;
-        const float a1 = S[li - h * sa];
-        const float b1 = hb1 ? S[li + h * sa] : 0.0f;
-        const float a3 = ha3 ? S[li - 3 * h * sa] : 0.0f;
-        const float b3 = hb3 ? S[li + 3 * h * sa] : 0.0f;
-        const float pred = predict(a3, a1, b1, b3, ha3, hb1, hb3, interp);
-        const float xv = xb[gidx(c[0], c[1], c[2])];
-        if (l == a.score_level) {
-          const double ad = fabs((double)xv - (double)pred);
-          if (isfinite(ad)) {
-            l1 += ad;
-            l1n += 1.0;
+      const int ax = k == 0 ? ax0 : (k == 1 ? ax1 : ax2);
+      // position of each physical axis in the order
+      const int j0 = ax0 == 0 ? 0 : (ax1 == 0 ? 1 : 2);
+      const int j1 = ax0 == 1 ? 0 : (ax1 == 1 ? 1 : 2);
+      const int j2 = ax0 == 2 ? 0 : (ax1 == 2 ? 1 : 2);
+      // axes before the pass axis: every h; the pass axis: h mod 2h; after: every 2h
+      const int s0 = j0 == k ? h : 0, s1 = j1 == k ? h : 0, s2 = j2 == k ? h : 0;
+      const int d0 = j0 < k ? h : 2 * h, d1 = j1 < k ? h : 2 * h, d2 = j2 < k ? h : 2 * h;
+      const int c0n = m0 - 1 >= s0 ? (m0 - 1 - s0) / d0 + 1 : 0;
+      const int c1n = m1 - 1 >= s1 ? (m1 - 1 - s1) / d1 + 1 : 0;
+      const int c2n = m2 - 1 >= s2 ? (m2 - 1 - s2) / d2 + 1 : 0;
+      const int sa = ax == 0 ? st0 : (ax == 1 ? st1 : 1);
+      const int na = ax == 0 ? m0 : (ax == 1 ? m1 : m2);
+      for (int row = warp; row < c0n * c1n; row += nw) {
+        const int i0 = row / c1n;
+        const int i1 = row - i0 * c1n;
+        const int z = s0 + i0 * d0, y = s1 + i1 * d1;
+        for (int i2 = lane; i2 < c2n; i2 += 32) {
+          const int xx = s2 + i2 * d2;
+          const int li = z * st0 + y * st1 + xx;
+          const int ca = ax == 0 ? z : (ax == 1 ? y : xx);
+          const bool hb1 = ca + h < na, ha3 = ca >= 3 * h, hb3 = ca + 3 * h < na;
+          const float a1 = S[li - h * sa];
+          const float b1 = hb1 ? S[li + h * sa] : 0.0f;
+          const float a3 = ha3 ? S[li - 3 * h * sa] : 0.0f;
+          const float b3 = hb3 ? S[li + 3 * h * sa] : 0.0f;
+          const float pred = predict(a3, a1, b1, b3, ha3, hb1, hb3, interp);
+          const float xv = S[li];  // not yet predicted: still the field value
+          if (l == a.score_level) {
+            const float ad = fabsf(__fsub_rn(xv, pred));
+            if (isfinite(ad)) {
+              l1.add(ad);
+              ++l1n;
+            }
           }
-        }
-        uint16_t code;
-        float rec;
-        if (quantize(xv, pred, el, two_e, inv, &code, &rec)) {
-          S[li] = rec;
-        } else {
-          code = 0;
-          S[li] = xv;
-          unp += 1.0;
-        }
-        if (a.hist) {
-          const unsigned kk = (unsigned)code - (unsigned)kTHistLo;
-          if (kk < (unsigned)kTHistWin)
-            atomicAdd(&SH[kk], 1u);
-          else
-            atomicAdd(&a.hist[(size_t)cand * 65536 + code], 1u);
+          uint16_t code;
+          float rec;
+          if (quantize(xv, pred, el, two_e, inv, &code, &rec)) {
+            S[li] = rec;
+          } else {
+            code = 0;
+            ++unp;
+          }
+          if (a.hist) {
+            const unsigned kk = (unsigned)code - (unsigned)kTHistLo;
+            if (kk < (unsigned)kTHistWin)
+              atomicAdd(&SH[kk], 1u);
+            else
+              atomicAdd(&a.hist[(size_t)cand * 65536 + code], 1u);
+          }
         }
       }
       __syncthreads();
     }
   }
 
-  double sse = 0.0, mx = 0.0, ss = 0.0, sn = 0.0;
-  if (a.metrics) {
-    for (int i = threadIdx.x; i < npts; i += blockDim.x) {
-      const int xx = i % n2;
-      const int r = i / n2;
-      const double d = (double)xb[gidx(r / n1, r % n1, xx)] - (double)S[i];
-      sse += d * d;
-      const double ad = fabs(d);
-      if (ad != ad || ad > mx) mx = ad;
+  KSum sse;
+  float mx = 0.0f;
+  double ss = 0.0, sn = 0.0;
+  if (a.metrics) {  // stop_level == 1: S is the whole block
+    const int n1 = a.bd[1], n2 = a.bd[2];
+    for (int row = warp; row < a.bd[0] * n1; row += nw) {
+      const int z = row / n1, y = row - (row / n1) * n1;
+      const float* src = xb + z * a.st0 + y * a.st1;
+      for (int xx = lane; xx < n2; xx += 32) {
+        const float d = __fsub_rn(src[xx], S[row * n2 + xx]);
+        sse.add(__fmul_rn(d, d));
+        const float ad = fabsf(d);
+        if (ad != ad || ad > mx) mx = ad;
+      }
     }
     if (a.ssim_win > 0) {
+      const int n0 = a.bd[0];
       const int w = a.ssim_win, sp = a.ssim_step;
       const int wz = a.is3d ? w : 1;
       auto cntw = [&](int n) { return n >= w ? (n - w) / sp + 1 : 0; };
       const int c0 = a.is3d ? cntw(n0) : 1, c1n = cntw(n1), c2n = cntw(n2);
-      const int nw = c0 * c1n * c2n;
+      const int nwin = c0 * c1n * c2n;
       const double np = (double)w * w * wz;
-      for (int wi = threadIdx.x; wi < nw; wi += blockDim.x) {
+      for (int wi = threadIdx.x; wi < nwin; wi += blockDim.x) {
         const int w2 = wi % c2n;
         const int r = wi / c2n;
         const int w1 = r % c1n;
         const int w0 = r / c1n;
-        double sx = 0, sy = 0, sxx = 0, syy = 0, sxy = 0;
+        // window moments in binary32, centred on the window means to keep the
+        // variances well conditioned; the SSIM formula itself in double
+        float sx = 0.0f, sy = 0.0f;
         for (int i = 0; i < wz; ++i)
-          for (int j = 0; j < w; ++j)
+          for (int j = 0; j < w; ++j) {
+            const int z = w0 * sp + i, y = w1 * sp + j;
+            const float* src = xb + z * a.st0 + y * a.st1 + w2 * sp;
+            const float* rec = S + (z * n1 + y) * n2 + w2 * sp;
             for (int k = 0; k < w; ++k) {
-              const int z = w0 * sp + i, y = w1 * sp + j, xx = w2 * sp + k;
-              const double xv = xb[gidx(z, y, xx)];
-              const double yv = S[(z * n1 + y) * n2 + xx];
-              sx += xv;
-              sy += yv;
-              sxx += xv * xv;
-              syy += yv * yv;
-              sxy += xv * yv;
+              sx = __fadd_rn(sx, src[k]);
+              sy = __fadd_rn(sy, rec[k]);
             }
-        const double mxx = sx / np, myy = sy / np;
-        const double vx = sxx / np - mxx * mxx, vy = syy / np - myy * myy;
-        const double cxy = sxy / np - mxx * myy;
+          }
+        const float fx = sx / (float)np, fy = sy / (float)np;
+        float vxx = 0.0f, vyy = 0.0f, vxy = 0.0f, rx = 0.0f, ry = 0.0f;
+        for (int i = 0; i < wz; ++i)
+          for (int j = 0; j < w; ++j) {
+            const int z = w0 * sp + i, y = w1 * sp + j;
+            const float* src = xb + z * a.st0 + y * a.st1 + w2 * sp;
+            const float* rec = S + (z * n1 + y) * n2 + w2 * sp;
+            for (int k = 0; k < w; ++k) {
+              const float dx = __fsub_rn(src[k], fx), dy = __fsub_rn(rec[k], fy);
+              rx = __fadd_rn(rx, dx);
+              ry = __fadd_rn(ry, dy);
+              vxx = __fadd_rn(vxx, __fmul_rn(dx, dx));
+              vyy = __fadd_rn(vyy, __fmul_rn(dy, dy));
+              vxy = __fadd_rn(vxy, __fmul_rn(dx, dy));
+            }
+          }
+        // exact-in-exact-arithmetic corrections for the rounded means
+        const double mxx = (double)fx + (double)rx / np, myy = (double)fy + (double)ry / np;
+        const double ex = (double)rx / np, ey = (double)ry / np;
+        const double vx = (double)vxx / np - ex * ex, vy = (double)vyy / np - ey * ey;
+        const double cxy = (double)vxy / np - ex * ey;
         ss += ((2.0 * mxx * myy + a.c1) * (2.0 * cxy + a.c2)) /
               ((mxx * mxx + myy * myy + a.c1) * (vx + vy + a.c2));
         sn += 1.0;
@@ -206,25 +253,21 @@ __global__ void __launch_bounds__(kTrialThreads, 1) trial_kernel(const TrialArgs
       if (SH[i]) atomicAdd(&a.hist[(size_t)cand * 65536 + kTHistLo + i], SH[i]);
   }
   // fixed-order block reduction
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double v[6] = {warp_sum(l1), warp_sum(l1n), warp_sum(unp), warp_sum(sse), warp_max(mx),
-                 warp_sum(ss)};
-  const double snw = warp_sum(sn);
+  const double v[7] = {warp_sum(l1.value()), warp_sum((double)l1n), warp_sum((double)unp),
+                       warp_sum(sse.value()), warp_max((double)mx), warp_sum(ss), warp_sum(sn)};
   if (lane == 0)
-    for (int k = 0; k < 6; ++k) red[wid][k] = v[k];
-  __shared__ double sn_red[kTrialThreads / 32];
-  if (lane == 0) sn_red[wid] = snw;
+    for (int k = 0; k < 7; ++k) red[warp][k] = v[k];
   __syncthreads();
   if (threadIdx.x == 0) {
     double t[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) {
+    for (int wv = 0; wv < nw; ++wv) {
       t[0] += red[wv][0];
       t[1] += red[wv][1];
       t[2] += red[wv][2];
       t[3] += red[wv][3];
       if (red[wv][4] != red[wv][4] || red[wv][4] > t[4]) t[4] = red[wv][4];
       t[5] += red[wv][5];
-      t[6] += sn_red[wv];
+      t[6] += red[wv][6];
     }
     double* o = a.out + ((size_t)cand * a.nblocks + blk) * kOutStride;
     for (int k = 0; k < 7; ++k) o[k] = t[k];
@@ -381,8 +424,10 @@ class Tuner {
     a.is3d = r_.ndims == 3;
     a.c1 = (0.01 * vr_) * (0.01 * vr_);
     a.c2 = (0.03 * vr_) * (0.03 * vr_);
-    const int npb = sm_.bd[0] * sm_.bd[1] * sm_.bd[2];
-    const size_t smem = ((sizeof(float) * npb + 15) & ~size_t(15)) + sizeof(unsigned) * kTHistWin;
+    const int f = 1 << (stop_level - 1);
+    const int npb = ((sm_.bd[0] - 1) / f + 1) * ((sm_.bd[1] - 1) / f + 1) * ((sm_.bd[2] - 1) / f + 1);
+    const size_t smem = ((sizeof(float) * npb + 15) & ~size_t(15)) +
+                        (full ? sizeof(unsigned) * kTHistWin : 0);
     if (smem > 220 * 1024) return fail(QOZ_EUNSUPPORTED, "sample block too large (%d points)", npb);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute((const void*)trial_kernel,
