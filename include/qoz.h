@@ -93,6 +93,28 @@ typedef struct {
 qoz_status qoz_value_range(const float* d_x, int64_t n, float* h_min, float* h_max,
                            int64_t* h_count, void* stream);
 
+/* Value range without any allocation, for callers that cannot allocate
+ * device memory: code running where cudaMalloc is unavailable or forbidden
+ * (inside a host-side memory budget, a pre-planned arena, or a capture that
+ * must not add allocations).  The per-CTA partial results live in a
+ * library-owned static device array, about 10 KB, that every GPU which
+ * loads the library holds until the process exits; the caller passes only
+ * the input and the outputs.
+ *   d_minmax: device, 2 floats: min and max of the finite values of
+ *             d_x[0..n) (both 0 when there is none);
+ *   d_count:  device, 1 int64: number of finite values (may be NULL).
+ * n must not exceed QOZ_NOALLOC_MAX_VALUES (QOZ_EUNSUPPORTED otherwise).
+ * Asynchronous on `stream`; calls no cudaMalloc, cudaFree or other
+ * allocating routine.  The first call on a device looks up the scratch
+ * array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the one array, which keeps the
+ * last call's contents: calls whose work overlaps on the GPU (different
+ * streams, or several host threads) race and must be serialised by the
+ * caller.  The paper has no counterpart to this entry point. */
+#define QOZ_NOALLOC_MAX_VALUES ((int64_t)1 << 40)
+qoz_status qoz_value_range_noalloc(const float* d_x, int64_t n, float* d_minmax, int64_t* d_count,
+                                   void* stream);
+
 /* Compress (Sec. 5): value range, anchors (Sec. 5.2.1), then levels L..1 of
  * the interpolation predictor with level-wise bounds (Eq. ebl), each level's
  * dimension passes predicting from reconstructed values and quantizing

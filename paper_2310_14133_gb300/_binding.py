@@ -126,6 +126,7 @@ def lib():
         sig = {
             "qoz_last_error": (C.c_char_p, []),
             "qoz_value_range": (i32, [P, i64, P, P, P, P]),
+            "qoz_value_range_noalloc": (i32, [P, i64, P, P, P]),
             "qoz_compress": (i32, [P, Shape, f64, P, P, P, P]),
             "qoz_compress_abs": (i32, [P, Shape, f64, P, P, P, P]),
             "qoz_decompress": (i32, [P, P, P]),

@@ -9,7 +9,10 @@
 #include <cuda_runtime.h>
 
 #include <cfloat>
+#include <mutex>
 
+#include "../../include/qoz.h"
+#include "qoz_host.h"
 #include "qoz_internal.h"
 
 namespace qoz {
@@ -196,3 +199,113 @@ cudaError_t launch_bound_table(const float* pmin, const float* pmax,
 }
 
 }  // namespace qoz
+
+// ---------------------------------------------------------------------------
+// Value range with library-owned scratch in a static device array, for
+// callers that must not allocate device memory themselves (see
+// qoz_value_range_noalloc in qoz.h).
+
+namespace qoz {
+namespace {
+
+constexpr int kNoAllocParts = kRangeBlocks + 1;
+
+// Partial (min, max, count) of every CTA of one call; shared by all calls on
+// a device, so calls whose work overlaps on the GPU race.
+struct RangeScratch {
+  float pmin[kNoAllocParts];
+  float pmax[kNoAllocParts];
+  unsigned long long pcnt[kNoAllocParts];
+};
+__device__ __align__(256) RangeScratch g_range_scratch;
+
+// Folds the partials into the caller's outputs: {min, max} and the count of
+// finite values (0, 0 and 0 when there is none).
+__global__ void __launch_bounds__(kTableThreads)
+    range_fold_kernel(const RangeScratch* sc, int nparts, float* out_minmax,
+                      long long* out_count) {
+  float mn = FLT_MAX, mx = -FLT_MAX;
+  unsigned long long c = 0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+    if (sc->pcnt[i] == 0) continue;
+    mn = fminf(mn, sc->pmin[i]);
+    mx = fmaxf(mx, sc->pmax[i]);
+    c += sc->pcnt[i];
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    c += __shfl_xor_sync(0xffffffffu, c, off);
+  }
+  __shared__ float smn[32], smx[32];
+  __shared__ unsigned long long sc_[32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    smn[w] = mn;
+    smx[w] = mx;
+    sc_[w] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  mn = FLT_MAX;
+  mx = -FLT_MAX;
+  c = 0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+    mn = fminf(mn, smn[i]);
+    mx = fmaxf(mx, smx[i]);
+    c += sc_[i];
+  }
+  if (c == 0) {
+    mn = 0.0f;
+    mx = 0.0f;
+  }
+  out_minmax[0] = mn;
+  out_minmax[1] = mx;
+  if (out_count) *out_count = (long long)c;
+}
+
+std::mutex g_scratch_mu;
+RangeScratch* g_scratch_ptr[64] = {nullptr};
+
+}  // namespace
+}  // namespace qoz
+
+extern "C" qoz_status qoz_value_range_noalloc(const float* d_x, int64_t n, float* d_minmax,
+                                              int64_t* d_count, void* stream) {
+  using namespace qoz;
+  if (!d_x || !d_minmax || n < 0) return fail(QOZ_EINVAL, "invalid argument");
+  if (n > QOZ_NOALLOC_MAX_VALUES)
+    return fail(QOZ_EUNSUPPORTED, "qoz_value_range_noalloc: %lld values exceed the maximum of "
+                "%lld", (long long)n, (long long)QOZ_NOALLOC_MAX_VALUES);
+  if (reinterpret_cast<uintptr_t>(d_x) & 3) return fail(QOZ_EINVAL, "d_x must be 4-byte aligned");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 64) return fail(QOZ_EUNSUPPORTED, "device ordinal %d", dev);
+  RangeScratch* sc;
+  {
+    // once per device, with that device current: the device address of the
+    // static scratch (its host-side name is not a device address)
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_range_scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+      g_scratch_ptr[dev] = static_cast<RangeScratch*>(p);
+    }
+    sc = g_scratch_ptr[dev];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  // every partial slot the fold reads is written by this call (the range
+  // pass zeroes the counts of the CTAs it does not launch)
+  e = launch_check(launch_range(d_x, n, sc->pmin, sc->pmax, sc->pcnt, s));
+  if (e == cudaErrorMisalignedAddress) return fail(QOZ_EINVAL, "misaligned input");
+  if (e == cudaSuccess) {
+    range_fold_kernel<<<1, kTableThreads, 0, s>>>(sc, kNoAllocParts, d_minmax,
+                                                  reinterpret_cast<long long*>(d_count));
+    note_launch(1);
+    e = launch_check(cudaGetLastError());
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "value range (no allocation)");
+  return QOZ_OK;
+}
