@@ -150,15 +150,6 @@ void grid_dims(const Resolved& r, int k, long long g[3]) {
   for (int p = 0; p < 3; ++p) g[p] = ceil_div(r.n[p], 1LL << k);
 }
 
-// Compact per-grid scratch of the hierarchy: for k = 1..L-1 the
-// reconstruction (float) and, when compressing, the codes (uint16) of the
-// field subsampled by 2^k.
-struct Coarse {
-  size_t roff[QOZ_MAX_LEVELS + 1];
-  size_t coff[QOZ_MAX_LEVELS + 1];
-  size_t bytes;
-};
-
 Coarse coarse_layout(const Resolved& r, bool with_codes) {
   Coarse c;
   memset(&c, 0, sizeof(c));
@@ -546,7 +537,7 @@ qoz_status qoz_compute_metrics(const float* d_a, const float* d_b, qoz_shape sha
   cudaStream_t s = (cudaStream_t)stream;
   configure_pool_once();
   const int ne = err_metric_blocks();
-  const int ns = ssim_blocks();
+  const int ns = ssim_win > 0 ? ssim_parts(r.n, r.ndims == 3, ssim_win, ssim_step) : 0;
   void* scratch = nullptr;
   cudaError_t e = dev_alloc(&scratch, sizeof(double) * (2 * ne + ns), s);
   if (e != cudaSuccess) return fail(QOZ_ENOMEM, "metrics scratch: %s", cudaGetErrorString(e));
@@ -558,10 +549,10 @@ qoz_status qoz_compute_metrics(const float* d_a, const float* d_b, qoz_shape sha
   const double c2 = (0.03 * vrange) * (0.03 * vrange);
   if (e == cudaSuccess && ssim_win > 0)
     e = launch_check(launch_ssim(d_a, d_b, r.n, r.ndims == 3, ssim_win, ssim_step, c1, c2, pss,
-                                 ns, s));
+                                 s));
   std::vector<double> h(2 * ne + ns, 0.0);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(h.data(), scratch, sizeof(double) * (ssim_win > 0 ? 2 * ne + ns : 2 * ne),
+    e = cudaMemcpyAsync(h.data(), scratch, sizeof(double) * (2 * ne + ns),
                         cudaMemcpyDeviceToHost, s);
   dev_free(scratch, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -584,7 +575,7 @@ qoz_status qoz_compute_metrics(const float* d_a, const float* d_b, qoz_shape sha
     double ss = 0.0;
     for (int i = 0; i < ns; ++i) ss += h[2 * ne + i];
     out->ssim_windows = nw;
-    out->ssim = nw > 0 ? ss / (double)nw : NAN;
+    out->ssim = nw > 0 ? 1.0 - ss / (double)nw : NAN;  // parts hold sums of 1 - SSIM_w
   }
   return QOZ_OK;
 }
