@@ -122,7 +122,7 @@ def _peak_hbm():
 
 def _kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("qoz_level.cu", "qoz_device.cuh", "qoz_internal.h"):
+    for f in ("qoz_level_impl.cuh", "qoz_level.cu", "qoz_device.cuh", "qoz_internal.h"):
         with open(os.path.join(ROOT, "paper_2310_14133_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -168,6 +168,58 @@ void qoz_blob_free(qoz_blob* b);
 
 const char* qoz_last_error(void);
 
+/* ---------------------------------------------------------------- batches
+ * Compression of many fields together (the same method as qoz_compress on
+ * each field: Sec. 5.1 predictor, Sec. 5.2.1 anchors, Eq. ebl bounds).  A
+ * plan fixes the fields' shapes and parameters; every run then issues each
+ * level of all fields as one launch per kernel instance (fields sharing a
+ * level's order and dimensionality share the launch), so the small coarse
+ * levels of many fields fill the GPU together, and after the first run the
+ * whole device sequence replays as one CUDA graph.  Each field's blob holds
+ * exactly what qoz_compress / qoz_compress_abs would produce for it. */
+typedef struct qoz_batch qoz_batch;     /* opaque plan; owns device scratch */
+
+#define QOZ_BATCH_AUTOTUNE 1u   /* time the tile variants of the level-1 launches on the first run */
+#define QOZ_BATCH_NO_GRAPH 2u   /* issue the launches directly on every run (no CUDA graph) */
+
+/* shapes: nfields entries; params: nfields entries or NULL (defaults as in
+ * qoz_compress).  Allocates the plan's device scratch on the current device
+ * (synchronous).  Errors: QOZ_EINVAL for a bad shape, parameter or count
+ * (1 <= nfields <= 4096), QOZ_ENOMEM. */
+qoz_status qoz_batch_create(const qoz_shape* shapes, int32_t nfields, const qoz_params* params,
+                            uint32_t flags, qoz_batch** out);
+
+/* Compresses d_fields[i] (device, 4-byte aligned, the plan's shape i) with
+ * bound eb[i]: relative to the field's value range when eb_relative != 0
+ * (eb > 0), absolute otherwise (eb >= 0).  outs[i] receive blobs allocated
+ * stream-ordered on `stream` (free each with qoz_blob_free).  Synchronises
+ * `stream` once.  A plan serves one run at a time: calls on one plan must not
+ * overlap. */
+qoz_status qoz_batch_compress(qoz_batch* plan, const float* const* d_fields, const double* eb,
+                              int32_t eb_relative, void* stream, qoz_blob** outs);
+
+typedef struct {
+  int32_t nfields;
+  int32_t n_groups;            /* batched level launches per run */
+  int32_t launches_per_run;    /* kernel launches per run (all kernels of the sequence) */
+  int32_t graph;               /* 1 once the run sequence is a CUDA graph */
+  int32_t autotuned;           /* 1 once the tile variants were timed */
+  int32_t level1_groups;       /* number of level-1 launches */
+  int32_t level1_variant[16];  /* tile variant chosen for each (first 16) */
+  double level1_ms[16][2];     /* timed duration of each variant (autotune), else 0 */
+  int64_t ctas_per_run;        /* CTAs of all batched level launches */
+} qoz_batch_info;
+qoz_status qoz_batch_get_info(const qoz_batch* plan, qoz_batch_info* info);
+
+/* Releases the plan (synchronises the device first). */
+void qoz_batch_free(qoz_batch* plan);
+
+/* One-shot convenience: plan, run with the same relative bound for every
+ * field, release. */
+qoz_status qoz_compress_batch(const float* const* d_fields, const qoz_shape* shapes,
+                              int32_t nfields, double rel_eb, const qoz_params* params,
+                              void* stream, qoz_blob** outs);
+
 /* ---------------------------------------------------------------- metrics */
 
 typedef struct {

@@ -15,11 +15,16 @@ from ._binding import (  # noqa: F401
     STAGE_LEVEL,
     STAGE_RANGE,
     STAGE_SETUP,
+    BATCH_AUTOTUNE,
+    BATCH_NO_GRAPH,
+    Batch,
+    BatchInfo,
     Blob,
     QozError,
     Shape,
     compress,
     compress_abs,
+    compress_batch,
     compute_metrics,
     decompress,
     deserialize,

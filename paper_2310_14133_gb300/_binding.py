@@ -141,6 +141,11 @@ def lib():
             "qoz_profile_enable": (i32, [i32]),
             "qoz_tune": (i32, [P, Shape, f64, i32, f64, P, P, P]),
             "qoz_profile_read": (i32, [P, i32]),
+            "qoz_batch_create": (i32, [P, i32, P, C.c_uint32, P]),
+            "qoz_batch_compress": (i32, [P, P, P, i32, P, P]),
+            "qoz_batch_get_info": (i32, [P, P]),
+            "qoz_batch_free": (None, [P]),
+            "qoz_compress_batch": (i32, [P, P, i32, f64, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -168,6 +173,16 @@ def _shape_of(t: torch.Tensor) -> Shape:
     s = Shape()
     s.ndims = t.dim()
     for i, d in enumerate(t.shape):
+        s.dims[i] = int(d)
+    return s
+
+
+def _shape_tuple(dims) -> Shape:
+    if len(dims) not in (2, 3):
+        raise QozError(1, f"fields must be 2D or 3D (got {len(dims)} dimensions)")
+    s = Shape()
+    s.ndims = len(dims)
+    for i, d in enumerate(dims):
         s.dims[i] = int(d)
     return s
 
@@ -312,3 +327,84 @@ def compute_metrics(a: torch.Tensor, b: torch.Tensor, vrange: float, ssim_win: i
     _check(lib().qoz_compute_metrics(_dev_ptr(a), _dev_ptr(b), _shape_of(a), float(vrange),
                                      int(ssim_win), int(ssim_step), C.byref(m), _stream(stream)))
     return m
+
+
+BATCH_AUTOTUNE = 1
+BATCH_NO_GRAPH = 2
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("nfields", C.c_int32), ("n_groups", C.c_int32),
+                ("launches_per_run", C.c_int32), ("graph", C.c_int32),
+                ("autotuned", C.c_int32), ("level1_groups", C.c_int32),
+                ("level1_variant", C.c_int32 * 16), ("level1_ms", (C.c_double * 2) * 16),
+                ("ctas_per_run", C.c_int64)]
+
+
+def _params_array(params, shapes):
+    if params is None:
+        return None
+    if isinstance(params, Params):
+        params = [params] * len(shapes)
+    if len(params) != len(shapes):
+        raise ValueError("one Params per field")
+    return (Params * len(shapes))(*params)
+
+
+class Batch:
+    """A batched-compression plan for a fixed list of field shapes."""
+
+    def __init__(self, shapes, params=None, autotune: bool = False, graph: bool = True):
+        self.shapes = [tuple(int(d) for d in s) for s in shapes]
+        arr = (Shape * len(self.shapes))(*[_shape_tuple(s) for s in self.shapes])
+        self._params = _params_array(params, self.shapes)
+        flags = (BATCH_AUTOTUNE if autotune else 0) | (0 if graph else BATCH_NO_GRAPH)
+        h = C.c_void_p()
+        _check(lib().qoz_batch_create(arr, len(self.shapes), self._params, flags, C.byref(h)))
+        self._h = h
+
+    def compress(self, fields, eb, relative: bool = True, stream=None):
+        """Blobs of the fields (CUDA float32 tensors of the plan's shapes);
+        eb: one bound or one per field."""
+        n = len(self.shapes)
+        if len(fields) != n:
+            raise ValueError("one field per plan shape")
+        for f, s in zip(fields, self.shapes):
+            if tuple(f.shape) != s:
+                raise ValueError(f"field shape {tuple(f.shape)} != plan shape {s}")
+        ptrs = (C.c_void_p * n)(*[_dev_ptr(f).value for f in fields])
+        ebs = [float(eb)] * n if isinstance(eb, (int, float)) else [float(v) for v in eb]
+        eba = (C.c_double * n)(*ebs)
+        outs = (C.c_void_p * n)()
+        _check(lib().qoz_batch_compress(self._h, ptrs, eba, 1 if relative else 0,
+                                        _stream(stream), outs))
+        return [Blob(C.c_void_p(outs[i]), self.shapes[i]) for i in range(n)]
+
+    def info(self) -> BatchInfo:
+        inf = BatchInfo()
+        _check(lib().qoz_batch_get_info(self._h, C.byref(inf)))
+        return inf
+
+    def free(self):
+        if self._h:
+            lib().qoz_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def compress_batch(fields, rel_eb: float, params=None, stream=None):
+    """One-shot batched compression with one relative bound."""
+    shapes = [tuple(f.shape) for f in fields]
+    n = len(fields)
+    arr = (Shape * n)(*[_shape_tuple(s) for s in shapes])
+    ptrs = (C.c_void_p * n)(*[_dev_ptr(f).value for f in fields])
+    outs = (C.c_void_p * n)()
+    _check(lib().qoz_compress_batch(ptrs, arr, n, float(rel_eb), _params_array(params, shapes),
+                                    _stream(stream), outs))
+    return [Blob(C.c_void_p(outs[i]), shapes[i]) for i in range(n)]
+

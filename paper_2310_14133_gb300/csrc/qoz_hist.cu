@@ -73,8 +73,9 @@ __global__ void hist_remove_anchors(unsigned* hist, long long n_anchors) {
 
 constexpr int kSmemSort = 2048;
 
-__global__ void __launch_bounds__(1024) sort_small_kernel(long long* idx, float* val,
-                                                          long long n) {
+// Bitonic sort of n <= kSmemSort pairs by one block of 1024 threads, in
+// shared memory (padding keys are the largest index).
+__device__ __forceinline__ void sort_small_block(long long* idx, float* val, long long n) {
   __shared__ long long k[kSmemSort];
   __shared__ float v[kSmemSort];
   int P = 1;
@@ -107,6 +108,39 @@ __global__ void __launch_bounds__(1024) sort_small_kernel(long long* idx, float*
     idx[i] = k[i];
     val[i] = v[i];
   }
+}
+
+__global__ void __launch_bounds__(1024) sort_small_kernel(long long* idx, float* val,
+                                                          long long n) {
+  sort_small_block(idx, val, n);
+}
+
+// Batched compression, before the levels: zero each field's histogram (grid
+// y = field), list counter and flags.
+__global__ void __launch_bounds__(1024) batch_init_kernel(const BatchFieldDesc* __restrict__ d) {
+  const BatchFieldDesc& f = d[blockIdx.y];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 65536; i += gridDim.x * blockDim.x)
+    f.hist[i] = 0u;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *f.ul.count = 0ull;
+    *f.err = 0;
+    *f.host_sort = 0;
+  }
+}
+
+// Batched compression, after the levels: one block per field takes the
+// anchors out of bin 0 and sorts a list of at most kSmemSort entries; longer
+// lists are flagged for a sort driven from the host.
+__global__ void __launch_bounds__(1024) batch_finish_kernel(const BatchFieldDesc* __restrict__ d) {
+  const BatchFieldDesc& f = d[blockIdx.x];
+  if (threadIdx.x == 0) f.hist[0] -= (unsigned)(f.na[0] * f.na[1] * f.na[2]);
+  const long long cnt = (long long)*f.ul.count;  // same value in every thread
+  if (cnt <= 1) return;
+  if (cnt > f.ul.cap || cnt > kSmemSort) {
+    if (threadIdx.x == 0) *f.host_sort = 1;
+    return;
+  }
+  sort_small_block(f.ul.idx, f.ul.val, cnt);
 }
 
 __global__ void sort_fill_kernel(const long long* idx, const float* val, long long n,
@@ -196,6 +230,20 @@ cudaError_t launch_sort_pairs(long long* idx, float* val, long long n, long long
     }
   }
   sort_back_kernel<<<blocks, threads, 0, s>>>(tmp_idx, tmp_val, n, idx, val); note_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_init(const BatchFieldDesc* d, int nfields, cudaStream_t s) {
+  if (nfields <= 0) return cudaSuccess;
+  batch_init_kernel<<<dim3(16, nfields), 1024, 0, s>>>(d);
+  note_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_finish(const BatchFieldDesc* d, int nfields, cudaStream_t s) {
+  if (nfields <= 0) return cudaSuccess;
+  batch_finish_kernel<<<nfields, 1024, 0, s>>>(d);
+  note_launch(1);
   return cudaGetLastError();
 }
 

@@ -52,6 +52,26 @@ void dev_free(void* p, cudaStream_t s);
 cudaError_t launch_check(cudaError_t e);
 void configure_pool_once();
 
+struct LevelLaunch;
+
+// Compact per-grid scratch of the hierarchy: for k = 1..L-1 the
+// reconstruction (float) and, when compressing, the codes (uint16) of the
+// field subsampled by 2^k.
+struct Coarse {
+  size_t roff[QOZ_MAX_LEVELS + 1];
+  size_t coff[QOZ_MAX_LEVELS + 1];
+  size_t bytes;
+};
+
+// Geometry helpers of the level hierarchy (qoz_api.cu).
+void grid_dims(const Resolved& r, int k, long long g[3]);
+Coarse coarse_layout(const Resolved& r, bool with_codes);
+long long anchor_dims(const Resolved& r, long long na[3]);
+void level_geometry(const Resolved& r, int l, LevelLaunch* L);
+// Single-field compression behind qoz_compress / qoz_compress_abs.
+qoz_status compress_impl(const float* d_field, const qoz_shape& shape, bool rel, double eb,
+                         const qoz_params* p, float* d_recon, cudaStream_t s, qoz_blob** out);
+
 // Adds n to the library's kernel-launch counter.
 void note_launch(int n);
 

@@ -44,6 +44,38 @@ struct LevelLaunch {
 
 // Launch wrappers (qoz_level.cu)
 cudaError_t launch_level(const LevelLaunch& L, cudaStream_t s);
+// Sets the opt-in dynamic shared-memory size of a kernel once per device.
+cudaError_t ensure_smem_attr(const void* fn, unsigned long long* done_mask, size_t bytes);
+
+// Batched level launches (qoz_level_batch.cu).  One launch runs the same
+// level of many fields that share a kernel instance: the items are those
+// fields' LevelLaunch descriptors in device memory, and a per-CTA map names
+// the item each CTA works on; the CTA's tile is its index minus the item's
+// first CTA.  Only compression is batched.
+struct LevelItem {
+  LevelLaunch L;
+  int nt1, nt2;         // tiles along y and x
+  int vec;              // 16-byte row copies allowed (set per call: depends on x)
+  unsigned tile_begin;  // first CTA of this item in its launch
+};
+// Kernel instance of a batched launch: 2-D or 3-D, the level's order, whether
+// the launch accumulates the histogram (level 1), and the tile variant.
+struct LevelKey {
+  bool is2d;
+  int order3;
+  bool hist;
+  int variant;
+};
+constexpr int kLevelVariants = 2;
+// Tile extent (z, y, x) of a key's kernel instance.
+void level_tile_shape(const LevelKey& k, int t[3]);
+// Tiles of one item under the key's tile shape (nt[0] * nt[1] * nt[2]).
+long long level_item_tiles(const LevelKey& k, const LevelLaunch& L, long long nt[3]);
+// Prepares the kernel instance (shared-memory attribute); call before any
+// stream capture.
+cudaError_t level_batch_prepare(const LevelKey& k);
+cudaError_t launch_level_batch(const LevelKey& k, const LevelItem* d_items,
+                               const uint16_t* d_map, unsigned nblocks, cudaStream_t s);
 cudaError_t launch_anchor_gather(const float* x, float* anchors, const long long na[3],
                                  const long long fst[3], long long stride, cudaStream_t s);
 
@@ -55,6 +87,46 @@ cudaError_t launch_bound_table(const float* pmin, const float* pmax,
                                const unsigned long long* pcnt, int nparts, int use_range,
                                double eb, double alpha, double beta, int L, BoundTable* bt,
                                cudaStream_t s);
+
+// Per-field descriptor of a batched compression (device memory, rewritten
+// before each run because the field pointers and outputs change per call).
+struct BatchFieldDesc {
+  const float* x;
+  long long n;             // points
+  int chunk_begin, nchunks;  // this field's value-range chunks
+  int use_range, L;
+  double eb, alpha, beta;  // bound (relative when use_range), Eq. (ebl) parameters
+  BoundTable* bt;
+  float* anchors;
+  long long na[3];
+  long long fst0, fst1, stride;
+  unsigned* hist;
+  UnpredList ul;
+  int* err;
+  int* host_sort;          // out: 1 when the list was left for a host-driven sort
+};
+// A contiguous piece [begin, end) of one field for the value range.
+struct RangeChunk {
+  int field;
+  int pad;
+  long long begin, end;
+};
+constexpr long long kRangeChunk = 1LL << 20;
+
+// Batched value range (qoz_range.cu): one CTA per chunk, then one CTA per
+// field folds its chunks into the field's bound table (Eq. ebl).
+cudaError_t launch_range_batch(const BatchFieldDesc* d, const RangeChunk* chunks, int nchunks,
+                               float* pmin, float* pmax, unsigned long long* pcnt,
+                               cudaStream_t s);
+cudaError_t launch_bound_batch(const BatchFieldDesc* d, int nfields, const float* pmin,
+                               const float* pmax, const unsigned long long* pcnt, cudaStream_t s);
+// Batched setup and finish (qoz_hist.cu): zero each field's histogram,
+// counter and flags; afterwards take the anchors out of bin 0 and sort each
+// short unpredictable list by index on the device.
+cudaError_t launch_batch_init(const BatchFieldDesc* d, int nfields, cudaStream_t s);
+cudaError_t launch_batch_finish(const BatchFieldDesc* d, int nfields, cudaStream_t s);
+// Batched anchor gather (qoz_level.cu).
+cudaError_t launch_anchor_batch(const BatchFieldDesc* d, int nfields, cudaStream_t s);
 
 // Histogram and unpredictable ordering (qoz_hist.cu)
 cudaError_t launch_histogram(const uint16_t* codes, long long n, unsigned* hist,
@@ -68,9 +140,10 @@ size_t sort_pairs_scratch(long long n);
 cudaError_t launch_err_metrics(const float* a, const float* b, long long n, double* part_sse,
                                double* part_max, int nparts, cudaStream_t s);
 int err_metric_blocks();
+// SSIM partial sums of (1 - SSIM_w), one per part; ssim_parts() gives the count.
 cudaError_t launch_ssim(const float* a, const float* b, const long long dims[3], bool is3d,
-                        int win, int step, double c1, double c2, double* part_sum, int nparts,
+                        int win, int step, double c1, double c2, double* part_diss,
                         cudaStream_t s);
-int ssim_blocks();
+int ssim_parts(const long long dims[3], bool is3d, int win, int step);
 
 }  // namespace qoz

@@ -1,0 +1,100 @@
+// Batched level launches: one launch runs one level of many fields (Sec. 5.1
+// predictor, Sec. 5.2.2 level-wise bounds) whose kernel instance is the same.
+// Each CTA reads its item from the per-CTA map, copies the item's descriptor
+// into shared memory and runs the same tile code as the single-field launch,
+// so every field's codes, reconstruction, list and histogram are those of a
+// single-field compression.  Two tile shapes per instance are compiled; the
+// batch plan times them on its first run and keeps the faster.
+#include "qoz_level_impl.cuh"
+
+namespace qoz {
+namespace {
+
+template <int A0, int A1, int A2, int TZ, int TY, int TX, bool HIST>
+__global__ void __launch_bounds__(kThreads, 2)
+    level_batch_kernel(const LevelItem* __restrict__ items, const uint16_t* __restrict__ map) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(16) LevelItem it;
+  static_assert(sizeof(LevelItem) % 4 == 0 && sizeof(LevelItem) / 4 <= kThreads, "item copy");
+  if (threadIdx.x < sizeof(LevelItem) / 4) {
+    const unsigned k = map[blockIdx.x];
+    reinterpret_cast<unsigned*>(&it)[threadIdx.x] =
+        reinterpret_cast<const unsigned*>(items + k)[threadIdx.x];
+  }
+  __syncthreads();
+  level_tile<A0, A1, A2, TZ, TY, TX, false, HIST>(it.L, smem, (int)(blockIdx.x - it.tile_begin),
+                                                  it.nt1, it.nt2, it.vec);
+}
+
+struct Info {
+  const void* fn;
+  size_t smem;
+  int t[3];
+  unsigned long long* done;
+};
+
+template <int A0, int A1, int A2, int TZ, int TY, int TX, bool HIST>
+Info info_of() {
+  using G = Geo<A0, A1, A2, TZ, TY, TX>;
+  static unsigned long long done = 0;
+  constexpr size_t smem = G::smem_bytes(false, HIST);
+  static_assert(smem + sizeof(LevelItem) <= 112 * 1024, "two CTAs per SM");
+  return Info{(const void*)level_batch_kernel<A0, A1, A2, TZ, TY, TX, HIST>, smem, {TZ, TY, TX},
+              &done};
+}
+
+// Tile shapes: variant 0 is the single-field launch's shape; variant 1
+// trades halo along one axis for extent along another.
+template <bool HIST>
+Info info_h(int is2d, int order3, int v) {
+  if (is2d) {
+    if (order3 == 0)
+      return v ? info_of<0, 1, 2, 1, 64, 128, HIST>() : info_of<0, 1, 2, 1, 32, 128, HIST>();
+    return v ? info_of<0, 2, 1, 1, 64, 128, HIST>() : info_of<0, 2, 1, 1, 32, 128, HIST>();
+  }
+  switch (order3) {
+    case 0: return v ? info_of<0, 1, 2, 4, 32, 64, HIST>() : info_of<0, 1, 2, 8, 16, 64, HIST>();
+    case 1: return v ? info_of<0, 2, 1, 4, 32, 64, HIST>() : info_of<0, 2, 1, 8, 16, 64, HIST>();
+    case 2: return v ? info_of<1, 0, 2, 32, 4, 64, HIST>() : info_of<1, 0, 2, 16, 8, 64, HIST>();
+    case 3: return v ? info_of<1, 2, 0, 32, 4, 64, HIST>() : info_of<1, 2, 0, 16, 8, 64, HIST>();
+    case 4: return v ? info_of<2, 0, 1, 12, 12, 48, HIST>() : info_of<2, 0, 1, 12, 16, 32, HIST>();
+    default:
+      return v ? info_of<2, 1, 0, 12, 12, 48, HIST>() : info_of<2, 1, 0, 12, 16, 32, HIST>();
+  }
+}
+
+Info get_info(const LevelKey& k) {
+  const int v = k.variant ? 1 : 0;
+  return k.hist ? info_h<true>(k.is2d, k.order3, v) : info_h<false>(k.is2d, k.order3, v);
+}
+
+}  // namespace
+
+void level_tile_shape(const LevelKey& k, int t[3]) {
+  const Info in = get_info(k);
+  for (int i = 0; i < 3; ++i) t[i] = in.t[i];
+}
+
+long long level_item_tiles(const LevelKey& k, const LevelLaunch& L, long long nt[3]) {
+  int t[3];
+  level_tile_shape(k, t);
+  for (int i = 0; i < 3; ++i) nt[i] = L.g[i] > 0 ? (L.g[i] + t[i] - 1) / t[i] : 0;
+  return nt[0] * nt[1] * nt[2];
+}
+
+cudaError_t level_batch_prepare(const LevelKey& k) {
+  const Info in = get_info(k);
+  return ensure_smem_attr(in.fn, in.done, in.smem);
+}
+
+cudaError_t launch_level_batch(const LevelKey& k, const LevelItem* d_items, const uint16_t* d_map,
+                               unsigned nblocks, cudaStream_t s) {
+  if (nblocks == 0) return cudaSuccess;
+  const Info in = get_info(k);
+  void* args[] = {(void*)&d_items, (void*)&d_map};
+  cudaError_t e = cudaLaunchKernel(in.fn, dim3(nblocks), dim3(kThreads), args, in.smem, s);
+  note_launch(1);
+  return e;
+}
+
+}  // namespace qoz

@@ -94,6 +94,37 @@ __global__ void range_head_kernel(const float* __restrict__ x, int nhead, float*
   *pcnt = c;
 }
 
+// The bound table from the folded range: e = eb * vrange (relative) or eb,
+// then Eq. (ebl): e_l = e / min(alpha^(l-1), beta), alpha^(l-1) by repeated
+// multiplication in double; each entry rounded to binary32 once.
+__device__ void fill_bound_table(float mn, float mx, unsigned long long c, int use_range,
+                                 double eb, double alpha, double beta, int L, BoundTable* bt) {
+  if (c == 0) {
+    mn = 0.0f;
+    mx = 0.0f;
+  }
+  BoundTable t;
+  t.vmin = mn;
+  t.vmax = mx;
+  t.n_finite = (long long)c;
+  t.vrange = (double)mx - (double)mn;
+  t.e = use_range ? eb * t.vrange : eb;
+  double a = 1.0;
+  for (int l = 0; l < kMaxLevels; ++l) {
+    if (l < L) {
+      const double den = a < beta ? a : beta;
+      const double el = t.e / den;
+      t.el[l] = (float)el;
+      t.two_e[l] = (float)(2.0 * el);
+      t.inv[l] = (float)(1.0 / (2.0 * el));
+      a = a * alpha;
+    } else {
+      t.el[l] = t.two_e[l] = t.inv[l] = 0.0f;
+    }
+  }
+  *bt = t;
+}
+
 // One block folds the per-CTA partials (a tree over the threads), then one
 // thread evaluates Eq. (ebl).
 constexpr int kTableThreads = 1024;
@@ -133,32 +164,90 @@ __global__ void __launch_bounds__(kTableThreads)
     mx = fmaxf(mx, smx[i]);
     c += sc[i];
   }
-  if (c == 0) {
-    mn = 0.0f;
-    mx = 0.0f;
+  fill_bound_table(mn, mx, c, use_range, eb, alpha, beta, L, bt);
+}
+
+// Min / max / count across a block (warp shuffles, then the first warp);
+// the result is valid in thread 0.
+__device__ __forceinline__ void block_fold(float& mn, float& mx, unsigned long long& c) {
+  for (int off = 16; off > 0; off >>= 1) {
+    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    c += __shfl_xor_sync(0xffffffffu, c, off);
   }
-  BoundTable t;
-  t.vmin = mn;
-  t.vmax = mx;
-  t.n_finite = (long long)c;
-  t.vrange = (double)mx - (double)mn;
-  t.e = use_range ? eb * t.vrange : eb;
-  // Eq. (ebl): e_l = e / min(alpha^(l-1), beta), alpha^(l-1) by repeated
-  // multiplication in double; each entry rounded to binary32 once.
-  double a = 1.0;
-  for (int l = 0; l < kMaxLevels; ++l) {
-    if (l < L) {
-      const double den = a < beta ? a : beta;
-      const double el = t.e / den;
-      t.el[l] = (float)el;
-      t.two_e[l] = (float)(2.0 * el);
-      t.inv[l] = (float)(1.0 / (2.0 * el));
-      a = a * alpha;
-    } else {
-      t.el[l] = t.two_e[l] = t.inv[l] = 0.0f;
+  __shared__ float smn[32], smx[32];
+  __shared__ unsigned long long sc[32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    smn[w] = mn;
+    smx[w] = mx;
+    sc[w] = c;
+  }
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    mn = l < nw ? smn[l] : FLT_MAX;
+    mx = l < nw ? smx[l] : -FLT_MAX;
+    c = l < nw ? sc[l] : 0;
+    for (int off = 16; off > 0; off >>= 1) {
+      mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+      c += __shfl_xor_sync(0xffffffffu, c, off);
     }
   }
-  *bt = t;
+}
+
+// One CTA per chunk of one field: 16-byte loads over the chunk's aligned
+// body, scalar head and tail.
+__global__ void __launch_bounds__(kRangeThreads) range_batch_kernel(
+    const BatchFieldDesc* __restrict__ d, const RangeChunk* __restrict__ chunks, float* pmin,
+    float* pmax, unsigned long long* pcnt) {
+  const RangeChunk ch = chunks[blockIdx.x];
+  const float* x = d[ch.field].x;
+  float mn = FLT_MAX, mx = -FLT_MAX;
+  unsigned long long c = 0;
+  const uintptr_t a0 = reinterpret_cast<uintptr_t>(x + ch.begin);
+  long long head = (long long)(((16 - (a0 & 15)) & 15) / 4);
+  if (head > ch.end - ch.begin) head = ch.end - ch.begin;
+  const long long b4 = ch.begin + head;
+  const long long n4 = (ch.end - b4) / 4;
+  const float4* x4 = reinterpret_cast<const float4*>(x + b4);
+  for (long long i = threadIdx.x; i < n4; i += blockDim.x) {
+    const float4 v = __ldcs(x4 + i);
+    fold(v.x, mn, mx, c);
+    fold(v.y, mn, mx, c);
+    fold(v.z, mn, mx, c);
+    fold(v.w, mn, mx, c);
+  }
+  if ((long long)threadIdx.x < head) fold(x[ch.begin + threadIdx.x], mn, mx, c);
+  for (long long i = b4 + 4 * n4 + threadIdx.x; i < ch.end; i += blockDim.x)
+    fold(x[i], mn, mx, c);
+  block_fold(mn, mx, c);
+  if (threadIdx.x == 0) {
+    pmin[blockIdx.x] = mn;
+    pmax[blockIdx.x] = mx;
+    pcnt[blockIdx.x] = c;
+  }
+}
+
+// One CTA per field: fold the field's chunk partials, evaluate Eq. (ebl).
+__global__ void __launch_bounds__(256) bound_batch_kernel(const BatchFieldDesc* __restrict__ d,
+                                                          const float* pmin, const float* pmax,
+                                                          const unsigned long long* pcnt) {
+  const BatchFieldDesc& f = d[blockIdx.x];
+  float mn = FLT_MAX, mx = -FLT_MAX;
+  unsigned long long c = 0;
+  if (f.use_range)
+    for (int i = threadIdx.x; i < f.nchunks; i += blockDim.x) {
+      const int k = f.chunk_begin + i;
+      if (pcnt[k] == 0) continue;
+      mn = fminf(mn, pmin[k]);
+      mx = fmaxf(mx, pmax[k]);
+      c += pcnt[k];
+    }
+  block_fold(mn, mx, c);
+  if (threadIdx.x == 0)
+    fill_bound_table(mn, mx, c, f.use_range, f.eb, f.alpha, f.beta, f.L, f.bt);
 }
 
 }  // namespace
@@ -194,6 +283,23 @@ cudaError_t launch_bound_table(const float* pmin, const float* pmax,
                                cudaStream_t s) {
   bound_table_kernel<<<1, kTableThreads, 0, s>>>(pmin, pmax, pcnt, nparts, use_range, eb, alpha,
                                                   beta, L, bt);
+  note_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_range_batch(const BatchFieldDesc* d, const RangeChunk* chunks, int nchunks,
+                               float* pmin, float* pmax, unsigned long long* pcnt,
+                               cudaStream_t s) {
+  if (nchunks <= 0) return cudaSuccess;
+  range_batch_kernel<<<nchunks, kRangeThreads, 0, s>>>(d, chunks, pmin, pmax, pcnt);
+  note_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bound_batch(const BatchFieldDesc* d, int nfields, const float* pmin,
+                               const float* pmax, const unsigned long long* pcnt, cudaStream_t s) {
+  if (nfields <= 0) return cudaSuccess;
+  bound_batch_kernel<<<nfields, 256, 0, s>>>(d, pmin, pmax, pcnt);
   note_launch(1);
   return cudaGetLastError();
 }
