@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
 baseline leg of the benchmark may import this package; the product path
 (the CUDA library and its binding) never does, and the two share no code.
 
-`build()` compiles qoz_oracle.cpp and qoz_oracle_tune.cpp with
+`build()` compiles qoz_oracle.cpp, qoz_oracle_tune.cpp and qoz_oracle_learn.cpp with
 -O2 -ffp-contract=off (no fused multiply-add, so binary32 arithmetic rounds
 after every operation, as the CUDA side does with explicit _rn intrinsics).
 """
@@ -20,7 +20,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
-_SOURCES = ["qoz_oracle.cpp", "qoz_oracle_tune.cpp"]
+_SOURCES = ["qoz_oracle.cpp", "qoz_oracle_tune.cpp", "qoz_oracle_learn.cpp"]
 _lib = None
 
 MAX_LEVELS = 8
@@ -101,6 +101,10 @@ def lib():
             "orc_trial_metric": (f64, [P, i32, f64]),
             "orc_table1": (i32, [f64, f64, f64, f64, f64, f64, P]),
             "orc_tune": (i32, [P, i32, P, f64, f64, i32, f64, P, P]),
+            "orc_features": (i32, [P, i32, P, f64, f64, P, i64, P, P]),
+            "orc_mlp_forward": (None, [P, P, P, P, i64, P]),
+            "orc_mlp_loss_grad": (f64, [P, P, P, P, P, i64, P]),
+            "orc_adam_step": (None, [P, P, P, P, i64, i64, f64, f64, f64, f64]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -327,3 +331,72 @@ def tune(x, e_user: float, vrange: float, metric: int, target=float("nan"), opts
     if rc != 0:
         raise ValueError("orc_tune failed")
     return r
+
+
+# ------------------------------------------------------------ learned tuner
+NFEAT, NHID, NOUT = 64, 128, 16
+NPARAM = NHID * NFEAT + NHID + NHID * NHID + NHID + NOUT * NHID + NOUT
+HEADS = ((0, 2), (2, 6), (8, 5), (13, 3))   # (offset, length): interp, order, alpha, beta
+
+
+def features(x, rel_eb: float, vrange: float, block: int, rate: float):
+    """The 64 features of the blocks sampled with (block, rate)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    d = _dims(x.shape)
+    org, bd, _ = sample_blocks(x.shape, block, rate)
+    org = np.ascontiguousarray(org, dtype=np.int64)
+    bdv = np.ones(3, dtype=np.int64)
+    bdv[:len(bd)] = bd
+    out = np.zeros(NFEAT, dtype=np.float64)
+    rc = lib().orc_features(_ptr(x), x.ndim, _ptr(d), float(rel_eb), float(vrange), _ptr(org),
+                            len(org), _ptr(bdv), _ptr(out))
+    if rc != 0:
+        raise ValueError("orc_features failed")
+    return out
+
+
+def features_blocks(x, rel_eb: float, vrange: float, origins, block_dims):
+    """Features over explicit blocks (origins [nb, 3], block_dims per axis)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    d = _dims(x.shape)
+    org = np.ascontiguousarray(origins, dtype=np.int64).reshape(-1, 3)
+    bdv = np.ones(3, dtype=np.int64)
+    bdv[:len(block_dims)] = block_dims
+    out = np.zeros(NFEAT, dtype=np.float64)
+    rc = lib().orc_features(_ptr(x), x.ndim, _ptr(d), float(rel_eb), float(vrange), _ptr(org),
+                            len(org), _ptr(bdv), _ptr(out))
+    if rc != 0:
+        raise ValueError("orc_features failed")
+    return out
+
+
+def _f64(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None:
+        assert a.size == n
+    return a
+
+
+def mlp_forward(params, mean, sd, X):
+    X = _f64(X).reshape(-1, NFEAT)
+    out = np.zeros((X.shape[0], NOUT), dtype=np.float64)
+    lib().orc_mlp_forward(_ptr(_f64(params, NPARAM)), _ptr(_f64(mean, NFEAT)),
+                          _ptr(_f64(sd, NFEAT)), _ptr(X), X.shape[0], _ptr(out))
+    return out
+
+
+def mlp_loss_grad(params, mean, sd, X, labels, want_grad=True):
+    X = _f64(X).reshape(-1, NFEAT)
+    lab = np.ascontiguousarray(labels, dtype=np.int32).reshape(-1, 4)
+    g = np.zeros(NPARAM, dtype=np.float64) if want_grad else None
+    loss = lib().orc_mlp_loss_grad(_ptr(_f64(params, NPARAM)), _ptr(_f64(mean, NFEAT)),
+                                   _ptr(_f64(sd, NFEAT)), _ptr(X), _ptr(lab), X.shape[0],
+                                   _ptr(g) if want_grad else None)
+    return float(loss), g
+
+
+def adam_step(params, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """In place on params, m, v (float64 arrays)."""
+    lib().orc_adam_step(_ptr(params), _ptr(_f64(grad)), _ptr(m), _ptr(v), params.size, int(t),
+                        float(lr), float(beta1), float(beta2), float(eps))
+

@@ -171,6 +171,29 @@ int orc_table1(double b1, double m1, double b2, double m2, double b2p, double m2
 int orc_tune(const float* x, int ndims, const int64_t* dims, double e_user, double vrange,
              int metric, double target, const orc_tune_opts* o, orc_tune_result* out);
 
+/* ---------------------------------------------------------- learned tuner
+ * (qoz_oracle_learn.cpp: definitions in its header comment) */
+#define ORC_NFEAT 64
+#define ORC_H 128
+#define ORC_NOUT 16
+#define ORC_NPARAM (ORC_H * ORC_NFEAT + ORC_H + ORC_H * ORC_H + ORC_H + ORC_NOUT * ORC_H + ORC_NOUT)
+
+/* The 64 features of the sampled blocks (origins / block_dims as written by
+ * orc_sample_blocks). */
+int orc_features(const float* x, int ndims, const int64_t* dims, double rel_eb, double vrange,
+                 const int64_t* origins, int64_t nblocks, const int64_t* block_dims,
+                 double* out);
+/* logits[B][16] of raw features X[B][64]. */
+void orc_mlp_forward(const double* params, const double* mean, const double* sd,
+                     const double* X, int64_t B, double* logits);
+/* Mean over the batch of the summed per-head cross-entropies; grad (may be
+ * NULL) receives its gradient (ORC_NPARAM values, packed like params). */
+double orc_mlp_loss_grad(const double* params, const double* mean, const double* sd,
+                         const double* X, const int32_t* labels, int64_t B, double* grad);
+/* One Adam step (t = 1 for the first step). */
+void orc_adam_step(double* params, const double* grad, double* m, double* v, int64_t n,
+                   int64_t t, double lr, double beta1, double beta2, double eps);
+
 #ifdef __cplusplus
 }
 #endif
