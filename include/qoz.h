@@ -284,6 +284,75 @@ qoz_status qoz_tune(const float* d_field, qoz_shape shape, double rel_eb, qoz_me
                     double target, const qoz_tune_opts* opts, void* stream,
                     qoz_tune_report* out);
 
+/* ---------------------------------------------------------- learned tuner
+ * A network that proposes the tuner's choices from features of the sampled
+ * blocks, in place of the sampled trials.  The paper's concluding section
+ * leaves better selection policies and hyper-parameter auto-tuning to future
+ * work; the features and the network are this library's definitions:
+ *
+ * Features (64), over the sampled blocks of Sec. 6.1 (each block on its own)
+ * with e = rel_eb * vrange (1 if 0) and L(v) = log2(1 + v / e):
+ *   [0] log10(rel_eb); [1] log10(vrange / sigma), sigma the deviation of the
+ *   sampled values (0 if either is 0); [2] ndims / 3; [3] log2(points) / 30;
+ *   [4..6] L(mean |first difference|) per axis; [7..9] L(mean |second
+ *   difference|) per axis (2-D: third slot 0); [10..33] fractions of points
+ *   in 24 bins of floor(log2(|forward gradient| / e)) + 12, clamped (0 in
+ *   bin 0); [34..57] the same for |x - first-order Lorenzo prediction| / e;
+ *   [58..60] L(mean |x - linear interpolation|), [61..63] L(mean |x - cubic
+ *   interpolation|), at half-strides 1, 2, 4 along every axis with the
+ *   predictor's stencils (Sec. 5.1), targets with all four neighbours in
+ *   their block.
+ * Network: z = (f - mean) / std; h1 = relu(W1 z + b1) (128);
+ *   h2 = relu(W2 h1 + b2) (128); logits = W3 h2 + b3 (16): heads [0:2]
+ *   interpolator (linear, cubic), [2:8] dimension order (2-D: first two
+ *   used), [8:13] alpha, [13:16] beta, indices into the tuner's candidate
+ *   sets.  Loss: batch mean of the summed per-head softmax cross-entropies.
+ *   Parameters are packed W1 (128 x 64, row-major), b1, W2 (128 x 128), b2,
+ *   W3 (16 x 128), b3 (QOZ_MLP_PARAMS floats). */
+#define QOZ_NFEATURES 64
+#define QOZ_MLP_PARAMS 26896
+typedef struct qoz_model qoz_model;    /* opaque; weights, normalisation, Adam state on the device */
+
+/* Features of d_field (value range pass, sampling with opts as in qoz_tune)
+ * into h_features (host, 64 doubles) and/or d_features (device, 64 floats);
+ * either may be NULL.  Synchronises `stream`. */
+qoz_status qoz_features(const float* d_field, qoz_shape shape, double rel_eb,
+                        const qoz_tune_opts* opts, double* h_features, float* d_features,
+                        void* stream);
+
+/* A model on the current device: He-uniform weights from a splitmix64
+ * sequence seeded by `seed`, zero biases, mean 0 / std 1 normalisation. */
+qoz_status qoz_model_create(uint64_t seed, qoz_model** out);
+/* Replace parameters (QOZ_MLP_PARAMS floats; resets the Adam state) and/or
+ * the 64-entry normalisation; any pointer may be NULL.  Synchronous. */
+qoz_status qoz_model_set(qoz_model* m, const float* h_params, const float* h_mean,
+                         const float* h_sd);
+qoz_status qoz_model_get(const qoz_model* m, float* h_params, float* h_mean, float* h_sd);
+/* Logits (n x 16, device) of n feature rows (n x 64, device). */
+qoz_status qoz_model_forward(const qoz_model* m, const float* d_features, int64_t n,
+                             float* d_logits, void* stream);
+/* Gradient of the loss (device, QOZ_MLP_PARAMS floats; may be NULL) for n
+ * rows with labels (n x 4 int32, device: interpolator, order, alpha index,
+ * beta index); h_loss (may be NULL) receives the loss and then the call
+ * synchronises. */
+qoz_status qoz_model_gradient(qoz_model* m, const float* d_features, const int32_t* d_labels,
+                              int64_t n, float* d_grad, float* h_loss, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on the
+ * gradient of the batch. */
+qoz_status qoz_model_train_step(qoz_model* m, const float* d_features, const int32_t* d_labels,
+                                int64_t n, float lr, float* h_loss, void* stream);
+void qoz_model_free(qoz_model* m);
+
+/* Tuning by the network: features, one forward pass, the argmax of each
+ * head (one interpolator and order for every level, alpha and beta from
+ * opts' candidate sets, which must hold 5 and 3 values).  The bound is
+ * rel_eb * vrange, or with a PSNR target the uniform-error estimate
+ * vrange sqrt(3) 10^(-target / 20) when that is smaller.  The report's B and
+ * M are NaN (no trial ran).  Synchronises `stream`. */
+qoz_status qoz_tune_learned(const float* d_field, qoz_shape shape, double rel_eb,
+                            qoz_metric metric, double target, const qoz_tune_opts* opts,
+                            const qoz_model* model, void* stream, qoz_tune_report* out);
+
 /* ---------------------------------------------------------------- profiling */
 
 /* Stage ids of the per-stage timers. */

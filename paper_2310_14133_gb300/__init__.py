@@ -20,6 +20,10 @@ from ._binding import (  # noqa: F401
     Batch,
     BatchInfo,
     Blob,
+    HEADS,
+    MLP_PARAMS,
+    Model,
+    NFEATURES,
     QozError,
     Shape,
     compress,
@@ -28,6 +32,7 @@ from ._binding import (  # noqa: F401
     compute_metrics,
     decompress,
     deserialize,
+    features,
     lib,
     library_path,
     make_params,
@@ -35,5 +40,6 @@ from ._binding import (  # noqa: F401
     profile_enable,
     profile_read,
     tune,
+    tune_learned,
     value_range,
 )

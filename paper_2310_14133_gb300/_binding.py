@@ -8,6 +8,7 @@ import ctypes as C
 import math
 import os
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -146,6 +147,15 @@ def lib():
             "qoz_batch_get_info": (i32, [P, P]),
             "qoz_batch_free": (None, [P]),
             "qoz_compress_batch": (i32, [P, P, i32, f64, P, P, P]),
+            "qoz_features": (i32, [P, Shape, f64, P, P, P, P]),
+            "qoz_model_create": (i32, [C.c_uint64, P]),
+            "qoz_model_set": (i32, [P, P, P, P]),
+            "qoz_model_get": (i32, [P, P, P, P]),
+            "qoz_model_forward": (i32, [P, P, i64, P, P]),
+            "qoz_model_gradient": (i32, [P, P, P, i64, P, P, P]),
+            "qoz_model_train_step": (i32, [P, P, P, i64, C.c_float, P, P]),
+            "qoz_model_free": (None, [P]),
+            "qoz_tune_learned": (i32, [P, Shape, f64, i32, f64, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -407,4 +417,109 @@ def compress_batch(fields, rel_eb: float, params=None, stream=None):
     _check(lib().qoz_compress_batch(ptrs, arr, n, float(rel_eb), _params_array(params, shapes),
                                     _stream(stream), outs))
     return [Blob(C.c_void_p(outs[i]), shapes[i]) for i in range(n)]
+
+
+# ------------------------------------------------------------ learned tuner
+NFEATURES = 64
+MLP_PARAMS = 26896
+HEADS = ((0, 2), (2, 6), (8, 5), (13, 3))   # (offset, length): interp, order, alpha, beta
+
+
+def features(x: torch.Tensor, rel_eb: float, opts=None, stream=None, device_out=None):
+    """The 64 features of the sampled blocks: float64 numpy array, or, with
+    device_out (a CUDA float32 tensor of 64 values), written there only."""
+    h = None
+    if device_out is None:
+        h = np.zeros(NFEATURES, dtype=np.float64)
+    _check(lib().qoz_features(_dev_ptr(x), _shape_of(x), float(rel_eb),
+                              C.byref(opts) if opts is not None else None,
+                              C.c_void_p(h.ctypes.data) if h is not None else None,
+                              _dev_ptr(device_out) if device_out is not None else None,
+                              _stream(stream)))
+    return h
+
+
+class Model:
+    """The tuner network on the GPU (weights, normalisation, Adam state)."""
+
+    def __init__(self, seed: int = 0):
+        h = C.c_void_p()
+        _check(lib().qoz_model_create(C.c_uint64(seed), C.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set(self, params=None, mean=None, sd=None):
+        def arr(a, n):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float32)
+            assert a.size == n
+            return a
+        p, m, s = arr(params, MLP_PARAMS), arr(mean, NFEATURES), arr(sd, NFEATURES)
+        _check(lib().qoz_model_set(self._h, *(C.c_void_p(a.ctypes.data) if a is not None
+                                              else None for a in (p, m, s))))
+
+    def get(self):
+        p = np.zeros(MLP_PARAMS, dtype=np.float32)
+        m = np.zeros(NFEATURES, dtype=np.float32)
+        s = np.zeros(NFEATURES, dtype=np.float32)
+        _check(lib().qoz_model_get(self._h, C.c_void_p(p.ctypes.data), C.c_void_p(m.ctypes.data),
+                                   C.c_void_p(s.ctypes.data)))
+        return p, m, s
+
+    def forward(self, feats: torch.Tensor, stream=None) -> torch.Tensor:
+        feats = feats.reshape(-1, NFEATURES)
+        out = torch.empty((feats.shape[0], 16), dtype=torch.float32, device="cuda")
+        _check(lib().qoz_model_forward(self._h, _dev_ptr(feats), feats.shape[0], _dev_ptr(out),
+                                       _stream(stream)))
+        return out
+
+    def gradient(self, feats: torch.Tensor, labels: torch.Tensor, stream=None):
+        feats = feats.reshape(-1, NFEATURES)
+        g = torch.empty(MLP_PARAMS, dtype=torch.float32, device="cuda")
+        loss = C.c_float()
+        _check(lib().qoz_model_gradient(self._h, _dev_ptr(feats), _dev_ptr(labels, torch.int32),
+                                        feats.shape[0], _dev_ptr(g), C.byref(loss),
+                                        _stream(stream)))
+        return float(loss.value), g
+
+    def train_step(self, feats: torch.Tensor, labels: torch.Tensor, lr: float, want_loss=False,
+                   stream=None):
+        feats = feats.reshape(-1, NFEATURES)
+        loss = C.c_float()
+        _check(lib().qoz_model_train_step(self._h, _dev_ptr(feats), _dev_ptr(labels, torch.int32),
+                                          feats.shape[0], C.c_float(lr),
+                                          C.byref(loss) if want_loss else None, _stream(stream)))
+        return float(loss.value) if want_loss else None
+
+    def save(self, path: str):
+        p, m, s = self.get()
+        np.savez(path, params=p, mean=m, sd=s)
+
+    def load(self, path: str):
+        d = np.load(path)
+        self.set(d["params"], d["mean"], d["sd"])
+
+    def free(self):
+        if self._h:
+            lib().qoz_model_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def tune_learned(x: torch.Tensor, rel_eb: float, model: Model, metric: int = 0,
+                 target: float = float("nan"), opts=None, stream=None):
+    rep = TuneReport()
+    _check(lib().qoz_tune_learned(_dev_ptr(x), _shape_of(x), float(rel_eb), int(metric),
+                                  float(target), C.byref(opts) if opts is not None else None,
+                                  model.handle, _stream(stream), C.byref(rep)))
+    return rep
 

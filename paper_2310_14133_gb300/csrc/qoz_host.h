@@ -72,6 +72,20 @@ void level_geometry(const Resolved& r, int l, LevelLaunch* L);
 qoz_status compress_impl(const float* d_field, const qoz_shape& shape, bool rel, double eb,
                          const qoz_params* p, float* d_recon, cudaStream_t s, qoz_blob** out);
 
+// Sampled blocks of the tuners (Sec. 6.1), in the embedded 3-D layout.
+struct Sampling {
+  std::vector<int> origins;  // 3 per block (embedded)
+  int nb = 0;
+  int bd[3] = {1, 1, 1};
+  long long npts = 0;
+  int Ls = 0;
+  long long anchors = 0;     // anchors over all blocks
+};
+Sampling sample_blocks(const Resolved& r, int b, double rate, int s);
+// Tuner options with the defaults filled in and checked (qoz_tune.cu).
+qoz_status resolve_tune_opts(const qoz_shape& shape, const Resolved& r,
+                             const qoz_tune_opts* opts_in, qoz_tune_opts* out);
+
 // Adds n to the library's kernel-launch counter.
 void note_launch(int n);
 

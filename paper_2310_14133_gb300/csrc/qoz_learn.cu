@@ -1,0 +1,743 @@
+// Learned tuner: features of the sampled blocks, a 64-128-128-16 ReLU
+// network trained on the GPU (forward, backward, Adam), and the tuning call
+// that replaces the sampled trials by one network evaluation.
+//
+// The paper leaves better selection policies and hyper-parameter
+// auto-tuning to future work (its concluding section); the features and the
+// network are this library's own definitions:
+//
+// Features, over the blocks of the sampled tuner (Sec. 6.1), each block on
+// its own, e = rel_eb * vrange (1 if 0), L(v) = log2(1 + v / e):
+//   [0] log10(rel_eb)  [1] log10(vrange / sigma) of the sampled values
+//   [2] ndims / 3      [3] log2(N) / 30
+//   [4..6] L(mean |first difference|) per axis, [7..9] the same for second
+//   differences (2-D: third slot 0);
+//   [10..33] fractions in 24 bins of floor(log2(|gradient| / e)) + 12;
+//   [34..57] the same for |x - Lorenzo prediction| / e;
+//   [58..60] / [61..63] L(mean |x - linear| / |x - cubic| interpolation) at
+//   half-strides 1, 2, 4 along every axis (Sec. 5.1 stencils, targets with
+//   all four neighbours in the block).
+// Sums run in double; integer bins are decided in double by frexp, which is
+// exact, from differences formed in the same order everywhere.
+//
+// Network: z = (f - mean) / std; h1 = relu(W1 z + b1); h2 = relu(W2 h1 + b2);
+// o = W3 h2 + b3; heads o[0:2] interpolator, o[2:8] dimension order,
+// o[8:13] alpha, o[13:16] beta; loss = mean over samples of the summed
+// per-head softmax cross-entropies.  Training kernels are deterministic:
+// per-CTA gradient partials are summed in a fixed order before Adam
+// (Kingma and Ba, bias-corrected moments).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/qoz.h"
+#include "qoz_host.h"
+#include "qoz_internal.h"
+
+using namespace qoz;
+
+namespace {
+
+constexpr int NF = 64, NH = 128, NO = 16;
+constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + NH * NF, OFF_W2 = OFF_B1 + NH,
+              OFF_B2 = OFF_W2 + NH * NH, OFF_W3 = OFF_B2 + NH, OFF_B3 = OFF_W3 + NO * NH,
+              NPARAM = OFF_B3 + NO;
+static_assert(NPARAM == QOZ_MLP_PARAMS, "packed parameter count");
+__constant__ int kHeadOff[4] = {0, 2, 8, 13};
+__constant__ int kHeadLen[4] = {2, 6, 5, 3};
+
+// ------------------------------------------------------------- features
+constexpr int kFeatThreads = 256;
+constexpr int kFeatChunk = 8192;     // block points per CTA
+constexpr int kNSum = 14;            // s1, s2, d1[3], d2[3], lin[3], cub[3]
+constexpr int kNCnt = 12 + 48;       // n, n1[3], n2[3], nint[3], ng, nl, gh[24], lh[24]
+
+struct FeatPart {
+  double sum[kNSum];
+  unsigned long long cnt[kNCnt];
+};
+
+struct FeatArgs {
+  const float* x;
+  long long n1, n2;        // embedded dims (n0 implied)
+  const int* origins;      // 3 per block (embedded)
+  int bd0, bd1, bd2;
+  int is2d;
+  int chunks;              // CTAs per block
+  double e;
+  double c;                // shift of the second moment
+  FeatPart* parts;
+};
+
+__device__ __forceinline__ int hist_bin(double g) {
+  if (!(g > 0.0)) return 0;
+  int ex = 0;
+  frexp(g, &ex);
+  int b = ex - 1 + 12;
+  return b < 0 ? 0 : (b > 23 ? 23 : b);
+}
+
+__global__ void __launch_bounds__(kFeatThreads) feature_kernel(const FeatArgs a) {
+  __shared__ unsigned sc[kNCnt];
+  __shared__ double sred[kFeatThreads / 32][kNSum];
+  for (int i = threadIdx.x; i < kNCnt; i += blockDim.x) sc[i] = 0u;
+  __syncthreads();
+  const int blk = blockIdx.y;
+  const long long o0 = a.origins[3 * blk], o1 = a.origins[3 * blk + 1],
+                  o2 = a.origins[3 * blk + 2];
+  const int bd[3] = {a.bd0, a.bd1, a.bd2};
+  const long long st[3] = {a.n1 * a.n2, a.n2, 1};
+  const long long bpts = (long long)a.bd0 * a.bd1 * a.bd2;
+  const long long p0 = (long long)blockIdx.x * kFeatChunk;
+  const long long p1 = min(bpts, p0 + kFeatChunk);
+  const int a_lo = a.is2d ? 1 : 0;  // active axes a_lo..2; slot = axis - a_lo
+  double sum[kNSum];
+#pragma unroll
+  for (int i = 0; i < kNSum; ++i) sum[i] = 0.0;
+  unsigned n = 0, n1[3] = {0, 0, 0}, n2[3] = {0, 0, 0}, nint[3] = {0, 0, 0}, ng = 0, nl = 0;
+  for (long long p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    int c[3];
+    long long r = p;
+    c[2] = (int)(r % bd[2]);
+    r /= bd[2];
+    c[1] = (int)(r % bd[1]);
+    c[0] = (int)(r / bd[1]);
+    const float* base = a.x + (o0 + c[0]) * st[0] + (o1 + c[1]) * st[1] + (o2 + c[2]);
+    auto X = [&](int dz, int dy, int dx) {
+      return (double)base[dz * st[0] + dy * st[1] + dx];
+    };
+    const double v = (double)base[0];
+    const double u = v - a.c;
+    sum[0] += u;
+    sum[1] += u * u;
+    ++n;
+    bool fwd = true, bwd = true;
+    double gs = 0.0;
+    for (int ax = a_lo; ax < 3; ++ax) {
+      const int k = ax - a_lo;
+      const int dz = ax == 0, dy = ax == 1, dx = ax == 2;
+      const bool hasf = c[ax] + 1 < bd[ax], hasb = c[ax] >= 1;
+      fwd = fwd && hasf;
+      bwd = bwd && hasb;
+      if (hasf) {
+        const double xf = X(dz, dy, dx);
+        sum[2 + k] += fabs(xf - v);
+        ++n1[k];
+        if (hasb) {
+          sum[5 + k] += fabs((xf + X(-dz, -dy, -dx)) - 2.0 * v);
+          ++n2[k];
+        }
+      }
+      for (int j = 0; j < 3; ++j) {
+        const int h = 1 << j;
+        if (c[ax] % (2 * h) != h || c[ax] - 3 * h < 0 || c[ax] + 3 * h > bd[ax] - 1) continue;
+        const double a3 = X(-3 * h * dz, -3 * h * dy, -3 * h * dx);
+        const double a1 = X(-h * dz, -h * dy, -h * dx);
+        const double b1 = X(h * dz, h * dy, h * dx);
+        const double b3 = X(3 * h * dz, 3 * h * dy, 3 * h * dx);
+        sum[8 + j] += fabs(v - (a1 + b1) * 0.5);
+        sum[11 + j] += fabs(v - (9.0 * (a1 + b1) - (a3 + b3)) / 16.0);
+        ++nint[j];
+      }
+    }
+    if (fwd) {
+      for (int ax = a_lo; ax < 3; ++ax) {
+        const double d = X(ax == 0, ax == 1, ax == 2) - v;
+        gs += d * d;
+      }
+      atomicAdd(&sc[12 + hist_bin(sqrt(gs) / a.e)], 1u);
+      ++ng;
+    }
+    if (bwd) {
+      double pred;
+      if (!a.is2d) {
+        const double s1 = (X(-1, 0, 0) + X(0, -1, 0)) + X(0, 0, -1);
+        const double s2 = (X(-1, -1, 0) + X(-1, 0, -1)) + X(0, -1, -1);
+        pred = (s1 - s2) + X(-1, -1, -1);
+      } else {
+        pred = (X(0, -1, 0) + X(0, 0, -1)) - X(0, -1, -1);
+      }
+      atomicAdd(&sc[36 + hist_bin(fabs(v - pred) / a.e)], 1u);
+      ++nl;
+    }
+  }
+  // counts (exact)
+  atomicAdd(&sc[0], n);
+  for (int k = 0; k < 3; ++k) {
+    atomicAdd(&sc[1 + k], n1[k]);
+    atomicAdd(&sc[4 + k], n2[k]);
+    atomicAdd(&sc[7 + k], nint[k]);
+  }
+  atomicAdd(&sc[10], ng);
+  atomicAdd(&sc[11], nl);
+  // sums: warp trees, then warps in order
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < kNSum; ++i) {
+    double v = sum[i];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (l == 0) sred[w][i] = v;
+  }
+  __syncthreads();
+  FeatPart* out = a.parts + (long long)blockIdx.y * a.chunks + blockIdx.x;
+  if (threadIdx.x < kNSum) {
+    double v = 0.0;
+    for (int k = 0; k < kFeatThreads / 32; ++k) v += sred[k][threadIdx.x];
+    out->sum[threadIdx.x] = v;
+  }
+  for (int i = threadIdx.x; i < kNCnt; i += blockDim.x) out->cnt[i] = sc[i];
+}
+
+// One thread: fold the partials in order, evaluate the 64 features.
+__global__ void feature_final_kernel(const FeatPart* parts, int nparts, double rel_eb,
+                                     double vrange, double e, double npoints, int ndims,
+                                     double* fd, float* ff) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s[kNSum];
+  unsigned long long c[kNCnt];
+  for (int i = 0; i < kNSum; ++i) s[i] = 0.0;
+  for (int i = 0; i < kNCnt; ++i) c[i] = 0ull;
+  for (int p = 0; p < nparts; ++p) {
+    for (int i = 0; i < kNSum; ++i) s[i] += parts[p].sum[i];
+    for (int i = 0; i < kNCnt; ++i) c[i] += parts[p].cnt[i];
+  }
+  double f[NF];
+  for (int i = 0; i < NF; ++i) f[i] = 0.0;
+  const double n = (double)c[0];
+  double var = 0.0;
+  if (c[0]) {
+    const double m = s[0] / n;
+    var = s[1] / n - m * m;
+    if (var < 0.0) var = 0.0;
+  }
+  const double sigma = sqrt(var);
+  f[0] = log10(rel_eb);
+  f[1] = (sigma > 0.0 && vrange > 0.0) ? log10(vrange / sigma) : 0.0;
+  f[2] = ndims / 3.0;
+  f[3] = log2(npoints) / 30.0;
+  for (int k = 0; k < ndims; ++k) {
+    f[4 + k] = c[1 + k] ? log2(1.0 + (s[2 + k] / (double)c[1 + k]) / e) : 0.0;
+    f[7 + k] = c[4 + k] ? log2(1.0 + (s[5 + k] / (double)c[4 + k]) / e) : 0.0;
+  }
+  for (int i = 0; i < 24; ++i) {
+    f[10 + i] = c[10] ? (double)c[12 + i] / (double)c[10] : 0.0;
+    f[34 + i] = c[11] ? (double)c[36 + i] / (double)c[11] : 0.0;
+  }
+  for (int j = 0; j < 3; ++j) {
+    f[58 + j] = c[7 + j] ? log2(1.0 + (s[8 + j] / (double)c[7 + j]) / e) : 0.0;
+    f[61 + j] = c[7 + j] ? log2(1.0 + (s[11 + j] / (double)c[7 + j]) / e) : 0.0;
+  }
+  for (int i = 0; i < NF; ++i) {
+    if (fd) fd[i] = f[i];
+    if (ff) ff[i] = (float)f[i];
+  }
+}
+
+// ------------------------------------------------------------- network
+constexpr int kMlpThreads = 256;
+constexpr int kMlpS = 16;  // samples per CTA
+
+struct MlpSmem {
+  float z[kMlpS][NF];
+  float h1[kMlpS][NH];
+  float h2[kMlpS][NH];
+  float o[kMlpS][NO];
+  float dout[kMlpS][NO];
+  float dh2[kMlpS][NH];
+  float dh1[kMlpS][NH];
+  float loss[kMlpS];
+};
+
+// Forward for kMlpS samples per CTA; TRAIN adds the loss, the backward pass
+// and this CTA's gradient partial (NPARAM floats at gpart + cta * NPARAM).
+template <bool TRAIN>
+__global__ void __launch_bounds__(kMlpThreads) mlp_kernel(
+    const float* __restrict__ P, const float* __restrict__ mean, const float* __restrict__ sd,
+    const float* __restrict__ X, const int* __restrict__ labels, long long B, float invB,
+    float* __restrict__ logits, float* __restrict__ gpart, float* __restrict__ lpart) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  MlpSmem& sm = *reinterpret_cast<MlpSmem*>(smraw);
+  const int t = threadIdx.x;
+  const long long s0 = (long long)blockIdx.x * kMlpS;
+  const float* W1 = P + OFF_W1;
+  const float* b1 = P + OFF_B1;
+  const float* W2 = P + OFF_W2;
+  const float* b2 = P + OFF_B2;
+  const float* W3 = P + OFF_W3;
+  const float* b3 = P + OFF_B3;
+  for (int i = t; i < kMlpS * NF; i += kMlpThreads) {
+    const int s = i / NF, f = i % NF;
+    const float d = sd[f] != 0.0f ? sd[f] : 1.0f;
+    sm.z[s][f] = s0 + s < B ? __fdiv_rn(__fsub_rn(X[(s0 + s) * NF + f], mean[f]), d) : 0.0f;
+  }
+  __syncthreads();
+  for (int i = t; i < kMlpS * NH; i += kMlpThreads) {
+    const int s = i / NH, o = i % NH;
+    float acc = b1[o];
+    for (int k = 0; k < NF; ++k) acc = __fadd_rn(acc, __fmul_rn(W1[o * NF + k], sm.z[s][k]));
+    sm.h1[s][o] = acc > 0.0f ? acc : 0.0f;
+  }
+  __syncthreads();
+  for (int i = t; i < kMlpS * NH; i += kMlpThreads) {
+    const int s = i / NH, o = i % NH;
+    float acc = b2[o];
+    for (int k = 0; k < NH; ++k) acc = __fadd_rn(acc, __fmul_rn(W2[o * NH + k], sm.h1[s][k]));
+    sm.h2[s][o] = acc > 0.0f ? acc : 0.0f;
+  }
+  __syncthreads();
+  for (int i = t; i < kMlpS * NO; i += kMlpThreads) {
+    const int s = i / NO, o = i % NO;
+    float acc = b3[o];
+    for (int k = 0; k < NH; ++k) acc = __fadd_rn(acc, __fmul_rn(W3[o * NH + k], sm.h2[s][k]));
+    sm.o[s][o] = acc;
+    if (!TRAIN && s0 + s < B) logits[(s0 + s) * NO + o] = acc;
+  }
+  if (!TRAIN) return;
+  __syncthreads();
+  // loss and d loss / d logits, one (sample, head) per thread
+  if (t < kMlpS * 4) {
+    const int s = t / 4, hd = t % 4;
+    const int off = kHeadOff[hd], len = kHeadLen[hd];
+    float l = 0.0f;
+    if (s0 + s < B) {
+      const int lab = labels[(s0 + s) * 4 + hd];
+      float mx = sm.o[s][off];
+      for (int j = 1; j < len; ++j) mx = fmaxf(mx, sm.o[s][off + j]);
+      float se = 0.0f;
+      for (int j = 0; j < len; ++j) se += expf(sm.o[s][off + j] - mx);
+      l = (logf(se) + mx) - sm.o[s][off + lab];
+      for (int j = 0; j < len; ++j)
+        sm.dout[s][off + j] = (expf(sm.o[s][off + j] - mx) / se - (j == lab ? 1.0f : 0.0f)) * invB;
+    } else {
+      for (int j = 0; j < len; ++j) sm.dout[s][off + j] = 0.0f;
+    }
+    // per-sample loss: heads summed in order by lane hd == 0 after a shuffle
+    const float l1 = __shfl_down_sync(0xffffffffu, l, 1, 4);
+    const float l2 = __shfl_down_sync(0xffffffffu, l, 2, 4);
+    const float l3 = __shfl_down_sync(0xffffffffu, l, 3, 4);
+    if (hd == 0) sm.loss[s] = ((l + l1) + l2) + l3;
+  }
+  __syncthreads();
+  for (int i = t; i < kMlpS * NH; i += kMlpThreads) {
+    const int s = i / NH, k = i % NH;
+    float acc = 0.0f;
+    for (int o = 0; o < NO; ++o) acc += W3[o * NH + k] * sm.dout[s][o];
+    sm.dh2[s][k] = sm.h2[s][k] > 0.0f ? acc : 0.0f;
+  }
+  __syncthreads();
+  for (int i = t; i < kMlpS * NH; i += kMlpThreads) {
+    const int s = i / NH, k = i % NH;
+    float acc = 0.0f;
+    for (int o = 0; o < NH; ++o) acc += W2[o * NH + k] * sm.dh2[s][o];
+    sm.dh1[s][k] = sm.h1[s][k] > 0.0f ? acc : 0.0f;
+  }
+  __syncthreads();
+  float* g = gpart + (long long)blockIdx.x * NPARAM;
+  for (int p = t; p < NPARAM; p += kMlpThreads) {
+    float acc = 0.0f;
+    if (p < OFF_B1) {
+      const int o = p / NF, k = p % NF;
+      for (int s = 0; s < kMlpS; ++s) acc += sm.dh1[s][o] * sm.z[s][k];
+    } else if (p < OFF_W2) {
+      const int o = p - OFF_B1;
+      for (int s = 0; s < kMlpS; ++s) acc += sm.dh1[s][o];
+    } else if (p < OFF_B2) {
+      const int q = p - OFF_W2, o = q / NH, k = q % NH;
+      for (int s = 0; s < kMlpS; ++s) acc += sm.dh2[s][o] * sm.h1[s][k];
+    } else if (p < OFF_W3) {
+      const int o = p - OFF_B2;
+      for (int s = 0; s < kMlpS; ++s) acc += sm.dh2[s][o];
+    } else if (p < OFF_B3) {
+      const int q = p - OFF_W3, o = q / NH, k = q % NH;
+      for (int s = 0; s < kMlpS; ++s) acc += sm.dout[s][o] * sm.h2[s][k];
+    } else {
+      const int o = p - OFF_B3;
+      for (int s = 0; s < kMlpS; ++s) acc += sm.dout[s][o];
+    }
+    g[p] = acc;
+  }
+  if (t == 0) {
+    float l = 0.0f;
+    for (int s = 0; s < kMlpS; ++s) l += sm.loss[s];
+    lpart[blockIdx.x] = l;
+  }
+}
+
+// Sum of the CTA partials (fixed order), then Adam on each parameter.
+__global__ void adam_kernel(float* __restrict__ P, float* __restrict__ m, float* __restrict__ v,
+                            const float* __restrict__ gpart, const float* __restrict__ lpart,
+                            int nparts, float invB, int update, float lr, float beta1,
+                            float beta2, float c1, float c2, float eps, float* grad_out,
+                            float* loss_out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p == 0 && loss_out) {
+    float l = 0.0f;
+    for (int c = 0; c < nparts; ++c) l += lpart[c];
+    *loss_out = l * invB;
+  }
+  if (p >= NPARAM) return;
+  float g = 0.0f;
+  for (int c = 0; c < nparts; ++c) g += gpart[(long long)c * NPARAM + p];
+  if (grad_out) grad_out[p] = g;
+  if (!update) return;
+  const float mm = beta1 * m[p] + (1.0f - beta1) * g;
+  const float vv = beta2 * v[p] + (1.0f - beta2) * g * g;
+  m[p] = mm;
+  v[p] = vv;
+  P[p] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+}
+
+}  // namespace
+
+struct qoz_model {
+  float* d_params = nullptr;
+  float* d_mean = nullptr;
+  float* d_sd = nullptr;
+  float* d_m = nullptr;
+  float* d_v = nullptr;
+  float* d_gpart = nullptr;
+  float* d_lpart = nullptr;
+  float* d_loss = nullptr;
+  long long gpart_ctas = 0;
+  long long t = 0;
+};
+
+namespace {
+
+// splitmix64: deterministic initial weights from the seed
+uint64_t splitmix(uint64_t& s) {
+  uint64_t z = (s += 0x9e3779b97f4a7c15ULL);
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+qoz_status ensure_partials(qoz_model* m, long long ctas) {
+  if (ctas <= m->gpart_ctas) return QOZ_OK;
+  cudaFree(m->d_gpart);
+  cudaFree(m->d_lpart);
+  m->d_gpart = nullptr;
+  m->d_lpart = nullptr;
+  m->gpart_ctas = 0;
+  if (cudaMalloc((void**)&m->d_gpart, sizeof(float) * NPARAM * ctas) != cudaSuccess ||
+      cudaMalloc((void**)&m->d_lpart, sizeof(float) * ctas) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(QOZ_ENOMEM, "model gradient partials");
+  }
+  m->gpart_ctas = ctas;
+  return QOZ_OK;
+}
+
+constexpr size_t kMlpSmem = sizeof(MlpSmem);
+
+template <bool TRAIN>
+cudaError_t launch_mlp(const qoz_model* m, const float* X, const int* labels, long long B,
+                       float* logits, cudaStream_t s) {
+  static unsigned long long done = 0;
+  cudaError_t e = ensure_smem_attr((const void*)mlp_kernel<TRAIN>, &done, kMlpSmem);
+  if (e != cudaSuccess) return e;
+  const long long ctas = (B + kMlpS - 1) / kMlpS;
+  mlp_kernel<TRAIN><<<(unsigned)ctas, kMlpThreads, kMlpSmem, s>>>(
+      m->d_params, m->d_mean, m->d_sd, X, labels, B, 1.0f / (float)B, logits, m->d_gpart,
+      m->d_lpart);
+  note_launch(1);
+  return cudaGetLastError();
+}
+
+// Gradient (and optionally one Adam step) on a batch.
+qoz_status grad_step(qoz_model* m, const float* X, const int* labels, long long B, int update,
+                     float lr, float* d_grad, float* h_loss, cudaStream_t s) {
+  if (!m || !X || !labels || B < 1) return fail(QOZ_EINVAL, "invalid argument");
+  const long long ctas = (B + kMlpS - 1) / kMlpS;
+  qoz_status st = ensure_partials(m, ctas);
+  if (st != QOZ_OK) return st;
+  cudaError_t e = launch_mlp<true>(m, X, labels, B, nullptr, s);
+  const double b1 = 0.9, b2 = 0.999;
+  const long long t = update ? m->t + 1 : m->t;
+  const float c1 = update ? (float)(1.0 - std::pow(b1, (double)t)) : 1.0f;
+  const float c2 = update ? (float)(1.0 - std::pow(b2, (double)t)) : 1.0f;
+  if (e == cudaSuccess) {
+    adam_kernel<<<(NPARAM + 255) / 256, 256, 0, s>>>(
+        m->d_params, m->d_m, m->d_v, m->d_gpart, m->d_lpart, (int)ctas, 1.0f / (float)B,
+        update, lr, (float)b1, (float)b2, c1, c2, 1e-8f, d_grad, m->d_loss);
+    note_launch(1);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && h_loss) {
+    e = cudaMemcpyAsync(h_loss, m->d_loss, sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "model step");
+  if (update) m->t = t;
+  return QOZ_OK;
+}
+
+// Features of the sampled blocks into device buffers fd (double, may be
+// NULL) / ff (float, may be NULL); returns the value range through vr.
+qoz_status features_impl(const float* d_field, const qoz_shape& shape, double rel_eb,
+                         const qoz_tune_opts* opts_in, double* fd, float* ff, cudaStream_t s,
+                         double* vr_out, double* vmin_out, double* vmax_out, Sampling* sm_out) {
+  if (!d_field) return fail(QOZ_EINVAL, "d_field is NULL");
+  if (!(rel_eb > 0.0 && std::isfinite(rel_eb))) return fail(QOZ_EINVAL, "rel_eb must be > 0");
+  Resolved r;
+  qoz_status st = resolve(shape, nullptr, &r);
+  if (st != QOZ_OK) return st;
+  qoz_tune_opts o;
+  if ((st = resolve_tune_opts(shape, r, opts_in, &o)) != QOZ_OK) return st;
+  float vmin, vmax;
+  int64_t cnt;
+  st = qoz_value_range(d_field, r.N, &vmin, &vmax, &cnt, s);
+  if (st != QOZ_OK) return st;
+  const double vr = (double)vmax - (double)vmin;
+  const double e0 = rel_eb * vr;
+  const double e = e0 > 0.0 ? e0 : 1.0;
+  Sampling sm = sample_blocks(r, o.block, o.rate, o.anchor_stride);
+  const long long bpts = (long long)sm.bd[0] * sm.bd[1] * sm.bd[2];
+  const int chunks = (int)((bpts + kFeatChunk - 1) / kFeatChunk);
+  const long long nparts = (long long)chunks * sm.nb;
+  if (sm.nb > 65535) return fail(QOZ_EUNSUPPORTED, "too many sampled blocks");
+  void* scratch = nullptr;
+  const size_t ob = ((size_t)sm.origins.size() * sizeof(int) + 255) & ~(size_t)255;
+  cudaError_t ce = dev_alloc(&scratch, ob + sizeof(FeatPart) * nparts, s);
+  if (ce != cudaSuccess) return fail(QOZ_ENOMEM, "feature scratch");
+  int* d_org = (int*)scratch;
+  FeatPart* parts = (FeatPart*)((char*)scratch + ob);
+  ce = cudaMemcpyAsync(d_org, sm.origins.data(), sizeof(int) * sm.origins.size(),
+                       cudaMemcpyHostToDevice, s);
+  // the moments are shifted by the first sampled value
+  float c0 = 0.0f;
+  if (ce == cudaSuccess) {
+    const long long i0 = ((long long)sm.origins[0] * r.n[1] + sm.origins[1]) * r.n[2] +
+                         sm.origins[2];
+    ce = cudaMemcpyAsync(&c0, d_field + i0, sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  }
+  if (ce == cudaSuccess) {
+    FeatArgs a;
+    a.x = d_field;
+    a.n1 = r.n[1];
+    a.n2 = r.n[2];
+    a.origins = d_org;
+    a.bd0 = sm.bd[0];
+    a.bd1 = sm.bd[1];
+    a.bd2 = sm.bd[2];
+    a.is2d = r.ndims == 2;
+    a.chunks = chunks;
+    a.e = e;
+    a.c = (double)c0;
+    a.parts = parts;
+    feature_kernel<<<dim3(chunks, sm.nb), kFeatThreads, 0, s>>>(a);
+    note_launch(1);
+    ce = cudaGetLastError();
+  }
+  if (ce == cudaSuccess) {
+    feature_final_kernel<<<1, 32, 0, s>>>(parts, (int)nparts, rel_eb, vr, e, (double)r.N,
+                                          r.ndims, fd, ff);
+    note_launch(1);
+    ce = cudaGetLastError();
+  }
+  dev_free(scratch, s);
+  if (ce != cudaSuccess) return cuda_fail(ce, "features");
+  if (vr_out) *vr_out = vr;
+  if (vmin_out) *vmin_out = vmin;
+  if (vmax_out) *vmax_out = vmax;
+  if (sm_out) *sm_out = sm;
+  return QOZ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qoz_status qoz_features(const float* d_field, qoz_shape shape, double rel_eb,
+                        const qoz_tune_opts* opts, double* h_features, float* d_features,
+                        void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  configure_pool_once();
+  double* d_tmp = nullptr;
+  if (h_features && dev_alloc((void**)&d_tmp, sizeof(double) * NF, s) != cudaSuccess)
+    return fail(QOZ_ENOMEM, "feature output");
+  qoz_status st = features_impl(d_field, shape, rel_eb, opts, d_tmp, d_features, s, nullptr,
+                                nullptr, nullptr, nullptr);
+  if (st == QOZ_OK && h_features) {
+    cudaError_t e = cudaMemcpyAsync(h_features, d_tmp, sizeof(double) * NF,
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_fail(e, "features read-back");
+  }
+  dev_free(d_tmp, s);
+  return st;
+}
+
+qoz_status qoz_model_create(uint64_t seed, qoz_model** out) {
+  if (!out) return fail(QOZ_EINVAL, "out is NULL");
+  *out = nullptr;
+  qoz_model* m = new qoz_model();
+  const size_t pb = sizeof(float) * NPARAM;
+  if (cudaMalloc((void**)&m->d_params, pb) != cudaSuccess ||
+      cudaMalloc((void**)&m->d_m, pb) != cudaSuccess ||
+      cudaMalloc((void**)&m->d_v, pb) != cudaSuccess ||
+      cudaMalloc((void**)&m->d_mean, sizeof(float) * NF) != cudaSuccess ||
+      cudaMalloc((void**)&m->d_sd, sizeof(float) * NF) != cudaSuccess ||
+      cudaMalloc((void**)&m->d_loss, sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    qoz_model_free(m);
+    return fail(QOZ_ENOMEM, "model allocation");
+  }
+  // He-uniform weights (bound sqrt(6 / fan_in)), zero biases, identity
+  // normalisation
+  std::vector<float> P(NPARAM, 0.0f), mean(NF, 0.0f), sd(NF, 1.0f);
+  uint64_t st = seed;
+  auto fill = [&](int off, int n, int fan_in) {
+    const double bound = std::sqrt(6.0 / fan_in);
+    for (int i = 0; i < n; ++i) {
+      const double u = (double)(splitmix(st) >> 11) * (1.0 / 9007199254740992.0);
+      P[off + i] = (float)((2.0 * u - 1.0) * bound);
+    }
+  };
+  fill(OFF_W1, NH * NF, NF);
+  fill(OFF_W2, NH * NH, NH);
+  fill(OFF_W3, NO * NH, NH);
+  const qoz_status s2 = qoz_model_set(m, P.data(), mean.data(), sd.data());
+  if (s2 != QOZ_OK) {
+    qoz_model_free(m);
+    return s2;
+  }
+  *out = m;
+  return QOZ_OK;
+}
+
+qoz_status qoz_model_set(qoz_model* m, const float* h_params, const float* h_mean,
+                         const float* h_sd) {
+  if (!m) return fail(QOZ_EINVAL, "model is NULL");
+  cudaError_t e = cudaSuccess;
+  if (h_params) {
+    e = cudaMemcpy(m->d_params, h_params, sizeof(float) * NPARAM, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(m->d_m, 0, sizeof(float) * NPARAM);
+    if (e == cudaSuccess) e = cudaMemset(m->d_v, 0, sizeof(float) * NPARAM);
+    m->t = 0;
+  }
+  if (e == cudaSuccess && h_mean)
+    e = cudaMemcpy(m->d_mean, h_mean, sizeof(float) * NF, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && h_sd)
+    e = cudaMemcpy(m->d_sd, h_sd, sizeof(float) * NF, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "model upload");
+  return QOZ_OK;
+}
+
+qoz_status qoz_model_get(const qoz_model* m, float* h_params, float* h_mean, float* h_sd) {
+  if (!m) return fail(QOZ_EINVAL, "model is NULL");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && h_params)
+    e = cudaMemcpy(h_params, m->d_params, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && h_mean)
+    e = cudaMemcpy(h_mean, m->d_mean, sizeof(float) * NF, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && h_sd)
+    e = cudaMemcpy(h_sd, m->d_sd, sizeof(float) * NF, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "model download");
+  return QOZ_OK;
+}
+
+qoz_status qoz_model_forward(const qoz_model* m, const float* d_features, int64_t n,
+                             float* d_logits, void* stream) {
+  if (!m || !d_features || !d_logits || n < 1) return fail(QOZ_EINVAL, "invalid argument");
+  cudaError_t e = launch_mlp<false>(m, d_features, nullptr, n, d_logits, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "model forward");
+  return QOZ_OK;
+}
+
+qoz_status qoz_model_gradient(qoz_model* m, const float* d_features, const int32_t* d_labels,
+                              int64_t n, float* d_grad, float* h_loss, void* stream) {
+  return grad_step(m, d_features, d_labels, n, 0, 0.0f, d_grad, h_loss, (cudaStream_t)stream);
+}
+
+qoz_status qoz_model_train_step(qoz_model* m, const float* d_features, const int32_t* d_labels,
+                                int64_t n, float lr, float* h_loss, void* stream) {
+  if (!(lr > 0.0f)) return fail(QOZ_EINVAL, "lr must be > 0");
+  return grad_step(m, d_features, d_labels, n, 1, lr, nullptr, h_loss, (cudaStream_t)stream);
+}
+
+void qoz_model_free(qoz_model* m) {
+  if (!m) return;
+  cudaFree(m->d_params);
+  cudaFree(m->d_m);
+  cudaFree(m->d_v);
+  cudaFree(m->d_mean);
+  cudaFree(m->d_sd);
+  cudaFree(m->d_gpart);
+  cudaFree(m->d_lpart);
+  cudaFree(m->d_loss);
+  delete m;
+}
+
+qoz_status qoz_tune_learned(const float* d_field, qoz_shape shape, double rel_eb,
+                            qoz_metric metric, double target, const qoz_tune_opts* opts,
+                            const qoz_model* model, void* stream, qoz_tune_report* out) {
+  if (!model || !out) return fail(QOZ_EINVAL, "NULL argument");
+  if (metric < QOZ_METRIC_MAXERR || metric > QOZ_METRIC_SSIM)
+    return fail(QOZ_EINVAL, "unknown metric %d", metric);
+  const bool target_mode = !std::isnan(target);
+  if (target_mode && metric != QOZ_METRIC_PSNR)
+    return fail(QOZ_EINVAL, "the learned tuner takes a PSNR target only");
+  cudaStream_t s = (cudaStream_t)stream;
+  configure_pool_once();
+  Resolved r;
+  qoz_status st = resolve(shape, nullptr, &r);
+  if (st != QOZ_OK) return st;
+  qoz_tune_opts o;
+  if ((st = resolve_tune_opts(shape, r, opts, &o)) != QOZ_OK) return st;
+  if (o.n_alpha != 5 || o.n_beta != 3)
+    return fail(QOZ_EINVAL, "the network's heads need 5 alpha and 3 beta candidates");
+  float* d_buf = nullptr;
+  if (dev_alloc((void**)&d_buf, sizeof(float) * (NF + NO), s) != cudaSuccess)
+    return fail(QOZ_ENOMEM, "tuner scratch");
+  double vr = 0.0, vmin = 0.0, vmax = 0.0;
+  Sampling sm;
+  st = features_impl(d_field, shape, rel_eb, &o, nullptr, d_buf, s, &vr, &vmin, &vmax, &sm);
+  float logits[NO];
+  if (st == QOZ_OK) {
+    cudaError_t e = launch_mlp<false>(model, d_buf, nullptr, 1, d_buf + NF, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(logits, d_buf + NF, sizeof(logits), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_fail(e, "learned tuner");
+  }
+  dev_free(d_buf, s);
+  if (st != QOZ_OK) return st;
+  auto argmax = [&](int off, int len) {
+    int b = 0;
+    for (int j = 1; j < len; ++j)
+      if (logits[off + j] > logits[off + b]) b = j;
+    return b;
+  };
+  const int interp = argmax(0, 2);
+  const int order = argmax(2, r.ndims == 3 ? 6 : 2);
+  const int ia = argmax(8, 5), ib = argmax(13, 3);
+  memset(out, 0, sizeof(*out));
+  for (int l = 0; l < QOZ_MAX_LEVELS; ++l) {
+    out->params.interp[l] = (uint8_t)interp;
+    out->params.order[l] = (uint8_t)order;
+  }
+  out->params.alpha = o.alphas[ia];
+  out->params.beta = o.betas[ib];
+  out->params.anchor_stride = o.anchor_stride;
+  double e = rel_eb * vr;
+  if (target_mode) {
+    // uniform-error estimate of the bound that meets the PSNR target
+    const double e0 = vr * std::sqrt(3.0) * std::pow(10.0, -target / 20.0);
+    if (e0 < e) e = e0;
+  }
+  out->abs_eb = e;
+  out->vmin = vmin;
+  out->vmax = vmax;
+  out->B = NAN;
+  out->M = NAN;
+  out->n_trials = 0;
+  out->n_blocks = sm.nb;
+  out->n_sampled_points = sm.npts;
+  return QOZ_OK;
+}
+
+}  // extern "C"

@@ -277,20 +277,14 @@ __global__ void __launch_bounds__(kTrialThreads, 1) trial_kernel(const TrialArgs
 
 // ------------------------------------------------------------- host side
 
-struct Sampling {
-  std::vector<int> origins;  // 3 per block (embedded)
-  int nb = 0;
-  int bd[3] = {1, 1, 1};
-  long long npts = 0;
-  int Ls = 0;
-  long long anchors = 0;     // anchors over all blocks
-};
 
 int floor_log2(long long v) {
   int l = 0;
   while ((2LL << l) <= v) ++l;
   return l;
 }
+
+}  // namespace
 
 // Uniform block sampling, Sec. 6.1: blocks of b+1 points per axis placed
 // every S = round(b r^(-1/d)) points while they fit; an axis shorter than a
@@ -332,6 +326,8 @@ Sampling sample_blocks(const Resolved& r, int b, double rate, int s) {
   sm.anchors = apb * sm.nb;
   return sm;
 }
+
+namespace {
 
 // Level bounds of Eq. (ebl) in double, each rounded to binary32 once.
 void fill_bounds(TrialCand* c, double e, double alpha, double beta, int L) {
@@ -520,19 +516,10 @@ int table1(double b1, double m1, double b2, double m2, double b2p, double m2p, d
 
 }  // namespace
 
-qoz_status tune_impl(const float* d_field, const qoz_shape& shape, double rel_eb, int metric,
-                     double target, const qoz_tune_opts* opts_in, cudaStream_t s,
-                     qoz_tune_report* out) {
-  if (!d_field || !out) return fail(QOZ_EINVAL, "NULL argument");
-  if (!(rel_eb > 0.0 && std::isfinite(rel_eb))) return fail(QOZ_EINVAL, "rel_eb must be > 0");
-  if (metric < QOZ_METRIC_MAXERR || metric > QOZ_METRIC_SSIM)
-    return fail(QOZ_EINVAL, "unknown metric %d", metric);
-  const bool target_mode = !std::isnan(target);
-  if (target_mode && metric == QOZ_METRIC_MAXERR)
-    return fail(QOZ_EINVAL, "a target needs the PSNR or SSIM metric");
-  Resolved r;
-  qoz_status st = resolve(shape, nullptr, &r);
-  if (st != QOZ_OK) return st;
+// Tuner options with the paper's defaults filled in (Sec. 7.1.4, Sec. 6.3.1)
+// and checked.
+qoz_status resolve_tune_opts(const qoz_shape& shape, const Resolved& r,
+                             const qoz_tune_opts* opts_in, qoz_tune_opts* out) {
   qoz_tune_opts o;
   memset(&o, 0, sizeof(o));
   if (opts_in) o = *opts_in;
@@ -569,6 +556,26 @@ qoz_status tune_impl(const float* d_field, const qoz_shape& shape, double rel_eb
     Resolved rr;
     if (resolve(shape, &chk, &rr) != QOZ_OK) return fail(QOZ_EINVAL, "invalid anchor stride");
   }
+  *out = o;
+  return QOZ_OK;
+}
+
+qoz_status tune_impl(const float* d_field, const qoz_shape& shape, double rel_eb, int metric,
+                     double target, const qoz_tune_opts* opts_in, cudaStream_t s,
+                     qoz_tune_report* out) {
+  if (!d_field || !out) return fail(QOZ_EINVAL, "NULL argument");
+  if (!(rel_eb > 0.0 && std::isfinite(rel_eb))) return fail(QOZ_EINVAL, "rel_eb must be > 0");
+  if (metric < QOZ_METRIC_MAXERR || metric > QOZ_METRIC_SSIM)
+    return fail(QOZ_EINVAL, "unknown metric %d", metric);
+  const bool target_mode = !std::isnan(target);
+  if (target_mode && metric == QOZ_METRIC_MAXERR)
+    return fail(QOZ_EINVAL, "a target needs the PSNR or SSIM metric");
+  Resolved r;
+  qoz_status st = resolve(shape, nullptr, &r);
+  if (st != QOZ_OK) return st;
+  qoz_tune_opts o;
+  if ((st = resolve_tune_opts(shape, r, opts_in, &o)) != QOZ_OK) return st;
+  const int d = r.ndims;
   int L = 0;
   while ((1 << L) < o.anchor_stride) ++L;
 

@@ -1,0 +1,169 @@
+"""Learned tuner on the GPU against the oracle: features of the sampled
+blocks (histogram fractions exact, other features within 1e-9), network
+forward / gradient / Adam within 1e-4 of the oracle's double-precision
+network, training that lowers the loss, and the tuning call's choices equal
+to the argmax of the oracle's logits."""
+
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2310_14133_gb300 import build
+    build.build()
+    import paper_2310_14133_gb300 as q
+    return q
+
+
+def _field(shape, seed, slope=5.0 / 3.0):
+    import synth
+    return synth.grf(shape, slope, seed=seed, n_modes=96, device="cuda").contiguous()
+
+
+CASES = [((100, 90, 110), 32, 0.005, 1e-3),    # one sampled block
+         ((256, 256, 256), 32, 0.005, 1e-4),   # eight blocks
+         ((20, 30, 40), 32, 0.005, 1e-2),      # no block fits: the whole field
+         ((37, 300, 29), 16, 0.005, 1e-3),     # blocks along one axis, whole extent on others
+         ((300, 517), 64, 0.01, 1e-3),         # 2-D, one block
+         ((1800, 3600), 64, 0.01, 1e-3)]       # 2-D, 18 blocks
+
+
+@pytest.mark.parametrize("shape,block,rate,rel", CASES)
+def test_features_parity(q, orc, shape, block, rate, rel):
+    x = _field(shape, seed=sum(shape))
+    opts = q.make_tune_opts(block=block, rate=rate)
+    f = q.features(x, rel, opts)
+    xn = x.cpu().numpy()
+    mn, mx, _ = orc.value_range(xn)
+    ref = orc.features(xn, rel, float(mx) - float(mn), block, rate)
+    assert np.array_equal(f[10:58], ref[10:58]), "histogram fractions"
+    np.testing.assert_allclose(f[:10], ref[:10], rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(f[58:], ref[58:], rtol=1e-9, atol=1e-12)
+    # the device copy is the same values in binary32
+    d = torch.empty(64, dtype=torch.float32, device="cuda")
+    q.features(x, rel, opts, device_out=d)
+    assert np.array_equal(d.cpu().numpy(), f.astype(np.float32))
+
+
+def _net(seed):
+    rng = np.random.default_rng(seed)
+    P = (rng.normal(0, 1, 26896) * 0.15).astype(np.float32)
+    mean = rng.normal(0, 1, 64).astype(np.float32)
+    sd = rng.uniform(0.5, 2.0, 64).astype(np.float32)
+    sd[7] = 0.0
+    return P, mean, sd
+
+
+def _data(seed, B):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(0, 2, (B, 64)).astype(np.float32)
+    lab = np.stack([rng.integers(0, n, B) for n in (2, 6, 5, 3)], axis=1).astype(np.int32)
+    return X, lab
+
+
+def _close(a, b, rel=1e-4):
+    scale = max(1e-30, float(np.abs(b).max()))
+    err = np.abs(a.astype(np.float64) - b)
+    assert np.all(err <= rel * np.abs(b) + 1e-5 * scale), float((err / scale).max())
+
+
+@pytest.mark.parametrize("B", [1, 16, 37])
+def test_network_forward_gradient_parity(q, orc, B):
+    P, mean, sd = _net(B)
+    X, lab = _data(100 + B, B)
+    m = q.Model(seed=1)
+    m.set(P, mean, sd)
+    Xd = torch.from_numpy(X).cuda()
+    labd = torch.from_numpy(lab).cuda()
+    logits = m.forward(Xd).cpu().numpy()
+    P64, mean64, sd64 = P.astype(np.float64), mean.astype(np.float64), sd.astype(np.float64)
+    ref = orc.mlp_forward(P64, mean64, sd64, X.astype(np.float64))
+    _close(logits, ref)
+    loss, g = m.gradient(Xd, labd)
+    rloss, rg = orc.mlp_loss_grad(P64, mean64, sd64, X.astype(np.float64), lab)
+    assert loss == pytest.approx(rloss, rel=1e-5)
+    _close(g.cpu().numpy(), rg)
+    # the gradient call leaves the weights alone
+    assert np.array_equal(m.get()[0], P)
+    m.free()
+
+
+def test_adam_step_parity(q, orc):
+    P, mean, sd = _net(5)
+    X, lab = _data(6, 40)
+    m = q.Model(seed=2)
+    m.set(P, mean, sd)
+    Xd, labd = torch.from_numpy(X).cuda(), torch.from_numpy(lab).cuda()
+    P64 = P.astype(np.float64)
+    mm, vv = np.zeros_like(P64), np.zeros_like(P64)
+    for t in (1, 2, 3):
+        _, rg = orc.mlp_loss_grad(P64, mean.astype(np.float64), sd.astype(np.float64),
+                                  X.astype(np.float64), lab)
+        orc.adam_step(P64, rg, mm, vv, t, lr=1e-3)
+        m.train_step(Xd, labd, 1e-3)
+        got = m.get()[0].astype(np.float64)
+        # an Adam step moves a parameter by at most lr (1 - b1) / sqrt(1 - b2);
+        # parameters with a clear gradient move the same way on both sides
+        assert np.abs(got - P.astype(np.float64)).max() <= t * 3.2e-3
+        big = np.abs(rg) > 1e-3 * np.abs(rg).max()
+        np.testing.assert_allclose(got[big], P64[big], rtol=0, atol=2e-5 * t)
+    m.free()
+
+
+def test_training_lowers_loss(q):
+    rng = np.random.default_rng(9)
+    B = 512
+    X = rng.normal(0, 1, (B, 64)).astype(np.float32)
+    W = rng.normal(0, 1, (64, 16))
+    z = X @ W
+    lab = np.stack([np.argmax(z[:, o:o + n], axis=1) for o, n in ((0, 2), (2, 6), (8, 5),
+                                                                  (13, 3))], 1).astype(np.int32)
+    m = q.Model(seed=3)
+    Xd, labd = torch.from_numpy(X).cuda(), torch.from_numpy(lab).cuda()
+    first = m.train_step(Xd, labd, 3e-3, want_loss=True)
+    for _ in range(300):
+        last = m.train_step(Xd, labd, 3e-3, want_loss=True)
+    assert last < 0.3 * first, (first, last)
+    m.free()
+
+
+@pytest.mark.parametrize("shape", [(96, 100, 120), (400, 700)])
+def test_tune_learned_follows_network(q, orc, shape):
+    x = _field(shape, seed=7)
+    P, mean, sd = _net(11)
+    m = q.Model()
+    m.set(P, mean, sd)
+    nd = len(shape)
+    block, rate = (32, 0.005) if nd == 3 else (64, 0.01)
+    opts = q.make_tune_opts(block=block, rate=rate, alphas=[1.0, 1.25, 1.5, 1.75, 2.0],
+                            betas=[2.0, 3.0, 4.0])
+    rep = q.tune_learned(x, 1e-3, m, opts=opts)
+    xn = x.cpu().numpy()
+    mn, mx, _ = orc.value_range(xn)
+    vr = float(mx) - float(mn)
+    f = orc.features(xn, 1e-3, vr, block, rate)
+    lo = orc.mlp_forward(P.astype(np.float64), mean.astype(np.float64), sd.astype(np.float64),
+                         f.astype(np.float32).astype(np.float64))[0]
+    want = []
+    for off, n in ((0, 2), (2, 6 if nd == 3 else 2), (8, 5), (13, 3)):
+        z = lo[off:off + n]
+        top = np.sort(z)[::-1]
+        assert top[0] - top[1] > 1e-3, "near-tie: choose another seed"
+        want.append(int(np.argmax(z)))
+    assert rep.params.interp[0] == want[0] and rep.params.order[0] == want[1]
+    assert rep.params.alpha == [1.0, 1.25, 1.5, 1.75, 2.0][want[2]]
+    assert rep.params.beta == [2.0, 3.0, 4.0][want[3]]
+    assert rep.abs_eb == 1e-3 * vr and rep.n_trials == 0
+    # PSNR target: the uniform-error estimate when it is below the bound
+    rep2 = q.tune_learned(x, 1e-2, m, metric=q.METRIC_PSNR, target=80.0, opts=opts)
+    assert rep2.abs_eb == pytest.approx(vr * math.sqrt(3) * 10 ** (-4.0), rel=1e-12)
+    m.free()
