@@ -54,6 +54,11 @@ def parse():
     ap.add_argument("--n", type=int, default=512, help="edge of the cubic field")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="compress", choices=["compress", "batch", "learned"],
+                    help="compress: the single-field step (default); batch: 48 2-D + 48 "
+                         "uneven 3-D fields through one batched plan; learned: train the "
+                         "tuner network, then learned vs sampled tuning")
+    ap.add_argument("--train", type=int, default=2000, help="learned: training fields")
     return ap.parse_args()
 
 
@@ -214,6 +219,164 @@ def cpu_baseline(x):
                       f"(rel bound 1e-3, max-CR mode), single-threaded, {dt:.1f} s"}
 
 
+
+def _events_ms(fn, reps, warm):
+    import torch
+    s = torch.cuda.current_stream()
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        fn()
+        b.record(s)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    ts.sort()
+    return ts[len(ts) // 2], ts
+
+
+def run_batch(args):
+    """48 CESM-shaped 2-D fields (1800 x 3600) and 48 uneven 3-D fields
+    (edges from {100, 128, 256, 384, 500}) compressed by one batched plan
+    (CUDA graph, level-1 tile variants timed on the first run), relative
+    bound 1e-3, default parameters.  value = input GB/s of whole batch runs
+    (CUDA events around qoz_batch_compress, blob allocation and count
+    read-back included)."""
+    import torch
+    import paper_2310_14133_gb300 as q
+    import synth
+    fields = [f.contiguous() for _, f in synth.config3_fields(48, 48, device="cuda")]
+    shapes = [tuple(f.shape) for f in fields]
+    nbytes = sum(4 * f.numel() for f in fields)
+    npts = nbytes // 4
+    plan = q.Batch(shapes, autotune=True)
+
+    def run():
+        for b in plan.compress(fields, REL_EB):
+            b.free()
+
+    q.profile_read(reset=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    run()   # autotune + graph capture
+    clocks.start()
+    time.sleep(0.3)
+    ms, all_ms = _events_ms(run, args.steps, max(3, args.warmup))
+    clk = clocks.stop()
+    inf = plan.info()
+    launches = q.profile_read(reset=True).launches
+    peak, peak_kind = _peak_hbm()
+    l1_ms = sum(min(inf.level1_ms[i][0], inf.level1_ms[i][1]) if inf.level1_ms[i][1] > 0
+                else inf.level1_ms[i][0] for i in range(inf.level1_groups))
+    achieved = LEVEL1_BYTES_PER_POINT * npts / (l1_ms * 1e-3) / 1e9 if l1_ms > 0 else None
+    line = {
+        "metric": "batch compress GB/s (FP32 in), bit-exact per field", "value":
+            nbytes / (ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "48 x 1800x3600 zonal bands + k^-3 noise, 48 x uneven 3-D "
+                               "k^-5/3 (edges {100,128,256,384,500}); rel bound 1e-3; "
+                               "default theta (cubic, order 0, alpha = beta = 1)",
+                   "fields": len(fields), "input_gb": nbytes / 1e9,
+                   "l2": "input 5.5 GB > 126 MB L2", "parallelism": "single GPU"},
+        "batch": {"groups": inf.n_groups, "launches_per_run": inf.launches_per_run,
+                  "graph": inf.graph, "ctas_per_run": inf.ctas_per_run,
+                  "level1_variant": [inf.level1_variant[i] for i in range(inf.level1_groups)],
+                  "level1_ms": [[inf.level1_ms[i][0], inf.level1_ms[i][1]]
+                                for i in range(inf.level1_groups)],
+                  "all_ms": all_ms},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None, "traffic": None,
+                     "kernel": "level_batch_kernel level 1 (autotune timings, CUDA events)",
+                     "algorithmic_bytes_per_launch": LEVEL1_BYTES_PER_POINT * npts,
+                     "peak_kind": peak_kind},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "e2e": None,
+    }
+    print(json.dumps(line), flush=True)
+    plan.free()
+
+
+def run_learned(args):
+    """Learned vs sampled tuning.  Training: --train fields from the training
+    recipe (slope ~ U[1, 4], edges {64, ..., 256}, relative bound log-uniform
+    in [1e-5, 1e-2]; 64 modes per field), labelled by the sampled tuner in
+    the maximum-compression mode; 200 epochs of Adam.  Test: the --n^3
+    k^-5/3 field of seed 4 at relative bounds sqrt(3) 10^(-P/20) for
+    P = 60, 80, 100 dB (the uniform-error bound of each PSNR).  value =
+    geometric mean of CR(learned) / CR(sampled); speedup = tuning time
+    sampled / learned (value range included on both sides)."""
+    import math
+    import numpy as np
+    import torch
+    import paper_2310_14133_gb300 as q
+    from paper_2310_14133_gb300 import learn
+    import synth
+    topts = q.make_tune_opts(**TUNE)
+    t0 = time.perf_counter()
+
+    def train_samples():
+        for i in range(args.train):
+            sp = synth.config4_train_spec(i)
+            x = synth.grf(sp["dims"], sp["slope"], seed=sp["seed"], n_modes=64, device="cuda")
+            yield x.contiguous(), sp["rel_eb"]
+
+    X, Y = learn.collect(train_samples(), topts)
+    t_label = time.perf_counter() - t0
+    model = q.Model(seed=4)
+    t1 = time.perf_counter()
+    losses = learn.fit(model, X, Y, epochs=200, batch=256, lr=3e-3)
+    torch.cuda.synchronize()
+    t_fit = time.perf_counter() - t1
+    acc = learn.accuracy(model, X, Y)
+
+    n = args.n
+    x = synth.grf((n, n, n), 5.0 / 3.0, seed=4, device="cuda").contiguous()
+    rows = []
+    for P in (60.0, 80.0, 100.0):
+        rel = math.sqrt(3.0) * 10.0 ** (-P / 20.0)
+        ms_s, _ = _events_ms(lambda: q.tune(x, rel, q.METRIC_MAXERR, float("nan"), topts),
+                             5, 2)
+        ms_l, _ = _events_ms(lambda: q.tune_learned(x, rel, model, opts=topts), 5, 2)
+        rs = q.tune(x, rel, q.METRIC_MAXERR, float("nan"), topts)
+        rl = q.tune_learned(x, rel, model, opts=topts)
+        res = {}
+        for name, params, e in (("sampled", rs.params, rs.abs_eb), ("learned", rl.params,
+                                                                    rl.abs_eb),
+                                ("default", q.make_params(3), rs.abs_eb)):
+            b = q.compress_abs(x, e, params)
+            res[name] = b.info().est_ratio
+            b.free()
+        rows.append({"psnr_db": P, "rel_eb": rel, "cr_sampled": res["sampled"],
+                     "cr_learned": res["learned"], "cr_default": res["default"],
+                     "ms_sampled": ms_s, "ms_learned": ms_l,
+                     "theta_sampled": [rs.params.interp[0], rs.params.order[0], rs.params.alpha,
+                                       rs.params.beta],
+                     "theta_learned": [rl.params.interp[0], rl.params.order[0], rl.params.alpha,
+                                       rl.params.beta]})
+    ratio = math.exp(sum(math.log(r["cr_learned"] / r["cr_sampled"]) for r in rows) / len(rows))
+    speed = math.exp(sum(math.log(r["ms_sampled"] / r["ms_learned"]) for r in rows) / len(rows))
+    gain = math.exp(sum(math.log(r["cr_learned"] / r["cr_default"]) for r in rows) / len(rows))
+    line = {
+        "metric": "learned vs sampled tune: CR ratio (geometric mean over 60/80/100 dB bounds)",
+        "value": ratio, "unit": "ratio", "n_gpus": 1, "steps": 5, "warmup": 2,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"train {args.train} fields (recipe slope U[1,4], edges "
+                               "64..256, rel bound 1e-5..1e-2), test {n}^3 k^-5/3 seed 4",
+                   "tuner_opts": TUNE, "parallelism": "single GPU"},
+        "speedup_sampled_over_learned": speed, "cr_gain_over_default": gain,
+        "rows": rows, "train": {"fields": int(X.shape[0]), "label_s": t_label,
+                                "fit_s": t_fit, "final_loss": losses[-1],
+                                "train_accuracy_per_head": acc},
+    }
+    print(json.dumps(line), flush=True)
+    model.free()
+
 def main():
     args = parse()
     rank = _env_int("RANK", 0)
@@ -221,6 +384,12 @@ def main():
     local = _env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batch":
+        run_batch(args)
+        return
+    if args.workload == "learned":
+        run_learned(args)
         return
 
     import torch

@@ -30,7 +30,12 @@
  *   [61..63] L(mean |x - cubic interpolation|) at h = 1, 2, 4
  * The interpolation residuals use the stencils of the predictor (Sec. 5.1)
  * on targets at block-local coordinate i = h (mod 2h) along each axis with
- * all four neighbours i +- h, i +- 3h inside the block.  floor(log2 g) comes
+ * all four neighbours i +- h, i +- 3h inside the block.
+ * Arithmetic: every difference, prediction, product and bin argument is a
+ * binary32 operation in the order written here (the sums of many terms are
+ * double); 1/e and 1/e^2 are rounded to binary32 once.  The gradient bin is
+ * floor(floor(log2(t)) / 2) + 12 with t = |gradient|^2 / e^2, which equals
+ * floor(log2(|gradient| / e)) + 12 without a square root; floor(log2) comes
  * from frexp, which is exact.
  *
  * Network: z = (f - mean) / std (std 0 taken as 1); h1 = relu(W1 z + b1);
@@ -49,14 +54,26 @@
 
 namespace {
 
-int hist_bin(double g) {
-  if (!(g > 0.0)) return 0;
+int clamp_bin(int b) { return b < 0 ? 0 : (b > 23 ? 23 : b); }
+
+// floor(log2 r) + 12 for a residual ratio r (0 -> bin 0)
+int res_bin(float r) {
+  if (!(r > 0.0f)) return 0;
+  if (std::isinf(r)) return 23;
   int ex = 0;
-  std::frexp(g, &ex);  // g = m 2^ex, m in [0.5, 1): floor(log2 g) = ex - 1
-  int b = ex - 1 + 12;
-  if (b < 0) b = 0;
-  if (b > 23) b = 23;
-  return b;
+  std::frexp(r, &ex);  // r = m 2^ex, m in [0.5, 1): floor(log2 r) = ex - 1
+  return clamp_bin(ex - 1 + 12);
+}
+
+// floor(log2 sqrt(t)) + 12 = floor(floor(log2 t) / 2) + 12 for t = g^2
+int grad_bin(float t) {
+  if (!(t > 0.0f)) return 0;
+  if (std::isinf(t)) return 23;
+  int ex = 0;
+  std::frexp(t, &ex);
+  const int k = ex - 1;
+  const int half = k >= 0 ? k / 2 : -((-k + 1) / 2);
+  return clamp_bin(half + 12);
 }
 
 double lscale(double v, double e) { return std::log2(1.0 + v / e); }
@@ -85,8 +102,10 @@ int orc_features(const float* x, int ndims, const int64_t* dims, double rel_eb, 
   auto at = [&](int64_t b, const int64_t* c) {
     int64_t idx = 0;
     for (int k = 0; k < ndims; ++k) idx += (origins[3 * b + k] + c[k]) * st[k];
-    return (double)x[idx];
+    return x[idx];
   };
+  const float inv_e = (float)(1.0 / e);
+  const float inv_e2 = (float)(1.0 / (e * e));
   const int64_t* bd = block_dims;
   int64_t bpts = 1;
   for (int k = 0; k < ndims; ++k) bpts *= bd[k];
@@ -102,7 +121,7 @@ int orc_features(const float* x, int ndims, const int64_t* dims, double rel_eb, 
         c[k] = r % bd[k];
         r /= bd[k];
       }
-      sum += at(b, c);
+      sum += (double)at(b, c);
       ++cnt;
     }
   const double mean = cnt ? sum / (double)cnt : 0.0;
@@ -114,7 +133,7 @@ int orc_features(const float* x, int ndims, const int64_t* dims, double rel_eb, 
         c[k] = r % bd[k];
         r /= bd[k];
       }
-      const double d = at(b, c) - mean;
+      const double d = (double)at(b, c) - mean;
       ss += d * d;
     }
   const double sigma = cnt ? std::sqrt(ss / (double)cnt) : 0.0;
@@ -139,18 +158,19 @@ int orc_features(const float* x, int ndims, const int64_t* dims, double rel_eb, 
         c[k] = r % bd[k];
         r /= bd[k];
       }
-      const double v = at(b, c);
+      const float v = at(b, c);
       // first and second differences along each axis
       for (int k = 0; k < ndims; ++k) {
         if (c[k] + 1 < bd[k]) {
           int64_t q[3] = {c[0], c[1], c[2]};
           q[k] += 1;
-          d1[k] += std::fabs(at(b, q) - v);
+          const float xq = at(b, q);
+          d1[k] += (double)std::fabs(xq - v);
           ++n1[k];
           if (c[k] >= 1) {
             int64_t m[3] = {c[0], c[1], c[2]};
             m[k] -= 1;
-            d2[k] += std::fabs((at(b, q) + at(b, m)) - 2.0 * v);
+            d2[k] += (double)std::fabs((xq + at(b, m)) - 2.0f * v);
             ++n2[k];
           }
         }
@@ -159,35 +179,35 @@ int orc_features(const float* x, int ndims, const int64_t* dims, double rel_eb, 
       bool fwd = true;
       for (int k = 0; k < ndims; ++k) fwd = fwd && c[k] + 1 < bd[k];
       if (fwd) {
-        double s = 0.0;
+        float s = 0.0f;
         for (int k = 0; k < ndims; ++k) {
           int64_t q[3] = {c[0], c[1], c[2]};
           q[k] += 1;
-          const double d = at(b, q) - v;
-          s += d * d;
+          const float d = at(b, q) - v;
+          s = s + d * d;
         }
-        ++gh[hist_bin(std::sqrt(s) / e)];
+        ++gh[grad_bin(s * inv_e2)];
         ++ng;
       }
       // Lorenzo residual
       bool bwd = true;
       for (int k = 0; k < ndims; ++k) bwd = bwd && c[k] >= 1;
       if (bwd) {
-        double pred;
+        float pred;
         if (ndims == 3) {
           auto nb = [&](int dz, int dy, int dx) {
             const int64_t q[3] = {c[0] - dz, c[1] - dy, c[2] - dx};
             return at(b, q);
           };
-          const double a = (nb(1, 0, 0) + nb(0, 1, 0)) + nb(0, 0, 1);
-          const double bb = (nb(1, 1, 0) + nb(1, 0, 1)) + nb(0, 1, 1);
+          const float a = (nb(1, 0, 0) + nb(0, 1, 0)) + nb(0, 0, 1);
+          const float bb = (nb(1, 1, 0) + nb(1, 0, 1)) + nb(0, 1, 1);
           pred = (a - bb) + nb(1, 1, 1);
         } else {
           const int64_t qy[3] = {c[0] - 1, c[1], 0}, qx[3] = {c[0], c[1] - 1, 0},
                         qxy[3] = {c[0] - 1, c[1] - 1, 0};
           pred = (at(b, qy) + at(b, qx)) - at(b, qxy);
         }
-        ++lh[hist_bin(std::fabs(v - pred) / e)];
+        ++lh[res_bin(std::fabs(v - pred) * inv_e)];
         ++nl;
       }
       // interpolation residuals at h = 1, 2, 4 along every axis
@@ -197,15 +217,15 @@ int orc_features(const float* x, int ndims, const int64_t* dims, double rel_eb, 
           if (c[k] % (2 * h) != h || c[k] - 3 * h < 0 || c[k] + 3 * h > bd[k] - 1) continue;
           int64_t q[3] = {c[0], c[1], c[2]};
           q[k] = c[k] - 3 * h;
-          const double a3 = at(b, q);
+          const float a3 = at(b, q);
           q[k] = c[k] - h;
-          const double a1 = at(b, q);
+          const float a1 = at(b, q);
           q[k] = c[k] + h;
-          const double b1 = at(b, q);
+          const float b1 = at(b, q);
           q[k] = c[k] + 3 * h;
-          const double b3 = at(b, q);
-          lin[j] += std::fabs(v - (a1 + b1) * 0.5);
-          cub[j] += std::fabs(v - (9.0 * (a1 + b1) - (a3 + b3)) / 16.0);
+          const float b3 = at(b, q);
+          lin[j] += (double)std::fabs(v - (a1 + b1) * 0.5f);
+          cub[j] += (double)std::fabs(v - ((9.0f * (a1 + b1)) - (a3 + b3)) * 0.0625f);
           ++nint[j];
         }
       }

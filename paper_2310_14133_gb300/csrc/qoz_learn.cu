@@ -17,8 +17,12 @@
 //   [58..60] / [61..63] L(mean |x - linear| / |x - cubic| interpolation) at
 //   half-strides 1, 2, 4 along every axis (Sec. 5.1 stencils, targets with
 //   all four neighbours in the block).
-// Sums run in double; integer bins are decided in double by frexp, which is
-// exact, from differences formed in the same order everywhere.
+// Differences, predictions, products and bin arguments are binary32
+// operations in one fixed order (so the integer bins, decided by frexp,
+// are the same on every implementation); 1/e and 1/e^2 are rounded to
+// binary32 once; sums over points are compensated binary32 per thread and
+// double across threads.  The gradient bin is floor(floor(log2 t) / 2) + 12
+// with t = |gradient|^2 / e^2 (no square root).
 //
 // Network: z = (f - mean) / std; h1 = relu(W1 z + b1); h2 = relu(W2 h1 + b2);
 // o = W3 h2 + b3; heads o[0:2] interpolator, o[2:8] dimension order,
@@ -66,18 +70,42 @@ struct FeatArgs {
   int bd0, bd1, bd2;
   int is2d;
   int chunks;              // CTAs per block
-  double e;
-  double c;                // shift of the second moment
+  float inv_e, inv_e2;     // (float)(1 / e), (float)(1 / e^2)
+  long long c_index;       // the value that shifts the second moment
   FeatPart* parts;
 };
 
-__device__ __forceinline__ int hist_bin(double g) {
-  if (!(g > 0.0)) return 0;
+__device__ __forceinline__ int clamp_bin(int b) { return b < 0 ? 0 : (b > 23 ? 23 : b); }
+
+__device__ __forceinline__ int res_bin(float r) {
+  if (!(r > 0.0f)) return 0;
+  if (isinf(r)) return 23;
   int ex = 0;
-  frexp(g, &ex);
-  int b = ex - 1 + 12;
-  return b < 0 ? 0 : (b > 23 ? 23 : b);
+  frexpf(r, &ex);
+  return clamp_bin(ex - 1 + 12);
 }
+
+__device__ __forceinline__ int grad_bin(float t) {
+  if (!(t > 0.0f)) return 0;
+  if (isinf(t)) return 23;
+  int ex = 0;
+  frexpf(t, &ex);
+  const int k = ex - 1;
+  const int half = k >= 0 ? k / 2 : -((-k + 1) / 2);
+  return clamp_bin(half + 12);
+}
+
+// Compensated binary32 sum (Kahan).
+struct KSumF {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = __fsub_rn(v, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
 
 __global__ void __launch_bounds__(kFeatThreads) feature_kernel(const FeatArgs a) {
   __shared__ unsigned sc[kNCnt];
@@ -85,83 +113,91 @@ __global__ void __launch_bounds__(kFeatThreads) feature_kernel(const FeatArgs a)
   for (int i = threadIdx.x; i < kNCnt; i += blockDim.x) sc[i] = 0u;
   __syncthreads();
   const int blk = blockIdx.y;
-  const long long o0 = a.origins[3 * blk], o1 = a.origins[3 * blk + 1],
-                  o2 = a.origins[3 * blk + 2];
-  const int bd[3] = {a.bd0, a.bd1, a.bd2};
-  const long long st[3] = {a.n1 * a.n2, a.n2, 1};
-  const long long bpts = (long long)a.bd0 * a.bd1 * a.bd2;
-  const long long p0 = (long long)blockIdx.x * kFeatChunk;
-  const long long p1 = min(bpts, p0 + kFeatChunk);
-  const int a_lo = a.is2d ? 1 : 0;  // active axes a_lo..2; slot = axis - a_lo
-  double sum[kNSum];
-#pragma unroll
-  for (int i = 0; i < kNSum; ++i) sum[i] = 0.0;
+  const int bd0 = a.bd0, bd1 = a.bd1, bd2 = a.bd2;
+  const int st0 = (int)(a.n1 * a.n2), st1 = (int)a.n2;  // field < 2^32 points: fits int
+  const float* blk_base = a.x + (long long)a.origins[3 * blk] * a.n1 * a.n2 +
+                          (long long)a.origins[3 * blk + 1] * a.n2 + a.origins[3 * blk + 2];
+  const double cshift = (double)__ldg(a.x + a.c_index);
+  const int bpts = bd0 * bd1 * bd2;
+  const int p0 = blockIdx.x * kFeatChunk;
+  const int p1 = min(bpts, p0 + kFeatChunk);
+  const bool is2d = a.is2d;
+  const int bdv[3] = {bd0, bd1, bd2};
+  const int stv[3] = {st0, st1, 1};
+  double m1 = 0.0, m2 = 0.0;
+  KSumF d1[3], d2[3], lin[3], cub[3];
   unsigned n = 0, n1[3] = {0, 0, 0}, n2[3] = {0, 0, 0}, nint[3] = {0, 0, 0}, ng = 0, nl = 0;
-  for (long long p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+  for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
     int c[3];
-    long long r = p;
-    c[2] = (int)(r % bd[2]);
-    r /= bd[2];
-    c[1] = (int)(r % bd[1]);
-    c[0] = (int)(r / bd[1]);
-    const float* base = a.x + (o0 + c[0]) * st[0] + (o1 + c[1]) * st[1] + (o2 + c[2]);
-    auto X = [&](int dz, int dy, int dx) {
-      return (double)base[dz * st[0] + dy * st[1] + dx];
-    };
-    const double v = (double)base[0];
-    const double u = v - a.c;
-    sum[0] += u;
-    sum[1] += u * u;
+    c[2] = p % bd2;
+    const int r = p / bd2;
+    c[1] = r % bd1;
+    c[0] = r / bd1;
+    const float* pt = blk_base + (long long)c[0] * st0 + (long long)c[1] * st1 + c[2];
+    const float v = pt[0];
+    const double u = (double)v - cshift;
+    m1 += u;
+    m2 += u * u;
     ++n;
     bool fwd = true, bwd = true;
-    double gs = 0.0;
-    for (int ax = a_lo; ax < 3; ++ax) {
-      const int k = ax - a_lo;
-      const int dz = ax == 0, dy = ax == 1, dx = ax == 2;
-      const bool hasf = c[ax] + 1 < bd[ax], hasb = c[ax] >= 1;
+    float gs = 0.0f;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      if (is2d && ax == 0) continue;
+      const int k = is2d ? ax - 1 : ax;
+      const int sa = stv[ax], ca = c[ax], ba = bdv[ax];
+      const bool hasf = ca + 1 < ba, hasb = ca >= 1;
       fwd = fwd && hasf;
       bwd = bwd && hasb;
       if (hasf) {
-        const double xf = X(dz, dy, dx);
-        sum[2 + k] += fabs(xf - v);
+        const float xf = pt[sa];
+        const float df = __fsub_rn(xf, v);
+        d1[k].add(fabsf(df));
         ++n1[k];
+        gs = __fadd_rn(gs, __fmul_rn(df, df));
         if (hasb) {
-          sum[5 + k] += fabs((xf + X(-dz, -dy, -dx)) - 2.0 * v);
+          d2[k].add(fabsf(__fsub_rn(__fadd_rn(xf, pt[-sa]), __fmul_rn(2.0f, v))));
           ++n2[k];
         }
       }
+#pragma unroll
       for (int j = 0; j < 3; ++j) {
         const int h = 1 << j;
-        if (c[ax] % (2 * h) != h || c[ax] - 3 * h < 0 || c[ax] + 3 * h > bd[ax] - 1) continue;
-        const double a3 = X(-3 * h * dz, -3 * h * dy, -3 * h * dx);
-        const double a1 = X(-h * dz, -h * dy, -h * dx);
-        const double b1 = X(h * dz, h * dy, h * dx);
-        const double b3 = X(3 * h * dz, 3 * h * dy, 3 * h * dx);
-        sum[8 + j] += fabs(v - (a1 + b1) * 0.5);
-        sum[11 + j] += fabs(v - (9.0 * (a1 + b1) - (a3 + b3)) / 16.0);
+        if ((ca & (2 * h - 1)) != h || ca - 3 * h < 0 || ca + 3 * h > ba - 1) continue;
+        const float a3 = pt[-3 * h * sa], a1 = pt[-h * sa], b1 = pt[h * sa], b3 = pt[3 * h * sa];
+        const float s1 = __fadd_rn(a1, b1);
+        lin[j].add(fabsf(__fsub_rn(v, __fmul_rn(s1, 0.5f))));
+        cub[j].add(fabsf(
+            __fsub_rn(v, __fmul_rn(__fsub_rn(__fmul_rn(9.0f, s1), __fadd_rn(a3, b3)), 0.0625f))));
         ++nint[j];
       }
     }
     if (fwd) {
-      for (int ax = a_lo; ax < 3; ++ax) {
-        const double d = X(ax == 0, ax == 1, ax == 2) - v;
-        gs += d * d;
-      }
-      atomicAdd(&sc[12 + hist_bin(sqrt(gs) / a.e)], 1u);
+      atomicAdd(&sc[12 + grad_bin(__fmul_rn(gs, a.inv_e2))], 1u);
       ++ng;
     }
     if (bwd) {
-      double pred;
-      if (!a.is2d) {
-        const double s1 = (X(-1, 0, 0) + X(0, -1, 0)) + X(0, 0, -1);
-        const double s2 = (X(-1, -1, 0) + X(-1, 0, -1)) + X(0, -1, -1);
-        pred = (s1 - s2) + X(-1, -1, -1);
+      float pred;
+      if (!is2d) {
+        const float sa = __fadd_rn(__fadd_rn(pt[-st0], pt[-st1]), pt[-1]);
+        const float sb = __fadd_rn(__fadd_rn(pt[-st0 - st1], pt[-st0 - 1]), pt[-st1 - 1]);
+        pred = __fadd_rn(__fsub_rn(sa, sb), pt[-st0 - st1 - 1]);
       } else {
-        pred = (X(0, -1, 0) + X(0, 0, -1)) - X(0, -1, -1);
+        pred = __fsub_rn(__fadd_rn(pt[-st1], pt[-1]), pt[-st1 - 1]);
       }
-      atomicAdd(&sc[36 + hist_bin(fabs(v - pred) / a.e)], 1u);
+      atomicAdd(&sc[36 + res_bin(__fmul_rn(fabsf(__fsub_rn(v, pred)), a.inv_e))], 1u);
       ++nl;
     }
+  }
+  double sum[kNSum];
+  sum[0] = m1;
+  sum[1] = m2;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    sum[2 + k] = d1[k].value();
+    sum[5 + k] = d2[k].value();
+    sum[8 + k] = lin[k].value();
+    sum[11 + k] = cub[k].value();
   }
   // counts (exact)
   atomicAdd(&sc[0], n);
@@ -190,19 +226,28 @@ __global__ void __launch_bounds__(kFeatThreads) feature_kernel(const FeatArgs a)
   for (int i = threadIdx.x; i < kNCnt; i += blockDim.x) out->cnt[i] = sc[i];
 }
 
-// One thread: fold the partials in order, evaluate the 64 features.
-__global__ void feature_final_kernel(const FeatPart* parts, int nparts, double rel_eb,
-                                     double vrange, double e, double npoints, int ndims,
-                                     double* fd, float* ff) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double s[kNSum];
-  unsigned long long c[kNCnt];
-  for (int i = 0; i < kNSum; ++i) s[i] = 0.0;
-  for (int i = 0; i < kNCnt; ++i) c[i] = 0ull;
-  for (int p = 0; p < nparts; ++p) {
-    for (int i = 0; i < kNSum; ++i) s[i] += parts[p].sum[i];
-    for (int i = 0; i < kNCnt; ++i) c[i] += parts[p].cnt[i];
+// Fold the partials (one thread per accumulated quantity, partials in
+// order), then one thread evaluates the 64 features.
+constexpr int kFinalThreads = 128;
+static_assert(kNSum + kNCnt <= kFinalThreads, "one thread per quantity");
+
+__global__ void __launch_bounds__(kFinalThreads)
+    feature_final_kernel(const FeatPart* parts, int nparts, double rel_eb, double vrange,
+                         double e, double npoints, int ndims, double* fd, float* ff) {
+  __shared__ double s[kNSum];
+  __shared__ unsigned long long c[kNCnt];
+  const int t = threadIdx.x;
+  if (t < kNSum) {
+    double v = 0.0;
+    for (int p = 0; p < nparts; ++p) v += parts[p].sum[t];
+    s[t] = v;
+  } else if (t < kNSum + kNCnt) {
+    unsigned long long v = 0ull;
+    for (int p = 0; p < nparts; ++p) v += parts[p].cnt[t - kNSum];
+    c[t - kNSum] = v;
   }
+  __syncthreads();
+  if (t != 0) return;
   double f[NF];
   for (int i = 0; i < NF; ++i) f[i] = 0.0;
   const double n = (double)c[0];
@@ -273,26 +318,54 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_kernel(
     sm.z[s][f] = s0 + s < B ? __fdiv_rn(__fsub_rn(X[(s0 + s) * NF + f], mean[f]), d) : 0.0f;
   }
   __syncthreads();
-  for (int i = t; i < kMlpS * NH; i += kMlpThreads) {
-    const int s = i / NH, o = i % NH;
-    float acc = b1[o];
-    for (int k = 0; k < NF; ++k) acc = __fadd_rn(acc, __fmul_rn(W1[o * NF + k], sm.z[s][k]));
-    sm.h1[s][o] = acc > 0.0f ? acc : 0.0f;
+  // dense layers: one warp per output row, the row's weights read once
+  // (coalesced) and applied to every sample of the CTA; lane partial sums
+  // are combined by a fixed shuffle tree
+  const int warp = t >> 5, lane = t & 31;
+  constexpr int kWarps = kMlpThreads / 32;
+  for (int o = warp; o < NH; o += kWarps) {
+    const float w0 = W1[o * NF + lane], w1 = W1[o * NF + 32 + lane];
+    for (int s = 0; s < kMlpS; ++s) {
+      float v = __fadd_rn(__fmul_rn(w0, sm.z[s][lane]), __fmul_rn(w1, sm.z[s][32 + lane]));
+      for (int off = 16; off > 0; off >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, off));
+      if (lane == 0) {
+        const float acc = __fadd_rn(b1[o], v);
+        sm.h1[s][o] = acc > 0.0f ? acc : 0.0f;
+      }
+    }
   }
   __syncthreads();
-  for (int i = t; i < kMlpS * NH; i += kMlpThreads) {
-    const int s = i / NH, o = i % NH;
-    float acc = b2[o];
-    for (int k = 0; k < NH; ++k) acc = __fadd_rn(acc, __fmul_rn(W2[o * NH + k], sm.h1[s][k]));
-    sm.h2[s][o] = acc > 0.0f ? acc : 0.0f;
+  for (int o = warp; o < NH; o += kWarps) {
+    float w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[j] = W2[o * NH + 32 * j + lane];
+    for (int s = 0; s < kMlpS; ++s) {
+      float v = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v = __fadd_rn(v, __fmul_rn(w[j], sm.h1[s][32 * j + lane]));
+      for (int off = 16; off > 0; off >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, off));
+      if (lane == 0) {
+        const float acc = __fadd_rn(b2[o], v);
+        sm.h2[s][o] = acc > 0.0f ? acc : 0.0f;
+      }
+    }
   }
   __syncthreads();
-  for (int i = t; i < kMlpS * NO; i += kMlpThreads) {
-    const int s = i / NO, o = i % NO;
-    float acc = b3[o];
-    for (int k = 0; k < NH; ++k) acc = __fadd_rn(acc, __fmul_rn(W3[o * NH + k], sm.h2[s][k]));
-    sm.o[s][o] = acc;
-    if (!TRAIN && s0 + s < B) logits[(s0 + s) * NO + o] = acc;
+  for (int o = warp; o < NO; o += kWarps) {
+    float w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[j] = W3[o * NH + 32 * j + lane];
+    for (int s = 0; s < kMlpS; ++s) {
+      float v = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v = __fadd_rn(v, __fmul_rn(w[j], sm.h2[s][32 * j + lane]));
+      for (int off = 16; off > 0; off >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, off));
+      if (lane == 0) {
+        const float acc = __fadd_rn(b3[o], v);
+        sm.o[s][o] = acc;
+        if (!TRAIN && s0 + s < B) logits[(s0 + s) * NO + o] = acc;
+      }
+    }
   }
   if (!TRAIN) return;
   __syncthreads();
@@ -498,6 +571,7 @@ qoz_status features_impl(const float* d_field, const qoz_shape& shape, double re
   const int chunks = (int)((bpts + kFeatChunk - 1) / kFeatChunk);
   const long long nparts = (long long)chunks * sm.nb;
   if (sm.nb > 65535) return fail(QOZ_EUNSUPPORTED, "too many sampled blocks");
+  if (bpts > 0x7fffffffLL) return fail(QOZ_EUNSUPPORTED, "sampled block too large");
   void* scratch = nullptr;
   const size_t ob = ((size_t)sm.origins.size() * sizeof(int) + 255) & ~(size_t)255;
   cudaError_t ce = dev_alloc(&scratch, ob + sizeof(FeatPart) * nparts, s);
@@ -506,14 +580,6 @@ qoz_status features_impl(const float* d_field, const qoz_shape& shape, double re
   FeatPart* parts = (FeatPart*)((char*)scratch + ob);
   ce = cudaMemcpyAsync(d_org, sm.origins.data(), sizeof(int) * sm.origins.size(),
                        cudaMemcpyHostToDevice, s);
-  // the moments are shifted by the first sampled value
-  float c0 = 0.0f;
-  if (ce == cudaSuccess) {
-    const long long i0 = ((long long)sm.origins[0] * r.n[1] + sm.origins[1]) * r.n[2] +
-                         sm.origins[2];
-    ce = cudaMemcpyAsync(&c0, d_field + i0, sizeof(float), cudaMemcpyDeviceToHost, s);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-  }
   if (ce == cudaSuccess) {
     FeatArgs a;
     a.x = d_field;
@@ -525,16 +591,18 @@ qoz_status features_impl(const float* d_field, const qoz_shape& shape, double re
     a.bd2 = sm.bd[2];
     a.is2d = r.ndims == 2;
     a.chunks = chunks;
-    a.e = e;
-    a.c = (double)c0;
+    a.inv_e = (float)(1.0 / e);
+    a.inv_e2 = (float)(1.0 / (e * e));
+    // the second moment is shifted by the first sampled value
+    a.c_index = ((long long)sm.origins[0] * r.n[1] + sm.origins[1]) * r.n[2] + sm.origins[2];
     a.parts = parts;
     feature_kernel<<<dim3(chunks, sm.nb), kFeatThreads, 0, s>>>(a);
     note_launch(1);
     ce = cudaGetLastError();
   }
   if (ce == cudaSuccess) {
-    feature_final_kernel<<<1, 32, 0, s>>>(parts, (int)nparts, rel_eb, vr, e, (double)r.N,
-                                          r.ndims, fd, ff);
+    feature_final_kernel<<<1, kFinalThreads, 0, s>>>(parts, (int)nparts, rel_eb, vr, e,
+                                                     (double)r.N, r.ndims, fd, ff);
     note_launch(1);
     ce = cudaGetLastError();
   }
