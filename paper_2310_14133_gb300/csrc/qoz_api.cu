@@ -150,6 +150,17 @@ void grid_dims(const Resolved& r, int k, long long g[3]) {
   for (int p = 0; p < 3; ++p) g[p] = ceil_div(r.n[p], 1LL << k);
 }
 
+// Row pitch of the compact array of the grid subsampled by 2^k: the field's
+// own rows at k = 0 and the anchor grid's at k = L (both dense); rounded up to
+// 8 values in between, so that every row of a coarse reconstruction (float)
+// or code (uint16) array starts on a 16-byte boundary (the tile kernel's
+// bulk tensor copies need that).
+long long grid_pitch(const Resolved& r, int k) {
+  long long g[3];
+  grid_dims(r, k, g);
+  return (k == 0 || k >= r.L) ? g[2] : (g[2] + 7) & ~7LL;
+}
+
 Coarse coarse_layout(const Resolved& r, bool with_codes) {
   Coarse c;
   memset(&c, 0, sizeof(c));
@@ -157,7 +168,7 @@ Coarse coarse_layout(const Resolved& r, bool with_codes) {
   for (int k = 1; k < r.L; ++k) {
     long long g[3];
     grid_dims(r, k, g);
-    const size_t n = (size_t)(g[0] * g[1] * g[2]);
+    const size_t n = (size_t)(g[0] * g[1] * grid_pitch(r, k));
     c.roff[k] = tot;
     tot += (n * sizeof(float) + 255) & ~(size_t)255;
     if (with_codes) {
@@ -185,11 +196,12 @@ void level_geometry(const Resolved& r, int l, LevelLaunch* L) {
     L->g[p] = g[p];
     L->xs[p] = f * fst[p];
   }
-  L->cs[0] = gc[1] * gc[2];
-  L->cs[1] = gc[2];
+  const long long pc = grid_pitch(r, l), pg = grid_pitch(r, l - 1);
+  L->cs[0] = gc[1] * pc;
+  L->cs[1] = pc;
   L->cs[2] = 1;
-  L->os[0] = g[1] * g[2];
-  L->os[1] = g[2];
+  L->os[0] = g[1] * pg;
+  L->os[1] = pg;
   L->os[2] = 1;
   L->is2d = r.ndims == 2;
   L->order3 = r.ndims == 3 ? r.p.order[l - 1] : (r.p.order[l - 1] == 0 ? 0 : 1);
@@ -219,6 +231,7 @@ cudaError_t run_levels(bool decompress, const Resolved& r, const float* x, uint1
       L.err = err;
     } else {
       L.x = x;
+      L.err = err;  // compress: bit 2 reports a tile copy that never landed
       L.cin = l == r.L ? nullptr : (const uint16_t*)(coarse_base + cl.coff[l]);
       L.cout = l > 1 ? (uint16_t*)(coarse_base + cl.coff[l - 1]) : codes;
       L.ul = ul;
@@ -347,7 +360,7 @@ qoz_status compress_impl(const float* d_field, const qoz_shape& shape, bool rel,
     UnpredList ul{uidx, uval, d_count, cap};
     if (e == cudaSuccess)
       e = run_levels(false, r, d_field, b->d_codes, b->d_anchors, coarse, cl, d_recon, d_bt, ul,
-                     nullptr, nullptr, 0, nullptr, b->d_hist, s);
+                     nullptr, nullptr, 0, b->d_err, b->d_hist, s);
     if (e == cudaSuccess) {
       ProfScope ps(QOZ_STAGE_HIST, s);
       e = launch_check(launch_hist_remove_anchors(b->d_hist, b->na, s));
@@ -357,8 +370,12 @@ qoz_status compress_impl(const float* d_field, const qoz_shape& shape, bool rel,
                           s);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(&hs->bt, d_bt, sizeof(BoundTable), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&hs->err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "compress"));
+    if (hs->err != 0)
+      return cleanup(fail(QOZ_ETIMEOUT, "a tile's bulk copy did not complete (flag %d)", hs->err));
 
     const long long count = (long long)hs->count;
     if (count > cap) {

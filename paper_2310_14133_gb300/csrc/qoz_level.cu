@@ -1,10 +1,114 @@
 // Single-field launches of the level kernel (templates in qoz_level_impl.cuh),
 // the anchor gather, and the kernel-attribute helper shared with the batched
 // launches.
+#include <cuda.h>
+
+#include <cstdlib>
+
 #include "qoz_level_impl.cuh"
 
 namespace qoz {
 namespace {
+
+// Level-1 compression with bulk tensor copies (see level_tile_tma).
+template <int A0, int A1, int A2, int TZ, int TY, int TX, bool HIST>
+__global__ void __launch_bounds__(kThreads, 2)
+    level_tma_kernel(const LevelLaunch a, int nt1, int nt2, const __grid_constant__ CUtensorMap mx,
+                     const __grid_constant__ CUtensorMap mrc,
+                     const __grid_constant__ CUtensorMap mcc,
+                     const __grid_constant__ CUtensorMap mout, int use_out) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  level_tile_tma<A0, A1, A2, TZ, TY, TX, HIST>(a, smem, &mbar, blockIdx.x, nt1, nt2, &mx, &mrc,
+                                               &mcc, use_out ? &mout : nullptr);
+}
+
+// A rank-3 tiled tensor map (dims and box innermost first; strides in bytes
+// of dims 1 and 2); false when the driver rejects it.
+bool encode_map(CUtensorMap* m, CUtensorMapDataType type, const void* base,
+                const unsigned long long dims[3], const unsigned long long strides[2],
+                const unsigned box[3]) {
+  const cuuint32_t es[3] = {1, 1, 1};
+  const cuuint64_t d[3] = {dims[0], dims[1], dims[2]};
+  const cuuint64_t st[2] = {strides[0], strides[1]};
+  const cuuint32_t bx[3] = {box[0], box[1], box[2]};
+  return cuTensorMapEncodeTiled(m, type, 3, const_cast<void*>(base), d, st, bx, es,
+                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool tma_enabled() {
+  static const int on = [] {
+    const char* e = getenv("QOZ_LEVEL_TMA");
+    return (e && e[0] == '0') ? 0 : 1;
+  }();
+  return on != 0;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// Runs the level-1 launch with bulk tensor copies when the grid is the field
+// itself and every array's rows start on 16-byte boundaries; returns false
+// (nothing launched) otherwise.
+template <int A0, int A1, int A2, int TZ, int TY, int TX, bool HIST>
+bool try_launch_tma(const LevelLaunch& a, cudaStream_t s, cudaError_t* err) {
+  using G = Geo<A0, A1, A2, TZ, TY, TX>;
+  if (!tma_enabled() || a.decompress || a.xs[2] != 1 || !a.cin || !a.rc) return false;
+  if (!aligned16(a.x) || !aligned16(a.rc) || !aligned16(a.cin)) return false;
+  if (a.xs[1] % 4 || a.xs[0] % 4 || a.cs[1] % 8 || a.cs[0] % 8) return false;
+  const unsigned long long g2 = a.g[2], g1 = a.g[1], g0 = a.g[0];
+  const unsigned long long c2 = (g2 + 1) / 2, c1 = (g1 + 1) / 2, c0 = (g0 + 1) / 2;
+  CUtensorMap mx, mrc, mcc, mout;
+  memset(&mout, 0, sizeof(mout));
+  {
+    const unsigned long long d[3] = {g2, g1, g0};
+    const unsigned long long st[2] = {4ull * a.xs[1], 4ull * a.xs[0]};
+    const unsigned bx[3] = {G::EX, G::EY, G::EZ};
+    if (!encode_map(&mx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, a.x, d, st, bx)) return false;
+  }
+  {
+    const unsigned long long d[3] = {c2, c1, c0};
+    const unsigned long long st[2] = {4ull * a.cs[1], 4ull * a.cs[0]};
+    const unsigned bx[3] = {G::CBX, G::CBY, G::CBZ};
+    if (!encode_map(&mrc, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, a.rc, d, st, bx)) return false;
+  }
+  {
+    const unsigned long long d[3] = {c2, c1, c0};
+    const unsigned long long st[2] = {2ull * a.cs[1], 2ull * a.cs[0]};
+    const unsigned bx[3] = {G::CCX, G::CCY, G::CCZ};
+    if (!encode_map(&mcc, CU_TENSOR_MAP_DATA_TYPE_UINT16, a.cin, d, st, bx)) return false;
+  }
+  int use_out = 0;
+  if (aligned16(a.cout) && a.os[1] % 8 == 0 && a.os[0] % 8 == 0) {
+    const unsigned long long d[3] = {g2, g1, g0};
+    const unsigned long long st[2] = {2ull * a.os[1], 2ull * a.os[0]};
+    const unsigned bx[3] = {TX, TY, TZ};
+    use_out = encode_map(&mout, CU_TENSOR_MAP_DATA_TYPE_UINT16, a.cout, d, st, bx) ? 1 : 0;
+  }
+  static unsigned long long done = 0;
+  constexpr size_t smem = G::tma_smem_bytes(HIST);
+  static_assert(smem + 64 <= 112 * 1024, "tile must leave room for two CTAs per SM");
+  const void* fn = (const void*)level_tma_kernel<A0, A1, A2, TZ, TY, TX, HIST>;
+  cudaError_t e = ensure_smem_attr(fn, &done, smem);
+  if (e != cudaSuccess) {
+    *err = e;
+    return true;
+  }
+  const long long nt0 = (a.g[0] + TZ - 1) / TZ;
+  const long long nt1 = (a.g[1] + TY - 1) / TY;
+  const long long nt2 = (a.g[2] + TX - 1) / TX;
+  const long long nb = nt0 * nt1 * nt2;
+  if (nb > 0x7fffffffLL) {
+    *err = cudaErrorInvalidConfiguration;
+    return true;
+  }
+  level_tma_kernel<A0, A1, A2, TZ, TY, TX, HIST><<<(unsigned)nb, kThreads, smem, s>>>(
+      a, (int)nt1, (int)nt2, mx, mrc, mcc, mout, use_out);
+  note_launch(1);
+  *err = cudaGetLastError();
+  return true;
+}
 
 template <int A0, int A1, int A2, int TZ, int TY, int TX, bool DECOMP, bool HIST>
 __global__ void __launch_bounds__(kThreads, 2) level_kernel(const LevelLaunch a, int nt1, int nt2,
@@ -30,6 +134,10 @@ __global__ void anchor_gather_kernel(const float* __restrict__ x, float* __restr
 template <int A0, int A1, int A2, int TZ, int TY, int TX, bool DECOMP, bool HIST>
 cudaError_t launch_one(const LevelLaunch& a, cudaStream_t s) {
   using G = Geo<A0, A1, A2, TZ, TY, TX>;
+  if constexpr (!DECOMP) {
+    cudaError_t te = cudaSuccess;
+    if (try_launch_tma<A0, A1, A2, TZ, TY, TX, HIST>(a, s, &te)) return te;
+  }
   static unsigned long long done = 0;
   constexpr size_t smem = G::smem_bytes(DECOMP, HIST);
   static_assert(smem <= 112 * 1024, "tile must leave room for two CTAs per SM");

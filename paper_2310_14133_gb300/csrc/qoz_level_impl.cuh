@@ -125,6 +125,25 @@ struct Geo {
     return NCMAIN + k * NOS + ((other + 2) >> 1);
   }
   __device__ static constexpr int cidx(int z, int y, int x) { return (z * TY + y) * TX + x; }
+  // Bulk-copy layout (level 1): the coarse reconstruction box covers even
+  // local coordinates -4 .. T + 2 (z, y) and -8 .. TX + 6 (x, so that its
+  // first column sits on a 16-byte boundary); the coarse code box covers the
+  // tile's own coarse points.
+  static constexpr int CBZ = TZ / 2 + 4, CBY = TY / 2 + 4, CBX = TX / 2 + 8;
+  static constexpr int kCB = CBZ * CBY * CBX;
+  static constexpr int CCZ = (TZ + 1) / 2, CCY = (TY + 1) / 2, CCX = TX / 2;
+  static constexpr int kCC = CCZ * CCY * CCX;
+  __device__ static constexpr int cbidx(int z, int y, int x) {
+    return ((z / 2 + 2) * CBY + (y / 2 + 2)) * CBX + (x / 2 + 4);
+  }
+  static constexpr size_t align128(size_t v) { return (v + 127) & ~size_t(127); }
+  static constexpr size_t kTmaS = align128(sizeof(float) * kS);
+  static constexpr size_t kTmaCB = align128(sizeof(float) * kCB);
+  static constexpr size_t kTmaC16 = align128(sizeof(uint16_t) * kC);
+  static constexpr size_t kTmaCC = align128(sizeof(uint16_t) * kCC);
+  __host__ __device__ static constexpr size_t tma_smem_bytes(bool hist) {
+    return 128 + kTmaS + kTmaCB + kTmaC16 + kTmaCC + (hist ? kHistBytes : 0);
+  }
   // true when every position the tile touches lies inside the grid
   __device__ static bool interior(int oz, int oy, int ox, int g0, int g1, int g2) {
     return oz >= 4 && oz + TZ + 4 <= g0 && oy >= 4 && oy + TY + 4 <= g1 && ox >= 4 &&
@@ -198,7 +217,7 @@ __device__ __forceinline__ void finish(const LevelLaunch& a, const Ctx& c, float
 
 // ---- a pass along z or y: lines along P, lanes on consecutive x, R = the
 // other of z and y.
-template <class G, int PASS, bool DECOMP, bool INTERIOR>
+template <class G, int PASS, bool DECOMP, bool INTERIOR, bool CBOX = false>
 __device__ __forceinline__ void pass_line(const LevelLaunch& a, const Ctx& c, float* S,
                                           const float* CR, const uint16_t* IN16,
                                           uint16_t* C16) {
@@ -241,8 +260,12 @@ __device__ __forceinline__ void pass_line(const LevelLaunch& a, const Ctx& c, fl
     for (int k = 0; k < SEG + 3; ++k) {
       const int pos = p0 - 2 + 2 * k;
       if (PASS == 1 && (pos < 0 || pos >= TP)) {
-        const int kk = pos < 0 ? 0 : (pos == TP ? 1 : 2);
-        w[k] = CR[G::side_row(kk, lr) * G::HX + ((lx + 4) >> 1)];
+        if constexpr (CBOX) {
+          w[k] = CR[G::cbidx(P == 0 ? pos : lr, P == 1 ? pos : lr, lx)];
+        } else {
+          const int kk = pos < 0 ? 0 : (pos == TP ? 1 : 2);
+          w[k] = CR[G::side_row(kk, lr) * G::HX + ((lx + 4) >> 1)];
+        }
       } else {
         w[k] = S[rbase + pos * SP];
       }
@@ -266,6 +289,44 @@ __device__ __forceinline__ void pass_line(const LevelLaunch& a, const Ctx& c, fl
   }
 }
 
+// ---- a pass along x on an interior tile: one odd-x target per lane in U
+// rows that share an item (consecutive rows along a no-halo axis, so the
+// whole item is inside the tile or outside it together).
+template <class G, int PASS, bool DECOMP, int U, bool ALONG_Y>
+__device__ __forceinline__ void pass_x_rows(const LevelLaunch& a, const Ctx& c, float* S,
+                                            const uint16_t* IN16, uint16_t* C16) {
+  constexpr int A0 = G::A0, A1 = G::A1, A2 = G::A2;
+  using SZ = Span<RoleOf<A0, A1, A2, PASS, 0>::value, G::TZ>;
+  using SY = Span<RoleOf<A0, A1, A2, PASS, 1>::value, G::TY>;
+  constexpr int NTX = G::TX / 2;
+  constexpr int NY = ALONG_Y ? SY::count / U : SY::count;
+  constexpr int NZ = ALONG_Y ? SZ::count : SZ::count / U;
+  constexpr int items = NZ * NY * NTX;
+  // shared-memory and code-tile distance between the rows of one item
+  constexpr int DS = ALONG_Y ? SY::step * G::EX : SZ::step * G::EY * G::EX;
+  constexpr int DC = ALONG_Y ? SY::step * G::TX : SZ::step * G::TY * G::TX;
+  for (int it = threadIdx.x; it < items; it += kThreads) {
+    const int mm = it % NTX;
+    const int t = it / NTX;
+    const int yi = t % NY;
+    const int zi = t / NY;
+    const int lz = SZ::start + (ALONG_Y ? zi : zi * U) * SZ::step;
+    const int ly = SY::start + (ALONG_Y ? yi * U : yi) * SY::step;
+    const int lx = 2 * mm + 1;
+    const bool inside = ALONG_Y ? (lz >= 0 && lz < G::TZ) : (ly >= 0 && ly < G::TY);
+    const int si0 = G::row(lz, ly) * G::EX + lx + 4;
+    const int ci0 = G::cidx(lz, ly, lx);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int si = si0 + u * DS;
+      const float pred = predict_full(S[si - 3], S[si - 1], S[si + 1], S[si + 3], c.interp);
+      const int uz = ALONG_Y ? lz : lz + u * SZ::step, uy = ALONG_Y ? ly + u * SY::step : ly;
+      finish<DECOMP>(a, c, S, IN16, si, pred, inside, C16 + ci0 + u * DC, c.oz + uz, c.oy + uy,
+                     c.ox + lx);
+    }
+  }
+}
+
 // ---- a pass along x: one odd-x target per lane.
 template <class G, int PASS, bool DECOMP, bool INTERIOR>
 __device__ __forceinline__ void pass_x(const LevelLaunch& a, const Ctx& c, float* S,
@@ -274,6 +335,14 @@ __device__ __forceinline__ void pass_x(const LevelLaunch& a, const Ctx& c, float
   using SZ = Span<RoleOf<A0, A1, A2, PASS, 0>::value, G::TZ>;
   using SY = Span<RoleOf<A0, A1, A2, PASS, 1>::value, G::TY>;
   constexpr int NTX = G::TX / 2;
+  if constexpr (INTERIOR && RoleOf<A0, A1, A2, PASS, 1>::value == kAny && SY::count % 4 == 0) {
+    pass_x_rows<G, PASS, DECOMP, 4, true>(a, c, S, IN16, C16);
+    return;
+  } else if constexpr (INTERIOR && RoleOf<A0, A1, A2, PASS, 0>::value == kAny &&
+                       SZ::count % 4 == 0) {
+    pass_x_rows<G, PASS, DECOMP, 4, false>(a, c, S, IN16, C16);
+    return;
+  }
   constexpr int items = SZ::count * SY::count * NTX;
   for (int it = threadIdx.x; it < items; it += kThreads) {
     const int mm = it % NTX;
@@ -298,14 +367,14 @@ __device__ __forceinline__ void pass_x(const LevelLaunch& a, const Ctx& c, float
   }
 }
 
-template <class G, int PASS, bool DECOMP, bool INTERIOR>
+template <class G, int PASS, bool DECOMP, bool INTERIOR, bool CBOX = false>
 __device__ __forceinline__ void run_pass(const LevelLaunch& a, const Ctx& c, float* S,
                                          const float* CR, const uint16_t* IN16, uint16_t* C16) {
   constexpr int P = PASS == 1 ? G::A0 : (PASS == 2 ? G::A1 : G::A2);
   if constexpr (P == 2)
     pass_x<G, PASS, DECOMP, INTERIOR>(a, c, S, IN16, C16);
   else
-    pass_line<G, PASS, DECOMP, INTERIOR>(a, c, S, CR, IN16, C16);
+    pass_line<G, PASS, DECOMP, INTERIOR, CBOX>(a, c, S, CR, IN16, C16);
 }
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
@@ -538,6 +607,233 @@ __device__ __forceinline__ void level_tile(const LevelLaunch& a, unsigned char* 
   }
 }
 
+
+// ---- level 1 with bulk tensor copies (TMA) ---------------------------------
+// The tile's input box (field over the main box, coarse reconstruction box,
+// coarse code box) arrives as three cp.async.bulk.tensor copies issued by
+// one thread and tracked by one mbarrier; the tile's codes leave as one
+// bulk tensor store.  The passes are the same as in level_tile (pass 1 reads
+// the coarse values beyond the tile along A0 from the coarse box).
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* m, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(m)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* m, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(m)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* m, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(m)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* map, int c0, int c1, int c2,
+                                            uint64_t* m) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(m))
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const void* map, int c0, int c1, int c2,
+                                             const void* src) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::
+                   "l"(map),
+               "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read0() {
+  asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+// Polls of the tile's mbarrier before the CTA gives up (a copy that has not
+// landed after this many polls is reported through a.err, bit 2).
+constexpr unsigned kTmaWaitPolls = 1u << 24;
+
+// map_x: the field (f32, dims x, y, z); map_rc: coarse reconstruction (f32);
+// map_cc: coarse codes (u16); map_out: the codes (u16), or nullptr to store
+// them with plain stores.
+template <int A0, int A1, int A2, int TZ, int TY, int TX, bool HIST>
+__device__ __forceinline__ void level_tile_tma(const LevelLaunch& a, unsigned char* smem_raw,
+                                               uint64_t* mbar, int b, int nt1, int nt2,
+                                               const void* map_x, const void* map_rc,
+                                               const void* map_cc, const void* map_out) {
+  using G = Geo<A0, A1, A2, TZ, TY, TX>;
+  // 128-byte aligned sub-buffers (bulk tensor copies need it)
+  unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  float* S = reinterpret_cast<float*>(smem);
+  float* CB = reinterpret_cast<float*>(smem + G::kTmaS);
+  uint16_t* C16 = reinterpret_cast<uint16_t*>(smem + G::kTmaS + G::kTmaCB);
+  uint16_t* CC = reinterpret_cast<uint16_t*>(smem + G::kTmaS + G::kTmaCB + G::kTmaC16);
+  unsigned* SH =
+      reinterpret_cast<unsigned*>(smem + G::kTmaS + G::kTmaCB + G::kTmaC16 + G::kTmaCC);
+
+  Ctx c;
+  {
+    const int tx = b % nt2;
+    b /= nt2;
+    const int ty = b % nt1;
+    const int tz = b / nt1;
+    c.oz = tz * TZ;
+    c.oy = ty * TY;
+    c.ox = tx * TX;
+  }
+  c.g0 = (int)a.g[0];
+  c.g1 = (int)a.g[1];
+  c.g2 = (int)a.g[2];
+  const int lvl = a.level - 1;
+  c.el = a.bt->el[lvl];
+  c.two_e = a.bt->two_e[lvl];
+  c.inv = a.bt->inv[lvl];
+  c.interp = a.interp;
+
+  if (threadIdx.x == 0) {
+    mbar_init(mbar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    constexpr unsigned kBytes = (unsigned)(sizeof(float) * (G::kS + G::kCB) +
+                                           sizeof(uint16_t) * G::kCC);
+    mbar_expect_tx(mbar, kBytes);
+    tma_load_3d(S, map_x, c.ox - 4, c.oy - G::HY, c.oz - G::HZ, mbar);
+    tma_load_3d(CB, map_rc, c.ox / 2 - 4, c.oy / 2 - 2, c.oz / 2 - 2, mbar);
+    tma_load_3d(CC, map_cc, c.ox / 2, c.oy / 2, c.oz / 2, mbar);
+  }
+  if (HIST)
+    for (int i = threadIdx.x; i < kHistWin; i += kThreads) SH[i] = 0;
+  bool landed = false;
+  for (unsigned it = 0; it < kTmaWaitPolls; ++it)
+    if (mbar_try_wait(mbar, 0)) {
+      landed = true;
+      break;
+    }
+  if (!__syncthreads_and(landed)) {
+    if (threadIdx.x == 0 && a.err) atomicOr(a.err, 2);
+    return;
+  }
+
+  // coarse values into the even positions of the main box's coarse rows
+  for (int i = threadIdx.x; i < G::NCMAIN * G::HX; i += kThreads) {
+    const int j = i % G::HX;
+    const int r = i / G::HX;
+    const int lz = G::ZLO + 2 * (r / G::NCY), ly = G::YLO + 2 * (r % G::NCY);
+    S[G::row(lz, ly) * G::EX + 2 * j] = CB[G::cbidx(lz, ly, 2 * j - 4)];
+  }
+  // the tile's coarse codes into the code tile
+  for (int i = threadIdx.x; i < G::kCC; i += kThreads) {
+    const int ix = i % G::CCX;
+    const int t = i / G::CCX;
+    const int iy = t % G::CCY;
+    const int iz = t / G::CCY;
+    C16[G::cidx(2 * iz, 2 * iy, 2 * ix)] = CC[i];
+  }
+  __syncthreads();
+
+  if (G::interior(c.oz, c.oy, c.ox, c.g0, c.g1, c.g2)) {
+    run_pass<G, 1, false, true, true>(a, c, S, CB, nullptr, C16);
+    __syncthreads();
+    run_pass<G, 2, false, true, true>(a, c, S, CB, nullptr, C16);
+    __syncthreads();
+    run_pass<G, 3, false, true, true>(a, c, S, CB, nullptr, C16);
+  } else {
+    run_pass<G, 1, false, false, true>(a, c, S, CB, nullptr, C16);
+    __syncthreads();
+    run_pass<G, 2, false, false, true>(a, c, S, CB, nullptr, C16);
+    __syncthreads();
+    run_pass<G, 3, false, false, true>(a, c, S, CB, nullptr, C16);
+  }
+  if (map_out) fence_proxy_async_smem();  // code tile written: visible to the bulk store
+  __syncthreads();
+  if (map_out && threadIdx.x == 0) {
+    tma_store_3d(map_out, c.ox, c.oy, c.oz, C16);
+    bulk_commit();
+  }
+
+  // histogram, reconstruction output and (without a store map) the codes,
+  // eight points per thread along x
+  static_assert(TX % 8 == 0, "tile rows hold whole groups of eight");
+  constexpr int NG = TZ * TY * (TX / 8);
+  const bool need_loop = HIST || a.rout || !map_out;
+  if (need_loop) {
+    const unsigned os0 = (unsigned)a.os[0], os1 = (unsigned)a.os[1];
+    const bool rows8 = (a.os[1] % 8) == 0 && (a.os[0] % 8) == 0;
+    const bool vec_codes = rows8 && (reinterpret_cast<uintptr_t>(a.cout) & 15) == 0;
+    const bool vec_rec = rows8 && (reinterpret_cast<uintptr_t>(a.rout) & 15) == 0;
+    for (int i = threadIdx.x; i < NG; i += kThreads) {
+      const int gx = i % (TX / 8);
+      const int t = i / (TX / 8);
+      const int ly = t % TY;
+      const int lz = t / TY;
+      const int lx = gx * 8;
+      const int cz = c.oz + lz, cy = c.oy + ly, cx = c.ox + lx;
+      if (cz >= c.g0 || cy >= c.g1 || cx >= c.g2) continue;
+      const unsigned oi = (unsigned)cz * os0 + (unsigned)cy * os1 + (unsigned)cx;
+      const bool full = cx + 8 <= c.g2;
+      const uint4 v = *reinterpret_cast<const uint4*>(C16 + G::cidx(lz, ly, lx));
+      if (!map_out) {
+        if (full && vec_codes) {
+          *reinterpret_cast<uint4*>(a.cout + oi) = v;
+        } else {
+          const uint16_t* cv = reinterpret_cast<const uint16_t*>(&v);
+          for (int k = 0; k < 8 && cx + k < c.g2; ++k) a.cout[oi + k] = cv[k];
+        }
+      }
+      if (HIST) {
+        const unsigned wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          if (cx + k >= c.g2) break;
+          const unsigned cd = (wv[k >> 1] >> (16 * (k & 1))) & 0xffffu;
+          const unsigned kk = cd - (unsigned)kHistLo;
+          if (kk < (unsigned)kHistWin)
+            atomicAdd(&SH[kk], 1u);
+          else
+            atomicAdd(&a.hist[cd], 1u);
+        }
+      }
+      if (a.rout) {
+        const float* srow = S + G::row(lz, ly) * G::EX + lx + 4;
+        const float4 v0 = *reinterpret_cast<const float4*>(srow);
+        const float4 v1 = *reinterpret_cast<const float4*>(srow + 4);
+        if (full && vec_rec) {
+          float4* o4 = reinterpret_cast<float4*>(a.rout + oi);
+          o4[0] = v0;
+          o4[1] = v1;
+        } else {
+          const float r8[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+          for (int k = 0; k < 8 && cx + k < c.g2; ++k) a.rout[oi + k] = r8[k];
+        }
+      }
+    }
+  }
+  if (HIST) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kHistWin; i += kThreads)
+      if (SH[i]) atomicAdd(&a.hist[kHistLo + i], SH[i]);
+  }
+  // the code tile must stay in shared memory until the store has read it
+  if (map_out && threadIdx.x == 0) bulk_wait_read0();
+}
 
 }  // namespace
 }  // namespace qoz

@@ -136,11 +136,24 @@ __global__ void __launch_bounds__(kTrialThreads, 1) trial_kernel(const TrialArgs
       const int c2n = m2 - 1 >= s2 ? (m2 - 1 - s2) / d2 + 1 : 0;
       const int sa = ax == 0 ? st0 : (ax == 1 ? st1 : 1);
       const int na = ax == 0 ? m0 : (ax == 1 ? m1 : m2);
-      for (int row = warp; row < c0n * c1n; row += nw) {
-        const int i0 = row / c1n;
+      // every target of the pass, flattened (x fastest) so that all lanes
+      // work; the quotients come from a binary32 reciprocal, which is exact
+      // for dividends below 70000 and divisors below 4100 (checked
+      // exhaustively), else from integer division
+      const int nrow = c0n * c1n;
+      const int items = nrow * c2n;
+      const bool fdiv = items < 70000 && c2n < 4100 && c1n < 4100;
+      const float rc2 = 1.0f / (float)(c2n > 0 ? c2n : 1);
+      const float rc1 = 1.0f / (float)(c1n > 0 ? c1n : 1);
+      for (int it = threadIdx.x; it < items; it += kTrialThreads) {
+        const int row =
+            fdiv ? __float2int_rz(__fmul_rn(__fadd_rn(__int2float_rn(it), 0.5f), rc2)) : it / c2n;
+        const int i2 = it - row * c2n;
+        const int i0 =
+            fdiv ? __float2int_rz(__fmul_rn(__fadd_rn(__int2float_rn(row), 0.5f), rc1)) : row / c1n;
         const int i1 = row - i0 * c1n;
         const int z = s0 + i0 * d0, y = s1 + i1 * d1;
-        for (int i2 = lane; i2 < c2n; i2 += 32) {
+        {
           const int xx = s2 + i2 * d2;
           const int li = z * st0 + y * st1 + xx;
           const int ca = ax == 0 ? z : (ax == 1 ? y : xx);
@@ -167,11 +180,17 @@ __global__ void __launch_bounds__(kTrialThreads, 1) trial_kernel(const TrialArgs
             ++unp;
           }
           if (a.hist) {
-            const unsigned kk = (unsigned)code - (unsigned)kTHistLo;
-            if (kk < (unsigned)kTHistWin)
-              atomicAdd(&SH[kk], 1u);
-            else
-              atomicAdd(&a.hist[(size_t)cand * 65536 + code], 1u);
+            // lanes with equal codes add once (smooth data puts most of a
+            // warp's codes in one or two bins)
+            const unsigned peers = __match_any_sync(__activemask(), (unsigned)code);
+            if (lane == __ffs(peers) - 1) {
+              const unsigned kk = (unsigned)code - (unsigned)kTHistLo;
+              const unsigned n = (unsigned)__popc(peers);
+              if (kk < (unsigned)kTHistWin)
+                atomicAdd(&SH[kk], n);
+              else
+                atomicAdd(&a.hist[(size_t)cand * 65536 + code], n);
+            }
           }
         }
       }

@@ -87,6 +87,17 @@ def test_orders_uneven_3d(q, orc, order, interp):
     run_parity(q, orc, x, 1e-3, interp=interp, order=order, alpha=1.25, beta=3.0)
 
 
+@pytest.mark.parametrize("order", range(6))
+@pytest.mark.parametrize("shape", [(37, 50, 148), (45, 70, 136)])
+def test_orders_bulk_copy_shapes(q, orc, order, shape):
+    # rows of 148 / 136 values start on 16-byte boundaries: level 1 takes the
+    # bulk tensor copies (loads only for 148, loads and the code store for
+    # 136), with ragged tiles on every axis
+    import synth
+    x = synth.grf(shape, 5.0 / 3.0, seed=20 + order, n_modes=96).numpy()
+    run_parity(q, orc, x, 1e-3, interp=order % 2, order=order, alpha=1.5, beta=2.0)
+
+
 def test_mixed_levels(q, orc):
     import synth
     x = synth.grf((70, 45, 99), 2.5, seed=3, n_modes=64).numpy()
