@@ -2,6 +2,7 @@
 // the anchor gather, and the kernel-attribute helper shared with the batched
 // launches.
 #include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include <cstdlib>
 
@@ -23,19 +24,38 @@ __global__ void __launch_bounds__(kThreads, 2)
                                                &mcc, use_out ? &mout : nullptr);
 }
 
+// The driver's tensor-map encoder, looked up through the runtime (the
+// library does not link the driver library itself, so that it loads on
+// hosts without a GPU driver); null when unavailable.
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
 // A rank-3 tiled tensor map (dims and box innermost first; strides in bytes
 // of dims 1 and 2); false when the driver rejects it.
 bool encode_map(CUtensorMap* m, CUtensorMapDataType type, const void* base,
                 const unsigned long long dims[3], const unsigned long long strides[2],
                 const unsigned box[3]) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
+  if (!enc) return false;
   const cuuint32_t es[3] = {1, 1, 1};
   const cuuint64_t d[3] = {dims[0], dims[1], dims[2]};
   const cuuint64_t st[2] = {strides[0], strides[1]};
   const cuuint32_t bx[3] = {box[0], box[1], box[2]};
-  return cuTensorMapEncodeTiled(m, type, 3, const_cast<void*>(base), d, st, bx, es,
-                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return enc(m, type, 3, const_cast<void*>(base), d, st, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 bool tma_enabled() {
