@@ -294,6 +294,90 @@ __global__ void __launch_bounds__(kTrialThreads, 1) trial_kernel(const TrialArgs
   }
 }
 
+// Optimal prefix-code cost of one candidate's pooled histogram (the rate
+// estimate of Sec. 6.1): one CTA compacts the non-zero counts, sorts them
+// and runs the two-queue merge (leaves and merged nodes both come out in
+// non-decreasing order; every merge adds its weight).  Integer arithmetic:
+// the same total as the host computation.  More than kHuffMax distinct codes
+// are left to the host (flag 1).
+constexpr int kHuffThreads = 1024;
+constexpr int kHuffMax = 4096;
+
+__global__ void __launch_bounds__(kHuffThreads)
+    huffman_cost_kernel(const unsigned* __restrict__ hist, unsigned long long* bits, int* flag) {
+  __shared__ unsigned cnt[kHuffMax];
+  __shared__ unsigned node[kHuffMax];  // merged weights: at most the sampled points (< 2^32)
+  __shared__ int nsh;
+  const unsigned* h = hist + (size_t)blockIdx.x * 65536;
+  const int t = threadIdx.x, lane = t & 31;
+  if (t == 0) nsh = 0;
+  __syncthreads();
+  // coalesced scan; each warp appends its non-zero counts (any order: they
+  // are sorted next)
+  for (int i = t; i < 65536; i += kHuffThreads) {
+    const unsigned v = h[i];
+    const unsigned ball = __ballot_sync(0xffffffffu, v != 0u);
+    if (ball == 0u) continue;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&nsh, __popc(ball));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (v != 0u) {
+      const int k = base + __popc(ball & ((1u << lane) - 1u));
+      if (k < kHuffMax) cnt[k] = v;
+    }
+  }
+  __syncthreads();
+  const int n = nsh;
+  if (n > kHuffMax) {
+    if (t == 0) {
+      flag[blockIdx.x] = 1;
+      bits[blockIdx.x] = 0ull;
+    }
+    return;
+  }
+  int P = 1;
+  while (P < n) P <<= 1;
+  for (int i = n + t; i < P; i += kHuffThreads) cnt[i] = 0xffffffffu;
+  __syncthreads();
+  for (int size = 2; size <= P; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = t; i < P; i += kHuffThreads) {
+        const int j = i ^ stride;
+        if (j > i) {
+          const bool up = (i & size) == 0;
+          const unsigned a = cnt[i], b = cnt[j];
+          if ((a > b) == up) {
+            cnt[i] = b;
+            cnt[j] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  if (t == 0) {
+    unsigned long long total = 0ull;
+    if (n == 1) {
+      total = cnt[0];
+    } else if (n > 1) {
+      int li = 0, ni = 0, nn = 0;
+      for (int m = 1; m < n; ++m) {
+        unsigned ab[2];
+        for (int k = 0; k < 2; ++k) {
+          if (ni < nn && (li >= n || node[ni] < cnt[li]))
+            ab[k] = node[ni++];
+          else
+            ab[k] = cnt[li++];
+        }
+        const unsigned sum = ab[0] + ab[1];
+        total += sum;
+        node[nn++] = sum;
+      }
+    }
+    bits[blockIdx.x] = total;
+    flag[blockIdx.x] = 0;
+  }
+}
+
 // ------------------------------------------------------------- host side
 
 
@@ -388,6 +472,7 @@ class Tuner {
     dev_free(d_cands_, s_);
     dev_free(d_out_, s_);
     dev_free(d_hist_, s_);
+    dev_free(d_bits_, s_);
   }
 
   qoz_status init() {
@@ -408,11 +493,14 @@ class Tuner {
       dev_free(d_cands_, s_);
       dev_free(d_out_, s_);
       dev_free(d_hist_, s_);
+      dev_free(d_bits_, s_);
       cap_c_ = nc;
       if (dev_alloc((void**)&d_cands_, sizeof(TrialCand) * nc, s_) != cudaSuccess ||
           dev_alloc((void**)&d_out_, sizeof(double) * kOutStride * nc * sm_.nb, s_) !=
               cudaSuccess ||
-          dev_alloc((void**)&d_hist_, sizeof(unsigned) * 65536 * (size_t)nc, s_) != cudaSuccess)
+          dev_alloc((void**)&d_hist_, sizeof(unsigned) * 65536 * (size_t)nc, s_) != cudaSuccess ||
+          dev_alloc((void**)&d_bits_, (sizeof(unsigned long long) + sizeof(int)) * nc, s_) !=
+              cudaSuccess)
         return fail(QOZ_ENOMEM, "tuner allocation");
     }
     cudaError_t e = cudaMemcpyAsync(d_cands_, cands.data(), sizeof(TrialCand) * nc,
@@ -454,18 +542,37 @@ class Tuner {
       e = launch_check(cudaGetLastError());
     }
     trials_ += nc;
+    unsigned long long* d_bits = reinterpret_cast<unsigned long long*>(d_bits_);
+    int* d_flag = reinterpret_cast<int*>(d_bits + nc);
+    if (e == cudaSuccess && full) {
+      huffman_cost_kernel<<<nc, kHuffThreads, 0, s_>>>(d_hist_, d_bits, d_flag);
+      note_launch(1);
+      e = launch_check(cudaGetLastError());
+    }
     std::vector<double> out((size_t)kOutStride * nc * sm_.nb);
-    std::vector<unsigned> hist;
+    std::vector<unsigned long long> hbits(nc, 0ull);
+    std::vector<int> hflag(nc, 0);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(out.data(), d_out_, sizeof(double) * out.size(), cudaMemcpyDeviceToHost,
                           s_);
-    if (e == cudaSuccess && full) {
-      hist.resize((size_t)65536 * nc);
-      e = cudaMemcpyAsync(hist.data(), d_hist_, sizeof(unsigned) * hist.size(),
+    if (e == cudaSuccess && full)
+      e = cudaMemcpyAsync(hbits.data(), d_bits, sizeof(unsigned long long) * nc,
                           cudaMemcpyDeviceToHost, s_);
-    }
+    if (e == cudaSuccess && full)
+      e = cudaMemcpyAsync(hflag.data(), d_flag, sizeof(int) * nc, cudaMemcpyDeviceToHost, s_);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s_);
     if (e != cudaSuccess) return cuda_fail(e, "tuner trial");
+    // histograms with too many distinct codes for the device sort: host
+    std::vector<unsigned> hist;
+    for (int c = 0; c < nc && full; ++c) {
+      if (!hflag[c]) continue;
+      hist.resize(65536);
+      e = cudaMemcpyAsync(hist.data(), d_hist_ + (size_t)c * 65536, sizeof(unsigned) * 65536,
+                          cudaMemcpyDeviceToHost, s_);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s_);
+      if (e != cudaSuccess) return cuda_fail(e, "tuner histogram");
+      hbits[c] = huffman_bits_u32(hist.data(), 65536);
+    }
     res->assign(nc, TrialResult{0, 0, 0});
     for (int c = 0; c < nc; ++c) {
       double l1 = 0, l1n = 0, unp = 0, sse = 0, mx = 0, ss = 0, sn = 0;
@@ -482,8 +589,7 @@ class Tuner {
       TrialResult& t = (*res)[c];
       t.l1_mean = l1n > 0 ? l1 / l1n : 0.0;
       if (full) {
-        const double bits = (double)huffman_bits_u32(&hist[(size_t)c * 65536], 65536) +
-                            32.0 * unp + 32.0 * (double)sm_.anchors;
+        const double bits = (double)hbits[c] + 32.0 * unp + 32.0 * (double)sm_.anchors;
         t.B = bits / (double)sm_.npts;
         if (metric_ == QOZ_METRIC_PSNR) {
           const double mse = sse / (double)sm_.npts;
@@ -511,6 +617,7 @@ class Tuner {
   TrialCand* d_cands_ = nullptr;
   double* d_out_ = nullptr;
   unsigned* d_hist_ = nullptr;
+  void* d_bits_ = nullptr;  // per candidate: prefix-code bits (u64), then host-fallback flags (int)
   int cap_c_ = 0;
   int trials_ = 0;
 };
