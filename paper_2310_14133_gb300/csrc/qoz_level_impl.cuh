@@ -45,6 +45,9 @@ constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kHistLo = kRadius - 2048;  // shared histogram window [32768-2048, 32768+2048)
 constexpr int kHistWin = 4096;
+// the bulk-copy kernel's smaller window [32768-512, 32768+512)
+constexpr int kTmaHistLo = kRadius - 512;
+constexpr int kTmaHistWin = 1024;
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -78,16 +81,17 @@ struct Span {
 // Targets per work item along a line of NT targets with `lines` lines: at
 // most 16 (register window), halved while the items would still fill no more
 // than half the block.
-__host__ __device__ constexpr int pick_seg(int NT, int lines) {
+__host__ __device__ constexpr int pick_seg(int NT, int lines, int threads = kThreads) {
   int seg = NT < 16 ? NT : 16;
-  while (seg > 4 && NT % (seg / 2) == 0 && (NT / seg) * lines * 2 <= kThreads) seg /= 2;
+  while (seg > 4 && NT % (seg / 2) == 0 && (NT / seg) * lines * 2 <= threads) seg /= 2;
   return seg;
 }
 
-template <int A0_, int A1_, int A2_, int TZ_, int TY_, int TX_>
+template <int A0_, int A1_, int A2_, int TZ_, int TY_, int TX_, int THR_ = kThreads>
 struct Geo {
   static constexpr int A0 = A0_, A1 = A1_, A2 = A2_;
   static constexpr int TZ = TZ_, TY = TY_, TX = TX_;
+  static constexpr int kThr = THR_;  // threads of the CTA that owns the tile
   __host__ __device__ static constexpr int T(int p) { return p == 0 ? TZ : (p == 1 ? TY : TX); }
   static constexpr int HZ = A0 == 0 ? 0 : kHalo;
   static constexpr int HY = A0 == 1 ? 0 : kHalo;
@@ -142,7 +146,7 @@ struct Geo {
   static constexpr size_t kTmaC16 = align128(sizeof(uint16_t) * kC);
   static constexpr size_t kTmaCC = align128(sizeof(uint16_t) * kCC);
   __host__ __device__ static constexpr size_t tma_smem_bytes(bool hist) {
-    return 128 + kTmaS + kTmaCB + kTmaC16 + kTmaCC + (hist ? kHistBytes : 0);
+    return 128 + kTmaS + kTmaCB + kTmaC16 + kTmaCC + (hist ? sizeof(unsigned) * kTmaHistWin : 0);
   }
   // true when every position the tile touches lies inside the grid
   __device__ static bool interior(int oz, int oy, int ox, int g0, int g1, int g2) {
@@ -232,7 +236,7 @@ __device__ __forceinline__ void pass_line(const LevelLaunch& a, const Ctx& c, fl
   constexpr int TP = G::T(P);
   constexpr int NT = TP / 2;
   if (NT == 0) return;
-  constexpr int SEG = NT == 0 ? 1 : (PASS == 1 ? NT : pick_seg(NT, SX::count * SR::count));
+  constexpr int SEG = NT == 0 ? 1 : (PASS == 1 ? NT : pick_seg(NT, SX::count * SR::count, G::kThr));
   constexpr int NSEG = NT / SEG;
   static_assert(NT == 0 || NT % SEG == 0, "segments must tile the line");
   static_assert(PASS != 1 || NSEG == 1 || NT == 0, "the first pass walks whole lines");
@@ -242,7 +246,7 @@ __device__ __forceinline__ void pass_line(const LevelLaunch& a, const Ctx& c, fl
   const int gP = gsel<P>(c), gR = gsel<R>(c);
   const int oP = osel<P>(c), oR = osel<R>(c);
 
-  for (int it = threadIdx.x; it < items; it += kThreads) {
+  for (int it = threadIdx.x; it < items; it += G::kThr) {
     const int m = it % SX::count;
     const int t = it / SX::count;
     const int ri = t % SR::count;
@@ -305,7 +309,7 @@ __device__ __forceinline__ void pass_x_rows(const LevelLaunch& a, const Ctx& c, 
   // shared-memory and code-tile distance between the rows of one item
   constexpr int DS = ALONG_Y ? SY::step * G::EX : SZ::step * G::EY * G::EX;
   constexpr int DC = ALONG_Y ? SY::step * G::TX : SZ::step * G::TY * G::TX;
-  for (int it = threadIdx.x; it < items; it += kThreads) {
+  for (int it = threadIdx.x; it < items; it += G::kThr) {
     const int mm = it % NTX;
     const int t = it / NTX;
     const int yi = t % NY;
@@ -344,7 +348,7 @@ __device__ __forceinline__ void pass_x(const LevelLaunch& a, const Ctx& c, float
     return;
   }
   constexpr int items = SZ::count * SY::count * NTX;
-  for (int it = threadIdx.x; it < items; it += kThreads) {
+  for (int it = threadIdx.x; it < items; it += G::kThr) {
     const int mm = it % NTX;
     const int t = it / NTX;
     const int yi = t % SY::count;
@@ -672,12 +676,12 @@ constexpr unsigned kTmaWaitPolls = 1u << 24;
 // map_x: the field (f32, dims x, y, z); map_rc: coarse reconstruction (f32);
 // map_cc: coarse codes (u16); map_out: the codes (u16), or nullptr to store
 // them with plain stores.
-template <int A0, int A1, int A2, int TZ, int TY, int TX, bool HIST>
+template <int A0, int A1, int A2, int TZ, int TY, int TX, int THR, bool HIST>
 __device__ __forceinline__ void level_tile_tma(const LevelLaunch& a, unsigned char* smem_raw,
                                                uint64_t* mbar, int b, int nt1, int nt2,
                                                const void* map_x, const void* map_rc,
                                                const void* map_cc, const void* map_out) {
-  using G = Geo<A0, A1, A2, TZ, TY, TX>;
+  using G = Geo<A0, A1, A2, TZ, TY, TX, THR>;
   // 128-byte aligned sub-buffers (bulk tensor copies need it)
   unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   float* S = reinterpret_cast<float*>(smem);
@@ -720,7 +724,7 @@ __device__ __forceinline__ void level_tile_tma(const LevelLaunch& a, unsigned ch
     tma_load_3d(CC, map_cc, c.ox / 2, c.oy / 2, c.oz / 2, mbar);
   }
   if (HIST)
-    for (int i = threadIdx.x; i < kHistWin; i += kThreads) SH[i] = 0;
+    for (int i = threadIdx.x; i < kTmaHistWin; i += THR) SH[i] = 0;
   bool landed = false;
   for (unsigned it = 0; it < kTmaWaitPolls; ++it)
     if (mbar_try_wait(mbar, 0)) {
@@ -733,14 +737,14 @@ __device__ __forceinline__ void level_tile_tma(const LevelLaunch& a, unsigned ch
   }
 
   // coarse values into the even positions of the main box's coarse rows
-  for (int i = threadIdx.x; i < G::NCMAIN * G::HX; i += kThreads) {
+  for (int i = threadIdx.x; i < G::NCMAIN * G::HX; i += THR) {
     const int j = i % G::HX;
     const int r = i / G::HX;
     const int lz = G::ZLO + 2 * (r / G::NCY), ly = G::YLO + 2 * (r % G::NCY);
     S[G::row(lz, ly) * G::EX + 2 * j] = CB[G::cbidx(lz, ly, 2 * j - 4)];
   }
   // the tile's coarse codes into the code tile
-  for (int i = threadIdx.x; i < G::kCC; i += kThreads) {
+  for (int i = threadIdx.x; i < G::kCC; i += THR) {
     const int ix = i % G::CCX;
     const int t = i / G::CCX;
     const int iy = t % G::CCY;
@@ -779,7 +783,7 @@ __device__ __forceinline__ void level_tile_tma(const LevelLaunch& a, unsigned ch
     const bool rows8 = (a.os[1] % 8) == 0 && (a.os[0] % 8) == 0;
     const bool vec_codes = rows8 && (reinterpret_cast<uintptr_t>(a.cout) & 15) == 0;
     const bool vec_rec = rows8 && (reinterpret_cast<uintptr_t>(a.rout) & 15) == 0;
-    for (int i = threadIdx.x; i < NG; i += kThreads) {
+    for (int i = threadIdx.x; i < NG; i += THR) {
       const int gx = i % (TX / 8);
       const int t = i / (TX / 8);
       const int ly = t % TY;
@@ -804,8 +808,8 @@ __device__ __forceinline__ void level_tile_tma(const LevelLaunch& a, unsigned ch
         for (int k = 0; k < 8; ++k) {
           if (cx + k >= c.g2) break;
           const unsigned cd = (wv[k >> 1] >> (16 * (k & 1))) & 0xffffu;
-          const unsigned kk = cd - (unsigned)kHistLo;
-          if (kk < (unsigned)kHistWin)
+          const unsigned kk = cd - (unsigned)kTmaHistLo;
+          if (kk < (unsigned)kTmaHistWin)
             atomicAdd(&SH[kk], 1u);
           else
             atomicAdd(&a.hist[cd], 1u);
@@ -828,8 +832,8 @@ __device__ __forceinline__ void level_tile_tma(const LevelLaunch& a, unsigned ch
   }
   if (HIST) {
     __syncthreads();
-    for (int i = threadIdx.x; i < kHistWin; i += kThreads)
-      if (SH[i]) atomicAdd(&a.hist[kHistLo + i], SH[i]);
+    for (int i = threadIdx.x; i < kTmaHistWin; i += THR)
+      if (SH[i]) atomicAdd(&a.hist[kTmaHistLo + i], SH[i]);
   }
   // the code tile must stay in shared memory until the store has read it
   if (map_out && threadIdx.x == 0) bulk_wait_read0();
