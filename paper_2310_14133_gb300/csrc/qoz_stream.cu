@@ -188,8 +188,14 @@ qoz_status qoz_blob_serialize(const qoz_blob* b, void* h_buf, size_t cap, size_t
   h.n_points = b->N;
   h.n_anchors = b->na;
   h.n_unpred = b->nu;
-  // zero the padding bytes so that the stream is a pure function of the blob
-  memset(out + sizeof(Header), 0, L.total - sizeof(Header));
+  // zero the padding after each section (under 8 bytes each) so that the
+  // stream is a pure function of the blob; the copies fill the rest
+  const size_t ends[4][2] = {{L.anchors + sizeof(float) * b->na, L.uidx},
+                             {L.uidx + sizeof(long long) * b->nu, L.uval},
+                             {L.uval + sizeof(float) * b->nu, L.codes},
+                             {L.codes + sizeof(uint16_t) * b->N, L.total}};
+  for (const auto& g : ends)
+    if (g[1] > g[0]) memset(out + g[0], 0, g[1] - g[0]);
   unsigned long long* d_acc = nullptr;
   cudaError_t e = dev_alloc((void**)&d_acc, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return fail(QOZ_ENOMEM, "checksum scratch");
