@@ -462,16 +462,23 @@ def main():
     if not args.no_e2e:
         hx = torch.empty((n, n, n), dtype=torch.float32, pin_memory=True)
         hx.copy_(x)
-        out = torch.empty(ser_bytes + 4096, dtype=torch.uint8, pin_memory=True)
-        # two device input buffers: the next step's host-to-device copy runs
-        # on its own stream while the current step compresses
+        # Three streams: the copy stream brings the next field in, the compute
+        # stream tunes and compresses, the read-back stream serializes each
+        # blob to pinned host memory while the next step computes (a blob is
+        # freed one step later, once its read-back is done).
+        outs = [torch.empty(ser_bytes + 4096, dtype=torch.uint8, pin_memory=True)
+                for _ in range(2)]
         bufs = [torch.empty_like(x), torch.empty_like(x)]
         copy_stream = torch.cuda.Stream()
+        d2h_stream = torch.cuda.Stream()
         ev_in = [torch.cuda.Event(), torch.cuda.Event()]
         ev_free = [torch.cuda.Event(), torch.cuda.Event()]
+        ev_done = [torch.cuda.Event(), torch.cuda.Event()]
+        ev_read = [torch.cuda.Event(), torch.cuda.Event()]
 
         def e2e_run(nsteps):
             cur = torch.cuda.current_stream()
+            pending = None
             with torch.cuda.stream(copy_stream):
                 bufs[0].copy_(hx, non_blocking=True)
                 ev_in[0].record(copy_stream)
@@ -486,9 +493,17 @@ def main():
                         ev_in[j].record(copy_stream)
                 cur.wait_event(ev_in[i])
                 b, _ = step(bufs[i])
-                b.serialize(out)
-                b.free()
+                ev_done[i].record(cur)
                 ev_free[i].record(cur)
+                d2h_stream.wait_event(ev_done[i])
+                b.serialize_async(outs[i], stream=d2h_stream)
+                ev_read[i].record(d2h_stream)
+                if pending is not None:
+                    cur.wait_event(pending[1])
+                    pending[0].free()
+                pending = (b, ev_read[i])
+            cur.wait_event(pending[1])
+            pending[0].free()
 
         e2e_run(2)
         barrier()
@@ -499,9 +514,10 @@ def main():
         e2e = {"value": 4.0 * N * world / e2e_s / 1e9, "unit": "GB/s",
                "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": ser_bytes,
                "ms_per_step": e2e_s * 1e3,
-               "pipeline": "each step copies its field from pinned host memory (on a copy "
-                           "stream, overlapping the previous step) and reads its serialized "
-                           "stream back to pinned host memory"}
+               "pipeline": "each step copies its field from pinned host memory (copy "
+                           "stream) and reads its serialized stream back to pinned host memory "
+                           "(asynchronous serialize on a read-back stream); the copies overlap "
+                           "the neighbouring steps' tune + compress"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,

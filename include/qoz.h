@@ -160,6 +160,15 @@ qoz_status qoz_blob_histogram(const qoz_blob* b, uint32_t* h_hist, void* stream)
  * h_buf = NULL only *used is set (the required size).  Synchronises. */
 qoz_status qoz_blob_serialize(const qoz_blob* b, void* h_buf, size_t cap, size_t* used,
                               void* stream);
+/* Same stream, enqueued without waiting: the payload copies are issued on
+ * `stream`, and a host callback on the stream writes the header once the
+ * copies are done.  h_buf must be pinned host memory (or the copies become
+ * synchronous) and must stay valid until the stream has passed the call; the
+ * stream is complete once the stream (or an event recorded after the call)
+ * is synchronized.  The blob must not be freed before then, except by
+ * stream-ordered qoz_blob_free on the same stream. */
+qoz_status qoz_blob_serialize_async(const qoz_blob* b, void* h_buf, size_t cap, size_t* used,
+                                    void* stream);
 qoz_status qoz_blob_deserialize(const void* h_buf, size_t size, void* stream, qoz_blob** out);
 
 /* Releases the blob's device memory, stream-ordered on the stream the blob

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <vector>
 
@@ -160,15 +161,10 @@ qoz_status qoz_blob_copy_arrays(const qoz_blob* b, uint16_t* d_codes, int64_t* d
   return QOZ_OK;
 }
 
-qoz_status qoz_blob_serialize(const qoz_blob* b, void* h_buf, size_t cap, size_t* used,
-                              void* stream) {
-  if (!b || !used) return fail(QOZ_EINVAL, "NULL argument");
-  const Layout L = layout_of(b->na, b->nu, b->N);
-  *used = L.total;
-  if (!h_buf) return QOZ_OK;
-  if (cap < L.total) return fail(QOZ_EINVAL, "buffer holds %zu bytes, %zu needed", cap, L.total);
-  cudaStream_t s = stream ? (cudaStream_t)stream : b->stream;
-  unsigned char* out = (unsigned char*)h_buf;
+namespace {
+
+// Header of a serialized blob, checksum not yet set.
+Header header_of(const qoz_blob* b) {
   Header h;
   memset(&h, 0, sizeof(h));
   memcpy(h.magic, kMagic, 8);
@@ -188,6 +184,13 @@ qoz_status qoz_blob_serialize(const qoz_blob* b, void* h_buf, size_t cap, size_t
   h.n_points = b->N;
   h.n_anchors = b->na;
   h.n_unpred = b->nu;
+  return h;
+}
+
+// Enqueues the payload checksum and the section copies; the device checksum
+// lands in the header's checksum slot of out (8 bytes at a fixed offset).
+cudaError_t enqueue_payload(const qoz_blob* b, const Layout& L, unsigned char* out,
+                            cudaStream_t s) {
   // zero the padding after each section (under 8 bytes each) so that the
   // stream is a pure function of the blob; the copies fill the rest
   const size_t ends[4][2] = {{L.anchors + sizeof(float) * b->na, L.uidx},
@@ -198,11 +201,11 @@ qoz_status qoz_blob_serialize(const qoz_blob* b, void* h_buf, size_t cap, size_t
     if (g[1] > g[0]) memset(out + g[0], 0, g[1] - g[0]);
   unsigned long long* d_acc = nullptr;
   cudaError_t e = dev_alloc((void**)&d_acc, sizeof(unsigned long long), s);
-  if (e != cudaSuccess) return fail(QOZ_ENOMEM, "checksum scratch");
+  if (e != cudaSuccess) return e;
   e = device_payload_sum(b, L, d_acc, s);
-  unsigned long long acc = 0;
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&acc, d_acc, sizeof(acc), cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(out + offsetof(Header, checksum), d_acc, sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && b->na)
     e = cudaMemcpyAsync(out + L.anchors, b->d_anchors, sizeof(float) * b->na,
                         cudaMemcpyDeviceToHost, s);
@@ -215,11 +218,63 @@ qoz_status qoz_blob_serialize(const qoz_blob* b, void* h_buf, size_t cap, size_t
     e = cudaMemcpyAsync(out + L.codes, b->d_codes, sizeof(uint16_t) * b->N,
                         cudaMemcpyDeviceToHost, s);
   dev_free(d_acc, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(e, "serialize");
+  return e;
+}
+
+// Writes the header once the payload checksum has landed in out.
+void finish_header(Header h, unsigned char* out) {
+  unsigned long long acc;
+  memcpy(&acc, out + offsetof(Header, checksum), sizeof(acc));
   h.checksum = 0;
   h.checksum = acc + host_checksum((const unsigned char*)&h, sizeof(Header), 0);
   memcpy(out, &h, sizeof(Header));
+}
+
+struct PendingHeader {
+  Header h;
+  unsigned char* out;
+};
+
+void CUDART_CB header_callback(void* p) {
+  PendingHeader* ph = static_cast<PendingHeader*>(p);
+  finish_header(ph->h, ph->out);
+  delete ph;
+}
+
+}  // namespace
+
+qoz_status qoz_blob_serialize(const qoz_blob* b, void* h_buf, size_t cap, size_t* used,
+                              void* stream) {
+  if (!b || !used) return fail(QOZ_EINVAL, "NULL argument");
+  const Layout L = layout_of(b->na, b->nu, b->N);
+  *used = L.total;
+  if (!h_buf) return QOZ_OK;
+  if (cap < L.total) return fail(QOZ_EINVAL, "buffer holds %zu bytes, %zu needed", cap, L.total);
+  cudaStream_t s = stream ? (cudaStream_t)stream : b->stream;
+  unsigned char* out = (unsigned char*)h_buf;
+  const Header h = header_of(b);
+  cudaError_t e = enqueue_payload(b, L, out, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "serialize");
+  finish_header(h, out);
+  return QOZ_OK;
+}
+
+qoz_status qoz_blob_serialize_async(const qoz_blob* b, void* h_buf, size_t cap, size_t* used,
+                                    void* stream) {
+  if (!b || !used || !h_buf) return fail(QOZ_EINVAL, "NULL argument");
+  const Layout L = layout_of(b->na, b->nu, b->N);
+  *used = L.total;
+  if (cap < L.total) return fail(QOZ_EINVAL, "buffer holds %zu bytes, %zu needed", cap, L.total);
+  cudaStream_t s = stream ? (cudaStream_t)stream : b->stream;
+  unsigned char* out = (unsigned char*)h_buf;
+  PendingHeader* ph = new PendingHeader{header_of(b), out};
+  cudaError_t e = enqueue_payload(b, L, out, s);
+  if (e == cudaSuccess) e = cudaLaunchHostFunc(s, header_callback, ph);
+  if (e != cudaSuccess) {
+    delete ph;
+    return cuda_fail(e, "serialize");
+  }
   return QOZ_OK;
 }
 

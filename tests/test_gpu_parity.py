@@ -229,6 +229,23 @@ def test_serialize_round_trip_and_corruption(q, orc):
         q.deserialize(buf[: len(buf) - 9].clone())
 
 
+def test_serialize_async_matches_sync(q):
+    import synth
+    x = synth.grf((33, 47, 64), 5.0 / 3.0, seed=9, n_modes=64).cuda()
+    blob = q.compress(x, 1e-3)
+    ref = blob.serialize()
+    s = torch.cuda.Stream()
+    out = torch.full((ref.numel() + 64,), 0xAB, dtype=torch.uint8, pin_memory=True)
+    used = blob.serialize_async(out, stream=s)
+    s.synchronize()
+    assert used == ref.numel()
+    assert torch.equal(out[:used], ref)
+    b2 = q.deserialize(out[:used].clone())
+    assert b2.info().n_unpredictable == blob.info().n_unpredictable
+    blob.free()
+    b2.free()
+
+
 def test_host_fault_injection(q, monkeypatch):
     x = torch.zeros((16, 16, 16), device="cuda")
     monkeypatch.setenv("QOZ_FAULT", "alloc")
