@@ -57,20 +57,19 @@ __device__ __forceinline__ float predict(float a3, float a1, float b1, float b3,
 // Linear-scale quantization (Sec. 5.1): bin width 2 e_l, index rounded half
 // away from zero; a point whose index leaves [-32767, 32767] or whose
 // reconstruction misses the bound is unpredictable (returns false).
+// Rounding half away from zero of d / (2 e_l) is trunc(d inv + sign(d) 0.5):
+// binary32 rounding is symmetric in sign, so this equals sign(d) times
+// floor(|d| inv + 0.5) bit for bit; d = 0 maps to bin 0 without the product
+// (which is NaN for e = 0), and adding 0 turns a -0 index into +0.
 __device__ __forceinline__ bool quantize(float x, float pred, float el, float two_e, float inv,
                                          uint16_t* code, float* rec) {
   const float d = __fsub_rn(x, pred);
-  int q = 0;
-  if (d != 0.0f) {
-    const float t = __fmul_rn(fabsf(d), inv);
-    const float m = floorf(__fadd_rn(t, 0.5f));
-    if (!(m < 32768.0f)) return false;
-    q = (int)m;
-    if (d < 0.0f) q = -q;
-  }
-  const float r = __fadd_rn(pred, __fmul_rn((float)q, two_e));
+  const float t = d == 0.0f ? 0.0f : __fmul_rn(d, inv);
+  const float qf = __fadd_rn(truncf(__fadd_rn(t, copysignf(0.5f, t))), 0.0f);
+  if (!(fabsf(qf) < 32768.0f)) return false;
+  const float r = __fadd_rn(pred, __fmul_rn(qf, two_e));
   if (!(fabsf(__fsub_rn(x, r)) <= el)) return false;
-  *code = (uint16_t)(q + kRadius);
+  *code = (uint16_t)(int)__fadd_rn(qf, 32768.0f);
   *rec = r;
   return true;
 }

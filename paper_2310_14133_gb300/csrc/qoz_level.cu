@@ -12,7 +12,7 @@ namespace qoz {
 namespace {
 
 // Level-1 compression with bulk tensor copies (see level_tile_tma).
-template <int A0, int A1, int A2, int TZ, int TY, int TX, int THR, bool HIST>
+template <int A0, int A1, int A2, int TZ, int TY, int TX, int THR, int IP, bool HIST>
 __global__ void __launch_bounds__(THR, 1024 / THR)
     level_tma_kernel(const LevelLaunch a, int nt1, int nt2, const __grid_constant__ CUtensorMap mx,
                      const __grid_constant__ CUtensorMap mrc,
@@ -20,8 +20,9 @@ __global__ void __launch_bounds__(THR, 1024 / THR)
                      const __grid_constant__ CUtensorMap mout, int use_out) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar;
-  level_tile_tma<A0, A1, A2, TZ, TY, TX, THR, HIST>(a, smem, &mbar, blockIdx.x, nt1, nt2, &mx,
-                                                    &mrc, &mcc, use_out ? &mout : nullptr);
+  level_tile_tma<A0, A1, A2, TZ, TY, TX, THR, IP, HIST>(a, smem, &mbar, blockIdx.x, nt1, nt2,
+                                                        &mx, &mrc, &mcc,
+                                                        use_out ? &mout : nullptr);
 }
 
 // The driver's tensor-map encoder, looked up through the runtime (the
@@ -71,9 +72,10 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 
 // Runs the level-1 launch with bulk tensor copies when the grid is the field
 // itself and every array's rows start on 16-byte boundaries; returns false
 // (nothing launched) otherwise.
-template <int A0, int A1, int A2, int TZ, int TY, int TX, int THR, bool HIST>
+template <int A0, int A1, int A2, int TZ, int TY, int TX, int THR, int IP, bool HIST>
 bool try_launch_tma(const LevelLaunch& a, cudaStream_t s, cudaError_t* err) {
-  using G = Geo<A0, A1, A2, TZ, TY, TX, THR>;
+  using G = Geo<A0, A1, A2, TZ, TY, TX, THR, IP>;
+  if (a.interp != IP) return false;
   if (!tma_enabled() || a.decompress || a.xs[2] != 1 || !a.cin || !a.rc) return false;
   if (!aligned16(a.x) || !aligned16(a.rc) || !aligned16(a.cin)) return false;
   if (a.xs[1] % 4 || a.xs[0] % 4 || a.cs[1] % 8 || a.cs[0] % 8) return false;
@@ -109,7 +111,7 @@ bool try_launch_tma(const LevelLaunch& a, cudaStream_t s, cudaError_t* err) {
   static unsigned long long done = 0;
   constexpr size_t smem = G::tma_smem_bytes(HIST);
   static_assert((smem + 1088) * (1024 / THR) <= 228 * 1024, "tiles must fit the CTAs per SM");
-  const void* fn = (const void*)level_tma_kernel<A0, A1, A2, TZ, TY, TX, THR, HIST>;
+  const void* fn = (const void*)level_tma_kernel<A0, A1, A2, TZ, TY, TX, THR, IP, HIST>;
   cudaError_t e = ensure_smem_attr(fn, &done, smem);
   if (e != cudaSuccess) {
     *err = e;
@@ -123,7 +125,7 @@ bool try_launch_tma(const LevelLaunch& a, cudaStream_t s, cudaError_t* err) {
     *err = cudaErrorInvalidConfiguration;
     return true;
   }
-  level_tma_kernel<A0, A1, A2, TZ, TY, TX, THR, HIST><<<(unsigned)nb, THR, smem, s>>>(
+  level_tma_kernel<A0, A1, A2, TZ, TY, TX, THR, IP, HIST><<<(unsigned)nb, THR, smem, s>>>(
       a, (int)nt1, (int)nt2, mx, mrc, mcc, mout, use_out);
   note_launch(1);
   *err = cudaGetLastError();
@@ -155,29 +157,43 @@ __global__ void anchor_gather_kernel(const float* __restrict__ x, float* __restr
 #ifndef QOZ_TMA_TILESET
 #define QOZ_TMA_TILESET 1
 #endif
+template <int A0, int A1, int A2, int IP, bool HIST>
+bool try_tma_order_ip(const LevelLaunch& a, cudaStream_t s, cudaError_t* err) {
+  if constexpr (A0 == 0 && QOZ_TMA_TILESET == 1)
+    return try_launch_tma<A0, A1, A2, 8, 16, 32, 256, IP, HIST>(a, s, err);
+  else if constexpr (A0 == 1 && QOZ_TMA_TILESET == 1)
+    return try_launch_tma<A0, A1, A2, 16, 8, 32, 256, IP, HIST>(a, s, err);
+  else if constexpr (A0 == 2 && QOZ_TMA_TILESET == 1)
+    return try_launch_tma<A0, A1, A2, 8, 8, 32, 256, IP, HIST>(a, s, err);
+  else if constexpr (A0 == 0)
+    return try_launch_tma<A0, A1, A2, 8, 16, 64, 512, IP, HIST>(a, s, err);
+  else if constexpr (A0 == 1)
+    return try_launch_tma<A0, A1, A2, 16, 8, 64, 512, IP, HIST>(a, s, err);
+  else
+    return try_launch_tma<A0, A1, A2, 12, 16, 32, 512, IP, HIST>(a, s, err);
+}
+
+// One instance per interpolator (the level's interpolator is a compile-time
+// constant inside the tile code).
 template <int A0, int A1, int A2, bool HIST>
 bool try_tma_order(const LevelLaunch& a, cudaStream_t s, cudaError_t* err) {
-  if constexpr (A0 == 0 && QOZ_TMA_TILESET == 1)
-    return try_launch_tma<A0, A1, A2, 8, 16, 32, 256, HIST>(a, s, err);
-  else if constexpr (A0 == 1 && QOZ_TMA_TILESET == 1)
-    return try_launch_tma<A0, A1, A2, 16, 8, 32, 256, HIST>(a, s, err);
-  else if constexpr (A0 == 2 && QOZ_TMA_TILESET == 1)
-    return try_launch_tma<A0, A1, A2, 8, 8, 32, 256, HIST>(a, s, err);
-  else if constexpr (A0 == 0)
-    return try_launch_tma<A0, A1, A2, 8, 16, 64, 512, HIST>(a, s, err);
-  else if constexpr (A0 == 1)
-    return try_launch_tma<A0, A1, A2, 16, 8, 64, 512, HIST>(a, s, err);
-  else
-    return try_launch_tma<A0, A1, A2, 12, 16, 32, 512, HIST>(a, s, err);
+  return a.interp == 1 ? try_tma_order_ip<A0, A1, A2, 1, HIST>(a, s, err)
+                       : try_tma_order_ip<A0, A1, A2, 0, HIST>(a, s, err);
 }
 
 template <int A0, int A1, int A2, int TZ, int TY, int TX, bool DECOMP, bool HIST>
 cudaError_t launch_one(const LevelLaunch& a, cudaStream_t s) {
   using G = Geo<A0, A1, A2, TZ, TY, TX>;
-  if constexpr (!DECOMP) {
+  if constexpr (!DECOMP && HIST) {  // level 1 of a compression (the histogram launch)
     cudaError_t te = cudaSuccess;
-    if (TZ > 1 && try_tma_order<A0, A1, A2, HIST>(a, s, &te)) return te;
-    if (TZ == 1 && try_launch_tma<A0, A1, A2, TZ, TY, TX, kThreads, HIST>(a, s, &te)) return te;
+    if constexpr (TZ > 1) {
+      if (try_tma_order<A0, A1, A2, HIST>(a, s, &te)) return te;
+    } else {
+      const bool done = a.interp == 1
+                            ? try_launch_tma<A0, A1, A2, TZ, TY, TX, kThreads, 1, HIST>(a, s, &te)
+                            : try_launch_tma<A0, A1, A2, TZ, TY, TX, kThreads, 0, HIST>(a, s, &te);
+      if (done) return te;
+    }
   }
   static unsigned long long done = 0;
   constexpr size_t smem = G::smem_bytes(DECOMP, HIST);

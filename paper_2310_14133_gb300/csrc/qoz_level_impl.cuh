@@ -87,11 +87,13 @@ __host__ __device__ constexpr int pick_seg(int NT, int lines, int threads = kThr
   return seg;
 }
 
-template <int A0_, int A1_, int A2_, int TZ_, int TY_, int TX_, int THR_ = kThreads>
+template <int A0_, int A1_, int A2_, int TZ_, int TY_, int TX_, int THR_ = kThreads,
+          int IP_ = -1>
 struct Geo {
   static constexpr int A0 = A0_, A1 = A1_, A2 = A2_;
   static constexpr int TZ = TZ_, TY = TY_, TX = TX_;
-  static constexpr int kThr = THR_;  // threads of the CTA that owns the tile
+  static constexpr int kThr = THR_;    // threads of the CTA that owns the tile
+  static constexpr int kInterp = IP_;  // interpolator fixed at compile time (-1: runtime)
   __host__ __device__ static constexpr int T(int p) { return p == 0 ? TZ : (p == 1 ? TY : TX); }
   static constexpr int HZ = A0 == 0 ? 0 : kHalo;
   static constexpr int HY = A0 == 1 ? 0 : kHalo;
@@ -169,6 +171,12 @@ __device__ __forceinline__ int gsel(const Ctx& c) {
 template <int P>
 __device__ __forceinline__ int osel(const Ctx& c) {
   return P == 0 ? c.oz : (P == 1 ? c.oy : c.ox);
+}
+
+// The level's interpolator: the compile-time one when the instance fixes it.
+template <class G>
+__device__ __forceinline__ int interp_of(const Ctx& c) {
+  return G::kInterp >= 0 ? G::kInterp : c.interp;
 }
 
 // Interpolation with every neighbour present (interior tiles).
@@ -281,10 +289,10 @@ __device__ __forceinline__ void pass_line(const LevelLaunch& a, const Ctx& c, fl
       if (!INTERIOR && cP >= gP) break;
       float pred;
       if (INTERIOR) {
-        pred = predict_full(w[j], w[j + 1], w[j + 2], w[j + 3], c.interp);
+        pred = predict_full(w[j], w[j + 1], w[j + 2], w[j + 3], interp_of<G>(c));
       } else {
         const bool hb1 = cP + 1 < gP, ha3 = cP >= 3, hb3 = cP + 3 < gP;
-        pred = predict(w[j], w[j + 1], w[j + 2], w[j + 3], ha3, hb1, hb3, c.interp);
+        pred = predict(w[j], w[j + 1], w[j + 2], w[j + 3], ha3, hb1, hb3, interp_of<G>(c));
       }
       const int lz = P == 0 ? pos : lr, ly = P == 1 ? pos : lr;
       finish<DECOMP>(a, c, S, IN16, rbase + pos * SP, pred, inside, C16 + G::cidx(lz, ly, lx),
@@ -323,7 +331,7 @@ __device__ __forceinline__ void pass_x_rows(const LevelLaunch& a, const Ctx& c, 
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int si = si0 + u * DS;
-      const float pred = predict_full(S[si - 3], S[si - 1], S[si + 1], S[si + 3], c.interp);
+      const float pred = predict_full(S[si - 3], S[si - 1], S[si + 1], S[si + 3], interp_of<G>(c));
       const int uz = ALONG_Y ? lz : lz + u * SZ::step, uy = ALONG_Y ? ly + u * SY::step : ly;
       finish<DECOMP>(a, c, S, IN16, si, pred, inside, C16 + ci0 + u * DC, c.oz + uz, c.oy + uy,
                      c.ox + lx);
@@ -361,10 +369,10 @@ __device__ __forceinline__ void pass_x(const LevelLaunch& a, const Ctx& c, float
     const float a3 = S[si - 3], a1 = S[si - 1], b1 = S[si + 1], b3 = S[si + 3];
     float pred;
     if (INTERIOR) {
-      pred = predict_full(a3, a1, b1, b3, c.interp);
+      pred = predict_full(a3, a1, b1, b3, interp_of<G>(c));
     } else {
       const bool hb1 = cx + 1 < c.g2, ha3 = cx >= 3, hb3 = cx + 3 < c.g2;
-      pred = predict(a3, a1, b1, b3, ha3, hb1, hb3, c.interp);
+      pred = predict(a3, a1, b1, b3, ha3, hb1, hb3, interp_of<G>(c));
     }
     const bool inside = lz >= 0 && lz < G::TZ && ly >= 0 && ly < G::TY;
     finish<DECOMP>(a, c, S, IN16, si, pred, inside, C16 + G::cidx(lz, ly, lx), cz, cy, cx);
@@ -676,12 +684,12 @@ constexpr unsigned kTmaWaitPolls = 1u << 24;
 // map_x: the field (f32, dims x, y, z); map_rc: coarse reconstruction (f32);
 // map_cc: coarse codes (u16); map_out: the codes (u16), or nullptr to store
 // them with plain stores.
-template <int A0, int A1, int A2, int TZ, int TY, int TX, int THR, bool HIST>
+template <int A0, int A1, int A2, int TZ, int TY, int TX, int THR, int IP, bool HIST>
 __device__ __forceinline__ void level_tile_tma(const LevelLaunch& a, unsigned char* smem_raw,
                                                uint64_t* mbar, int b, int nt1, int nt2,
                                                const void* map_x, const void* map_rc,
                                                const void* map_cc, const void* map_out) {
-  using G = Geo<A0, A1, A2, TZ, TY, TX, THR>;
+  using G = Geo<A0, A1, A2, TZ, TY, TX, THR, IP>;
   // 128-byte aligned sub-buffers (bulk tensor copies need it)
   unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   float* S = reinterpret_cast<float*>(smem);
