@@ -356,11 +356,29 @@ void qoz_model_free(qoz_model* m);
  * head (one interpolator and order for every level, alpha and beta from
  * opts' candidate sets, which must hold 5 and 3 values).  The bound is
  * rel_eb * vrange, or with a PSNR target the uniform-error estimate
- * vrange sqrt(3) 10^(-target / 20) when that is smaller.  The report's B and
- * M are NaN (no trial ran).  Synchronises `stream`. */
+ * vrange sqrt(3) 10^(-target / 20) when that is smaller (an SSIM target
+ * keeps rel_eb * vrange: qoz_tune_learned_verified sets the bound).  The
+ * report's B and M are NaN (no trial ran).  Synchronises `stream`. */
 qoz_status qoz_tune_learned(const float* d_field, qoz_shape shape, double rel_eb,
                             qoz_metric metric, double target, const qoz_tune_opts* opts,
                             const qoz_model* model, void* stream, qoz_tune_report* out);
+
+/* Sampled verification of a given setting (the trials of Sec. 6.1 on the
+ * sampled blocks): with target NaN one trial at rel_eb * vrange reports B and
+ * M; with a PSNR or SSIM target, trials at e0 (PSNR: the uniform-error
+ * estimate, SSIM: rel_eb * vrange) and at 0.8 e0 / 1.2 e0, then the target
+ * mode's secant (at most four more trials) picks the bound, capped at
+ * rel_eb * vrange.  The report's params are the given ones.  Synchronises. */
+qoz_status qoz_tune_verify(const float* d_field, qoz_shape shape, double rel_eb,
+                           qoz_metric metric, double target, const qoz_tune_opts* opts,
+                           const qoz_params* params, void* stream, qoz_tune_report* out);
+
+/* The network proposes (qoz_tune_learned), the sampled trials verify and set
+ * the bound (qoz_tune_verify). */
+qoz_status qoz_tune_learned_verified(const float* d_field, qoz_shape shape, double rel_eb,
+                                     qoz_metric metric, double target,
+                                     const qoz_tune_opts* opts, const qoz_model* model,
+                                     void* stream, qoz_tune_report* out);
 
 /* ---------------------------------------------------------------- profiling */
 

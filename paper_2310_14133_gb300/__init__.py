@@ -41,5 +41,7 @@ from ._binding import (  # noqa: F401
     profile_read,
     tune,
     tune_learned,
+    tune_learned_verified,
+    tune_verify,
     value_range,
 )

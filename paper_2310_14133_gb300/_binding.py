@@ -157,6 +157,8 @@ def lib():
             "qoz_model_train_step": (i32, [P, P, P, i64, C.c_float, P, P]),
             "qoz_model_free": (None, [P]),
             "qoz_tune_learned": (i32, [P, Shape, f64, i32, f64, P, P, P, P]),
+            "qoz_tune_learned_verified": (i32, [P, Shape, f64, i32, f64, P, P, P, P]),
+            "qoz_tune_verify": (i32, [P, Shape, f64, i32, f64, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -530,5 +532,24 @@ def tune_learned(x: torch.Tensor, rel_eb: float, model: Model, metric: int = 0,
     _check(lib().qoz_tune_learned(_dev_ptr(x), _shape_of(x), float(rel_eb), int(metric),
                                   float(target), C.byref(opts) if opts is not None else None,
                                   model.handle, _stream(stream), C.byref(rep)))
+    return rep
+
+
+def tune_learned_verified(x: torch.Tensor, rel_eb: float, model: Model, metric: int = 0,
+                          target: float = float("nan"), opts=None, stream=None):
+    rep = TuneReport()
+    _check(lib().qoz_tune_learned_verified(_dev_ptr(x), _shape_of(x), float(rel_eb), int(metric),
+                                           float(target),
+                                           C.byref(opts) if opts is not None else None,
+                                           model.handle, _stream(stream), C.byref(rep)))
+    return rep
+
+
+def tune_verify(x: torch.Tensor, rel_eb: float, params: Params, metric: int = 0,
+                target: float = float("nan"), opts=None, stream=None):
+    rep = TuneReport()
+    _check(lib().qoz_tune_verify(_dev_ptr(x), _shape_of(x), float(rel_eb), int(metric),
+                                 float(target), C.byref(opts) if opts is not None else None,
+                                 C.byref(params), _stream(stream), C.byref(rep)))
     return rep
 

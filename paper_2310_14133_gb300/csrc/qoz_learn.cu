@@ -747,8 +747,8 @@ qoz_status qoz_tune_learned(const float* d_field, qoz_shape shape, double rel_eb
   if (metric < QOZ_METRIC_MAXERR || metric > QOZ_METRIC_SSIM)
     return fail(QOZ_EINVAL, "unknown metric %d", metric);
   const bool target_mode = !std::isnan(target);
-  if (target_mode && metric != QOZ_METRIC_PSNR)
-    return fail(QOZ_EINVAL, "the learned tuner takes a PSNR target only");
+  if (target_mode && metric == QOZ_METRIC_MAXERR)
+    return fail(QOZ_EINVAL, "a target needs the PSNR or SSIM metric");
   cudaStream_t s = (cudaStream_t)stream;
   configure_pool_once();
   Resolved r;
@@ -792,7 +792,7 @@ qoz_status qoz_tune_learned(const float* d_field, qoz_shape shape, double rel_eb
   out->params.beta = o.betas[ib];
   out->params.anchor_stride = o.anchor_stride;
   double e = rel_eb * vr;
-  if (target_mode) {
+  if (target_mode && metric == QOZ_METRIC_PSNR) {
     // uniform-error estimate of the bound that meets the PSNR target
     const double e0 = vr * std::sqrt(3.0) * std::pow(10.0, -target / 20.0);
     if (e0 < e) e = e0;
@@ -806,6 +806,18 @@ qoz_status qoz_tune_learned(const float* d_field, qoz_shape shape, double rel_eb
   out->n_blocks = sm.nb;
   out->n_sampled_points = sm.npts;
   return QOZ_OK;
+}
+
+qoz_status qoz_tune_learned_verified(const float* d_field, qoz_shape shape, double rel_eb,
+                                     qoz_metric metric, double target,
+                                     const qoz_tune_opts* opts, const qoz_model* model,
+                                     void* stream, qoz_tune_report* out) {
+  qoz_tune_report proposal;
+  qoz_status st =
+      qoz_tune_learned(d_field, shape, rel_eb, metric, target, opts, model, stream, &proposal);
+  if (st != QOZ_OK) return st;
+  return qoz_tune_verify(d_field, shape, rel_eb, metric, target, opts, &proposal.params, stream,
+                         out);
 }
 
 }  // extern "C"

@@ -686,6 +686,50 @@ qoz_status resolve_tune_opts(const qoz_shape& shape, const Resolved& r,
   return QOZ_OK;
 }
 
+// A sampled (bound, bit rate, metric) point of the target mode.
+struct TargetPoint {
+  double e, B, M;
+};
+
+// Secant on (log e, M) for one setting from the last two points of *pts, at
+// most four more trials (bound capped at e_user, floored at e0 / 16); the
+// pick is the largest bound whose sampled metric meets the target, else the
+// smallest bound tried (capped at e_user).
+qoz_status target_secant(Tuner& T, const TrialCand& setting, double alpha, double beta, int Ls,
+                         double target, double e0, double e_user,
+                         std::vector<TargetPoint>* pts, TargetPoint* pick_out) {
+  for (int it = 0; it < 4; ++it) {
+    const TargetPoint pa = (*pts)[pts->size() - 2];
+    const TargetPoint pb = (*pts)[pts->size() - 1];
+    if (pa.M == pb.M) break;
+    const double le =
+        std::log(pb.e) + (target - pb.M) * (std::log(pa.e) - std::log(pb.e)) / (pa.M - pb.M);
+    double en = std::exp(le);
+    if (en > e_user) en = e_user;
+    if (en < e0 / 16.0) en = e0 / 16.0;
+    if (en == pb.e) break;
+    TrialCand c = setting;
+    fill_bounds(&c, en, alpha, beta, Ls);
+    std::vector<TrialResult> r1;
+    const qoz_status st = T.run({c}, 1, 0, true, &r1);
+    if (st != QOZ_OK) return st;
+    pts->push_back({en, r1[0].B, r1[0].M});
+  }
+  int pick = -1;
+  for (size_t k = 0; k < pts->size(); ++k)
+    if ((*pts)[k].M >= target && (*pts)[k].e <= e_user &&
+        (pick < 0 || (*pts)[k].e > (*pts)[pick].e))
+      pick = (int)k;
+  if (pick < 0) {
+    pick = 0;
+    for (size_t k = 1; k < pts->size(); ++k)
+      if ((*pts)[k].e < (*pts)[pick].e) pick = (int)k;
+  }
+  *pick_out = (*pts)[pick];
+  if (pick_out->e > e_user) pick_out->e = e_user;
+  return QOZ_OK;
+}
+
 qoz_status tune_impl(const float* d_field, const qoz_shape& shape, double rel_eb, int metric,
                      double target, const qoz_tune_opts* opts_in, cudaStream_t s,
                      qoz_tune_report* out) {
@@ -803,10 +847,7 @@ qoz_status tune_impl(const float* d_field, const qoz_shape& shape, double rel_eb
   int best_k = 0;
   double best_B = 0, best_M = 0, best_score = INFINITY, best_e = e0;
   bool have = false;
-  struct TP {
-    double e, B, M;
-  };
-  std::vector<TP> pts;
+  std::vector<TargetPoint> pts;
   for (int k = 0; k < nab; ++k) {
     const TrialResult& t = at(0, k);
     if (!target_mode) {
@@ -850,36 +891,13 @@ qoz_status tune_impl(const float* d_field, const qoz_shape& shape, double rel_eb
   fp.beta = o.betas[best_k % o.n_beta];
 
   if (target_mode) {
-    // secant on (log e, M) for the chosen setting, at most four more trials
-    for (int it = 0; it < 4; ++it) {
-      const TP pa = pts[pts.size() - 2];
-      const TP pb = pts[pts.size() - 1];
-      if (pa.M == pb.M) break;
-      const double le =
-          std::log(pb.e) + (target - pb.M) * (std::log(pa.e) - std::log(pb.e)) / (pa.M - pb.M);
-      double en = std::exp(le);
-      if (en > e_user) en = e_user;
-      if (en < e0 / 16.0) en = e0 / 16.0;
-      if (en == pb.e) break;
-      TrialCand c = chosen;
-      fill_bounds(&c, en, fp.alpha, fp.beta, sm.Ls);
-      std::vector<TrialResult> r1;
-      if ((st = T.run({c}, 1, 0, true, &r1)) != QOZ_OK) return st;
-      pts.push_back({en, r1[0].B, r1[0].M});
-    }
-    int pick = -1;
-    for (size_t k = 0; k < pts.size(); ++k)
-      if (pts[k].M >= target && pts[k].e <= e_user && (pick < 0 || pts[k].e > pts[pick].e))
-        pick = (int)k;
-    if (pick < 0) {
-      pick = 0;
-      for (size_t k = 1; k < pts.size(); ++k)
-        if (pts[k].e < pts[pick].e) pick = (int)k;
-    }
-    best_e = pts[pick].e;
-    if (best_e > e_user) best_e = e_user;
-    best_B = pts[pick].B;
-    best_M = pts[pick].M;
+    TargetPoint pk;
+    if ((st = target_secant(T, chosen, fp.alpha, fp.beta, sm.Ls, target, e0, e_user, &pts, &pk)) !=
+        QOZ_OK)
+      return st;
+    best_e = pk.e;
+    best_B = pk.B;
+    best_M = pk.M;
   } else {
     best_e = e_user;
   }
@@ -896,6 +914,86 @@ qoz_status tune_impl(const float* d_field, const qoz_shape& shape, double rel_eb
   return QOZ_OK;
 }
 
+// Sampled verification of one given setting (Sec. 6.1 trials): in the
+// fixed-bound mode one trial at the bound; with a target, trials at e0 and
+// at 0.8 e0 / 1.2 e0, then the target mode's secant on the bound.
+qoz_status verify_impl(const float* d_field, const qoz_shape& shape, double rel_eb, int metric,
+                       double target, const qoz_tune_opts* opts_in, const qoz_params* p_in,
+                       cudaStream_t s, qoz_tune_report* out) {
+  if (!d_field || !out || !p_in) return fail(QOZ_EINVAL, "NULL argument");
+  if (!(rel_eb > 0.0 && std::isfinite(rel_eb))) return fail(QOZ_EINVAL, "rel_eb must be > 0");
+  if (metric < QOZ_METRIC_MAXERR || metric > QOZ_METRIC_SSIM)
+    return fail(QOZ_EINVAL, "unknown metric %d", metric);
+  const bool target_mode = !std::isnan(target);
+  if (target_mode && metric == QOZ_METRIC_MAXERR)
+    return fail(QOZ_EINVAL, "a target needs the PSNR or SSIM metric");
+  Resolved r;
+  qoz_status st = resolve(shape, p_in, &r);
+  if (st != QOZ_OK) return st;
+  qoz_tune_opts o;
+  if ((st = resolve_tune_opts(shape, r, opts_in, &o)) != QOZ_OK) return st;
+  o.anchor_stride = r.p.anchor_stride;
+  const int d = r.ndims;
+  float vmin, vmax;
+  int64_t cnt;
+  st = qoz_value_range(d_field, r.N, &vmin, &vmax, &cnt, s);
+  if (st != QOZ_OK) return st;
+  const double vr = (double)vmax - (double)vmin;
+  const double e_user = rel_eb * vr;
+  Sampling sm = sample_blocks(r, o.block, o.rate, o.anchor_stride);
+  Tuner T(d_field, r, sm, s, metric, o.ssim_win, o.ssim_step, vr);
+  if ((st = T.init()) != QOZ_OK) return st;
+  TrialCand c;
+  memset(&c, 0, sizeof(c));
+  for (int l = 1; l <= kMaxLevels; ++l) set_axes(&c, l, d, 0);
+  for (int l = 1; l <= sm.Ls; ++l) {
+    c.interp[l - 1] = r.p.interp[l - 1];
+    set_axes(&c, l, d, r.p.order[l - 1]);
+  }
+  const double alpha = r.p.alpha, beta = r.p.beta;
+  double e0 = e_user;
+  if (target_mode && metric == QOZ_METRIC_PSNR) {
+    e0 = vr * std::sqrt(3.0) * std::pow(10.0, -target / 20.0);
+    if (e0 > e_user) e0 = e_user;
+  }
+  memset(out, 0, sizeof(*out));
+  std::vector<TrialResult> res;
+  if (!target_mode) {
+    TrialCand t = c;
+    fill_bounds(&t, e_user, alpha, beta, sm.Ls);
+    if ((st = T.run({t}, 1, 0, true, &res)) != QOZ_OK) return st;
+    out->abs_eb = e_user;
+    out->B = res[0].B;
+    out->M = res[0].M;
+  } else {
+    std::vector<TrialCand> tc;
+    const double scales[3] = {1.0, 0.8, 1.2};
+    for (double sc : scales) {
+      TrialCand t = c;
+      fill_bounds(&t, sc * e0, alpha, beta, sm.Ls);
+      tc.push_back(t);
+    }
+    if ((st = T.run(tc, 1, 0, true, &res)) != QOZ_OK) return st;
+    const TrialResult& t1 = res[0];
+    const double sc = t1.M >= target ? 1.2 : 0.8;
+    const TrialResult& t2 = res[sc > 1.0 ? 2 : 1];
+    std::vector<TargetPoint> pts = {{e0, t1.B, t1.M}, {sc * e0, t2.B, t2.M}};
+    TargetPoint pk;
+    if ((st = target_secant(T, c, alpha, beta, sm.Ls, target, e0, e_user, &pts, &pk)) != QOZ_OK)
+      return st;
+    out->abs_eb = pk.e;
+    out->B = pk.B;
+    out->M = pk.M;
+  }
+  out->params = r.p;
+  out->vmin = vmin;
+  out->vmax = vmax;
+  out->n_trials = T.trials();
+  out->n_blocks = sm.nb;
+  out->n_sampled_points = sm.npts;
+  return QOZ_OK;
+}
+
 }  // namespace qoz
 
 extern "C" qoz_status qoz_tune(const float* d_field, qoz_shape shape, double rel_eb,
@@ -904,3 +1002,12 @@ extern "C" qoz_status qoz_tune(const float* d_field, qoz_shape shape, double rel
   return qoz::tune_impl(d_field, shape, rel_eb, (int)metric, target, opts, (cudaStream_t)stream,
                         out);
 }
+
+extern "C" qoz_status qoz_tune_verify(const float* d_field, qoz_shape shape, double rel_eb,
+                                      qoz_metric metric, double target,
+                                      const qoz_tune_opts* opts, const qoz_params* params,
+                                      void* stream, qoz_tune_report* out) {
+  return qoz::verify_impl(d_field, shape, rel_eb, (int)metric, target, opts, params,
+                          (cudaStream_t)stream, out);
+}
+

@@ -106,3 +106,34 @@ def test_full_size_512_sampled_tuner(q, orc):
     rep, ref = _compare(q, orc, x, 1e-3, 0, float("nan"), 32, 0.005, 6,
                         [1.0, 1.25, 1.5, 1.75, 2.0], [2.0, 3.0, 4.0])
     assert rep.n_blocks == 27
+
+
+@pytest.mark.parametrize("metric,target", [(1, 70.0), (2, 0.9995)])
+def test_verify_reproduces_target_mode(q, orc, metric, target):
+    """Sampled verification of the setting the target mode chose runs the same
+    trials (e0, then 0.8 e0 or 1.2 e0, then the secant), so it reproduces the
+    tuner's bound, rate and metric exactly."""
+    x = _field(64, seed=31)
+    xd = torch.from_numpy(x).cuda()
+    qo = q.make_tune_opts(block=16, rate=0.05)
+    rep = q.tune(xd, 1e-2, metric, target, qo)
+    ver = q.tune_verify(xd, 1e-2, rep.params, metric, target, qo)
+    assert ver.abs_eb == rep.abs_eb and ver.B == rep.B and ver.M == rep.M
+    assert list(ver.params.interp) == list(rep.params.interp)
+
+
+def test_verify_fixed_bound_matches_oracle_trial(q, orc):
+    x = _field(64, seed=32)
+    xd = torch.from_numpy(x).cuda()
+    qo = q.make_tune_opts(block=16, rate=0.05)
+    p = q.make_params(3, interp=[1, 0, 1, 1, 0], order=[2, 5, 0, 1, 3], alpha=1.5, beta=3.0)
+    ver = q.tune_verify(xd, 1e-3, p, q.METRIC_PSNR, float("nan"), qo)
+    mn, mx, _ = orc.value_range(x)
+    vr = float(mx) - float(mn)
+    org, bd, _ = orc.sample_blocks(x.shape, 16, 0.05)
+    op = orc.make_params(3, interp=[1, 0, 1, 1, 0], order=[2, 5, 0, 1, 3], alpha=1.5, beta=3.0,
+                         anchor_stride=16)
+    t = orc.block_trial(x, org, bd, op, 1e-3 * vr, vrange=vr)
+    assert ver.abs_eb == 1e-3 * vr and ver.n_trials == 1
+    assert ver.B == pytest.approx(t.B, rel=1e-12)
+    assert ver.M == pytest.approx(orc.trial_metric(t, 1, vr), rel=1e-6)
