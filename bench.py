@@ -55,10 +55,12 @@ def parse():
     ap.add_argument("--n", type=int, default=512, help="edge of the cubic field")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="compress", choices=["compress", "batch", "learned"],
+    ap.add_argument("--workload", default="compress",
+                    choices=["compress", "batch", "learned", "ssim"],
                     help="compress: the single-field step (default); batch: 48 2-D + 48 "
                          "uneven 3-D fields through one batched plan; learned: train the "
-                         "tuner network, then learned vs sampled tuning")
+                         "tuner network, then learned vs sampled tuning; ssim: SSIM targets "
+                         "0.99 / 0.999, network proposes, sampled trials verify")
     ap.add_argument("--train", type=int, default=2000, help="learned: training fields")
     return ap.parse_args()
 
@@ -378,6 +380,84 @@ def run_learned(args):
     print(json.dumps(line), flush=True)
     model.free()
 
+
+def _train_model(q, learn, synth, ntrain, topts):
+    def train_samples():
+        for i in range(ntrain):
+            sp = synth.config4_train_spec(i)
+            x = synth.grf(sp["dims"], sp["slope"], seed=sp["seed"], n_modes=64, device="cuda")
+            yield x.contiguous(), sp["rel_eb"]
+
+    X, Y = learn.collect(train_samples(), topts)
+    model = q.Model(seed=4)
+    learn.fit(model, X, Y, epochs=200, batch=256, lr=3e-3)
+    return model
+
+
+def run_ssim(args):
+    """The 1024^3 k^-5/3 field with 64 vortex tubes (--n to change the edge) at
+    SSIM targets 0.99 and 0.999 (7^3 windows, step 2), bound capped at 1e-2 and
+    1e-3 of the value range.  The network proposes the setting and the sampled trials
+    set the bound (qoz_tune_learned_verified); the sampled tuner's target mode
+    runs beside it.  Each setting is compressed, decompressed and scored with
+    the full-field SSIM on the GPU.  value = compress GB/s (FP32 in) of the
+    learned setting at target 0.999."""
+    import torch
+    import paper_2310_14133_gb300 as q
+    from paper_2310_14133_gb300 import learn
+    import synth
+    topts = q.make_tune_opts(**TUNE)
+    model = _train_model(q, learn, synth, args.train, topts)
+    n = args.n
+    x = synth.config5_field(n, device="cuda").contiguous()
+    N = x.numel()
+    vr = None
+    rows = []
+    value = None
+    # the bound cap (the user's relative bound) per target: the secant searches
+    # between it and 1/16 of it
+    for target, cap in ((0.99, 1e-2), (0.999, 1e-3)):
+        for tuner in ("learned_verified", "sampled"):
+            if tuner == "sampled":
+                fn = lambda: q.tune(x, cap, q.METRIC_SSIM, target, topts)
+            else:
+                fn = lambda: q.tune_learned_verified(x, cap, model, q.METRIC_SSIM, target, topts)
+            ms_tune, _ = _events_ms(fn, 3, 1)
+            rep = fn()
+            vr = rep.vmax - rep.vmin
+            ms_c, _ = _events_ms(lambda: q.compress_abs(x, rep.abs_eb, rep.params).free(), 5, 2)
+            blob = q.compress_abs(x, rep.abs_eb, rep.params)
+            y = torch.empty_like(x)
+            ms_d, _ = _events_ms(lambda: q.decompress(blob, y), 5, 2)
+            q.decompress(blob, y)
+            m = q.compute_metrics(x, y, vr, 7, 2)
+            inf = blob.info()
+            row = {"target_ssim": target, "rel_cap": cap, "tuner": tuner, "ms_tune": ms_tune,
+                   "compress_gbs": 4.0 * N / (ms_c * 1e-3) / 1e9,
+                   "decompress_gbs": 4.0 * N / (ms_d * 1e-3) / 1e9,
+                   "ssim": m.ssim, "sampled_ssim": rep.M, "psnr": m.psnr,
+                   "max_abs_err": m.max_abs_err, "abs_eb": rep.abs_eb,
+                   "est_ratio": inf.est_ratio, "n_trials": rep.n_trials,
+                   "theta": [rep.params.interp[0], rep.params.order[0], rep.params.alpha,
+                             rep.params.beta]}
+            rows.append(row)
+            if tuner == "learned_verified" and target == 0.999:
+                value = row["compress_gbs"]
+            blob.free()
+    line = {
+        "metric": "compress GB/s (FP32 in) at SSIM target 0.999, network proposes + sampled "
+                  "verification", "value": value, "unit": "GB/s", "n_gpus": 1, "steps": 5,
+        "warmup": 2, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{n}^3 k^-5/3 GRF + 64 Gaussian vortex tubes (seed 5); SSIM "
+                               "7^3 windows step 2; bound capped at 1e-2 (target 0.99) and "
+                               "1e-3 (0.999) of the range",
+                   "tuner_opts": TUNE, "train_fields": args.train, "parallelism": "single GPU"},
+        "rows": rows,
+    }
+    print(json.dumps(line), flush=True)
+    model.free()
+
 def main():
     args = parse()
     rank = _env_int("RANK", 0)
@@ -391,6 +471,9 @@ def main():
         return
     if args.workload == "learned":
         run_learned(args)
+        return
+    if args.workload == "ssim":
+        run_ssim(args)
         return
 
     import torch
