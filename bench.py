@@ -272,8 +272,7 @@ def run_batch(args):
     inf = plan.info()
     launches = q.profile_read(reset=True).launches
     peak, peak_kind = _peak_hbm()
-    l1_ms = sum(min(inf.level1_ms[i][0], inf.level1_ms[i][1]) if inf.level1_ms[i][1] > 0
-                else inf.level1_ms[i][0] for i in range(inf.level1_groups))
+    l1_ms = sum(min(v for v in inf.level1_ms[i] if v > 0) for i in range(inf.level1_groups))
     achieved = LEVEL1_BYTES_PER_POINT * npts / (l1_ms * 1e-3) / 1e9 if l1_ms > 0 else None
     line = {
         "metric": "batch compress GB/s (FP32 in), bit-exact per field", "value":
@@ -288,8 +287,7 @@ def run_batch(args):
         "batch": {"groups": inf.n_groups, "launches_per_run": inf.launches_per_run,
                   "graph": inf.graph, "ctas_per_run": inf.ctas_per_run,
                   "level1_variant": [inf.level1_variant[i] for i in range(inf.level1_groups)],
-                  "level1_ms": [[inf.level1_ms[i][0], inf.level1_ms[i][1]]
-                                for i in range(inf.level1_groups)],
+                  "level1_ms": [list(inf.level1_ms[i]) for i in range(inf.level1_groups)],
                   "all_ms": all_ms},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if achieved else None, "traffic": None,

@@ -188,7 +188,8 @@ const char* qoz_last_error(void);
  * exactly what qoz_compress / qoz_compress_abs would produce for it. */
 typedef struct qoz_batch qoz_batch;     /* opaque plan; owns device scratch */
 
-#define QOZ_BATCH_AUTOTUNE 1u   /* time the tile variants of the level-1 launches on the first run */
+#define QOZ_BATCH_AUTOTUNE 1u   /* time the variants of the level-1 launches on the first run
+                                   (otherwise level 1 takes bulk tensor copies where the arrays allow) */
 #define QOZ_BATCH_NO_GRAPH 2u   /* issue the launches directly on every run (no CUDA graph) */
 
 /* shapes: nfields entries; params: nfields entries or NULL (defaults as in
@@ -214,8 +215,8 @@ typedef struct {
   int32_t graph;               /* 1 once the run sequence is a CUDA graph */
   int32_t autotuned;           /* 1 once the tile variants were timed */
   int32_t level1_groups;       /* number of level-1 launches */
-  int32_t level1_variant[16];  /* tile variant chosen for each (first 16) */
-  double level1_ms[16][2];     /* timed duration of each variant (autotune), else 0 */
+  int32_t level1_variant[16];  /* variant chosen for each (first 16): 0, 1 row-copy tiles, 2 bulk copies */
+  double level1_ms[16][3];     /* timed duration of each variant (autotune; 1e30: not possible), else 0 */
   int64_t ctas_per_run;        /* CTAs of all batched level launches */
 } qoz_batch_info;
 qoz_status qoz_batch_get_info(const qoz_batch* plan, qoz_batch_info* info);

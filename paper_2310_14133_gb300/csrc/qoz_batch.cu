@@ -41,6 +41,7 @@ struct Group {
 // One (field, level) launch inside a group, before pointers are filled.
 struct ItemRef {
   int field, level;
+  LevelKey key;  // the group's kernel instance
 };
 
 }  // namespace
@@ -72,12 +73,14 @@ struct qoz_batch {
   std::vector<LevelItem> items;   // geometry part (pointers filled per run)
   std::vector<uint16_t> map;
   LevelItem* d_items = nullptr;
+  LevelTmaMaps* d_maps = nullptr;  // per item; written for bulk-copy items only
   uint16_t* d_map = nullptr;
   size_t map_cap = 0;
   BatchFieldDesc* d_desc = nullptr;
   // pinned host
   BatchFieldDesc* h_desc = nullptr;
   LevelItem* h_items = nullptr;
+  LevelTmaMaps* h_maps = nullptr;
   char* h_back = nullptr;  // read-back of [bt | cnt | hs]
   size_t back_bytes = 0;
   // graph
@@ -85,6 +88,8 @@ struct qoz_batch {
   cudaGraphExec_t exec = nullptr;
   int graph_rel = -1;  // eb_relative the graph was captured with
   bool autotuned = false;
+  bool no_bulk = false;  // a run's arrays did not allow bulk copies: row copies from then on
+  bool any_bulk = false;  // the current layout has bulk-copy launches
   int launches = 0;
 };
 
@@ -124,12 +129,16 @@ LevelKey key_of(const Resolved& r, int l, int variant) {
   k.is2d = r.ndims == 2;
   k.order3 = r.ndims == 3 ? r.p.order[l - 1] : (r.p.order[l - 1] == 0 ? 0 : 1);
   k.hist = l == 1;
+  k.interp = r.p.interp[l - 1];
   k.variant = variant;
   return k;
 }
 
+// Level-1 launches are also split by interpolator (the bulk-copy kernel
+// fixes it at compile time).
 bool same_instance(const LevelKey& a, const LevelKey& b) {
-  return a.is2d == b.is2d && a.order3 == b.order3 && a.hist == b.hist;
+  return a.is2d == b.is2d && a.order3 == b.order3 && a.hist == b.hist &&
+         (!a.hist || a.interp == b.interp);
 }
 
 // Builds the groups, items and CTA maps for the given level-1 variants
@@ -139,6 +148,7 @@ qoz_status build_launches(qoz_batch* p, const std::vector<int>& l1_variant) {
   p->refs.clear();
   p->items.clear();
   p->map.clear();
+  p->any_bulk = false;
   int Lmax = 0;
   for (int f = 0; f < p->nf; ++f) Lmax = std::max(Lmax, p->r[f].L);
   int l1_index = 0;
@@ -154,7 +164,11 @@ qoz_status build_launches(qoz_batch* p, const std::vector<int>& l1_variant) {
     }
     for (LevelKey k : keys) {
       if (l == 1) {
-        k.variant = l1_index < (int)l1_variant.size() ? l1_variant[l1_index] : 0;
+        k.variant = l1_index < (int)l1_variant.size()
+                        ? l1_variant[l1_index]
+                        : (p->no_bulk ? 0 : kLevelVariantBulk);
+        if (k.variant == kLevelVariantBulk && p->no_bulk) k.variant = 0;
+        if (k.variant == kLevelVariantBulk) p->any_bulk = true;
         ++l1_index;
       }
       Group g;
@@ -181,7 +195,7 @@ qoz_status build_launches(qoz_batch* p, const std::vector<int>& l1_variant) {
         if (blocks > 0x7fffffffULL) return fail(QOZ_EUNSUPPORTED, "batched launch too large");
         p->map.insert(p->map.end(), (size_t)tiles, idx);
         p->items.push_back(it);
-        p->refs.push_back(ItemRef{f, l});
+        p->refs.push_back(ItemRef{f, l, k});
       }
       g.nitems = (int)p->items.size() - g.item_begin;
       g.nblocks = (unsigned)blocks;
@@ -215,14 +229,18 @@ qoz_status alloc_items(qoz_batch* p) {
   for (int f = 0; f < p->nf; ++f) n += (size_t)p->r[f].L;
   n = std::max<size_t>(n, 1);
   if (cudaMalloc((void**)&p->d_items, sizeof(LevelItem) * n) != cudaSuccess ||
-      cudaMallocHost((void**)&p->h_items, sizeof(LevelItem) * n) != cudaSuccess)
+      cudaMallocHost((void**)&p->h_items, sizeof(LevelItem) * n) != cudaSuccess ||
+      cudaMalloc((void**)&p->d_maps, sizeof(LevelTmaMaps) * n) != cudaSuccess ||
+      cudaMallocHost((void**)&p->h_maps, sizeof(LevelTmaMaps) * n) != cudaSuccess)
     return fail(QOZ_ENOMEM, "batch item table");
   return QOZ_OK;
 }
 
-// Per-run pointers into the pinned tables.
-void fill_tables(qoz_batch* p, const float* const* x, const double* eb, int rel,
+// Per-run pointers into the pinned tables; false when a bulk-copy item's
+// arrays do not allow its tensor maps (nothing else is affected).
+bool fill_tables(qoz_batch* p, const float* const* x, const double* eb, int rel,
                  qoz_blob* const* outs) {
+  bool maps_ok = true;
   for (int f = 0; f < p->nf; ++f) {
     const Resolved& r = p->r[f];
     BatchFieldDesc& d = p->h_desc[f];
@@ -264,7 +282,10 @@ void fill_tables(qoz_batch* p, const float* const* x, const double* eb, int rel,
     it.vec = it.L.xs[2] == 1 && (it.L.xs[1] % 4) == 0 && (it.L.xs[0] % 4) == 0 &&
              (reinterpret_cast<uintptr_t>(it.L.x) & 15) == 0;
     p->h_items[i] = it;
+    if (p->refs[i].key.variant == kLevelVariantBulk)
+      maps_ok = maps_ok && level_tma_maps(p->refs[i].key, it.L, &p->h_maps[i]);
   }
+  return maps_ok;
 }
 
 // The run's device sequence on stream s (captured or issued directly).
@@ -274,6 +295,9 @@ cudaError_t enqueue(qoz_batch* p, int rel, cudaStream_t s) {
                                   cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && !p->items.empty())
     e = cudaMemcpyAsync(p->d_items, p->h_items, sizeof(LevelItem) * p->items.size(),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && p->any_bulk)
+    e = cudaMemcpyAsync(p->d_maps, p->h_maps, sizeof(LevelTmaMaps) * p->items.size(),
                         cudaMemcpyHostToDevice, s);
   auto step = [&](cudaError_t r) {
     if (e == cudaSuccess) {
@@ -290,7 +314,8 @@ cudaError_t enqueue(qoz_batch* p, int rel, cudaStream_t s) {
   if (e == cudaSuccess) step(launch_anchor_batch(p->d_desc, p->nf, s));
   for (const Group& g : p->groups)
     if (e == cudaSuccess)
-      step(launch_level_batch(g.key, p->d_items, p->d_map + g.map_begin, g.nblocks, s));
+      step(launch_level_batch(g.key, p->d_items, p->d_map + g.map_begin, p->d_maps, g.nblocks,
+                              s));
   if (e == cudaSuccess) step(launch_batch_finish(p->d_desc, p->nf, s));
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(p->h_back, p->d_scratch + p->off_bt, p->back_bytes,
@@ -356,7 +381,10 @@ qoz_status autotune(qoz_batch* p, int rel, const float* const* x, const double* 
     if (st == QOZ_OK) st = upload_maps(p);
     if (st == QOZ_OK) st = prepare_kernels(p);
     if (st != QOZ_OK) break;
-    fill_tables(p, x, eb, rel, outs);
+    if (!fill_tables(p, x, eb, rel, outs)) {
+      for (int k = 0; k < n1; ++k) ms[k][v] = 1e30;  // bulk copies not possible here
+      continue;
+    }
     cudaError_t e = enqueue(p, rel, s);  // coarse levels in place for this layout
     int k = 0;
     for (const Group& g : p->groups) {
@@ -364,7 +392,8 @@ qoz_status autotune(qoz_batch* p, int rel, const float* const* x, const double* 
       float best = 1e30f;
       for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
         cudaEventRecord(a, s);
-        e = launch_level_batch(g.key, p->d_items, p->d_map + g.map_begin, g.nblocks, s);
+        e = launch_level_batch(g.key, p->d_items, p->d_map + g.map_begin, p->d_maps, g.nblocks,
+                               s);
         cudaEventRecord(b, s);
         if (e == cudaSuccess) e = cudaEventSynchronize(b);
         float t = 0.f;
@@ -410,10 +439,12 @@ void free_plan(qoz_batch* p) {
   cudaFree(p->d_pmax);
   cudaFree(p->d_pcnt);
   cudaFree(p->d_items);
+  cudaFree(p->d_maps);
   cudaFree(p->d_map);
   cudaFree(p->d_desc);
   cudaFreeHost(p->h_desc);
   cudaFreeHost(p->h_items);
+  cudaFreeHost(p->h_maps);
   cudaFreeHost(p->h_back);
   delete p;
 }
@@ -563,8 +594,19 @@ qoz_status qoz_batch_compress(qoz_batch* p, const float* const* d_fields, const 
     st = autotune(p, rel, d_fields, eb, outs, s);
     if (st == QOZ_OK) drop_graph(p);
   }
+  if (st == QOZ_OK && !fill_tables(p, d_fields, eb, rel, outs)) {
+    // this run's arrays rule out bulk copies: row copies from now on
+    p->no_bulk = true;
+    std::vector<int> l1;
+    for (const Group& g : p->groups)
+      if (g.level == 1) l1.push_back(g.key.variant == kLevelVariantBulk ? 0 : g.key.variant);
+    st = build_launches(p, l1);
+    if (st == QOZ_OK) st = upload_maps(p);
+    if (st == QOZ_OK) st = prepare_kernels(p);
+    drop_graph(p);
+    if (st == QOZ_OK) fill_tables(p, d_fields, eb, rel, outs);
+  }
   if (st == QOZ_OK) {
-    fill_tables(p, d_fields, eb, rel, outs);
     const bool use_graph = !(p->flags & QOZ_BATCH_NO_GRAPH);
     if (use_graph && (!p->exec || p->graph_rel != rel)) st = capture(p, rel);
     if (st == QOZ_OK) {
@@ -648,7 +690,7 @@ qoz_status qoz_batch_get_info(const qoz_batch* p, qoz_batch_info* info) {
     if (g.level != 1) continue;
     if (k < 16) {
       info->level1_variant[k] = g.key.variant;
-      for (int v = 0; v < kLevelVariants && v < 2; ++v) info->level1_ms[k][v] = g.ms[v];
+      for (int v = 0; v < kLevelVariants; ++v) info->level1_ms[k][v] = g.ms[v];
     }
     ++k;
   }

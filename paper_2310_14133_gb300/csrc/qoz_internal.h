@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "qoz_device.cuh"
@@ -59,14 +60,26 @@ struct LevelItem {
   unsigned tile_begin;  // first CTA of this item in its launch
 };
 // Kernel instance of a batched launch: 2-D or 3-D, the level's order, whether
-// the launch accumulates the histogram (level 1), and the tile variant.
+// the launch accumulates the histogram (level 1), the level's interpolator
+// and the tile variant (0, 1: row copies; 2: bulk tensor copies, level 1
+// only, which needs the tensor maps of each item).
 struct LevelKey {
   bool is2d;
   int order3;
   bool hist;
+  int interp;
   int variant;
 };
-constexpr int kLevelVariants = 2;
+constexpr int kLevelVariants = 3;
+constexpr int kLevelVariantBulk = 2;
+// Tensor maps of one item of a bulk-copy launch (device memory).
+struct alignas(64) LevelTmaMaps {
+  CUtensorMap x, rc, cc, out;
+  int use_out;
+};
+// Encodes an item's tensor maps for the key's bulk-copy tiles; false when
+// the item's arrays do not meet the bulk-copy alignment rules.
+bool level_tma_maps(const LevelKey& k, const LevelLaunch& L, LevelTmaMaps* m);
 // Tile extent (z, y, x) of a key's kernel instance.
 void level_tile_shape(const LevelKey& k, int t[3]);
 // Tiles of one item under the key's tile shape (nt[0] * nt[1] * nt[2]).
@@ -75,7 +88,8 @@ long long level_item_tiles(const LevelKey& k, const LevelLaunch& L, long long nt
 // stream capture.
 cudaError_t level_batch_prepare(const LevelKey& k);
 cudaError_t launch_level_batch(const LevelKey& k, const LevelItem* d_items,
-                               const uint16_t* d_map, unsigned nblocks, cudaStream_t s);
+                               const uint16_t* d_map, const LevelTmaMaps* d_maps,
+                               unsigned nblocks, cudaStream_t s);
 cudaError_t launch_anchor_gather(const float* x, float* anchors, const long long na[3],
                                  const long long fst[3], long long stride, cudaStream_t s);
 

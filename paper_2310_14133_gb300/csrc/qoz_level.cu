@@ -72,42 +72,55 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 
 // Runs the level-1 launch with bulk tensor copies when the grid is the field
 // itself and every array's rows start on 16-byte boundaries; returns false
 // (nothing launched) otherwise.
-template <int A0, int A1, int A2, int TZ, int TY, int TX, int THR, int IP, bool HIST>
-bool try_launch_tma(const LevelLaunch& a, cudaStream_t s, cudaError_t* err) {
-  using G = Geo<A0, A1, A2, TZ, TY, TX, THR, IP>;
-  if (a.interp != IP) return false;
+// Tensor maps of a level-1 launch for tiles TZ x TY x TX with halos HZ, HY:
+// the field box, the coarse reconstruction box, the coarse code box and (when
+// the code array's rows allow) the code tile store; false when an array
+// does not meet the bulk-copy alignment rules.
+bool encode_level_maps(const LevelLaunch& a, int TZ, int TY, int TX, int HZ, int HY,
+                       LevelTmaMaps* m) {
   if (!tma_enabled() || a.decompress || a.xs[2] != 1 || !a.cin || !a.rc) return false;
   if (!aligned16(a.x) || !aligned16(a.rc) || !aligned16(a.cin)) return false;
   if (a.xs[1] % 4 || a.xs[0] % 4 || a.cs[1] % 8 || a.cs[0] % 8) return false;
   const unsigned long long g2 = a.g[2], g1 = a.g[1], g0 = a.g[0];
   const unsigned long long c2 = (g2 + 1) / 2, c1 = (g1 + 1) / 2, c0 = (g0 + 1) / 2;
-  CUtensorMap mx, mrc, mcc, mout;
-  memset(&mout, 0, sizeof(mout));
+  memset(m, 0, sizeof(*m));
   {
     const unsigned long long d[3] = {g2, g1, g0};
     const unsigned long long st[2] = {4ull * a.xs[1], 4ull * a.xs[0]};
-    const unsigned bx[3] = {G::EX, G::EY, G::EZ};
-    if (!encode_map(&mx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, a.x, d, st, bx)) return false;
+    const unsigned bx[3] = {(unsigned)(TX + 8), (unsigned)(TY + 2 * HY), (unsigned)(TZ + 2 * HZ)};
+    if (!encode_map(&m->x, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, a.x, d, st, bx)) return false;
   }
   {
     const unsigned long long d[3] = {c2, c1, c0};
     const unsigned long long st[2] = {4ull * a.cs[1], 4ull * a.cs[0]};
-    const unsigned bx[3] = {G::CBX, G::CBY, G::CBZ};
-    if (!encode_map(&mrc, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, a.rc, d, st, bx)) return false;
+    const unsigned bx[3] = {(unsigned)(TX / 2 + 8), (unsigned)(TY / 2 + 4), (unsigned)(TZ / 2 + 4)};
+    if (!encode_map(&m->rc, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, a.rc, d, st, bx)) return false;
   }
   {
     const unsigned long long d[3] = {c2, c1, c0};
     const unsigned long long st[2] = {2ull * a.cs[1], 2ull * a.cs[0]};
-    const unsigned bx[3] = {G::CCX, G::CCY, G::CCZ};
-    if (!encode_map(&mcc, CU_TENSOR_MAP_DATA_TYPE_UINT16, a.cin, d, st, bx)) return false;
+    const unsigned bx[3] = {(unsigned)(TX / 2), (unsigned)((TY + 1) / 2), (unsigned)((TZ + 1) / 2)};
+    if (!encode_map(&m->cc, CU_TENSOR_MAP_DATA_TYPE_UINT16, a.cin, d, st, bx)) return false;
   }
-  int use_out = 0;
+  m->use_out = 0;
   if (aligned16(a.cout) && a.os[1] % 8 == 0 && a.os[0] % 8 == 0) {
     const unsigned long long d[3] = {g2, g1, g0};
     const unsigned long long st[2] = {2ull * a.os[1], 2ull * a.os[0]};
-    const unsigned bx[3] = {TX, TY, TZ};
-    use_out = encode_map(&mout, CU_TENSOR_MAP_DATA_TYPE_UINT16, a.cout, d, st, bx) ? 1 : 0;
+    const unsigned bx[3] = {(unsigned)TX, (unsigned)TY, (unsigned)TZ};
+    m->use_out = encode_map(&m->out, CU_TENSOR_MAP_DATA_TYPE_UINT16, a.cout, d, st, bx) ? 1 : 0;
   }
+  return true;
+}
+
+// Runs the level-1 launch with bulk tensor copies when the grid is the field
+// itself and every array's rows start on 16-byte boundaries; returns false
+// (nothing launched) otherwise.
+template <int A0, int A1, int A2, int TZ, int TY, int TX, int THR, int IP, bool HIST>
+bool try_launch_tma(const LevelLaunch& a, cudaStream_t s, cudaError_t* err) {
+  using G = Geo<A0, A1, A2, TZ, TY, TX, THR, IP>;
+  if (a.interp != IP) return false;
+  LevelTmaMaps m;
+  if (!encode_level_maps(a, TZ, TY, TX, G::HZ, G::HY, &m)) return false;
   static unsigned long long done = 0;
   constexpr size_t smem = G::tma_smem_bytes(HIST);
   static_assert((smem + 1088) * (1024 / THR) <= 228 * 1024, "tiles must fit the CTAs per SM");
@@ -126,7 +139,7 @@ bool try_launch_tma(const LevelLaunch& a, cudaStream_t s, cudaError_t* err) {
     return true;
   }
   level_tma_kernel<A0, A1, A2, TZ, TY, TX, THR, IP, HIST><<<(unsigned)nb, THR, smem, s>>>(
-      a, (int)nt1, (int)nt2, mx, mrc, mcc, mout, use_out);
+      a, (int)nt1, (int)nt2, m.x, m.rc, m.cc, m.out, m.use_out);
   note_launch(1);
   *err = cudaGetLastError();
   return true;
@@ -153,24 +166,10 @@ __global__ void anchor_gather_kernel(const float* __restrict__ x, float* __restr
   }
 }
 
-// Tiles of the bulk-copy launches: (TZ, TY, TX, threads) per order class.
-#ifndef QOZ_TMA_TILESET
-#define QOZ_TMA_TILESET 1
-#endif
 template <int A0, int A1, int A2, int IP, bool HIST>
 bool try_tma_order_ip(const LevelLaunch& a, cudaStream_t s, cudaError_t* err) {
-  if constexpr (A0 == 0 && QOZ_TMA_TILESET == 1)
-    return try_launch_tma<A0, A1, A2, 8, 16, 32, 256, IP, HIST>(a, s, err);
-  else if constexpr (A0 == 1 && QOZ_TMA_TILESET == 1)
-    return try_launch_tma<A0, A1, A2, 16, 8, 32, 256, IP, HIST>(a, s, err);
-  else if constexpr (A0 == 2 && QOZ_TMA_TILESET == 1)
-    return try_launch_tma<A0, A1, A2, 8, 8, 32, 256, IP, HIST>(a, s, err);
-  else if constexpr (A0 == 0)
-    return try_launch_tma<A0, A1, A2, 8, 16, 64, 512, IP, HIST>(a, s, err);
-  else if constexpr (A0 == 1)
-    return try_launch_tma<A0, A1, A2, 16, 8, 64, 512, IP, HIST>(a, s, err);
-  else
-    return try_launch_tma<A0, A1, A2, 12, 16, 32, 512, IP, HIST>(a, s, err);
+  constexpr TmaTile t = tma_tile_for(false, A0);
+  return try_launch_tma<A0, A1, A2, t.tz, t.ty, t.tx, t.thr, IP, HIST>(a, s, err);
 }
 
 // One instance per interpolator (the level's interpolator is a compile-time
@@ -189,9 +188,10 @@ cudaError_t launch_one(const LevelLaunch& a, cudaStream_t s) {
     if constexpr (TZ > 1) {
       if (try_tma_order<A0, A1, A2, HIST>(a, s, &te)) return te;
     } else {
-      const bool done = a.interp == 1
-                            ? try_launch_tma<A0, A1, A2, TZ, TY, TX, kThreads, 1, HIST>(a, s, &te)
-                            : try_launch_tma<A0, A1, A2, TZ, TY, TX, kThreads, 0, HIST>(a, s, &te);
+      constexpr TmaTile t = tma_tile_for(true, A0);
+      const bool done =
+          a.interp == 1 ? try_launch_tma<A0, A1, A2, t.tz, t.ty, t.tx, t.thr, 1, HIST>(a, s, &te)
+                        : try_launch_tma<A0, A1, A2, t.tz, t.ty, t.tx, t.thr, 0, HIST>(a, s, &te);
       if (done) return te;
     }
   }
@@ -299,6 +299,12 @@ cudaError_t launch_anchor_batch(const BatchFieldDesc* d, int nfields, cudaStream
   anchor_batch_kernel<<<dim3(8, nfields), 256, 0, s>>>(d);
   note_launch(1);
   return cudaGetLastError();
+}
+
+bool level_tma_maps(const LevelKey& k, const LevelLaunch& L, LevelTmaMaps* m) {
+  const int a0 = k.is2d ? 0 : kOrderAxis0[k.order3];
+  const TmaTile t = tma_tile_for(k.is2d, a0);
+  return encode_level_maps(L, t.tz, t.ty, t.tx, halo_z(a0), halo_y(a0), m);
 }
 
 }  // namespace qoz

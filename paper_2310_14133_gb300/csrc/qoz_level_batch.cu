@@ -3,8 +3,9 @@
 // Each CTA reads its item from the per-CTA map, copies the item's descriptor
 // into shared memory and runs the same tile code as the single-field launch,
 // so every field's codes, reconstruction, list and histogram are those of a
-// single-field compression.  Two tile shapes per instance are compiled; the
-// batch plan times them on its first run and keeps the faster.
+// single-field compression.  Two row-copy tile shapes per instance are
+// compiled, and for level 1 the bulk-copy kernel; the batch plan times them
+// on its first run and keeps the fastest.
 #include "qoz_level_impl.cuh"
 
 namespace qoz {
@@ -26,10 +27,31 @@ __global__ void __launch_bounds__(kThreads, 2)
                                                   it.nt1, it.nt2, it.vec);
 }
 
+// Level 1 with bulk tensor copies: the item's tensor maps sit in device
+// memory next to the item table.
+template <int A0, int A1, int A2, int TZ, int TY, int TX, int THR, int IP>
+__global__ void __launch_bounds__(THR, 1024 / THR)
+    level_tma_batch_kernel(const LevelItem* __restrict__ items, const uint16_t* __restrict__ map,
+                           const LevelTmaMaps* __restrict__ maps) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(16) LevelItem it;
+  __shared__ __align__(8) uint64_t mbar;
+  const unsigned k = map[blockIdx.x];
+  if (threadIdx.x < sizeof(LevelItem) / 4)
+    reinterpret_cast<unsigned*>(&it)[threadIdx.x] =
+        reinterpret_cast<const unsigned*>(items + k)[threadIdx.x];
+  __syncthreads();
+  const LevelTmaMaps* mp = maps + k;
+  level_tile_tma<A0, A1, A2, TZ, TY, TX, THR, IP, true>(
+      it.L, smem, &mbar, (int)(blockIdx.x - it.tile_begin), it.nt1, it.nt2, &mp->x, &mp->rc,
+      &mp->cc, mp->use_out ? &mp->out : nullptr);
+}
+
 struct Info {
   const void* fn;
   size_t smem;
   int t[3];
+  int threads;
   unsigned long long* done;
 };
 
@@ -40,7 +62,32 @@ Info info_of() {
   constexpr size_t smem = G::smem_bytes(false, HIST);
   static_assert(smem + sizeof(LevelItem) <= 112 * 1024, "two CTAs per SM");
   return Info{(const void*)level_batch_kernel<A0, A1, A2, TZ, TY, TX, HIST>, smem, {TZ, TY, TX},
-              &done};
+              kThreads, &done};
+}
+
+template <int A0, int A1, int A2, bool IS2D, int IP>
+Info info_tma() {
+  constexpr TmaTile t = tma_tile_for(IS2D, A0);
+  using G = Geo<A0, A1, A2, t.tz, t.ty, t.tx, t.thr, IP>;
+  static unsigned long long done = 0;
+  constexpr size_t smem = G::tma_smem_bytes(true);
+  static_assert((smem + sizeof(LevelItem) + 1088) * (1024 / t.thr) <= 228 * 1024,
+                "tiles must fit the CTAs per SM");
+  return Info{(const void*)level_tma_batch_kernel<A0, A1, A2, t.tz, t.ty, t.tx, t.thr, IP>, smem,
+              {t.tz, t.ty, t.tx}, t.thr, &done};
+}
+
+template <int IP>
+Info info_tma_ip(int is2d, int order3) {
+  if (is2d) return order3 == 0 ? info_tma<0, 1, 2, true, IP>() : info_tma<0, 2, 1, true, IP>();
+  switch (order3) {
+    case 0: return info_tma<0, 1, 2, false, IP>();
+    case 1: return info_tma<0, 2, 1, false, IP>();
+    case 2: return info_tma<1, 0, 2, false, IP>();
+    case 3: return info_tma<1, 2, 0, false, IP>();
+    case 4: return info_tma<2, 0, 1, false, IP>();
+    default: return info_tma<2, 1, 0, false, IP>();
+  }
 }
 
 // Tile shapes: variant 0 is the single-field launch's shape; variant 1
@@ -64,6 +111,8 @@ Info info_h(int is2d, int order3, int v) {
 }
 
 Info get_info(const LevelKey& k) {
+  if (k.variant == kLevelVariantBulk)
+    return k.interp == 1 ? info_tma_ip<1>(k.is2d, k.order3) : info_tma_ip<0>(k.is2d, k.order3);
   const int v = k.variant ? 1 : 0;
   return k.hist ? info_h<true>(k.is2d, k.order3, v) : info_h<false>(k.is2d, k.order3, v);
 }
@@ -88,11 +137,11 @@ cudaError_t level_batch_prepare(const LevelKey& k) {
 }
 
 cudaError_t launch_level_batch(const LevelKey& k, const LevelItem* d_items, const uint16_t* d_map,
-                               unsigned nblocks, cudaStream_t s) {
+                               const LevelTmaMaps* d_maps, unsigned nblocks, cudaStream_t s) {
   if (nblocks == 0) return cudaSuccess;
   const Info in = get_info(k);
-  void* args[] = {(void*)&d_items, (void*)&d_map};
-  cudaError_t e = cudaLaunchKernel(in.fn, dim3(nblocks), dim3(kThreads), args, in.smem, s);
+  void* args[] = {(void*)&d_items, (void*)&d_map, (void*)&d_maps};
+  cudaError_t e = cudaLaunchKernel(in.fn, dim3(nblocks), dim3(in.threads), args, in.smem, s);
   note_launch(1);
   return e;
 }

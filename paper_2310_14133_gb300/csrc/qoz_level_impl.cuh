@@ -87,6 +87,10 @@ __host__ __device__ constexpr int pick_seg(int NT, int lines, int threads = kThr
   return seg;
 }
 
+// Halo of a tile along z and y: the axis interpolated first (A0) needs none.
+__host__ __device__ constexpr int halo_z(int a0) { return a0 == 0 ? 0 : kHalo; }
+__host__ __device__ constexpr int halo_y(int a0) { return a0 == 1 ? 0 : kHalo; }
+
 template <int A0_, int A1_, int A2_, int TZ_, int TY_, int TX_, int THR_ = kThreads,
           int IP_ = -1>
 struct Geo {
@@ -95,8 +99,8 @@ struct Geo {
   static constexpr int kThr = THR_;    // threads of the CTA that owns the tile
   static constexpr int kInterp = IP_;  // interpolator fixed at compile time (-1: runtime)
   __host__ __device__ static constexpr int T(int p) { return p == 0 ? TZ : (p == 1 ? TY : TX); }
-  static constexpr int HZ = A0 == 0 ? 0 : kHalo;
-  static constexpr int HY = A0 == 1 ? 0 : kHalo;
+  static constexpr int HZ = halo_z(A0);
+  static constexpr int HY = halo_y(A0);
   static constexpr int EZ = TZ + 2 * HZ, EY = TY + 2 * HY;
   static constexpr int EX = TX + 8;  // local x in [-4, TX + 4), stored at x + 4
   static constexpr int HX = EX / 2;  // even x of a row: -4, -2, ..., TX + 2
@@ -676,6 +680,22 @@ __device__ __forceinline__ void bulk_wait_read0() {
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
+
+// Tile (z, y, x extents and threads) of the bulk-copy level-1 launches, by
+// the axis the level's order takes first: the first axis carries no halo and
+// gets the short extent; 256-thread CTAs, four per SM.  2-D fields (z extent
+// 1) take 32 x 128 tiles with 512 threads.
+struct TmaTile {
+  int tz, ty, tx, thr;
+};
+__host__ __device__ constexpr TmaTile tma_tile_for(bool is2d, int a0) {
+  return is2d ? TmaTile{1, 32, 128, 512}
+              : (a0 == 0 ? TmaTile{8, 16, 32, 256}
+                         : (a0 == 1 ? TmaTile{16, 8, 32, 256} : TmaTile{8, 8, 32, 256}));
+}
+// The first axis of each 3-D order (orders enumerate the axis permutations
+// lexicographically).
+constexpr int kOrderAxis0[6] = {0, 0, 1, 1, 2, 2};
 
 // Polls of the tile's mbarrier before the CTA gives up (a copy that has not
 // landed after this many polls is reported through a.err, bit 2).

@@ -117,11 +117,35 @@ def test_batch_absolute_bounds_and_autotune(q, orc):
     inf = plan.info()
     assert inf.autotuned == 1 and inf.level1_groups >= 1
     for i in range(min(16, inf.level1_groups)):
-        assert inf.level1_variant[i] in (0, 1)
+        assert inf.level1_variant[i] in (0, 1, 2)
         assert inf.level1_ms[i][0] > 0 and inf.level1_ms[i][1] > 0
     for x, b, e, op in zip(fields, blobs, ebs, ops):
         _vs_oracle(orc, b, x.cpu().numpy(), e, op)
         b.free()
+    plan.free()
+
+
+# every row starts on a 16-byte boundary: level 1 takes the bulk tensor copies
+BULK_SHAPES = [(37, 50, 148), (64, 128), (33, 33, 36), (300, 520), (20, 70, 40)]
+
+
+@pytest.mark.parametrize("autotune", [False, True])
+def test_batch_bulk_copies_match_oracle(q, orc, autotune):
+    fields = _fields(7, BULK_SHAPES)
+    qps, ops = _params(q, orc, BULK_SHAPES, 10)
+    plan = q.Batch(BULK_SHAPES, qps, autotune=autotune)
+    for run in range(2):
+        if run == 1:
+            fields = _fields(8, BULK_SHAPES)
+        blobs = plan.compress(fields, 1e-3)
+        for x, b, qp, op in zip(fields, blobs, qps, ops):
+            xn = x.cpu().numpy()
+            mn, mx, _ = orc.value_range(xn)
+            _vs_oracle(orc, b, xn, 1e-3 * (float(mx) - float(mn)), op)
+            b.free()
+    inf = plan.info()
+    if not autotune:
+        assert all(inf.level1_variant[i] == 2 for i in range(inf.level1_groups))
     plan.free()
 
 
