@@ -38,7 +38,8 @@ qoz_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 // Host-side fault injection for the failure-path tests: QOZ_FAULT is a
-// comma-separated list of steps to fail ("alloc", "launch", "header").
+// comma-separated list of steps to fail ("alloc", "launch", "header",
+// "tma_wait").
 bool fault_injected(const char* step) {
   const char* env = getenv("QOZ_FAULT");
   if (!env || !*env) return false;
@@ -232,6 +233,12 @@ cudaError_t run_levels(bool decompress, const Resolved& r, const float* x, uint1
     } else {
       L.x = x;
       L.err = err;  // compress: bit 2 reports a tile copy that never landed
+      if (l == 1 && fault_injected("tma_wait")) {
+        // host fault injection: the tile barrier expects 16 bytes that never
+        // come, so every bounded wait runs out after 4096 polls
+        L.extra_tx = 16;
+        L.wait_polls = 4096;
+      }
       L.cin = l == r.L ? nullptr : (const uint16_t*)(coarse_base + cl.coff[l]);
       L.cout = l > 1 ? (uint16_t*)(coarse_base + cl.coff[l - 1]) : codes;
       L.ul = ul;

@@ -41,6 +41,11 @@ struct LevelLaunch {
   long long nu;
   int* err;           // decompress: set to 1 if a code-0 point has no list entry
   unsigned* hist;     // compress, level 1: 65536-bin code histogram (optional)
+  // bulk-copy tiles: bytes the tile's mbarrier expects beyond its copies (0;
+  // a positive value is the host fault injection that makes the wait run
+  // out) and the wait's poll limit (0: the default)
+  int extra_tx;
+  int wait_polls;
 };
 
 // Launch wrappers (qoz_level.cu)

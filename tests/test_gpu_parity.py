@@ -246,6 +246,21 @@ def test_serialize_async_matches_sync(q):
     b2.free()
 
 
+def test_bulk_copy_wait_times_out_cleanly(q, monkeypatch):
+    # the level-1 tile barrier is told to expect 16 bytes more than its
+    # copies bring: every tile's bounded wait runs out, the launch reports
+    # the timeout, and the context stays usable
+    x = torch.rand((40, 48, 64), device="cuda")
+    monkeypatch.setenv("QOZ_FAULT", "tma_wait")
+    with pytest.raises(q.QozError) as ei:
+        q.compress(x, 1e-3)
+    assert ei.value.status == 5
+    monkeypatch.delenv("QOZ_FAULT")
+    b = q.compress(x, 1e-3)
+    assert b.info().n_points == x.numel()
+    b.free()
+
+
 def test_host_fault_injection(q, monkeypatch):
     x = torch.zeros((16, 16, 16), device="cuda")
     monkeypatch.setenv("QOZ_FAULT", "alloc")
