@@ -120,6 +120,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(value: float, dist=None) -> float:
+    """The largest value over the ranks (a replicated job takes as long as its
+    slowest rank); the value itself without a process group."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gbs(points_per_rank: int, world: int, seconds: float) -> float:
+    """Whole-job FP32 input GB/s: every rank compresses its own field."""
+    return 4.0 * points_per_rank * world / seconds / 1e9
+
+
 def _peak_hbm():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -524,12 +541,9 @@ def main():
     clk = clocks.stop()
     q.profile_enable(False)
     prof = q.profile_read(reset=True)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     ms_step = ms / args.steps
-    value = 4.0 * N * world / (ms_step * 1e-3) / 1e9
+    value = job_gbs(N, world, ms_step * 1e-3)
 
     lvl1_ms = prof.ms[q.STAGE_LEVEL + 1] / max(1, prof.calls[q.STAGE_LEVEL + 1])
     pq_ms = sum(prof.ms[q.STAGE_LEVEL + l] for l in range(1, 9)) / args.steps
