@@ -82,6 +82,12 @@ struct alignas(64) LevelTmaMaps {
   CUtensorMap x, rc, cc, out;
   int use_out;
 };
+// A rank-3 tiled tensor map (dims and box innermost first, strides in bytes
+// of dims 1 and 2, zero fill outside the array); false when the driver's
+// encoder is unavailable or rejects the map.
+bool encode_tensor_map_3d(CUtensorMap* m, CUtensorMapDataType type, const void* base,
+                          const unsigned long long dims[3], const unsigned long long strides[2],
+                          const unsigned box[3]);
 // Encodes an item's tensor maps for the key's bulk-copy tiles; false when
 // the item's arrays do not meet the bulk-copy alignment rules.
 bool level_tma_maps(const LevelKey& k, const LevelLaunch& L, LevelTmaMaps* m);

@@ -9,26 +9,11 @@
 #include "qoz_level_impl.cuh"
 
 namespace qoz {
-namespace {
-
-// Level-1 compression with bulk tensor copies (see level_tile_tma).
-template <int A0, int A1, int A2, int TZ, int TY, int TX, int THR, int IP, bool HIST>
-__global__ void __launch_bounds__(THR, 1024 / THR)
-    level_tma_kernel(const LevelLaunch a, int nt1, int nt2, const __grid_constant__ CUtensorMap mx,
-                     const __grid_constant__ CUtensorMap mrc,
-                     const __grid_constant__ CUtensorMap mcc,
-                     const __grid_constant__ CUtensorMap mout, int use_out) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t mbar;
-  level_tile_tma<A0, A1, A2, TZ, TY, TX, THR, IP, HIST>(a, smem, &mbar, blockIdx.x, nt1, nt2,
-                                                        &mx, &mrc, &mcc,
-                                                        use_out ? &mout : nullptr);
-}
 
 // The driver's tensor-map encoder, looked up through the runtime (the
 // library does not link the driver library itself, so that it loads on
 // hosts without a GPU driver); null when unavailable.
-PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+static PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -45,7 +30,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
 
 // A rank-3 tiled tensor map (dims and box innermost first; strides in bytes
 // of dims 1 and 2); false when the driver rejects it.
-bool encode_map(CUtensorMap* m, CUtensorMapDataType type, const void* base,
+bool encode_tensor_map_3d(CUtensorMap* m, CUtensorMapDataType type, const void* base,
                 const unsigned long long dims[3], const unsigned long long strides[2],
                 const unsigned box[3]) {
   const PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
@@ -57,6 +42,22 @@ bool encode_map(CUtensorMap* m, CUtensorMapDataType type, const void* base,
   return enc(m, type, 3, const_cast<void*>(base), d, st, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+namespace {
+
+// Level-1 compression with bulk tensor copies (see level_tile_tma).
+template <int A0, int A1, int A2, int TZ, int TY, int TX, int THR, int IP, bool HIST>
+__global__ void __launch_bounds__(THR, 1024 / THR)
+    level_tma_kernel(const LevelLaunch a, int nt1, int nt2, const __grid_constant__ CUtensorMap mx,
+                     const __grid_constant__ CUtensorMap mrc,
+                     const __grid_constant__ CUtensorMap mcc,
+                     const __grid_constant__ CUtensorMap mout, int use_out) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  level_tile_tma<A0, A1, A2, TZ, TY, TX, THR, IP, HIST>(a, smem, &mbar, blockIdx.x, nt1, nt2,
+                                                        &mx, &mrc, &mcc,
+                                                        use_out ? &mout : nullptr);
 }
 
 bool tma_enabled() {
@@ -88,26 +89,26 @@ bool encode_level_maps(const LevelLaunch& a, int TZ, int TY, int TX, int HZ, int
     const unsigned long long d[3] = {g2, g1, g0};
     const unsigned long long st[2] = {4ull * a.xs[1], 4ull * a.xs[0]};
     const unsigned bx[3] = {(unsigned)(TX + 8), (unsigned)(TY + 2 * HY), (unsigned)(TZ + 2 * HZ)};
-    if (!encode_map(&m->x, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, a.x, d, st, bx)) return false;
+    if (!encode_tensor_map_3d(&m->x, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, a.x, d, st, bx)) return false;
   }
   {
     const unsigned long long d[3] = {c2, c1, c0};
     const unsigned long long st[2] = {4ull * a.cs[1], 4ull * a.cs[0]};
     const unsigned bx[3] = {(unsigned)(TX / 2 + 8), (unsigned)(TY / 2 + 4), (unsigned)(TZ / 2 + 4)};
-    if (!encode_map(&m->rc, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, a.rc, d, st, bx)) return false;
+    if (!encode_tensor_map_3d(&m->rc, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, a.rc, d, st, bx)) return false;
   }
   {
     const unsigned long long d[3] = {c2, c1, c0};
     const unsigned long long st[2] = {2ull * a.cs[1], 2ull * a.cs[0]};
     const unsigned bx[3] = {(unsigned)(TX / 2), (unsigned)((TY + 1) / 2), (unsigned)((TZ + 1) / 2)};
-    if (!encode_map(&m->cc, CU_TENSOR_MAP_DATA_TYPE_UINT16, a.cin, d, st, bx)) return false;
+    if (!encode_tensor_map_3d(&m->cc, CU_TENSOR_MAP_DATA_TYPE_UINT16, a.cin, d, st, bx)) return false;
   }
   m->use_out = 0;
   if (aligned16(a.cout) && a.os[1] % 8 == 0 && a.os[0] % 8 == 0) {
     const unsigned long long d[3] = {g2, g1, g0};
     const unsigned long long st[2] = {2ull * a.os[1], 2ull * a.os[0]};
     const unsigned bx[3] = {(unsigned)TX, (unsigned)TY, (unsigned)TZ};
-    m->use_out = encode_map(&m->out, CU_TENSOR_MAP_DATA_TYPE_UINT16, a.cout, d, st, bx) ? 1 : 0;
+    m->use_out = encode_tensor_map_3d(&m->out, CU_TENSOR_MAP_DATA_TYPE_UINT16, a.cout, d, st, bx) ? 1 : 0;
   }
   return true;
 }

@@ -22,6 +22,7 @@
 #include "../../include/qoz.h"
 #include "qoz_host.h"
 #include "qoz_internal.h"
+#include "qoz_tma.cuh"
 
 namespace qoz {
 namespace {
@@ -52,6 +53,8 @@ struct TrialArgs {
   int metrics;             // accumulate sse / max error / SSIM after the last level
   int ssim_win, ssim_step, is3d;
   double c1, c2;
+  int use_tma;             // full-resolution block by one bulk tensor copy (tensor map given)
+  int pitch;               // row pitch of the block in shared memory (values)
 };
 
 // Compensated (Kahan) binary32 accumulator for per-target sums: double
@@ -82,13 +85,21 @@ __device__ __forceinline__ double warp_max(double v) {
 // and level l of the block is level l - stop_level + 1 of the subsampled
 // grid (half-stride 2^(l - stop_level)).  x becomes the reconstruction in
 // place, target by target.
-__global__ void __launch_bounds__(kTrialThreads, 1) trial_kernel(const TrialArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
+// Polls of the block copy's mbarrier before the CTA gives up (the out slot's
+// flag then reports it).
+constexpr unsigned kTrialWaitPolls = 1u << 24;
+
+__global__ void __launch_bounds__(kTrialThreads, 1)
+    trial_kernel(const TrialArgs a, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mbar;
   const int f = 1 << (a.stop_level - 1);
   const int m0 = (a.bd[0] - 1) / f + 1, m1 = (a.bd[1] - 1) / f + 1, m2 = (a.bd[2] - 1) / f + 1;
-  const int mt = m0 * m1 * m2;
-  float* S = reinterpret_cast<float*>(smem);
-  unsigned* SH = reinterpret_cast<unsigned*>(smem + ((sizeof(float) * mt + 15) & ~size_t(15)));
+  const int P = a.pitch;  // >= m2 (+ the bulk copy's 16-byte shift)
+  // 128-byte aligned block buffer; the histogram window after it
+  unsigned char* base = smem + ((128u - (smem_u32(smem) & 127u)) & 127u);
+  unsigned* SH = reinterpret_cast<unsigned*>(
+      base + (((size_t)sizeof(float) * m0 * m1 * P + 15) & ~size_t(15)));
   __shared__ double red[kTrialThreads / 32][7];
 
   const int cand = blockIdx.x / a.nblocks;
@@ -98,25 +109,68 @@ __global__ void __launch_bounds__(kTrialThreads, 1) trial_kernel(const TrialArgs
   const float* xb = a.x + (long long)oz * a.st0 + (long long)oy * a.st1 + ox;
   const long long fs0 = (long long)f * a.st0, fs1 = (long long)f * a.st1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  // the bulk copy starts at the 16-byte boundary at or below the block's x
+  // origin; the block itself then starts ox mod 4 values into the buffer
+  float* S = reinterpret_cast<float*>(base) + (a.use_tma ? (ox & 3) : 0);
 
-  for (int row = warp; row < m0 * m1; row += nw) {
-    const int z = row / m1, y = row - (row / m1) * m1;
-    const float* src = xb + z * fs0 + y * fs1;
-    float* dst = S + row * m2;
-    for (int xx = lane; xx < m2; xx += 32) {
-      const unsigned d = (unsigned)__cvta_generic_to_shared(dst + xx);
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src + xx * f)
-                   : "memory");
+  if (a.use_tma) {
+    if (threadIdx.x == 0) {
+      mbar_init(&mbar, 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      mbar_expect_tx(&mbar, (unsigned)(sizeof(float) * m0 * m1 * P));
+      tma_load_3d(base, &tmap, ox & ~3, oy, oz, &mbar);
+    }
+  } else {
+    for (int row = warp; row < m0 * m1; row += nw) {
+      const int z = row / m1, y = row - (row / m1) * m1;
+      const float* src = xb + z * fs0 + y * fs1;
+      float* dst = S + row * P;
+      for (int xx = lane; xx < m2; xx += 32) {
+        const unsigned d = (unsigned)__cvta_generic_to_shared(dst + xx);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src + xx * f)
+                     : "memory");
+      }
     }
   }
   if (a.hist)
     for (int i = threadIdx.x; i < kTHistWin; i += blockDim.x) SH[i] = 0;
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
-  __syncthreads();
+  if (a.use_tma) {
+    bool landed = false;
+    for (unsigned it = 0; it < kTrialWaitPolls; ++it)
+      if (mbar_try_wait(&mbar, 0)) {
+        landed = true;
+        break;
+      }
+    if (!__syncthreads_and(landed)) {
+      if (threadIdx.x == 0) a.out[((size_t)cand * a.nblocks + blk) * kOutStride + 7] = 1.0;
+      return;
+    }
+  } else {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+  }
 
-  KSum l1;
+  KSum l1, sse;
+  float mx = 0.0f;
   int l1n = 0, unp = 0;
-  const int st1 = m2, st0 = m1 * m2;
+  const int st1 = P, st0 = m1 * P;
+  if (a.metrics) {
+    // the block's anchors (never targets) reconstruct exactly: they add to
+    // the squared and maximum error only through non-finite values
+    const int as = 1 << (a.Ls - a.stop_level + 1);
+    const int n0 = (m0 - 1) / as + 1, n1a = (m1 - 1) / as + 1, n2a = (m2 - 1) / as + 1;
+    for (int i = threadIdx.x; i < n0 * n1a * n2a; i += kTrialThreads) {
+      const int i2 = i % n2a, r = i / n2a;
+      const float v = S[(r / n1a) * as * st0 + (r % n1a) * as * st1 + i2 * as];
+      const float d = __fsub_rn(v, v);
+      sse.add(__fmul_rn(d, d));
+      const float ad = fabsf(d);
+      if (ad != ad || ad > mx) mx = ad;
+    }
+  }
   for (int l = a.Ls; l >= a.stop_level; --l) {
     const int h = 1 << (l - a.stop_level);
     const float el = C.el[l - 1], two_e = C.two_e[l - 1], inv = C.inv[l - 1];
@@ -177,7 +231,14 @@ __global__ void __launch_bounds__(kTrialThreads, 1) trial_kernel(const TrialArgs
             S[li] = rec;
           } else {
             code = 0;
+            rec = xv;
             ++unp;
+          }
+          if (a.metrics) {  // every non-anchor point is a target once
+            const float d = __fsub_rn(xv, rec);
+            sse.add(__fmul_rn(d, d));
+            const float ad = fabsf(d);
+            if (ad != ad || ad > mx) mx = ad;
           }
           if (a.hist) {
             // lanes with equal codes add once (smooth data puts most of a
@@ -198,21 +259,9 @@ __global__ void __launch_bounds__(kTrialThreads, 1) trial_kernel(const TrialArgs
     }
   }
 
-  KSum sse;
-  float mx = 0.0f;
   double ss = 0.0, sn = 0.0;
   if (a.metrics) {  // stop_level == 1: S is the whole block
     const int n1 = a.bd[1], n2 = a.bd[2];
-    for (int row = warp; row < a.bd[0] * n1; row += nw) {
-      const int z = row / n1, y = row - (row / n1) * n1;
-      const float* src = xb + z * a.st0 + y * a.st1;
-      for (int xx = lane; xx < n2; xx += 32) {
-        const float d = __fsub_rn(src[xx], S[row * n2 + xx]);
-        sse.add(__fmul_rn(d, d));
-        const float ad = fabsf(d);
-        if (ad != ad || ad > mx) mx = ad;
-      }
-    }
     if (a.ssim_win > 0) {
       const int n0 = a.bd[0];
       const int w = a.ssim_win, sp = a.ssim_step;
@@ -233,7 +282,7 @@ __global__ void __launch_bounds__(kTrialThreads, 1) trial_kernel(const TrialArgs
           for (int j = 0; j < w; ++j) {
             const int z = w0 * sp + i, y = w1 * sp + j;
             const float* src = xb + z * a.st0 + y * a.st1 + w2 * sp;
-            const float* rec = S + (z * n1 + y) * n2 + w2 * sp;
+            const float* rec = S + (z * n1 + y) * P + w2 * sp;
             for (int k = 0; k < w; ++k) {
               sx = __fadd_rn(sx, src[k]);
               sy = __fadd_rn(sy, rec[k]);
@@ -245,7 +294,7 @@ __global__ void __launch_bounds__(kTrialThreads, 1) trial_kernel(const TrialArgs
           for (int j = 0; j < w; ++j) {
             const int z = w0 * sp + i, y = w1 * sp + j;
             const float* src = xb + z * a.st0 + y * a.st1 + w2 * sp;
-            const float* rec = S + (z * n1 + y) * n2 + w2 * sp;
+            const float* rec = S + (z * n1 + y) * P + w2 * sp;
             for (int k = 0; k < w; ++k) {
               const float dx = __fsub_rn(src[k], fx), dy = __fsub_rn(rec[k], fy);
               rx = __fadd_rn(rx, dx);
@@ -480,6 +529,20 @@ class Tuner {
       return fail(QOZ_ENOMEM, "tuner allocation");
     cudaMemcpyAsync(d_orig_, sm_.origins.data(), sizeof(int) * sm_.origins.size(),
                     cudaMemcpyHostToDevice, s_);
+    // full-resolution blocks arrive by one bulk tensor copy when the field's
+    // rows start on 16-byte boundaries: the copy starts at the boundary at or
+    // below each block's x origin, so rows hold up to 3 more values
+    memset(&tmap_, 0, sizeof(tmap_));
+    tma_pitch_ = (sm_.bd[2] + 3 + 3) & ~3;
+    const long long st1 = r_.n[2], st0 = r_.n[1] * r_.n[2];
+    if ((reinterpret_cast<uintptr_t>(x_) & 15) == 0 && st1 % 4 == 0 && st0 % 4 == 0 &&
+        tma_pitch_ <= 256 && sm_.bd[1] <= 256 && sm_.bd[0] <= 256) {
+      const unsigned long long d[3] = {(unsigned long long)r_.n[2], (unsigned long long)r_.n[1],
+                                       (unsigned long long)r_.n[0]};
+      const unsigned long long st[2] = {4ull * st1, 4ull * st0};
+      const unsigned bx[3] = {(unsigned)tma_pitch_, (unsigned)sm_.bd[1], (unsigned)sm_.bd[0]};
+      tma_ok_ = encode_tensor_map_3d(&tmap_, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, x_, d, st, bx);
+    }
     return QOZ_OK;
   }
 
@@ -528,16 +591,24 @@ class Tuner {
     a.c1 = (0.01 * vr_) * (0.01 * vr_);
     a.c2 = (0.03 * vr_) * (0.03 * vr_);
     const int f = 1 << (stop_level - 1);
-    const int npb = ((sm_.bd[0] - 1) / f + 1) * ((sm_.bd[1] - 1) / f + 1) * ((sm_.bd[2] - 1) / f + 1);
-    const size_t smem = ((sizeof(float) * npb + 15) & ~size_t(15)) +
-                        (full ? sizeof(unsigned) * kTHistWin : 0);
-    if (smem > 220 * 1024) return fail(QOZ_EUNSUPPORTED, "sample block too large (%d points)", npb);
+    const int m2 = (sm_.bd[2] - 1) / f + 1;
+    const long long rows = (long long)((sm_.bd[0] - 1) / f + 1) * ((sm_.bd[1] - 1) / f + 1);
+    auto smem_for = [&](int pitch) {
+      return (size_t)128 + ((sizeof(float) * rows * pitch + 15) & ~size_t(15)) +
+             (full ? sizeof(unsigned) * kTHistWin : 0);
+    };
+    a.use_tma = (tma_ok_ && f == 1 && smem_for(tma_pitch_) <= 220 * 1024) ? 1 : 0;
+    a.pitch = a.use_tma ? tma_pitch_ : m2;
+    const long long npb = rows * a.pitch;
+    const size_t smem = smem_for(a.pitch);
+    if (smem > 220 * 1024)
+      return fail(QOZ_EUNSUPPORTED, "sample block too large (%lld points)", npb);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute((const void*)trial_kernel,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
       ProfScope ps(QOZ_STAGE_TUNE, s_);
-      trial_kernel<<<nc * sm_.nb, kTrialThreads, smem, s_>>>(a);
+      trial_kernel<<<nc * sm_.nb, kTrialThreads, smem, s_>>>(a, tmap_);
       note_launch(1);
       e = launch_check(cudaGetLastError());
     }
@@ -573,6 +644,8 @@ class Tuner {
       if (e != cudaSuccess) return cuda_fail(e, "tuner histogram");
       hbits[c] = huffman_bits_u32(hist.data(), 65536);
     }
+    for (size_t i = 7; i < out.size(); i += kOutStride)
+      if (out[i] != 0.0) return fail(QOZ_ETIMEOUT, "a sample block's bulk copy did not complete");
     res->assign(nc, TrialResult{0, 0, 0});
     for (int c = 0; c < nc; ++c) {
       double l1 = 0, l1n = 0, unp = 0, sse = 0, mx = 0, ss = 0, sn = 0;
@@ -618,6 +691,9 @@ class Tuner {
   double* d_out_ = nullptr;
   unsigned* d_hist_ = nullptr;
   void* d_bits_ = nullptr;  // per candidate: prefix-code bits (u64), then host-fallback flags (int)
+  CUtensorMap tmap_;        // the field, boxes of one full-resolution sample block
+  bool tma_ok_ = false;
+  int tma_pitch_ = 0;
   int cap_c_ = 0;
   int trials_ = 0;
 };
