@@ -427,6 +427,71 @@ __global__ void __launch_bounds__(kHuffThreads)
   }
 }
 
+// Algorithm 1 on the device, one level at a time: the level's candidates
+// (interpolator, order) are scored by the mean |x - pred| of their trial
+// (sums over the blocks in block order, in double, as on the host); the
+// first candidate within 1e-12 relative of the best wins; the choice is
+// recorded and the next level's candidates are built (levels above keep the
+// choices made), so the levels run back to back without the host.
+struct Alg1Ctl {
+  unsigned char ci[16], co[16];  // candidate interpolators and orders
+  unsigned char chi[kMaxLevels], cho[kMaxLevels];  // choices per level
+  double score[kMaxLevels];
+};
+
+__constant__ int kPermDev[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+__device__ void set_axes_dev(TrialCand* c, int level, int ndims, int order) {
+  const int o3 = ndims == 3 ? order : (order == 0 ? 0 : 1);
+  for (int k = 0; k < 3; ++k) c->axes[level - 1][k] = (unsigned char)kPermDev[o3][k];
+}
+
+__global__ void __launch_bounds__(32) alg1_select_kernel(const double* __restrict__ out, int nc,
+                                                          int nb, int l, int Ls,
+                                                          const TrialCand base, int ndims,
+                                                          Alg1Ctl* ctl, TrialCand* cands) {
+  __shared__ double mean[32];
+  __shared__ int pick;
+  const int c = threadIdx.x;
+  if (c < nc) {  // one lane per candidate: its blocks summed in block order
+    double l1 = 0.0, l1n = 0.0;
+#pragma unroll 4
+    for (int b = 0; b < nb; ++b) {
+      l1 += out[((size_t)c * nb + b) * kOutStride + 0];
+      l1n += out[((size_t)c * nb + b) * kOutStride + 1];
+    }
+    mean[c] = l1n > 0 ? l1 / l1n : 0.0;
+  }
+  __syncwarp();
+  if (c == 0) {
+    double best = 0.0;
+    int bi = 0;
+    for (int k = 0; k < nc; ++k) {
+      const double cur = mean[k];
+      if (k == 0 || cur < best - 1e-12 * best) {
+        best = cur;
+        bi = k;
+      }
+    }
+    ctl->chi[l - 1] = ctl->ci[bi];
+    ctl->cho[l - 1] = ctl->co[bi];
+    ctl->score[l - 1] = best;
+    pick = bi;
+  }
+  __syncwarp();
+  if (l == 1 || c >= nc) return;
+  TrialCand t = base;
+  for (int ll = l + 1; ll <= Ls; ++ll) {
+    t.interp[ll - 1] = ctl->chi[ll - 1];
+    set_axes_dev(&t, ll, ndims, ctl->cho[ll - 1]);
+  }
+  t.interp[l - 1] = ctl->ci[pick];
+  set_axes_dev(&t, l, ndims, ctl->co[pick]);
+  t.interp[l - 2] = ctl->ci[c];
+  set_axes_dev(&t, l - 1, ndims, ctl->co[c]);
+  cands[c] = t;
+}
+
 // ------------------------------------------------------------- host side
 
 
@@ -546,12 +611,59 @@ class Tuner {
     return QOZ_OK;
   }
 
-  // Runs the given candidates; fills per-candidate results.  hist/metrics
-  // only when stop_level == 1.
-  qoz_status run(const std::vector<TrialCand>& cands, int stop_level, int score_level,
-                 bool full, std::vector<TrialResult>* res) {
-    const int nc = (int)cands.size();
-    if (nc == 0) return QOZ_OK;
+  // Algorithm 1 over levels Ls..1 on the device (alg1_select_kernel), one
+  // read-back at the end: the chosen interpolator and order per level and
+  // the winning mean |x - pred|.
+  qoz_status alg1(const TrialCand& base, const std::vector<std::pair<int, int>>& cl, int ndims,
+                  unsigned char* chi, unsigned char* cho, double* score) {
+    const int nc = (int)cl.size();
+    if (nc == 0 || nc > 16) return fail(QOZ_EINVAL, "1..16 Algorithm 1 candidates");
+    qoz_status st = ensure(nc);
+    if (st != QOZ_OK) return st;
+    Alg1Ctl h;
+    memset(&h, 0, sizeof(h));
+    for (int c = 0; c < nc; ++c) {
+      h.ci[c] = (unsigned char)cl[c].first;
+      h.co[c] = (unsigned char)cl[c].second;
+    }
+    std::vector<TrialCand> top;
+    for (int c = 0; c < nc; ++c) {
+      TrialCand t = base;
+      t.interp[sm_.Ls - 1] = h.ci[c];
+      set_axes(&t, sm_.Ls, ndims, h.co[c]);
+      top.push_back(t);
+    }
+    Alg1Ctl* d_ctl = nullptr;
+    cudaError_t e = dev_alloc((void**)&d_ctl, sizeof(Alg1Ctl), s_);
+    if (e != cudaSuccess) return fail(QOZ_ENOMEM, "tuner allocation");
+    e = cudaMemcpyAsync(d_ctl, &h, sizeof(h), cudaMemcpyHostToDevice, s_);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_cands_, top.data(), sizeof(TrialCand) * nc, cudaMemcpyHostToDevice,
+                          s_);
+    for (int l = sm_.Ls; l >= 1 && e == cudaSuccess; --l) {
+      st = launch(nc, l, l, false);
+      if (st != QOZ_OK) {
+        dev_free(d_ctl, s_);
+        return st;
+      }
+      alg1_select_kernel<<<1, 32, 0, s_>>>(d_out_, nc, sm_.nb, l, sm_.Ls, base, ndims, d_ctl,
+                                           d_cands_);
+      note_launch(1);
+      e = launch_check(cudaGetLastError());
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_ctl, sizeof(h), cudaMemcpyDeviceToHost, s_);
+    dev_free(d_ctl, s_);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s_);
+    if (e != cudaSuccess) return cuda_fail(e, "Algorithm 1");
+    for (int l = 1; l <= sm_.Ls; ++l) {
+      chi[l - 1] = h.chi[l - 1];
+      cho[l - 1] = h.cho[l - 1];
+      score[l - 1] = h.score[l - 1];
+    }
+    return QOZ_OK;
+  }
+
+  qoz_status ensure(int nc) {
     if (nc > cap_c_) {
       dev_free(d_cands_, s_);
       dev_free(d_out_, s_);
@@ -566,10 +678,14 @@ class Tuner {
               cudaSuccess)
         return fail(QOZ_ENOMEM, "tuner allocation");
     }
-    cudaError_t e = cudaMemcpyAsync(d_cands_, cands.data(), sizeof(TrialCand) * nc,
-                                    cudaMemcpyHostToDevice, s_);
-    if (e == cudaSuccess && full)
-      e = cudaMemsetAsync(d_hist_, 0, sizeof(unsigned) * 65536 * (size_t)nc, s_);
+    return QOZ_OK;
+  }
+
+  // Launches the trials of the nc candidates already in d_cands_ (and, with
+  // `full`, their prefix-code costs); no read-back.
+  qoz_status launch(int nc, int stop_level, int score_level, bool full) {
+    cudaError_t e = cudaSuccess;
+    if (full) e = cudaMemsetAsync(d_hist_, 0, sizeof(unsigned) * 65536 * (size_t)nc, s_);
     TrialArgs a;
     memset(&a, 0, sizeof(a));
     a.x = x_;
@@ -620,6 +736,24 @@ class Tuner {
       note_launch(1);
       e = launch_check(cudaGetLastError());
     }
+    if (e != cudaSuccess) return cuda_fail(e, "tuner trial");
+    return QOZ_OK;
+  }
+
+  // Runs the given candidates; fills per-candidate results.  hist/metrics
+  // only when stop_level == 1.
+  qoz_status run(const std::vector<TrialCand>& cands, int stop_level, int score_level,
+                 bool full, std::vector<TrialResult>* res) {
+    const int nc = (int)cands.size();
+    if (nc == 0) return QOZ_OK;
+    qoz_status st = ensure(nc);
+    if (st != QOZ_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(d_cands_, cands.data(), sizeof(TrialCand) * nc,
+                                    cudaMemcpyHostToDevice, s_);
+    if (e != cudaSuccess) return cuda_fail(e, "tuner trial");
+    if ((st = launch(nc, stop_level, score_level, full)) != QOZ_OK) return st;
+    unsigned long long* d_bits = reinterpret_cast<unsigned long long*>(d_bits_);
+    int* d_flag = reinterpret_cast<int*>(d_bits + nc);
     std::vector<double> out((size_t)kOutStride * nc * sm_.nb);
     std::vector<unsigned long long> hbits(nc, 0ull);
     std::vector<int> hflag(nc, 0);
@@ -863,34 +997,9 @@ qoz_status tune_impl(const float* d_field, const qoz_shape& shape, double rel_eb
   unsigned char ch_interp[kMaxLevels] = {0}, ch_order[kMaxLevels] = {0};
   fill_bounds(&base, e0, 1.0, 1.0, sm.Ls);
 
-  // ---- Algorithm 1, from the top sampled level down
+  // ---- Algorithm 1, from the top sampled level down (choices on the device)
   std::vector<TrialResult> res;
-  for (int l = sm.Ls; l >= 1; --l) {
-    std::vector<TrialCand> tc;
-    for (auto& cd : cands) {
-      TrialCand c = base;
-      for (int ll = l + 1; ll <= sm.Ls; ++ll) {
-        c.interp[ll - 1] = ch_interp[ll - 1];
-        set_axes(&c, ll, d, ch_order[ll - 1]);
-      }
-      c.interp[l - 1] = (unsigned char)cd.first;
-      set_axes(&c, l, d, cd.second);
-      tc.push_back(c);
-    }
-    if ((st = T.run(tc, l, l, false, &res)) != QOZ_OK) return st;
-    double best = INFINITY;
-    int bi = 0;
-    for (size_t c = 0; c < res.size(); ++c) {
-      const double cur = res[c].l1_mean;
-      if (c == 0 || cur < best - 1e-12 * best) {
-        best = cur;
-        bi = (int)c;
-      }
-    }
-    ch_interp[l - 1] = (unsigned char)cands[bi].first;
-    ch_order[l - 1] = (unsigned char)cands[bi].second;
-    out->alg1_score[l - 1] = best;
-  }
+  if ((st = T.alg1(base, cands, d, ch_interp, ch_order, out->alg1_score)) != QOZ_OK) return st;
   qoz_params fp;
   memset(&fp, 0, sizeof(fp));
   fp.anchor_stride = o.anchor_stride;
