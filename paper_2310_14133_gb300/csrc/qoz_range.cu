@@ -21,12 +21,19 @@ namespace {
 constexpr int kRangeThreads = 512;
 constexpr int kRangeBlocks = 152 * 4;  // 4 resident CTAs on each of the 152 SMs
 
-__device__ __forceinline__ void fold(float v, float& mn, float& mx, unsigned long long& c) {
+template <typename C>
+__device__ __forceinline__ void fold(float v, float& mn, float& mx, C& c) {
   if (isfinite(v)) {
     mn = fminf(mn, v);
     mx = fmaxf(mx, v);
     ++c;
   }
+}
+__device__ __forceinline__ void fold4(const float4& v, float& mn, float& mx, unsigned& c) {
+  fold(v.x, mn, mx, c);
+  fold(v.y, mn, mx, c);
+  fold(v.z, mn, mx, c);
+  fold(v.w, mn, mx, c);
 }
 
 __global__ void __launch_bounds__(kRangeThreads) range_kernel(const float* __restrict__ x,
@@ -34,20 +41,26 @@ __global__ void __launch_bounds__(kRangeThreads) range_kernel(const float* __res
                                                               float* pmax,
                                                               unsigned long long* pcnt) {
   float mn = FLT_MAX, mx = -FLT_MAX;
-  unsigned long long c = 0;
+  // per-thread count: at most 4 ceil(n / 4 / threads) + 1 values, far below
+  // 2^32 for any field that fits in device memory
+  unsigned ct = 0;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
-  // 16-byte aligned body (the caller passes the aligned start), scalar tail
+  // 16-byte aligned body (the caller passes the aligned start), four
+  // independent loads in flight per thread, then a scalar tail
   const long long n4 = n / 4;
   const float4* x4 = reinterpret_cast<const float4*>(x);
-  for (long long i = tid; i < n4; i += nth) {
-    const float4 v = __ldcs(x4 + i);
-    fold(v.x, mn, mx, c);
-    fold(v.y, mn, mx, c);
-    fold(v.z, mn, mx, c);
-    fold(v.w, mn, mx, c);
+  long long i = tid;
+  for (; i + 3 * nth < n4; i += 4 * nth) {
+    float4 v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = __ldcs(x4 + i + k * nth);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) fold4(v[k], mn, mx, ct);
   }
-  for (long long i = 4 * n4 + tid; i < n; i += nth) fold(x[i], mn, mx, c);
+  for (; i < n4; i += nth) fold4(__ldcs(x4 + i), mn, mx, ct);
+  for (long long j = 4 * n4 + tid; j < n; j += nth) fold(x[j], mn, mx, ct);
+  unsigned long long c = ct;
 
   for (int off = 16; off > 0; off >>= 1) {
     mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, off));

@@ -27,7 +27,12 @@
 namespace qoz {
 namespace {
 
+// Threads per trial CTA: the full-resolution block (stop level 1, up to
+// 33^3 values in shared memory, one CTA per SM) gets 512; the subsampled
+// blocks of the coarser Algorithm 1 levels (17^3 values and fewer) get 128,
+// so that several CTAs share an SM and the grid fits in one wave.
 constexpr int kTrialThreads = 512;
+constexpr int kTrialThreadsCoarse = 128;
 constexpr int kTHistLo = kRadius - 2048;
 constexpr int kTHistWin = 4096;
 constexpr int kOutStride = 8;  // per (candidate, block): l1, l1_cnt, unpred, sse, maxerr, ssim_sum, ssim_n, pad
@@ -75,8 +80,30 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   return v;
 }
-__device__ __forceinline__ double warp_max(double v) {
-  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+
+// Merges another compensated sum (s2 - c2) into k: the rounding error of
+// s + s2 is recovered exactly (Knuth's two-sum, symmetric in its operands,
+// so every lane of a butterfly ends with the same value) and moved into the
+// compensation.  Binary32 only: double arithmetic issues at a small fraction
+// of the binary32 rate on this part and dominated the short trials.
+__device__ __forceinline__ void ksum_merge(KSum& k, float s2, float c2) {
+  const float t = __fadd_rn(k.s, s2);
+  const float bb = __fsub_rn(t, k.s);
+  const float err = __fadd_rn(__fsub_rn(k.s, __fsub_rn(t, bb)), __fsub_rn(s2, bb));
+  k.c = __fsub_rn(__fadd_rn(k.c, c2), err);
+  k.s = t;
+}
+__device__ __forceinline__ void warp_ksum(KSum& k) {
+  for (int off = 16; off > 0; off >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, k.s, off);
+    const float c2 = __shfl_xor_sync(0xffffffffu, k.c, off);
+    ksum_merge(k, s2, c2);
+  }
+}
+// Maximum that keeps a NaN once one is seen.
+__device__ __forceinline__ float nan_max(float m, float v) { return (v != v || v > m) ? v : m; }
+__device__ __forceinline__ float warp_nan_max(float v) {
+  for (int off = 16; off > 0; off >>= 1) v = nan_max(v, __shfl_xor_sync(0xffffffffu, v, off));
   return v;
 }
 
@@ -89,7 +116,8 @@ __device__ __forceinline__ double warp_max(double v) {
 // flag then reports it).
 constexpr unsigned kTrialWaitPolls = 1u << 24;
 
-__global__ void __launch_bounds__(kTrialThreads, 1)
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 1 : 4)
     trial_kernel(const TrialArgs a, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar;
@@ -100,7 +128,9 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
   unsigned char* base = smem + ((128u - (smem_u32(smem) & 127u)) & 127u);
   unsigned* SH = reinterpret_cast<unsigned*>(
       base + (((size_t)sizeof(float) * m0 * m1 * P + 15) & ~size_t(15)));
-  __shared__ double red[kTrialThreads / 32][7];
+  __shared__ float redf[THREADS / 32][5];     // l1 (s, c), sse (s, c), max error
+  __shared__ unsigned redu[THREADS / 32][2];  // l1 count, unpredictable count
+  __shared__ double redd[THREADS / 32][2];    // SSIM sum, window count
 
   const int cand = blockIdx.x / a.nblocks;
   const int blk = blockIdx.x % a.nblocks;
@@ -162,7 +192,7 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
     // the squared and maximum error only through non-finite values
     const int as = 1 << (a.Ls - a.stop_level + 1);
     const int n0 = (m0 - 1) / as + 1, n1a = (m1 - 1) / as + 1, n2a = (m2 - 1) / as + 1;
-    for (int i = threadIdx.x; i < n0 * n1a * n2a; i += kTrialThreads) {
+    for (int i = threadIdx.x; i < n0 * n1a * n2a; i += THREADS) {
       const int i2 = i % n2a, r = i / n2a;
       const float v = S[(r / n1a) * as * st0 + (r % n1a) * as * st1 + i2 * as];
       const float d = __fsub_rn(v, v);
@@ -199,7 +229,7 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
       const bool fdiv = items < 70000 && c2n < 4100 && c1n < 4100;
       const float rc2 = 1.0f / (float)(c2n > 0 ? c2n : 1);
       const float rc1 = 1.0f / (float)(c1n > 0 ? c1n : 1);
-      for (int it = threadIdx.x; it < items; it += kTrialThreads) {
+      for (int it = threadIdx.x; it < items; it += THREADS) {
         const int row =
             fdiv ? __float2int_rz(__fmul_rn(__fadd_rn(__int2float_rn(it), 0.5f), rc2)) : it / c2n;
         const int i2 = it - row * c2n;
@@ -320,26 +350,56 @@ __global__ void __launch_bounds__(kTrialThreads, 1)
     for (int i = threadIdx.x; i < kTHistWin; i += blockDim.x)
       if (SH[i]) atomicAdd(&a.hist[(size_t)cand * 65536 + kTHistLo + i], SH[i]);
   }
-  // fixed-order block reduction
-  const double v[7] = {warp_sum(l1.value()), warp_sum((double)l1n), warp_sum((double)unp),
-                       warp_sum(sse.value()), warp_max((double)mx), warp_sum(ss), warp_sum(sn)};
-  if (lane == 0)
-    for (int k = 0; k < 7; ++k) red[warp][k] = v[k];
+  // fixed-order block reduction: warps, then warp 0 over the warps' partials
+  warp_ksum(l1);
+  warp_ksum(sse);
+  mx = warp_nan_max(mx);
+  const unsigned l1c = __reduce_add_sync(0xffffffffu, (unsigned)l1n);
+  const unsigned unc = __reduce_add_sync(0xffffffffu, (unsigned)unp);
+  if (a.ssim_win > 0) {
+    ss = warp_sum(ss);
+    sn = warp_sum(sn);
+  }
+  if (lane == 0) {
+    redf[warp][0] = l1.s;
+    redf[warp][1] = l1.c;
+    redf[warp][2] = sse.s;
+    redf[warp][3] = sse.c;
+    redf[warp][4] = mx;
+    redu[warp][0] = l1c;
+    redu[warp][1] = unc;
+    redd[warp][0] = ss;
+    redd[warp][1] = sn;
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double t[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int wv = 0; wv < nw; ++wv) {
-      t[0] += red[wv][0];
-      t[1] += red[wv][1];
-      t[2] += red[wv][2];
-      t[3] += red[wv][3];
-      if (red[wv][4] != red[wv][4] || red[wv][4] > t[4]) t[4] = red[wv][4];
-      t[5] += red[wv][5];
-      t[6] += red[wv][6];
+  if (warp == 0) {
+    const bool on = lane < nw;
+    KSum t1, t3;
+    t1.s = on ? redf[lane][0] : 0.0f;
+    t1.c = on ? redf[lane][1] : 0.0f;
+    t3.s = on ? redf[lane][2] : 0.0f;
+    t3.c = on ? redf[lane][3] : 0.0f;
+    warp_ksum(t1);
+    warp_ksum(t3);
+    const float m = warp_nan_max(on ? redf[lane][4] : 0.0f);
+    const unsigned c1 = __reduce_add_sync(0xffffffffu, on ? redu[lane][0] : 0u);
+    const unsigned c2 = __reduce_add_sync(0xffffffffu, on ? redu[lane][1] : 0u);
+    double s5 = 0.0, s6 = 0.0;
+    if (a.ssim_win > 0) {
+      s5 = warp_sum(on ? redd[lane][0] : 0.0);
+      s6 = warp_sum(on ? redd[lane][1] : 0.0);
     }
-    double* o = a.out + ((size_t)cand * a.nblocks + blk) * kOutStride;
-    for (int k = 0; k < 7; ++k) o[k] = t[k];
-    o[7] = 0.0;
+    if (lane == 0) {
+      double* o = a.out + ((size_t)cand * a.nblocks + blk) * kOutStride;
+      o[0] = t1.value();
+      o[1] = (double)c1;
+      o[2] = (double)c2;
+      o[3] = t3.value();
+      o[4] = (double)m;
+      o[5] = s5;
+      o[6] = s6;
+      o[7] = 0.0;
+    }
   }
 }
 
@@ -357,22 +417,36 @@ __global__ void __launch_bounds__(kHuffThreads)
   __shared__ unsigned cnt[kHuffMax];
   __shared__ unsigned node[kHuffMax];  // merged weights: at most the sampled points (< 2^32)
   __shared__ int nsh;
-  const unsigned* h = hist + (size_t)blockIdx.x * 65536;
+  const uint4* h4 = reinterpret_cast<const uint4*>(hist + (size_t)blockIdx.x * 65536);
   const int t = threadIdx.x, lane = t & 31;
   if (t == 0) nsh = 0;
   __syncthreads();
-  // coalesced scan; each warp appends its non-zero counts (any order: they
-  // are sorted next)
-  for (int i = t; i < 65536; i += kHuffThreads) {
-    const unsigned v = h[i];
-    const unsigned ball = __ballot_sync(0xffffffffu, v != 0u);
-    if (ball == 0u) continue;
-    int base = 0;
-    if (lane == 0) base = atomicAdd(&nsh, __popc(ball));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (v != 0u) {
-      const int k = base + __popc(ball & ((1u << lane) - 1u));
-      if (k < kHuffMax) cnt[k] = v;
+  // coalesced 16-byte scan, kBatch loads in flight per thread; each warp
+  // appends its non-zero counts (any order: they are sorted next)
+  constexpr int kVec = 65536 / 4 / kHuffThreads, kBatch = 4;
+  for (int j0 = 0; j0 < kVec; j0 += kBatch) {
+    uint4 v[kBatch];
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) v[j] = h4[(j0 + j) * kHuffThreads + t];
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+      const unsigned q[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+      const int nz = (q[0] != 0u) + (q[1] != 0u) + (q[2] != 0u) + (q[3] != 0u);
+      if (__ballot_sync(0xffffffffu, nz != 0) == 0u) continue;
+      int inc = nz;  // inclusive prefix over the warp
+      for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += y;
+      }
+      int base = 0;
+      if (lane == 31) base = atomicAdd(&nsh, inc);
+      int k = __shfl_sync(0xffffffffu, base, 31) + inc - nz;
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (q[e] != 0u) {
+          if (k < kHuffMax) cnt[k] = q[e];
+          ++k;
+        }
     }
   }
   __syncthreads();
@@ -408,18 +482,30 @@ __global__ void __launch_bounds__(kHuffThreads)
     if (n == 1) {
       total = cnt[0];
     } else if (n > 1) {
+      // queue heads in registers, the next leaf prefetched: each pick is a
+      // compare on registers (the sorted leaves are padded with 0xffffffff)
       int li = 0, ni = 0, nn = 0;
+      unsigned hl = cnt[0], hl2 = cnt[1], hn = 0u;
       for (int m = 1; m < n; ++m) {
         unsigned ab[2];
+#pragma unroll
         for (int k = 0; k < 2; ++k) {
-          if (ni < nn && (li >= n || node[ni] < cnt[li]))
-            ab[k] = node[ni++];
-          else
-            ab[k] = cnt[li++];
+          if (ni < nn && (li >= n || hn < hl)) {
+            ab[k] = hn;
+            ++ni;
+            hn = ni < nn ? node[ni] : 0u;
+          } else {
+            ab[k] = hl;
+            ++li;
+            hl = hl2;
+            hl2 = li + 1 < P ? cnt[li + 1] : 0xffffffffu;
+          }
         }
         const unsigned sum = ab[0] + ab[1];
         total += sum;
-        node[nn++] = sum;
+        node[nn] = sum;
+        if (ni == nn) hn = sum;
+        ++nn;
       }
     }
     bits[blockIdx.x] = total;
@@ -429,10 +515,11 @@ __global__ void __launch_bounds__(kHuffThreads)
 
 // Algorithm 1 on the device, one level at a time: the level's candidates
 // (interpolator, order) are scored by the mean |x - pred| of their trial
-// (sums over the blocks in block order, in double, as on the host); the
-// first candidate within 1e-12 relative of the best wins; the choice is
-// recorded and the next level's candidates are built (levels above keep the
-// choices made), so the levels run back to back without the host.
+// (one warp per candidate sums its blocks in double, lane-strided with a
+// fixed butterfly); the first candidate within 1e-12 relative of the best
+// wins; the choice is recorded and the next level's candidates are built
+// (levels above keep the choices made), so the levels run back to back
+// without the host.
 struct Alg1Ctl {
   unsigned char ci[16], co[16];  // candidate interpolators and orders
   unsigned char chi[kMaxLevels], cho[kMaxLevels];  // choices per level
@@ -446,24 +533,28 @@ __device__ void set_axes_dev(TrialCand* c, int level, int ndims, int order) {
   for (int k = 0; k < 3; ++k) c->axes[level - 1][k] = (unsigned char)kPermDev[o3][k];
 }
 
-__global__ void __launch_bounds__(32) alg1_select_kernel(const double* __restrict__ out, int nc,
-                                                          int nb, int l, int Ls,
-                                                          const TrialCand base, int ndims,
-                                                          Alg1Ctl* ctl, TrialCand* cands) {
-  __shared__ double mean[32];
+constexpr int kAlg1MaxCand = 16;
+
+__global__ void __launch_bounds__(32 * kAlg1MaxCand)
+    alg1_select_kernel(const double* __restrict__ out, int nc, int nb, int l, int Ls,
+                       const TrialCand base, int ndims, Alg1Ctl* ctl, TrialCand* cands) {
+  __shared__ double mean[kAlg1MaxCand];
+  __shared__ Alg1Ctl h;
   __shared__ int pick;
-  const int c = threadIdx.x;
-  if (c < nc) {  // one lane per candidate: its blocks summed in block order
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) h = *ctl;
+  if (warp < nc) {
     double l1 = 0.0, l1n = 0.0;
-#pragma unroll 4
-    for (int b = 0; b < nb; ++b) {
-      l1 += out[((size_t)c * nb + b) * kOutStride + 0];
-      l1n += out[((size_t)c * nb + b) * kOutStride + 1];
+    for (int b = lane; b < nb; b += 32) {
+      l1 += out[((size_t)warp * nb + b) * kOutStride + 0];
+      l1n += out[((size_t)warp * nb + b) * kOutStride + 1];
     }
-    mean[c] = l1n > 0 ? l1 / l1n : 0.0;
+    l1 = warp_sum(l1);
+    l1n = warp_sum(l1n);
+    if (lane == 0) mean[warp] = l1n > 0 ? l1 / l1n : 0.0;
   }
-  __syncwarp();
-  if (c == 0) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
     double best = 0.0;
     int bi = 0;
     for (int k = 0; k < nc; ++k) {
@@ -473,22 +564,26 @@ __global__ void __launch_bounds__(32) alg1_select_kernel(const double* __restric
         bi = k;
       }
     }
-    ctl->chi[l - 1] = ctl->ci[bi];
-    ctl->cho[l - 1] = ctl->co[bi];
+    h.chi[l - 1] = h.ci[bi];
+    h.cho[l - 1] = h.co[bi];
+    h.score[l - 1] = best;
+    ctl->chi[l - 1] = h.ci[bi];
+    ctl->cho[l - 1] = h.co[bi];
     ctl->score[l - 1] = best;
     pick = bi;
   }
-  __syncwarp();
+  __syncthreads();
+  const int c = threadIdx.x;
   if (l == 1 || c >= nc) return;
   TrialCand t = base;
   for (int ll = l + 1; ll <= Ls; ++ll) {
-    t.interp[ll - 1] = ctl->chi[ll - 1];
-    set_axes_dev(&t, ll, ndims, ctl->cho[ll - 1]);
+    t.interp[ll - 1] = h.chi[ll - 1];
+    set_axes_dev(&t, ll, ndims, h.cho[ll - 1]);
   }
-  t.interp[l - 1] = ctl->ci[pick];
-  set_axes_dev(&t, l, ndims, ctl->co[pick]);
-  t.interp[l - 2] = ctl->ci[c];
-  set_axes_dev(&t, l - 1, ndims, ctl->co[c]);
+  t.interp[l - 1] = h.ci[pick];
+  set_axes_dev(&t, l, ndims, h.co[pick]);
+  t.interp[l - 2] = h.ci[c];
+  set_axes_dev(&t, l - 1, ndims, h.co[c]);
   cands[c] = t;
 }
 
@@ -617,7 +712,7 @@ class Tuner {
   qoz_status alg1(const TrialCand& base, const std::vector<std::pair<int, int>>& cl, int ndims,
                   unsigned char* chi, unsigned char* cho, double* score) {
     const int nc = (int)cl.size();
-    if (nc == 0 || nc > 16) return fail(QOZ_EINVAL, "1..16 Algorithm 1 candidates");
+    if (nc == 0 || nc > kAlg1MaxCand) return fail(QOZ_EINVAL, "1..16 Algorithm 1 candidates");
     qoz_status st = ensure(nc);
     if (st != QOZ_OK) return st;
     Alg1Ctl h;
@@ -646,8 +741,8 @@ class Tuner {
         dev_free(d_ctl, s_);
         return st;
       }
-      alg1_select_kernel<<<1, 32, 0, s_>>>(d_out_, nc, sm_.nb, l, sm_.Ls, base, ndims, d_ctl,
-                                           d_cands_);
+      alg1_select_kernel<<<1, 32 * nc, 0, s_>>>(d_out_, nc, sm_.nb, l, sm_.Ls, base, ndims,
+                                                 d_ctl, d_cands_);
       note_launch(1);
       e = launch_check(cudaGetLastError());
     }
@@ -719,12 +814,18 @@ class Tuner {
     const size_t smem = smem_for(a.pitch);
     if (smem > 220 * 1024)
       return fail(QOZ_EUNSUPPORTED, "sample block too large (%lld points)", npb);
+    const bool coarse = stop_level > 1;
+    const void* fn = coarse ? (const void*)trial_kernel<kTrialThreadsCoarse>
+                            : (const void*)trial_kernel<kTrialThreads>;
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute((const void*)trial_kernel,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
       ProfScope ps(QOZ_STAGE_TUNE, s_);
-      trial_kernel<<<nc * sm_.nb, kTrialThreads, smem, s_>>>(a, tmap_);
+      const unsigned grid = (unsigned)(nc * sm_.nb);
+      if (coarse)
+        trial_kernel<kTrialThreadsCoarse><<<grid, kTrialThreadsCoarse, smem, s_>>>(a, tmap_);
+      else
+        trial_kernel<kTrialThreads><<<grid, kTrialThreads, smem, s_>>>(a, tmap_);
       note_launch(1);
       e = launch_check(cudaGetLastError());
     }
