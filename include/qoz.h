@@ -403,6 +403,11 @@ typedef struct {
 /* Turns per-stage event timing on or off (process-wide; off by default).
  * The launch counter always runs. */
 qoz_status qoz_profile_enable(int32_t enable);
+/* Selects the stages that record events while timing is on: bit i of mask
+ * enables stage i (process-wide; all stages by default).  Each timed stage
+ * adds two event records to its stream, so a caller timing a whole pipeline
+ * selects only the stages it reads. */
+qoz_status qoz_profile_stages(uint32_t mask);
 /* Folds in all recorded stages (synchronising on their events) and copies
  * the totals; reset != 0 clears them and the launch counter afterwards. */
 qoz_status qoz_profile_read(qoz_stage_times* out, int32_t reset);

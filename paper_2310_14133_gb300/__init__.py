@@ -14,7 +14,9 @@ from ._binding import (  # noqa: F401
     STAGE_HIST,
     STAGE_LEVEL,
     STAGE_RANGE,
+    STAGE_METRICS,
     STAGE_SETUP,
+    STAGE_TUNE,
     BATCH_AUTOTUNE,
     BATCH_NO_GRAPH,
     Batch,

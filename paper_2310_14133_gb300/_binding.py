@@ -53,7 +53,11 @@ class StageTimes(C.Structure):
                 ("launches", C.c_int64)]
 
 
-def profile_enable(on: bool = True):
+def profile_enable(on: bool = True, stages=None):
+    """Turns per-stage event timing on or off; `stages` (an iterable of stage
+    ids) limits the timed stages, None times all of them."""
+    mask = 0xFFFFFFFF if stages is None else sum(1 << int(i) for i in stages)
+    _check(lib().qoz_profile_stages(mask))
     _check(lib().qoz_profile_enable(1 if on else 0))
 
 
@@ -141,6 +145,7 @@ def lib():
             "qoz_blob_free": (None, [P]),
             "qoz_compute_metrics": (i32, [P, P, Shape, f64, i32, i32, P, P]),
             "qoz_profile_enable": (i32, [i32]),
+            "qoz_profile_stages": (i32, [C.c_uint32]),
             "qoz_tune": (i32, [P, Shape, f64, i32, f64, P, P, P]),
             "qoz_profile_read": (i32, [P, i32]),
             "qoz_batch_create": (i32, [P, i32, P, C.c_uint32, P]),

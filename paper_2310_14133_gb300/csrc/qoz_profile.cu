@@ -24,6 +24,7 @@ struct Pending {
 
 std::mutex g_mu;
 std::atomic<bool> g_on{false};
+std::atomic<unsigned> g_mask{0xffffffffu};
 std::atomic<long long> g_launches{0};
 std::vector<Pending> g_pending;
 std::vector<cudaEvent_t> g_free;
@@ -60,6 +61,7 @@ void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 ProfScope::ProfScope(int stage, cudaStream_t s) : stage_(stage), s_(s), a_(nullptr) {
   if (!g_on.load(std::memory_order_relaxed) || stage < 0 || stage >= QOZ_PROF_STAGES) return;
+  if (!((g_mask.load(std::memory_order_relaxed) >> stage) & 1u)) return;
   std::lock_guard<std::mutex> lk(g_mu);
   a_ = take_event();
   if (a_ && cudaEventRecord(a_, s_) != cudaSuccess) {
@@ -89,6 +91,11 @@ extern "C" {
 qoz_status qoz_profile_enable(int32_t enable) {
   std::lock_guard<std::mutex> lk(g_mu);
   g_on.store(enable != 0);
+  return QOZ_OK;
+}
+
+qoz_status qoz_profile_stages(uint32_t mask) {
+  g_mask.store(mask);
   return QOZ_OK;
 }
 

@@ -57,7 +57,8 @@ struct TrialArgs {
   double* out;             // [ncand][nblocks][kOutStride]
   int metrics;             // accumulate sse / max error / SSIM after the last level
   int ssim_win, ssim_step, is3d;
-  double c1, c2;
+  double c1, c2;           // SSIM constants (used when bt is null)
+  const BoundTable* bt;    // value range on the device: SSIM constants from its range
   int use_tma;             // full-resolution block by one bulk tensor copy (tensor map given)
   int pitch;               // row pitch of the block in shared memory (values)
 };
@@ -293,6 +294,12 @@ __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 1 : 4)
   if (a.metrics) {  // stop_level == 1: S is the whole block
     const int n1 = a.bd[1], n2 = a.bd[2];
     if (a.ssim_win > 0) {
+      double c1 = a.c1, c2 = a.c2;
+      if (a.bt) {
+        const double vr = a.bt->vrange;
+        c1 = __dmul_rn(__dmul_rn(0.01, vr), __dmul_rn(0.01, vr));
+        c2 = __dmul_rn(__dmul_rn(0.03, vr), __dmul_rn(0.03, vr));
+      }
       const int n0 = a.bd[0];
       const int w = a.ssim_win, sp = a.ssim_step;
       const int wz = a.is3d ? w : 1;
@@ -339,8 +346,8 @@ __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 1 : 4)
         const double ex = (double)rx / np, ey = (double)ry / np;
         const double vx = (double)vxx / np - ex * ex, vy = (double)vyy / np - ey * ey;
         const double cxy = (double)vxy / np - ex * ey;
-        ss += ((2.0 * mxx * myy + a.c1) * (2.0 * cxy + a.c2)) /
-              ((mxx * mxx + myy * myy + a.c1) * (vx + vy + a.c2));
+        ss += ((2.0 * mxx * myy + c1) * (2.0 * cxy + c2)) /
+              ((mxx * mxx + myy * myy + c1) * (vx + vy + c2));
         sn += 1.0;
       }
     }
@@ -535,9 +542,63 @@ __device__ void set_axes_dev(TrialCand* c, int level, int ndims, int order) {
 
 constexpr int kAlg1MaxCand = 16;
 
+// Level bounds of Eq. (ebl) for one candidate: e_l = e / min(alpha^(l-1),
+// beta) in double, each entry rounded to binary32 once (the same operations,
+// in the same order, as the host's fill_bounds).
+__device__ void fill_bounds_dev(TrialCand* c, double e, double alpha, double beta, int L) {
+  double a = 1.0;
+  for (int l = 0; l < kMaxLevels; ++l) {
+    if (l < L) {
+      const double den = a < beta ? a : beta;
+      const double el = __ddiv_rn(e, den);
+      const double two = __dmul_rn(2.0, el);
+      c->el[l] = __double2float_rn(el);
+      c->two_e[l] = __double2float_rn(two);
+      c->inv[l] = __double2float_rn(__ddiv_rn(1.0, two));
+      a = __dmul_rn(a, alpha);
+    } else {
+      c->el[l] = c->two_e[l] = c->inv[l] = 0.0f;
+    }
+  }
+}
+
+// The tuner's starting bound e0 from the device value range: the user's
+// bound rel * range, or, for a PSNR target (Sec. 6.3.2), the smaller of that
+// and range * sqrt(3) * 10^(-P / 20) (both factors evaluated on the host).
+struct E0Spec {
+  int psnr_target;
+  double sqrt3, p10;
+};
+__device__ double e0_dev(const BoundTable& bt, const E0Spec& sp) {
+  double e0 = bt.e;  // rel * range (the bound table was filled with eb = rel)
+  if (sp.psnr_target) {
+    const double t = __dmul_rn(__dmul_rn(bt.vrange, sp.sqrt3), sp.p10);
+    e0 = t > e0 ? e0 : t;
+  }
+  return e0;
+}
+
+// The (alpha, beta) candidates of Sec. 6.3, built on the device once
+// Algorithm 1 has chosen every level: candidate k = (si * na + ia) * nb + ib
+// at bound scales[si] * e0.
+struct AbSpec {
+  int n_alpha, n_beta, n_scales;
+  double alphas[8], betas[8], scales[3];
+};
+
+// Bounds of the top-level Algorithm 1 candidates (alpha = beta = 1, every
+// level at e0) and e0 itself, from the device value range.
+__global__ void alg1_setup_kernel(TrialCand* cands, int nc, const BoundTable* bt,
+                                  const E0Spec sp, int Ls, double* e0_out) {
+  const double e0 = e0_dev(*bt, sp);
+  if (threadIdx.x == 0) *e0_out = e0;
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) fill_bounds_dev(&cands[c], e0, 1.0, 1.0, Ls);
+}
+
 __global__ void __launch_bounds__(32 * kAlg1MaxCand)
     alg1_select_kernel(const double* __restrict__ out, int nc, int nb, int l, int Ls,
-                       const TrialCand base, int ndims, Alg1Ctl* ctl, TrialCand* cands) {
+                       const TrialCand base, int ndims, Alg1Ctl* ctl, TrialCand* cands,
+                       const AbSpec ab, const double* e0p) {
   __shared__ double mean[kAlg1MaxCand];
   __shared__ Alg1Ctl h;
   __shared__ int pick;
@@ -573,13 +634,29 @@ __global__ void __launch_bounds__(32 * kAlg1MaxCand)
     pick = bi;
   }
   __syncthreads();
-  const int c = threadIdx.x;
-  if (l == 1 || c >= nc) return;
-  TrialCand t = base;
-  for (int ll = l + 1; ll <= Ls; ++ll) {
-    t.interp[ll - 1] = h.chi[ll - 1];
-    set_axes_dev(&t, ll, ndims, h.cho[ll - 1]);
+  if (l == 1) {
+    // every level chosen: the (alpha, beta) candidates, when asked for
+    const int nab = ab.n_alpha * ab.n_beta;
+    if (nab == 0) return;
+    const double e0 = *e0p;
+    for (int k = threadIdx.x; k < ab.n_scales * nab; k += blockDim.x) {
+      TrialCand t = base;
+      for (int ll = 1; ll <= Ls; ++ll) {
+        t.interp[ll - 1] = h.chi[ll - 1];
+        set_axes_dev(&t, ll, ndims, h.cho[ll - 1]);
+      }
+      const int si = k / nab, kk = k - si * nab;
+      fill_bounds_dev(&t, __dmul_rn(ab.scales[si], e0), ab.alphas[kk / ab.n_beta],
+                      ab.betas[kk % ab.n_beta], Ls);
+      cands[k] = t;
+    }
+    return;
   }
+  const int c = threadIdx.x;
+  if (c >= nc) return;
+  // candidate c of level l - 1: its current entry (levels above l already
+  // chosen, the bounds filled on the device) with level l set to the pick
+  TrialCand t = cands[c];
   t.interp[l - 1] = h.ci[pick];
   set_axes_dev(&t, l, ndims, h.co[pick]);
   t.interp[l - 2] = h.ci[c];
@@ -670,6 +747,28 @@ struct TrialResult {
   double l1_mean;
 };
 
+// Pinned host staging for the tuner's read-backs, one per host thread (a
+// tuner call synchronises before it returns, so one call uses it at a
+// time); grows on demand.
+void* pinned_stage(size_t bytes) {
+  static thread_local void* p = nullptr;
+  static thread_local size_t cap = 0;
+  if (bytes > cap) {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+    if (cudaMallocHost(&p, bytes) != cudaSuccess) {
+      p = nullptr;
+      return nullptr;
+    }
+    cap = bytes;
+  }
+  return p;
+}
+
+static_assert(sizeof(BoundTable) <= 256 && sizeof(Alg1Ctl) <= 256,
+              "tuner range scratch layout");
+
 class Tuner {
  public:
   Tuner(const float* x, const Resolved& r, const Sampling& sm, cudaStream_t s, int metric,
@@ -682,6 +781,7 @@ class Tuner {
     dev_free(d_out_, s_);
     dev_free(d_hist_, s_);
     dev_free(d_bits_, s_);
+    dev_free(d_range_, s_);
   }
 
   qoz_status init() {
@@ -706,14 +806,43 @@ class Tuner {
     return QOZ_OK;
   }
 
-  // Algorithm 1 over levels Ls..1 on the device (alg1_select_kernel), one
-  // read-back at the end: the chosen interpolator and order per level and
-  // the winning mean |x - pred|.
-  qoz_status alg1(const TrialCand& base, const std::vector<std::pair<int, int>>& cl, int ndims,
-                  unsigned char* chi, unsigned char* cho, double* score) {
+  // Value range of the field on the device (per-CTA partials, then the
+  // bound table with eb = rel, so its e is rel * range): the trial bounds and
+  // the SSIM constants follow from it without a host round trip.  Also holds
+  // the Algorithm 1 control block and e0.
+  qoz_status start_range(double rel) {
+    const int np = range_partial_blocks();
+    if (!d_range_ && dev_alloc(&d_range_, kRangeOff + np * (sizeof(float) * 2 + 8) + 64, s_) !=
+                         cudaSuccess)
+      return fail(QOZ_ENOMEM, "tuner allocation");
+    char* base = static_cast<char*>(d_range_);
+    d_bt_ = reinterpret_cast<BoundTable*>(base);
+    d_ctl_ = reinterpret_cast<Alg1Ctl*>(base + kCtlOff);
+    d_e0_ = reinterpret_cast<double*>(base + kE0Off);
+    float* pmin = reinterpret_cast<float*>(base + kRangeOff);
+    float* pmax = pmin + np;
+    unsigned long long* pcnt =
+        reinterpret_cast<unsigned long long*>(((uintptr_t)(pmax + np) + 15) & ~(uintptr_t)15);
+    cudaError_t e = launch_check(launch_range(x_, r_.N, pmin, pmax, pcnt, s_));
+    if (e == cudaSuccess)
+      e = launch_check(launch_bound_table(pmin, pmax, pcnt, np, 1, rel, 1.0, 1.0, 1, d_bt_, s_));
+    if (e != cudaSuccess) return cuda_fail(e, "tuner value range");
+    return QOZ_OK;
+  }
+
+  // Algorithm 1 over levels Ls..1 on the device, enqueued only: the
+  // top-level candidates get their bounds from the device value range
+  // (alg1_setup_kernel), each level's trials are followed by
+  // alg1_select_kernel (choice + next level's candidates) and the last one
+  // builds the (alpha, beta) candidates of `ab` in d_cands_.  The choices
+  // are read back by collect().  Needs start_range() first.
+  qoz_status alg1_enqueue(const TrialCand& base, const std::vector<std::pair<int, int>>& cl,
+                          int ndims, const E0Spec& sp, const AbSpec& ab) {
     const int nc = (int)cl.size();
     if (nc == 0 || nc > kAlg1MaxCand) return fail(QOZ_EINVAL, "1..16 Algorithm 1 candidates");
-    qoz_status st = ensure(nc);
+    if (!d_range_) return fail(QOZ_EINVAL, "tuner value range not started");
+    const int nab = ab.n_alpha * ab.n_beta * ab.n_scales;
+    qoz_status st = ensure(nc > nab ? nc : nab);
     if (st != QOZ_OK) return st;
     Alg1Ctl h;
     memset(&h, 0, sizeof(h));
@@ -728,33 +857,23 @@ class Tuner {
       set_axes(&t, sm_.Ls, ndims, h.co[c]);
       top.push_back(t);
     }
-    Alg1Ctl* d_ctl = nullptr;
-    cudaError_t e = dev_alloc((void**)&d_ctl, sizeof(Alg1Ctl), s_);
-    if (e != cudaSuccess) return fail(QOZ_ENOMEM, "tuner allocation");
-    e = cudaMemcpyAsync(d_ctl, &h, sizeof(h), cudaMemcpyHostToDevice, s_);
+    cudaError_t e = cudaMemcpyAsync(d_ctl_, &h, sizeof(h), cudaMemcpyHostToDevice, s_);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(d_cands_, top.data(), sizeof(TrialCand) * nc, cudaMemcpyHostToDevice,
                           s_);
-    for (int l = sm_.Ls; l >= 1 && e == cudaSuccess; --l) {
-      st = launch(nc, l, l, false);
-      if (st != QOZ_OK) {
-        dev_free(d_ctl, s_);
-        return st;
-      }
-      alg1_select_kernel<<<1, 32 * nc, 0, s_>>>(d_out_, nc, sm_.nb, l, sm_.Ls, base, ndims,
-                                                 d_ctl, d_cands_);
+    if (e == cudaSuccess) {
+      alg1_setup_kernel<<<1, 32, 0, s_>>>(d_cands_, nc, d_bt_, sp, sm_.Ls, d_e0_);
       note_launch(1);
       e = launch_check(cudaGetLastError());
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_ctl, sizeof(h), cudaMemcpyDeviceToHost, s_);
-    dev_free(d_ctl, s_);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s_);
-    if (e != cudaSuccess) return cuda_fail(e, "Algorithm 1");
-    for (int l = 1; l <= sm_.Ls; ++l) {
-      chi[l - 1] = h.chi[l - 1];
-      cho[l - 1] = h.cho[l - 1];
-      score[l - 1] = h.score[l - 1];
+    for (int l = sm_.Ls; l >= 1 && e == cudaSuccess; --l) {
+      if ((st = launch(nc, l, l, false)) != QOZ_OK) return st;
+      alg1_select_kernel<<<1, 32 * nc, 0, s_>>>(d_out_, nc, sm_.nb, l, sm_.Ls, base, ndims,
+                                                 d_ctl_, d_cands_, ab, d_e0_);
+      note_launch(1);
+      e = launch_check(cudaGetLastError());
     }
+    if (e != cudaSuccess) return cuda_fail(e, "Algorithm 1");
     return QOZ_OK;
   }
 
@@ -801,6 +920,7 @@ class Tuner {
     a.is3d = r_.ndims == 3;
     a.c1 = (0.01 * vr_) * (0.01 * vr_);
     a.c2 = (0.03 * vr_) * (0.03 * vr_);
+    a.bt = d_bt_;
     const int f = 1 << (stop_level - 1);
     const int m2 = (sm_.bd[2] - 1) / f + 1;
     const long long rows = (long long)((sm_.bd[0] - 1) / f + 1) * ((sm_.bd[1] - 1) / f + 1);
@@ -853,21 +973,48 @@ class Tuner {
                                     cudaMemcpyHostToDevice, s_);
     if (e != cudaSuccess) return cuda_fail(e, "tuner trial");
     if ((st = launch(nc, stop_level, score_level, full)) != QOZ_OK) return st;
+    return collect(nc, full, res, nullptr, nullptr);
+  }
+
+  // Reads back the results of the last launch (nc candidates), and, when
+  // asked, the Algorithm 1 control block and the device value range (which
+  // then sets the range used for PSNR), with one synchronisation through a
+  // pinned staging buffer; folds the blocks of each candidate.
+  qoz_status collect(int nc, bool full, std::vector<TrialResult>* res, Alg1Ctl* ctl,
+                     BoundTable* bt) {
     unsigned long long* d_bits = reinterpret_cast<unsigned long long*>(d_bits_);
     int* d_flag = reinterpret_cast<int*>(d_bits + nc);
-    std::vector<double> out((size_t)kOutStride * nc * sm_.nb);
-    std::vector<unsigned long long> hbits(nc, 0ull);
-    std::vector<int> hflag(nc, 0);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(out.data(), d_out_, sizeof(double) * out.size(), cudaMemcpyDeviceToHost,
+    const size_t n_out = (size_t)kOutStride * nc * sm_.nb;
+    auto up16 = [](size_t v) { return (v + 15) & ~size_t(15); };
+    const size_t o_bits = up16(sizeof(double) * n_out);
+    const size_t o_flag = o_bits + up16(sizeof(unsigned long long) * nc);
+    const size_t o_ctl = o_flag + up16(sizeof(int) * nc);
+    const size_t o_bt = o_ctl + up16(sizeof(Alg1Ctl));
+    char* hs = static_cast<char*>(pinned_stage(o_bt + sizeof(BoundTable)));
+    if (!hs) return fail(QOZ_ENOMEM, "pinned staging buffer");
+    const double* out = reinterpret_cast<const double*>(hs);
+    unsigned long long* hbits = reinterpret_cast<unsigned long long*>(hs + o_bits);
+    int* hflag = reinterpret_cast<int*>(hs + o_flag);
+    cudaError_t e =
+        cudaMemcpyAsync(hs, d_out_, sizeof(double) * n_out, cudaMemcpyDeviceToHost, s_);
+    if (e == cudaSuccess && full)
+      e = cudaMemcpyAsync(hbits, d_bits, sizeof(unsigned long long) * nc, cudaMemcpyDeviceToHost,
                           s_);
     if (e == cudaSuccess && full)
-      e = cudaMemcpyAsync(hbits.data(), d_bits, sizeof(unsigned long long) * nc,
-                          cudaMemcpyDeviceToHost, s_);
-    if (e == cudaSuccess && full)
-      e = cudaMemcpyAsync(hflag.data(), d_flag, sizeof(int) * nc, cudaMemcpyDeviceToHost, s_);
+      e = cudaMemcpyAsync(hflag, d_flag, sizeof(int) * nc, cudaMemcpyDeviceToHost, s_);
+    if (e == cudaSuccess && ctl)
+      e = cudaMemcpyAsync(hs + o_ctl, d_ctl_, sizeof(Alg1Ctl), cudaMemcpyDeviceToHost, s_);
+    if (e == cudaSuccess && bt)
+      e = cudaMemcpyAsync(hs + o_bt, d_bt_, sizeof(BoundTable), cudaMemcpyDeviceToHost, s_);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s_);
     if (e != cudaSuccess) return cuda_fail(e, "tuner trial");
+    if (ctl) memcpy(ctl, hs + o_ctl, sizeof(Alg1Ctl));
+    if (bt) {
+      memcpy(bt, hs + o_bt, sizeof(BoundTable));
+      vr_ = bt->vrange;
+    }
+    std::vector<unsigned long long> bits(nc, 0ull);
+    for (int c = 0; c < nc && full; ++c) bits[c] = hbits[c];
     // histograms with too many distinct codes for the device sort: host
     std::vector<unsigned> hist;
     for (int c = 0; c < nc && full; ++c) {
@@ -877,9 +1024,9 @@ class Tuner {
                           cudaMemcpyDeviceToHost, s_);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s_);
       if (e != cudaSuccess) return cuda_fail(e, "tuner histogram");
-      hbits[c] = huffman_bits_u32(hist.data(), 65536);
+      bits[c] = huffman_bits_u32(hist.data(), 65536);
     }
-    for (size_t i = 7; i < out.size(); i += kOutStride)
+    for (size_t i = 7; i < n_out; i += kOutStride)
       if (out[i] != 0.0) return fail(QOZ_ETIMEOUT, "a sample block's bulk copy did not complete");
     res->assign(nc, TrialResult{0, 0, 0});
     for (int c = 0; c < nc; ++c) {
@@ -897,8 +1044,8 @@ class Tuner {
       TrialResult& t = (*res)[c];
       t.l1_mean = l1n > 0 ? l1 / l1n : 0.0;
       if (full) {
-        const double bits = (double)hbits[c] + 32.0 * unp + 32.0 * (double)sm_.anchors;
-        t.B = bits / (double)sm_.npts;
+        const double nbits = (double)bits[c] + 32.0 * unp + 32.0 * (double)sm_.anchors;
+        t.B = nbits / (double)sm_.npts;
         if (metric_ == QOZ_METRIC_PSNR) {
           const double mse = sse / (double)sm_.npts;
           t.M = mse == 0.0 ? INFINITY : 20.0 * std::log10(vr_ / std::sqrt(mse));
@@ -926,6 +1073,13 @@ class Tuner {
   double* d_out_ = nullptr;
   unsigned* d_hist_ = nullptr;
   void* d_bits_ = nullptr;  // per candidate: prefix-code bits (u64), then host-fallback flags (int)
+  // device value range scratch: bound table, Algorithm 1 control, e0, then
+  // the range partials
+  static constexpr size_t kCtlOff = 256, kE0Off = 512, kRangeOff = 1024;
+  void* d_range_ = nullptr;
+  BoundTable* d_bt_ = nullptr;
+  Alg1Ctl* d_ctl_ = nullptr;
+  double* d_e0_ = nullptr;
   CUtensorMap tmap_;        // the field, boxes of one full-resolution sample block
   bool tma_ok_ = false;
   int tma_pitch_ = 0;
@@ -1060,22 +1214,16 @@ qoz_status tune_impl(const float* d_field, const qoz_shape& shape, double rel_eb
   int L = 0;
   while ((1 << L) < o.anchor_stride) ++L;
 
-  float vmin, vmax;
-  int64_t cnt;
-  st = qoz_value_range(d_field, r.N, &vmin, &vmax, &cnt, s);
-  if (st != QOZ_OK) return st;
-  const double vr = (double)vmax - (double)vmin;
-  const double e_user = rel_eb * vr;
-
+  // the value range stays on the device until the single read-back below:
+  // Algorithm 1 and the (alpha, beta) trials take their bounds from it there
   Sampling sm = sample_blocks(r, o.block, o.rate, o.anchor_stride);
-  Tuner T(d_field, r, sm, s, metric, o.ssim_win, o.ssim_step, vr);
+  Tuner T(d_field, r, sm, s, metric, o.ssim_win, o.ssim_step, NAN);
   if ((st = T.init()) != QOZ_OK) return st;
-
-  double e0 = e_user;
-  if (target_mode && metric == QOZ_METRIC_PSNR) {
-    e0 = vr * std::sqrt(3.0) * std::pow(10.0, -target / 20.0);
-    if (e0 > e_user) e0 = e_user;
-  }
+  if ((st = T.start_range(rel_eb)) != QOZ_OK) return st;
+  E0Spec sp;
+  sp.psnr_target = target_mode && metric == QOZ_METRIC_PSNR;
+  sp.sqrt3 = std::sqrt(3.0);
+  sp.p10 = sp.psnr_target ? std::pow(10.0, -target / 20.0) : 0.0;
 
   // candidate interpolators: linear before cubic, then the orders
   std::vector<std::pair<int, int>> cands;
@@ -1092,15 +1240,46 @@ qoz_status tune_impl(const float* d_field, const qoz_shape& shape, double rel_eb
   }
 
   memset(out, 0, sizeof(*out));
-  TrialCand base;
+  TrialCand base;  // bounds are filled on the device
   memset(&base, 0, sizeof(base));
   for (int l = 1; l <= kMaxLevels; ++l) set_axes(&base, l, d, 0);
   unsigned char ch_interp[kMaxLevels] = {0}, ch_order[kMaxLevels] = {0};
-  fill_bounds(&base, e0, 1.0, 1.0, sm.Ls);
 
-  // ---- Algorithm 1, from the top sampled level down (choices on the device)
+  // ---- Algorithm 1, from the top sampled level down (choices on the
+  // device), then the alpha / beta candidates at e0 and, batched, at 0.8 e0
+  // and 1.2 e0 (built on the device from the choices); one read-back
+  const int nab = o.n_alpha * o.n_beta;
+  const bool need_scaled = metric != QOZ_METRIC_MAXERR;
+  AbSpec ab;
+  memset(&ab, 0, sizeof(ab));
+  ab.n_alpha = o.n_alpha;
+  ab.n_beta = o.n_beta;
+  ab.n_scales = need_scaled ? 3 : 1;
+  for (int i = 0; i < o.n_alpha; ++i) ab.alphas[i] = o.alphas[i];
+  for (int i = 0; i < o.n_beta; ++i) ab.betas[i] = o.betas[i];
+  ab.scales[0] = 1.0;
+  ab.scales[1] = 0.8;
+  ab.scales[2] = 1.2;
   std::vector<TrialResult> res;
-  if ((st = T.alg1(base, cands, d, ch_interp, ch_order, out->alg1_score)) != QOZ_OK) return st;
+  Alg1Ctl ctl;
+  BoundTable bt;
+  if ((st = T.alg1_enqueue(base, cands, d, sp, ab)) != QOZ_OK) return st;
+  if ((st = T.launch(ab.n_scales * nab, 1, 0, true)) != QOZ_OK) return st;
+  if ((st = T.collect(ab.n_scales * nab, true, &res, &ctl, &bt)) != QOZ_OK) return st;
+  for (int l = 1; l <= sm.Ls; ++l) {
+    ch_interp[l - 1] = ctl.chi[l - 1];
+    ch_order[l - 1] = ctl.cho[l - 1];
+    out->alg1_score[l - 1] = ctl.score[l - 1];
+  }
+  const float vmin = bt.vmin, vmax = bt.vmax;
+  const double vr = (double)vmax - (double)vmin;
+  const double e_user = rel_eb * vr;
+  // the same e0 as the device's (the same operations on the same range)
+  double e0 = e_user;
+  if (sp.psnr_target) {
+    e0 = vr * sp.sqrt3 * sp.p10;
+    if (e0 > e_user) e0 = e_user;
+  }
   qoz_params fp;
   memset(&fp, 0, sizeof(fp));
   fp.anchor_stride = o.anchor_stride;
@@ -1110,24 +1289,12 @@ qoz_status tune_impl(const float* d_field, const qoz_shape& shape, double rel_eb
     fp.order[l - 1] = ch_order[src - 1];
   }
 
-  // ---- alpha / beta candidates at e0 and, batched, at 0.8 e0 and 1.2 e0
+  // ---- alpha / beta selection (Table I) over the batched results
   TrialCand chosen = base;
   for (int l = 1; l <= sm.Ls; ++l) {
     chosen.interp[l - 1] = ch_interp[l - 1];
     set_axes(&chosen, l, d, ch_order[l - 1]);
   }
-  const int nab = o.n_alpha * o.n_beta;
-  const bool need_scaled = metric != QOZ_METRIC_MAXERR;
-  std::vector<TrialCand> tc;
-  const double scales[3] = {1.0, 0.8, 1.2};
-  for (int si = 0; si < (need_scaled ? 3 : 1); ++si)
-    for (int ia = 0; ia < o.n_alpha; ++ia)
-      for (int ib = 0; ib < o.n_beta; ++ib) {
-        TrialCand c = chosen;
-        fill_bounds(&c, scales[si] * e0, o.alphas[ia], o.betas[ib], sm.Ls);
-        tc.push_back(c);
-      }
-  if ((st = T.run(tc, 1, 0, true, &res)) != QOZ_OK) return st;
   auto at = [&](int si, int k) -> const TrialResult& { return res[(size_t)si * nab + k]; };
 
   int best_k = 0;
