@@ -246,6 +246,27 @@ def test_serialize_async_matches_sync(q):
     b2.free()
 
 
+def test_profile_stage_mask(q):
+    # only the selected stages record events; the launch counter always runs
+    import synth
+    x = synth.grf((40, 48, 64), 5.0 / 3.0, seed=4, n_modes=32).cuda()
+    q.profile_read(reset=True)
+    q.profile_enable(True, stages=[q.STAGE_LEVEL + 1])
+    q.compress(x, 1e-3).free()
+    torch.cuda.synchronize()
+    q.profile_enable(False)
+    t = q.profile_read(reset=True)
+    assert t.calls[q.STAGE_LEVEL + 1] == 1 and t.ms[q.STAGE_LEVEL + 1] > 0
+    assert sum(t.calls[i] for i in range(32) if i != q.STAGE_LEVEL + 1) == 0
+    assert t.launches > 0
+    q.profile_enable(True)  # all stages again
+    q.compress(x, 1e-3).free()
+    torch.cuda.synchronize()
+    q.profile_enable(False)
+    t = q.profile_read(reset=True)
+    assert t.calls[q.STAGE_RANGE] == 1 and t.calls[q.STAGE_LEVEL + 2] == 1
+
+
 def test_bulk_copy_wait_times_out_cleanly(q, monkeypatch):
     # the level-1 tile barrier is told to expect 16 bytes more than its
     # copies bring: every tile's bounded wait runs out, the launch reports
