@@ -4,7 +4,8 @@ TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
 baseline leg of the benchmark may import this package; the product path
 (the CUDA library and its binding) never does, and the two share no code.
 
-`build()` compiles qoz_oracle.cpp, qoz_oracle_tune.cpp and qoz_oracle_learn.cpp with
+`build()` compiles qoz_oracle.cpp, qoz_oracle_tune.cpp, qoz_oracle_learn.cpp and
+qoz_oracle_entropy.cpp with
 -O2 -ffp-contract=off (no fused multiply-add, so binary32 arithmetic rounds
 after every operation, as the CUDA side does with explicit _rn intrinsics).
 """
@@ -20,7 +21,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
-_SOURCES = ["qoz_oracle.cpp", "qoz_oracle_tune.cpp", "qoz_oracle_learn.cpp"]
+_SOURCES = ["qoz_oracle.cpp", "qoz_oracle_tune.cpp", "qoz_oracle_learn.cpp",
+            "qoz_oracle_entropy.cpp"]
 _lib = None
 
 MAX_LEVELS = 8
@@ -91,6 +93,10 @@ def lib():
             "orc_anchor_count": (i64, [i32, P, i32]),
             "orc_histogram": (None, [P, i32, P, i32, P]),
             "orc_huffman_bits": (C.c_uint64, [P, i32]),
+            "orc_huffman_lengths": (i32, [P, i32, P]),
+            "orc_canonical_codes": (None, [P, i32, P]),
+            "orc_huffman_encode": (i64, [P, i64, i32, P, P, P, P, i64]),
+            "orc_huffman_decode": (i32, [P, P, i64, i32, P, P, i32, P]),
             "orc_estimate_bits": (f64, [P, i64, i64]),
             "orc_max_abs_err": (f64, [P, P, i64]),
             "orc_mse": (f64, [P, P, i64]),
@@ -221,6 +227,53 @@ def histogram(codes: np.ndarray, anchor_stride: int) -> np.ndarray:
 def huffman_bits(hist) -> int:
     h = np.ascontiguousarray(hist, dtype=np.uint64)
     return int(lib().orc_huffman_bits(_ptr(h), h.size))
+
+
+def huffman_lengths(hist):
+    """Code length per symbol (uint8 array) and the longest length."""
+    h = np.ascontiguousarray(hist, dtype=np.uint64)
+    ln = np.zeros(h.size, dtype=np.uint8)
+    mx = int(lib().orc_huffman_lengths(_ptr(h), h.size, _ptr(ln)))
+    return ln, mx
+
+
+def canonical_codes(lengths):
+    ln = np.ascontiguousarray(lengths, dtype=np.uint8)
+    code = np.zeros(ln.size, dtype=np.uint64)
+    lib().orc_canonical_codes(_ptr(ln), ln.size, _ptr(code))
+    return code
+
+
+ENTROPY_CHUNK = 4096
+
+
+def huffman_encode(symbols, lengths, codes, chunk: int = ENTROPY_CHUNK):
+    """(words uint32, offs uint64) of the chunked MSB-first stream."""
+    s = np.ascontiguousarray(symbols, dtype=np.uint16).ravel()
+    ln = np.ascontiguousarray(lengths, dtype=np.uint8)
+    cd = np.ascontiguousarray(codes, dtype=np.uint64)
+    nch = (s.size + chunk - 1) // chunk
+    offs = np.zeros(nch + 1, dtype=np.uint64)
+    cap = int(np.sum(ln[s].astype(np.int64)) // 32) + nch + 1
+    words = np.zeros(max(cap, 1), dtype=np.uint32)
+    w = int(lib().orc_huffman_encode(_ptr(s), s.size, chunk, _ptr(ln), _ptr(cd), _ptr(offs),
+                                     _ptr(words), words.size))
+    if w < 0:
+        raise ValueError(f"encode failed ({w})")
+    return words[:w].copy(), offs
+
+
+def huffman_decode(words, offs, n: int, lengths, codes, chunk: int = ENTROPY_CHUNK):
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    o = np.ascontiguousarray(offs, dtype=np.uint64)
+    ln = np.ascontiguousarray(lengths, dtype=np.uint8)
+    cd = np.ascontiguousarray(codes, dtype=np.uint64)
+    out = np.zeros(n, dtype=np.uint16)
+    st = int(lib().orc_huffman_decode(_ptr(w), _ptr(o), n, chunk, _ptr(ln), _ptr(cd), ln.size,
+                                      _ptr(out)))
+    if st != 0:
+        raise ValueError("decode failed")
+    return out
 
 
 def estimate_bits(hist, n_unpred: int, n_anchors: int) -> float:

@@ -83,6 +83,18 @@ void orc_histogram(const uint16_t* codes, int ndims, const int64_t* dims,
  * counts hist[0..K-1]; a single used symbol costs 1 bit per occurrence. */
 uint64_t orc_huffman_bits(const uint64_t* hist, int K);
 
+/* Entropy stage (qoz_oracle_entropy.cpp): Huffman code lengths of hist[0..K-1]
+ * with the stated tie rule (returns the longest length, 0 if no symbol is
+ * used); canonical codes from the lengths; chunked MSB-first encoding (returns
+ * the total 32-bit words, < 0 on error); decoding (0 on success). */
+int orc_huffman_lengths(const uint64_t* hist, int K, uint8_t* len);
+void orc_canonical_codes(const uint8_t* len, int K, uint64_t* code);
+int64_t orc_huffman_encode(const uint16_t* sym, int64_t n, int chunk, const uint8_t* len,
+                           const uint64_t* code, uint64_t* offs, uint32_t* words,
+                           int64_t cap_words);
+int orc_huffman_decode(const uint32_t* words, const uint64_t* offs, int64_t n, int chunk,
+                       const uint8_t* len, const uint64_t* code, int K, uint16_t* out);
+
 /* Rate estimate: Huffman bits of the codes + 32 bits per unpredictable value
  * + 32 bits per anchor. */
 double orc_estimate_bits(const uint64_t* hist, int64_t n_unpred, int64_t n_anchors);
