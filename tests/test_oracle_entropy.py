@@ -1,7 +1,7 @@
 """Pins of the oracle's entropy stage (canonical Huffman coding of the
 quantization codes) against values fixed outside it: a textbook Huffman
 example, the canonical-code example of RFC 1951, Kraft's equality, the
-optimal cost (itself pinned by brute force in test_oracle_predictor.py),
+optimal cost (itself pinned by brute force in test_oracle_metrics.py),
 prefix-freeness, a hand-worked bit layout and round trips."""
 
 import itertools
