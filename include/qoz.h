@@ -155,20 +155,43 @@ qoz_status qoz_blob_copy_arrays(const qoz_blob* b, uint16_t* d_codes, int64_t* d
 /* Copy the 65536-bin histogram of the non-anchor codes to h_hist (uint32). */
 qoz_status qoz_blob_histogram(const qoz_blob* b, uint32_t* h_hist, void* stream);
 
-/* Serialized form: header (magic, version, shape, bound, params, counts),
- * anchors, unpredictable list, codes, CRC32 of everything before it.  With
+/* Serialized form (format 2): a 160-byte header (magic, version, shape,
+ * bound, params, counts, checksum), the anchors (float32), the unpredictable
+ * indices (int64) and values (float32), then the code section: the codes of
+ * all N points (anchors carry code 0) in canonical Huffman code, the entropy
+ * stage the rate estimate of Sec. 6.1 stands for.  The code section holds a
+ * 288-byte fixed part (used symbols, longest code, chunk size 4096, chunk and
+ * word counts, number of codes per length 0..63), the used symbols in
+ * (length, symbol) order, the n_chunks + 1 word offsets (uint64) and the
+ * stream (uint32 words; each chunk starts on a word, codes most significant
+ * bit first from each word's most significant bit).  Code lengths follow
+ * Huffman's construction with ties going to the leaf queue; codes are
+ * RFC 1951's canonical assignment.  Every part is padded to 8 bytes.  The
+ * checksum is a 64-bit sum of splitmix64-mixed 8-byte words.
+ *
+ * The stream's length depends on the code table, which is built on the
+ * device: serialization synchronises `stream` once to learn it.  With
  * h_buf = NULL only *used is set (the required size).  Synchronises. */
 qoz_status qoz_blob_serialize(const qoz_blob* b, void* h_buf, size_t cap, size_t* used,
                               void* stream);
-/* Same stream, enqueued without waiting: the payload copies are issued on
- * `stream`, and a host callback on the stream writes the header once the
- * copies are done.  h_buf must be pinned host memory (or the copies become
- * synchronous) and must stay valid until the stream has passed the call; the
- * stream is complete once the stream (or an event recorded after the call)
- * is synchronized.  The blob must not be freed before then, except by
- * stream-ordered qoz_blob_free on the same stream. */
+/* Same stream: after the one synchronisation that sizes the stream (*used is
+ * set on return), the coding, the payload copies and a host callback that
+ * writes the header are enqueued on `stream` without waiting.  h_buf must be
+ * pinned host memory (or the copies become synchronous) and must stay valid
+ * until the stream has passed the call; the stream is complete once the
+ * stream (or an event recorded after the call) is synchronized.  The blob
+ * must not be freed before then, except by stream-ordered qoz_blob_free on
+ * the same stream. */
 qoz_status qoz_blob_serialize_async(const qoz_blob* b, void* h_buf, size_t cap, size_t* used,
                                     void* stream);
+/* An upper bound on the serialized size, from the counts alone (no device
+ * work): an optimal prefix code averages under 17 bits per symbol on a
+ * 65536-symbol alphabet, and each chunk adds at most one partial word. */
+qoz_status qoz_blob_serialize_bound(const qoz_blob* b, size_t* bound);
+/* Parses a serialized stream (format 2) onto the device: checks the header,
+ * the code section (a complete canonical code, consistent chunk offsets) and
+ * the unpredictable list on the host, decodes the codes on the device and
+ * verifies the checksum.  QOZ_ECORRUPT for any inconsistency.  Synchronises. */
 qoz_status qoz_blob_deserialize(const void* h_buf, size_t size, void* stream, qoz_blob** out);
 
 /* Releases the blob's device memory, stream-ordered on the stream the blob

@@ -141,6 +141,7 @@ def lib():
             "qoz_blob_histogram": (i32, [P, P, P]),
             "qoz_blob_serialize": (i32, [P, P, C.c_size_t, P, P]),
             "qoz_blob_serialize_async": (i32, [P, P, C.c_size_t, P, P]),
+            "qoz_blob_serialize_bound": (i32, [P, P]),
             "qoz_blob_deserialize": (i32, [P, C.c_size_t, P, P]),
             "qoz_blob_free": (None, [P]),
             "qoz_compute_metrics": (i32, [P, P, Shape, f64, i32, i32, P, P]),
@@ -285,6 +286,12 @@ class Blob:
         _check(lib().qoz_blob_serialize(self._h, C.c_void_p(out.data_ptr()), out.numel(),
                                         C.byref(used), _stream(stream)))
         return out[:used.value]
+
+    def serialize_bound(self) -> int:
+        """Upper bound on the serialized size (no device work)."""
+        b = C.c_size_t()
+        _check(lib().qoz_blob_serialize_bound(self._h, C.byref(b)))
+        return b.value
 
     def serialize_async(self, out: torch.Tensor, stream=None) -> int:
         """Enqueues the serialized stream into `out` (pinned host uint8) on the

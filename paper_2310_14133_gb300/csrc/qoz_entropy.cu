@@ -1,0 +1,643 @@
+// Entropy stage: canonical Huffman coding of the quantization codes, the
+// encoder that the rate estimate of Sec. 6.1 stands for (the paper follows
+// Huffman coding with a dictionary coder; that lossless pass is not part of
+// this stage).
+//
+// Definitions (the paper names Huffman coding but fixes none of these):
+//   - symbols: the 16-bit code of every point in field order, anchors
+//     included (they carry code 0);
+//   - construction: the used symbols sorted by (count, symbol) form the leaf
+//     queue, merged nodes a second queue in creation order; each pick takes
+//     the node-queue head when its weight is strictly below the leaf head's
+//     (or no leaf is left), otherwise the leaf; a symbol's code length is its
+//     depth, a lone symbol gets length 1;
+//   - canonical codes (RFC 1951 Sec. 3.2.2): consecutive integers in
+//     (length, symbol) order;
+//   - stream: chunks of kEntropyChunk symbols, each starting on a 32-bit
+//     word, codes most significant bit first, words filled from their most
+//     significant bit, the tail of a chunk's last word zero.
+//
+// Kernels: one CTA builds the table (shared memory up to kHuffSmemSym used
+// symbols, a global workspace beyond); the encoder counts each chunk's words,
+// scans them into word offsets and writes the chunks (one warp per chunk,
+// each lane a run of consecutive symbols); the decoder walks one chunk per
+// thread with a 12-bit lookup table and the canonical search for longer
+// codes, checking every index against the stream it was given.
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "../../include/qoz.h"
+#include "qoz_host.h"
+#include "qoz_internal.h"
+
+namespace qoz {
+namespace {
+
+constexpr int kSymbols = 65536;
+constexpr int kTabThreads = 1024;
+constexpr int kHuffSmemSym = 4096;  // used symbols handled in shared memory
+constexpr int kLut = 12;            // bits of the decoder's lookup table
+
+// Workspace of the table kernel (device memory).
+struct HuffWork {
+  unsigned long long keys[kSymbols];   // (count << 16 | symbol), then (length << 16 | symbol)
+  unsigned long long nodew[kSymbols];  // merged-node weights
+  int child[2 * kSymbols];             // children of each merged node (leaf i, node n + j)
+  unsigned char depth[kSymbols];       // merged-node depths
+  unsigned char leaf_len[kSymbols];    // code length of leaf i (sorted order)
+  unsigned char len[kSymbols];         // code length per symbol (encoder)
+  unsigned long long code[kSymbols];   // canonical code per symbol << 6 | its length (encoder)
+  int err;  // 1: a code longer than kMaxCodeLen; 2: a code without a table entry
+};
+
+__device__ __forceinline__ void bitonic_sort(unsigned long long* k, int P) {
+  for (int size = 2; size <= P; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int j = i ^ stride;
+        if (j > i) {
+          const bool up = (i & size) == 0;
+          const unsigned long long a = k[i], b = k[j];
+          if ((a > b) == up) {
+            k[i] = b;
+            k[j] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kTabThreads)
+    huff_table_kernel(const unsigned* __restrict__ hist, long long extra0, HuffWork* w,
+                      HuffFixed* fx, uint16_t* sym_out) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ int nsh, maxlen_sh, err_sh;
+  __shared__ unsigned bl[64];
+  __shared__ unsigned long long first_code[64];
+  __shared__ int first_index[64];
+  const int t = threadIdx.x;
+  if (t == 0) {
+    nsh = 0;
+    maxlen_sh = 0;
+    err_sh = 0;
+  }
+  if (t < 64) bl[t] = 0;
+  for (int s = t; s < kSymbols; s += kTabThreads) {
+    w->len[s] = 0;
+    w->code[s] = 0ull;
+  }
+  __syncthreads();
+  // used symbols in any order (sorted next); anchors add to symbol 0.  The
+  // histogram is read as 16-byte vectors, four loads in flight per thread.
+  unsigned long long* gk = w->keys;
+  const uint4* h4 = reinterpret_cast<const uint4*>(hist);
+  constexpr int kVec = kSymbols / 4 / kTabThreads;  // 16
+  for (int j0 = 0; j0 < kVec; j0 += 4) {
+    uint4 v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = h4[(j0 + j) * kTabThreads + t];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int s0 = 4 * ((j0 + j) * kTabThreads + t);
+      const unsigned cv[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const unsigned long long c =
+            (unsigned long long)cv[k] + (s0 + k == 0 ? (unsigned long long)extra0 : 0ull);
+        if (c) gk[atomicAdd(&nsh, 1)] = (c << 16) | (unsigned long long)(s0 + k);
+      }
+    }
+  }
+  __syncthreads();
+  const int n = nsh;
+  const bool small = n <= kHuffSmemSym;
+  unsigned long long* keys = small ? reinterpret_cast<unsigned long long*>(sm) : w->keys;
+  unsigned long long* nodew = small ? keys + kHuffSmemSym : w->nodew;
+  int* child = small ? reinterpret_cast<int*>(nodew + kHuffSmemSym) : w->child;
+  unsigned char* depth = small ? reinterpret_cast<unsigned char*>(child + 2 * kHuffSmemSym)
+                               : w->depth;
+  unsigned char* leaf_len = small ? depth + kHuffSmemSym : w->leaf_len;
+  int P = 1;
+  while (P < n) P <<= 1;
+  if (small)
+    for (int i = t; i < n; i += kTabThreads) keys[i] = gk[i];
+  for (int i = n + t; i < P; i += kTabThreads) keys[i] = ~0ull;
+  __syncthreads();
+  bitonic_sort(keys, P);
+
+  if (t == 0 && n == 1) {
+    leaf_len[0] = 1;
+    maxlen_sh = 1;
+  } else if (t == 0 && n > 1) {
+    // two-queue merge, heads in registers
+    int li = 0, ni = 0, nn = 0;
+    unsigned long long hl = keys[0] >> 16, hn = 0ull;
+    for (int m = 0; m < n - 1; ++m) {
+      int id[2];
+      unsigned long long wt[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        if (ni < nn && (li >= n || hn < hl)) {
+          id[k] = n + ni;
+          wt[k] = hn;
+          ++ni;
+          hn = ni < nn ? nodew[ni] : 0ull;
+        } else {
+          id[k] = li;
+          wt[k] = hl;
+          ++li;
+          hl = li < n ? (keys[li] >> 16) : ~0ull;
+        }
+      }
+      const unsigned long long sum = wt[0] + wt[1];
+      nodew[nn] = sum;
+      child[2 * nn] = id[0];
+      child[2 * nn + 1] = id[1];
+      if (ni == nn) hn = sum;
+      ++nn;
+    }
+    // depths from the root (the last merged node) down
+    int mx = 0, bad = 0;
+    depth[n - 2] = 0;
+    for (int j = n - 2; j >= 0; --j) {
+      const int d = depth[j] + 1;
+      if (d > kMaxCodeLen) {
+        bad = 1;
+        break;
+      }
+      for (int k = 0; k < 2; ++k) {
+        const int ch = child[2 * j + k];
+        if (ch >= n)
+          depth[ch - n] = (unsigned char)d;
+        else {
+          leaf_len[ch] = (unsigned char)d;
+          mx = d > mx ? d : mx;
+        }
+      }
+    }
+    maxlen_sh = mx;
+    err_sh = bad;
+  }
+  __syncthreads();
+  if (err_sh) {
+    if (t == 0) w->err = 1;
+    return;
+  }
+  // lengths per symbol; keys become (length << 16 | symbol)
+  for (int i = t; i < n; i += kTabThreads) {
+    const int s = (int)(keys[i] & 0xffffull);
+    const int L = leaf_len[i];
+    w->len[s] = (unsigned char)L;
+    atomicAdd(&bl[L], 1u);
+    keys[i] = ((unsigned long long)L << 16) | (unsigned long long)s;
+  }
+  __syncthreads();
+  bitonic_sort(keys, P);
+  const int maxlen = maxlen_sh;
+  if (t == 0) {
+    unsigned long long c = 0ull;
+    int idx = 0;
+    first_code[0] = 0ull;
+    first_index[0] = 0;
+    for (int b = 1; b <= maxlen; ++b) {
+      c = (c + (b == 1 ? 0ull : bl[b - 1])) << 1;
+      first_code[b] = c;
+      first_index[b] = idx;
+      idx += (int)bl[b];
+    }
+    fx->n_sym = (uint32_t)n;
+    fx->max_len = (uint32_t)maxlen;
+    fx->chunk = (uint32_t)kEntropyChunk;
+    fx->flags = 0u;
+    for (int b = 0; b < 64; ++b) fx->bl_count[b] = b <= maxlen ? bl[b] : 0u;
+    w->err = 0;
+  }
+  __syncthreads();
+  for (int i = t; i < n; i += kTabThreads) {
+    const int L = (int)(keys[i] >> 16);
+    const int s = (int)(keys[i] & 0xffffull);
+    w->code[s] = ((first_code[L] + (unsigned long long)(i - first_index[L])) << 6) |
+                 (unsigned long long)L;
+    sym_out[i] = (uint16_t)s;
+  }
+}
+
+// Words of each chunk (one warp per chunk; the lanes read the chunk's codes
+// as consecutive 16-byte vectors and sum their code lengths).
+constexpr int kRun = kEntropyChunk / 32;  // symbols of one lane's run (encoder)
+constexpr int kVecPerChunk = kEntropyChunk / 8;
+
+__device__ __forceinline__ void load8(const uint16_t* __restrict__ sym, long long i, long long n,
+                                      uint32_t v[4]) {
+  if (i + 8 <= n) {
+    const uint4 q = *reinterpret_cast<const uint4*>(sym + i);
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+  } else {
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t lo = i + 2 * k < n ? sym[i + 2 * k] : 0u;
+      const uint32_t hi = i + 2 * k + 1 < n ? sym[i + 2 * k + 1] : 0u;
+      v[k] = lo | (hi << 16);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    huff_count_kernel(const uint16_t* __restrict__ sym, long long n,
+                      const unsigned char* __restrict__ len, long long nchunks,
+                      unsigned long long* __restrict__ offs, int* err) {
+  const long long c = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= nchunks) return;
+  const long long base = c * kEntropyChunk;
+  unsigned bits = 0;
+  bool missing = false;  // a code the table has no entry for
+  for (int j = 0; j < kVecPerChunk / 32; ++j) {
+    const long long i = base + 8ll * (j * 32 + lane);
+    if (i >= n) break;
+    uint32_t v[4];
+    load8(sym, i, n, v);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (i + k >= n) break;
+      const unsigned L = len[(v[k >> 1] >> (16 * (k & 1))) & 0xffffu];
+      missing |= L == 0u;
+      bits += L;
+    }
+  }
+  if (missing) atomicOr(err, 2);
+  for (int off = 16; off > 0; off >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, off);
+  if (lane == 0) offs[c] = (bits + 31) / 32;
+}
+
+// Exclusive scan of the per-chunk word counts in place (one CTA); offs[n]
+// receives the total, which also lands in the section's fixed part.  Each
+// warp owns a contiguous segment and reads it lane-strided (coalesced),
+// eight rounds of loads in flight.
+__global__ void __launch_bounds__(1024)
+    chunk_scan_kernel(unsigned long long* offs, long long nchunks, HuffFixed* fx) {
+  __shared__ unsigned long long wsum[32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long seg = (nchunks + 31) / 32;
+  const long long b = warp * seg, e = b + seg < nchunks ? b + seg : nchunks;
+  unsigned long long s = 0;
+  for (long long i0 = b; i0 < e; i0 += 32 * 8) {
+    unsigned long long v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const long long i = i0 + 32 * k + lane;
+      v[k] = i < e ? offs[i] : 0ull;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += v[k];
+  }
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) wsum[warp] = s;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned long long x = wsum[lane];
+    unsigned long long inc = x;
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, off);
+      if (lane >= off) inc += y;
+    }
+    wsum[lane] = inc - x;
+    if (lane == 31) {
+      offs[nchunks] = inc;
+      fx->n_chunks = (uint64_t)nchunks;
+      fx->n_words = (uint64_t)inc;
+    }
+  }
+  __syncthreads();
+  unsigned long long carry = wsum[warp];
+  for (long long i0 = b; i0 < e; i0 += 32 * 8) {
+    unsigned long long v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const long long i = i0 + 32 * k + lane;
+      v[k] = i < e ? offs[i] : 0ull;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      unsigned long long inc = v[k];
+      for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += y;
+      }
+      const long long i = i0 + 32 * k + lane;
+      if (i < e) offs[i] = carry + inc - v[k];
+      carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
+  }
+}
+
+// The chunks' bits (one warp per chunk).  The chunk's codes are read as
+// consecutive 16-byte vectors and transposed through shared memory into one
+// run of kRun consecutive codes per lane (rows padded to 65 words: the
+// lanes' reads fall in distinct banks).  A lane places its run from its bit
+// offset in the chunk; words the run covers whole are stored, the first and
+// last (shared with the neighbouring runs) are OR-ed into the zeroed stream.
+constexpr int kEncWarps = 4;  // 33 KB of static shared memory per CTA
+constexpr int kRowWords = kRun / 2 + 1;
+
+// Appends L <= 32 bits to the lane's accumulator (nacc < 32 pending bits
+// before, so at most one word completes).
+__device__ __forceinline__ void put_bits(unsigned long long& acc, int& nacc, unsigned long long v,
+                                         int L, uint32_t* out, long long& wi, bool& first,
+                                         bool shared_first) {
+  acc = (acc << L) | v;
+  nacc += L;
+  if (nacc >= 32) {
+    nacc -= 32;
+    const uint32_t w = (uint32_t)(acc >> nacc);
+    acc &= (1ull << nacc) - 1ull;
+    if (first && shared_first)
+      atomicOr(out + wi, w);
+    else
+      out[wi] = w;
+    ++wi;
+    first = false;
+  }
+}
+
+template <bool LONG>
+__global__ void __launch_bounds__(32 * kEncWarps)
+    huff_encode_kernel(const uint16_t* __restrict__ sym, long long n,
+                       const unsigned long long* __restrict__ entry, long long nchunks,
+                       const unsigned long long* __restrict__ offs, uint32_t* words) {
+  __shared__ uint32_t stage[kEncWarps][32 * kRowWords];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long c = (long long)blockIdx.x * kEncWarps + warp;
+  if (c >= nchunks) return;
+  const long long base = c * kEntropyChunk;
+  uint32_t* st = stage[warp];
+  for (int j = 0; j < kVecPerChunk / 32; ++j) {
+    const int q = j * 32 + lane;  // vector q holds codes 8q .. 8q + 7 of the chunk
+    uint32_t v[4];
+    load8(sym, base + 8ll * q, n, v);
+    const int row = q / (kRun / 8), col = 4 * (q % (kRun / 8));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) st[row * kRowWords + col + k] = v[k];
+  }
+  __syncwarp();
+  const long long b = base + (long long)lane * kRun;
+  const int cnt = b >= n ? 0 : (int)(b + kRun < n ? kRun : n - b);
+  const uint32_t* mine = st + lane * kRowWords;
+  auto sym_at = [&](int k) -> int { return (int)((mine[k >> 1] >> (16 * (k & 1))) & 0xffffu); };
+  unsigned long long bits = 0;
+  for (int k = 0; k < cnt; ++k) bits += entry[sym_at(k)] & 63ull;
+  unsigned long long start = bits;  // inclusive scan over the lanes
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned long long v = __shfl_up_sync(0xffffffffu, start, off);
+    if (lane >= off) start += v;
+  }
+  start -= bits;
+  if (bits == 0) return;
+  uint32_t* out = words + offs[c];
+  long long wi = (long long)(start >> 5);
+  int nacc = (int)(start & 31);  // pending bits (leading zeros of the first word)
+  unsigned long long acc = 0ull;
+  bool first = true;
+  const bool shared_first = (start & 31) != 0;
+  for (int k = 0; k < cnt; ++k) {
+    const unsigned long long en = entry[sym_at(k)];
+    const int L = (int)(en & 63ull);
+    const unsigned long long cv = en >> 6;
+    if (LONG && L > 32) {  // the high part first
+      put_bits(acc, nacc, cv >> 32, L - 32, out, wi, first, shared_first);
+      put_bits(acc, nacc, cv & 0xffffffffull, 32, out, wi, first, shared_first);
+    } else {
+      put_bits(acc, nacc, cv, L, out, wi, first, shared_first);
+    }
+  }
+  if (nacc > 0) atomicOr(out + wi, (uint32_t)(acc << (32 - nacc)));
+}
+
+// Decoder tables in shared memory: 12-bit lookup (symbol << 8 | length, 0
+// for prefixes of longer codes) and the canonical first code / index per
+// length.
+struct DecTables {
+  uint32_t lut[1 << kLut];
+  unsigned long long first_code[64];
+  unsigned first_index[64];
+  unsigned count[64];
+};
+
+__global__ void __launch_bounds__(128)
+    huff_decode_kernel(const uint32_t* __restrict__ words,
+                       const unsigned long long* __restrict__ offs, long long nchunks,
+                       long long n, const HuffFixed* __restrict__ fx,
+                       const uint16_t* __restrict__ syms, uint16_t* __restrict__ out, int* err) {
+  __shared__ DecTables T;
+  const int t = threadIdx.x;
+  const int maxlen = (int)fx->max_len;
+  const unsigned nsym = fx->n_sym;
+  for (int i = t; i < (1 << kLut); i += blockDim.x) T.lut[i] = 0u;
+  if (t == 0) {
+    unsigned long long c = 0ull;
+    unsigned idx = 0;
+    for (int b = 0; b < 64; ++b) {
+      if (b >= 1) c = (c + (b == 1 ? 0ull : fx->bl_count[b - 1])) << 1;
+      T.first_code[b] = c;
+      T.first_index[b] = idx;
+      T.count[b] = b >= 1 && b <= maxlen ? fx->bl_count[b] : 0u;
+      idx += T.count[b];
+    }
+  }
+  __syncthreads();
+  // lookup entries of the codes with length <= kLut
+  for (unsigned i = t; i < nsym; i += blockDim.x) {
+    int L = 1;
+    while (L <= maxlen && i >= T.first_index[L] + T.count[L]) ++L;
+    if (L > kLut) continue;
+    const unsigned long long cv = T.first_code[L] + (i - T.first_index[L]);
+    const unsigned lo = (unsigned)(cv << (kLut - L)), hi = (unsigned)((cv + 1) << (kLut - L));
+    for (unsigned k = lo; k < hi && k < (1u << kLut); ++k)
+      T.lut[k] = ((uint32_t)syms[i] << 8) | (uint32_t)L;
+  }
+  __syncthreads();
+  const long long c = blockIdx.x * (long long)blockDim.x + t;
+  if (c >= nchunks) return;
+  const unsigned long long w0 = offs[c], w1 = offs[c + 1];
+  if (w1 < w0) {
+    atomicOr(err, 4);
+    return;
+  }
+  const unsigned long long nbits = (w1 - w0) * 32ull;
+  const uint32_t* W = words + w0;
+  auto word_at = [&](unsigned long long k) -> unsigned long long {
+    return k < w1 - w0 ? (unsigned long long)W[k] : 0ull;
+  };
+  unsigned long long bp = 0;  // bit position in the chunk
+  const long long b = c * kEntropyChunk;
+  const long long e = b + kEntropyChunk < n ? b + kEntropyChunk : n;
+  long long cw = -1;
+  unsigned long long win = 0ull;  // the 64 bits from word cw on
+  uint32_t grp[4] = {0u, 0u, 0u, 0u};  // eight decoded codes, stored as one 16-byte vector
+  for (long long i = b; i < e; ++i) {
+    const long long wk = (long long)(bp >> 5);
+    if (wk != cw) {
+      win = (word_at(wk) << 32) | word_at(wk + 1);
+      cw = wk;
+    }
+    const unsigned long long top = win << (bp & 31);  // >= 33 valid bits
+    const uint32_t ent = T.lut[top >> (64 - kLut)];
+    int L = (int)(ent & 0xffu);
+    int s;
+    if (L) {
+      s = (int)(ent >> 8);
+    } else {
+      // canonical search over the longer lengths, bit by bit from the stream
+      unsigned long long v = top >> (64 - kLut);
+      s = -1;
+      L = kLut;
+      while (L < maxlen) {
+        ++L;
+        const unsigned long long q = bp + (unsigned long long)(L - 1);
+        v = (v << 1) | ((word_at(q >> 5) >> (31 - (q & 31))) & 1ull);
+        if (v >= T.first_code[L] && v - T.first_code[L] < T.count[L]) {
+          const unsigned long long k = T.first_index[L] + (v - T.first_code[L]);
+          if (k < nsym) s = syms[k];
+          break;
+        }
+      }
+      if (s < 0) {
+        atomicOr(err, 4);
+        return;
+      }
+    }
+    bp += (unsigned long long)L;
+    if (bp > nbits) {
+      atomicOr(err, 4);
+      return;
+    }
+    const int g = (int)(i - b) & 7;  // chunks start on multiples of eight codes
+    grp[g >> 1] |= (uint32_t)s << (16 * (g & 1));
+    if (g == 7) {
+      *reinterpret_cast<uint4*>(out + (i - 7)) = make_uint4(grp[0], grp[1], grp[2], grp[3]);
+      grp[0] = grp[1] = grp[2] = grp[3] = 0u;
+    }
+  }
+  const long long tail = (e - b) & 7;  // the last partial group
+  for (long long k = 0; k < tail; ++k)
+    out[e - tail + k] = (uint16_t)(grp[k >> 1] >> (16 * (k & 1)));
+}
+
+}  // namespace
+
+size_t huff_fixed_bytes() { return sizeof(HuffFixed); }
+
+void huff_free(HuffEncoded* h, cudaStream_t s) {
+  dev_free(h->d_work, s);
+  dev_free(h->d_section, s);
+  dev_free(h->d_words, s);
+  memset(h, 0, sizeof(*h));
+}
+
+qoz_status huff_encode(const qoz_blob* b, cudaStream_t s, HuffEncoded* h, bool sizes_only) {
+  memset(h, 0, sizeof(*h));
+  h->n_chunks = (b->N + kEntropyChunk - 1) / kEntropyChunk;
+  // the section's fixed part and symbol list, then the chunk offsets
+  h->sym_bytes = pad8_bytes(sizeof(uint16_t) * kSymbols);
+  const size_t sec = sizeof(HuffFixed) + h->sym_bytes + sizeof(unsigned long long) * (h->n_chunks + 1);
+  cudaError_t e = dev_alloc(&h->d_work, sizeof(HuffWork), s);
+  if (e == cudaSuccess) e = dev_alloc(&h->d_section, sec, s);
+  if (e != cudaSuccess) {
+    huff_free(h, s);
+    return fail(QOZ_ENOMEM, "entropy workspace");
+  }
+  HuffWork* w = static_cast<HuffWork*>(h->d_work);
+  HuffFixed* fx = static_cast<HuffFixed*>(h->d_section);
+  uint16_t* syms = reinterpret_cast<uint16_t*>(static_cast<char*>(h->d_section) + sizeof(HuffFixed));
+  unsigned long long* offs = reinterpret_cast<unsigned long long*>(
+      static_cast<char*>(h->d_section) + sizeof(HuffFixed) + h->sym_bytes);
+  e = cudaMemsetAsync(h->d_section, 0, sec, s);
+  constexpr size_t kTabSmem = (size_t)kHuffSmemSym * (8 + 8 + 8 + 1 + 1);
+  static unsigned long long attr_done = 0;
+  if (e == cudaSuccess)
+    e = ensure_smem_attr((const void*)huff_table_kernel, &attr_done, kTabSmem);
+  if (e == cudaSuccess) {
+    huff_table_kernel<<<1, kTabThreads, kTabSmem, s>>>(b->d_hist, b->na, w, fx, syms);
+    note_launch(1);
+    e = launch_check(cudaGetLastError());
+  }
+  const long long nch = h->n_chunks;
+  const unsigned grid = (unsigned)((nch * 32 + 255) / 256);
+  if (e == cudaSuccess && nch > 0) {
+    huff_count_kernel<<<grid, 256, 0, s>>>(b->d_codes, b->N, w->len, nch, offs, &w->err);
+    note_launch(1);
+    e = launch_check(cudaGetLastError());
+  }
+  if (e == cudaSuccess) {
+    chunk_scan_kernel<<<1, 1024, 0, s>>>(offs, nch, fx);
+    note_launch(1);
+    e = launch_check(cudaGetLastError());
+  }
+  // sizes to the host (one synchronisation): the stream's length is known
+  // only once the table and the counts exist
+  HuffFixed hf;
+  int werr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hf, fx, sizeof(hf), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&werr, &w->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    huff_free(h, s);
+    return cuda_fail(e, "entropy table");
+  }
+  if (werr & 1) {
+    huff_free(h, s);
+    return fail(QOZ_EUNSUPPORTED, "a Huffman code longer than %d bits", kMaxCodeLen);
+  }
+  if (werr) {
+    huff_free(h, s);
+    return fail(QOZ_ECORRUPT, "the blob's histogram does not cover its codes");
+  }
+  h->fixed = hf;
+  h->n_words = (long long)hf.n_words;
+  if (h->n_words > 0 && !sizes_only) {
+    e = dev_alloc((void**)&h->d_words, sizeof(uint32_t) * (size_t)h->n_words + 8, s);
+    if (e != cudaSuccess) {
+      huff_free(h, s);
+      return fail(QOZ_ENOMEM, "entropy stream");
+    }
+    e = cudaMemsetAsync(h->d_words, 0, sizeof(uint32_t) * (size_t)h->n_words + 8, s);
+    if (e == cudaSuccess) {
+      const unsigned eg = (unsigned)((nch + kEncWarps - 1) / kEncWarps);
+      if (hf.max_len > 32)
+        huff_encode_kernel<true><<<eg, 32 * kEncWarps, 0, s>>>(b->d_codes, b->N, w->code, nch,
+                                                                offs, h->d_words);
+      else
+        huff_encode_kernel<false><<<eg, 32 * kEncWarps, 0, s>>>(b->d_codes, b->N, w->code, nch,
+                                                                 offs, h->d_words);
+      note_launch(1);
+      e = launch_check(cudaGetLastError());
+    }
+    if (e != cudaSuccess) {
+      huff_free(h, s);
+      return cuda_fail(e, "entropy encode");
+    }
+  }
+  dev_free(h->d_work, s);
+  h->d_work = nullptr;
+  return QOZ_OK;
+}
+
+cudaError_t huff_decode(const void* d_section, const uint32_t* d_words, long long nchunks,
+                        long long N, uint16_t* d_codes, int* d_err, cudaStream_t s) {
+  if (nchunks <= 0) return cudaSuccess;
+  const HuffFixed* fx = static_cast<const HuffFixed*>(d_section);
+  const uint16_t* syms =
+      reinterpret_cast<const uint16_t*>(static_cast<const char*>(d_section) + sizeof(HuffFixed));
+  const unsigned long long* offs = reinterpret_cast<const unsigned long long*>(
+      static_cast<const char*>(d_section) + sizeof(HuffFixed) + pad8_bytes(sizeof(uint16_t) * kSymbols));
+  const unsigned grid = (unsigned)((nchunks + 127) / 128);
+  huff_decode_kernel<<<grid, 128, 0, s>>>(d_words, offs, nchunks, N, fx, syms, d_codes, d_err);
+  note_launch(1);
+  return cudaGetLastError();
+}
+
+}  // namespace qoz

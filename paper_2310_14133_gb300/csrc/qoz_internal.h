@@ -5,6 +5,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "../../include/qoz.h"
 #include "qoz_device.cuh"
 
 namespace qoz {
@@ -170,5 +171,44 @@ cudaError_t launch_ssim(const float* a, const float* b, const long long dims[3],
                         int win, int step, double c1, double c2, double* part_diss,
                         cudaStream_t s);
 int ssim_parts(const long long dims[3], bool is3d, int win, int step);
+
+// Entropy stage (qoz_entropy.cu): canonical Huffman coding of the codes.
+constexpr int kEntropyChunk = 4096;  // symbols per independently coded chunk
+constexpr int kMaxCodeLen = 58;      // longest code the coder handles
+
+// Fixed part of the serialized code section (288 bytes): counts, then the
+// number of codes of each length 0..63.
+struct HuffFixed {
+  uint32_t n_sym, max_len, chunk, flags;
+  uint64_t n_chunks, n_words;
+  uint32_t bl_count[64];
+};
+static_assert(sizeof(HuffFixed) == 288, "code section header layout");
+
+inline size_t pad8_bytes(size_t v) { return (v + 7) & ~(size_t)7; }
+
+// A blob's coded stream on the device: d_section holds the fixed part, room
+// for 65536 symbols (sym_bytes) and the n_chunks + 1 word offsets; d_words
+// the n_words stream words.
+struct HuffEncoded {
+  HuffFixed fixed;
+  long long n_chunks, n_words;
+  size_t sym_bytes;
+  void* d_work;
+  void* d_section;
+  uint32_t* d_words;
+};
+
+// Builds the code table from the blob's histogram (anchors added back to
+// symbol 0), counts, scans and (unless sizes_only) writes the chunks;
+// synchronises once on s to learn the stream's length.  huff_free releases
+// (stream-ordered).
+qoz_status huff_encode(const qoz_blob* b, cudaStream_t s, HuffEncoded* h, bool sizes_only);
+void huff_free(HuffEncoded* h, cudaStream_t s);
+// Decodes nchunks chunks into d_codes (N symbols) from a device section laid
+// out as huff_encode's; bit 2 of *d_err reports a stream that does not
+// decode.
+cudaError_t huff_decode(const void* d_section, const uint32_t* d_words, long long nchunks,
+                        long long N, uint16_t* d_codes, int* d_err, cudaStream_t s);
 
 }  // namespace qoz
