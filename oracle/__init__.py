@@ -26,7 +26,7 @@ _SOURCES = ["qoz_oracle.cpp", "qoz_oracle_tune.cpp", "qoz_oracle_learn.cpp",
 _lib = None
 
 MAX_LEVELS = 8
-METRIC_MAXERR, METRIC_PSNR, METRIC_SSIM = 0, 1, 2
+METRIC_MAXERR, METRIC_PSNR, METRIC_SSIM, METRIC_AC = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -69,7 +69,8 @@ class Trial(C.Structure):
     _fields_ = [("bits", C.c_double), ("B", C.c_double), ("npts", C.c_int64),
                 ("n_unpred", C.c_int64), ("n_anchors", C.c_int64),
                 ("max_err", C.c_double), ("sse", C.c_double),
-                ("ssim_sum", C.c_double), ("ssim_n", C.c_int64), ("stats", LevelStats)]
+                ("ssim_sum", C.c_double), ("ssim_n", C.c_int64), ("stats", LevelStats),
+                ("ac", C.c_double)]
 
 
 class TuneResult(C.Structure):
@@ -100,6 +101,8 @@ def lib():
             "orc_estimate_bits": (f64, [P, i64, i64]),
             "orc_max_abs_err": (f64, [P, P, i64]),
             "orc_mse": (f64, [P, P, i64]),
+            "orc_autocorr": (f64, [P, P, i64, i64]),
+            "orc_autocorr_blocks": (f64, [P, P, i64, i64]),
             "orc_psnr": (f64, [P, P, i64, f64]),
             "orc_ssim": (f64, [P, P, i32, P, i32, i32, f64, P, P]),
             "orc_sample_blocks": (i64, [i32, P, i32, f64, P, i64, P, P]),
@@ -274,6 +277,22 @@ def huffman_decode(words, offs, n: int, lengths, codes, chunk: int = ENTROPY_CHU
     if st != 0:
         raise ValueError("decode failed")
     return out
+
+
+def autocorr(a, b, lag: int = 1) -> float:
+    """Eq. (ac) of the errors b - a over the flattened arrays."""
+    a = np.ascontiguousarray(a, dtype=np.float32).ravel()
+    b = np.ascontiguousarray(b, dtype=np.float32).ravel()
+    return float(lib().orc_autocorr(_ptr(a), _ptr(b), a.size, lag))
+
+
+def autocorr_blocks(errors, sizes, lag: int = 1) -> float:
+    """Eq. (ac) over errors cut into consecutive blocks of the given sizes:
+    pairs inside a block, mean and variance over all."""
+    e = np.ascontiguousarray(errors, dtype=np.float64).ravel()
+    st = np.concatenate([[0], np.cumsum(np.asarray(sizes, dtype=np.int64))]).astype(np.int64)
+    assert st[-1] == e.size
+    return float(lib().orc_autocorr_blocks(_ptr(e), _ptr(st), st.size - 1, lag))
 
 
 def estimate_bits(hist, n_unpred: int, n_anchors: int) -> float:

@@ -406,6 +406,35 @@ uint64_t orc_huffman_bits(const uint64_t* hist, int K) {
   return bits;
 }
 
+double orc_autocorr_blocks(const double* e, const int64_t* starts, int64_t nblocks, int64_t k) {
+  /* Eq. (ac), two passes: mean and variance of all errors first, then the
+   * lag-k products inside each block. */
+  const int64_t n = starts[nblocks];
+  if (n <= 0) return 0.0;
+  double mu = 0.0;
+  for (int64_t i = 0; i < n; ++i) mu += e[i];
+  mu /= (double)n;
+  double var = 0.0;
+  for (int64_t i = 0; i < n; ++i) var += (e[i] - mu) * (e[i] - mu);
+  var /= (double)n;
+  double cov = 0.0;
+  int64_t pairs = 0;
+  for (int64_t j = 0; j < nblocks; ++j)
+    for (int64_t i = starts[j]; i + k < starts[j + 1]; ++i) {
+      cov += (e[i] - mu) * (e[i + k] - mu);
+      ++pairs;
+    }
+  if (pairs == 0 || var == 0.0) return 0.0;
+  return (cov / (double)pairs) / var;
+}
+
+double orc_autocorr(const float* a, const float* b, int64_t n, int64_t k) {
+  std::vector<double> e(n > 0 ? n : 0);
+  for (int64_t i = 0; i < n; ++i) e[i] = (double)b[i] - (double)a[i];
+  const int64_t starts[2] = {0, n > 0 ? n : 0};
+  return orc_autocorr_blocks(e.data(), starts, 1, k);
+}
+
 double orc_estimate_bits(const uint64_t* hist, int64_t n_unpred, int64_t n_anchors) {
   return (double)orc_huffman_bits(hist, 65536) + 32.0 * (double)n_unpred +
          32.0 * (double)n_anchors;

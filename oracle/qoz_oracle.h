@@ -102,6 +102,14 @@ double orc_estimate_bits(const uint64_t* hist, int64_t n_unpred, int64_t n_ancho
 /* Metrics, Sec. 3 */
 double orc_max_abs_err(const float* a, const float* b, int64_t n);
 double orc_mse(const float* a, const float* b, int64_t n);
+/* Eq. (ac): autocorrelation at lag k of the errors e_i = b_i - a_i over the
+ * flattened arrays: the mean over the n - k pairs of (e_i - mu)(e_{i+k} - mu)
+ * divided by sigma^2, mu and sigma^2 the population mean and variance of all
+ * n errors; 0 when sigma^2 = 0 or n <= k. */
+double orc_autocorr(const float* a, const float* b, int64_t n, int64_t k);
+/* The same over errors cut into blocks (block j = e[starts[j] .. starts[j+1])):
+ * pairs stay inside a block, mu and sigma^2 are over all errors. */
+double orc_autocorr_blocks(const double* e, const int64_t* starts, int64_t nblocks, int64_t k);
 double orc_psnr(const float* a, const float* b, int64_t n, double vrange);
 /* Mean SSIM over all box windows of edge `win` placed every `step` points
  * that lie fully inside the array; c1 = (0.01 vrange)^2, c2 = (0.03 vrange)^2.
@@ -118,6 +126,7 @@ double orc_ssim(const float* a, const float* b, int ndims, const int64_t* dims,
 #define ORC_METRIC_MAXERR 0
 #define ORC_METRIC_PSNR 1
 #define ORC_METRIC_SSIM 2
+#define ORC_METRIC_AC 3   /* lag-1 autocorrelation of the errors, lower is better */
 
 typedef struct {
   int32_t block;          /* sample block size b (power of two); blocks hold b+1 points per axis */
@@ -140,6 +149,7 @@ typedef struct {
   double ssim_sum;
   int64_t ssim_n;
   orc_level_stats stats;  /* summed over blocks */
+  double ac;              /* lag-1 error autocorrelation, pooled over the blocks */
 } orc_trial;
 
 typedef struct {
@@ -165,7 +175,8 @@ int orc_block_trial(const float* x, int ndims, const int64_t* dims,
                     const orc_params* p, double e, int stop_level, int ssim_win, int ssim_step,
                     double vrange, orc_trial* out);
 
-/* Metric value of a trial, higher is better: PSNR (dB), SSIM, or -max error. */
+/* Metric value of a trial, higher is better: PSNR (dB), SSIM, -AC (lag 1,
+ * pooled over the blocks) or -max error. */
 double orc_trial_metric(const orc_trial* t, int metric, double vrange);
 
 /* Table I comparison of the incumbent I = (b1, m1) with the challenger

@@ -117,6 +117,8 @@ int orc_block_trial(const float* x, int ndims, const int64_t* dims,
   std::vector<int64_t> uidx(bn);
   std::vector<float> uval(bn);
   std::vector<uint64_t> hist(65536, 0), bh(65536);
+  std::vector<double> errs;           /* errors of every block, block after block */
+  std::vector<int64_t> starts(1, 0);  /* where each block's errors start */
   for (int64_t k = 0; k < nblocks; ++k) {
     const int64_t* o = origins + 3 * k;
     /* cut the block out of the field */
@@ -145,6 +147,8 @@ int orc_block_trial(const float* x, int ndims, const int64_t* dims,
       out->stats.l1[l] += st.l1[l];
       out->stats.cnt[l] += st.cnt[l];
     }
+    for (int64_t i = 0; i < bn; ++i) errs.push_back((double)rec[i] - (double)blk[i]);
+    starts.push_back((int64_t)errs.size());
     const double me = orc_max_abs_err(blk.data(), rec.data(), bn);
     if (me > out->max_err || me != me) out->max_err = me;
     out->sse += orc_mse(blk.data(), rec.data(), bn) * (double)bn;
@@ -159,6 +163,7 @@ int orc_block_trial(const float* x, int ndims, const int64_t* dims,
   }
   out->bits = orc_estimate_bits(hist.data(), out->n_unpred, out->n_anchors);
   out->B = out->npts > 0 ? out->bits / (double)out->npts : 0.0;
+  out->ac = orc_autocorr_blocks(errs.data(), starts.data(), nblocks, 1);
   return 0;
 }
 
@@ -169,6 +174,7 @@ double orc_trial_metric(const orc_trial* t, int metric, double vrange) {
     return 20.0 * std::log10(vrange / std::sqrt(mse));
   }
   if (metric == ORC_METRIC_SSIM) return t->ssim_n > 0 ? t->ssim_sum / (double)t->ssim_n : NAN;
+  if (metric == ORC_METRIC_AC) return -t->ac;
   return -t->max_err;
 }
 
@@ -220,6 +226,7 @@ int orc_tune(const float* x, int ndims, const int64_t* dims, double e_user, doub
   bp.beta = 1.0;
 
   const bool target_mode = !std::isnan(target);
+  if (target_mode && metric == ORC_METRIC_AC) return 1; /* AC has no target mode (reading) */
   double e0 = e_user;
   if (target_mode && metric == ORC_METRIC_PSNR) {
     e0 = vrange * std::sqrt(3.0) * std::pow(10.0, -target / 20.0);

@@ -1,6 +1,7 @@
 """Pins for the oracle's metrics (Sec. 3: PSNR Eq. (psnr), SSIM Eq. (ssim),
-Eq. (ssim2)) and rate estimate (Sec. 6.1: Huffman coding of the pooled
-quantization bins), against closed forms, a library SSIM and brute force."""
+Eq. (ssim2), the error autocorrelation Eq. (ac)) and rate estimate (Sec. 6.1:
+Huffman coding of the pooled quantization bins), against closed forms, a
+library SSIM and brute force."""
 
 import itertools
 import math
@@ -142,3 +143,72 @@ def test_estimate_bits_and_histogram(orc):
     assert np.array_equal(h, want.astype(np.uint64))
     nu = len(r["unpred_idx"])
     assert orc.estimate_bits(h, nu, na) == orc.huffman_bits(h) + 32 * nu + 32 * na
+
+
+# ---- Eq. (ac): autocorrelation of the compression errors
+
+def _ac_pair(e):
+    """Original zeros and reconstruction e: the errors are e exactly."""
+    e = np.asarray(e, dtype=np.float32)
+    return np.zeros_like(e), e
+
+
+def test_ac_alternating_errors(orc):
+    # e_i = (-1)^i: mean 0, variance 1, every lag-1 product -1 and every
+    # lag-2 product +1, so AC(1) = -1 and AC(2) = 1 exactly
+    a, b = _ac_pair([(-1.0) ** i for i in range(1000)])
+    assert orc.autocorr(a, b, 1) == -1.0
+    assert orc.autocorr(a, b, 2) == 1.0
+
+
+@pytest.mark.parametrize("period,k", [(8, 1), (8, 2), (10, 3), (16, 4)])
+def test_ac_cosine_closed_form(orc, period, k):
+    # e_i = cos(w i) over whole periods: AC(k) = cos(w k) + O(1 / ((N - k) sin w))
+    n = 100000 - 100000 % period
+    w = 2.0 * np.pi / period
+    a, b = _ac_pair(np.cos(w * np.arange(n)))
+    assert orc.autocorr(a, b, k) == pytest.approx(np.cos(w * k), abs=2e-4)
+
+
+def test_ac_ar1_process(orc):
+    # e_i = phi e_{i-1} + white noise: AC(k) -> phi^k
+    rng = np.random.default_rng(3)
+    phi, n = 0.6, 400000
+    eta = rng.standard_normal(n)
+    e = np.empty(n)
+    e[0] = eta[0]
+    for i in range(1, n):
+        e[i] = phi * e[i - 1] + eta[i]
+    a, b = _ac_pair(e)
+    assert orc.autocorr(a, b, 1) == pytest.approx(phi, abs=0.01)
+    assert orc.autocorr(a, b, 2) == pytest.approx(phi ** 2, abs=0.01)
+
+
+def test_ac_affine_invariance_and_degenerate(orc):
+    rng = np.random.default_rng(4)
+    e = rng.standard_normal(5000).astype(np.float32)
+    a, b = _ac_pair(e)
+    a2, b2 = _ac_pair(2.0 * e.astype(np.float64) + 3.0)
+    assert orc.autocorr(a2, b2, 1) == pytest.approx(orc.autocorr(a, b, 1), abs=1e-6)
+    # the sign convention of the error does not matter
+    assert orc.autocorr(b, a, 1) == pytest.approx(orc.autocorr(a, b, 1), abs=1e-12)
+    # constant error (zero variance) and lags past the end give 0
+    a, b = _ac_pair(np.full(100, 0.25))
+    assert orc.autocorr(a, b, 1) == 0.0
+    a, b = _ac_pair([1.0, -1.0, 2.0])
+    assert orc.autocorr(a, b, 3) == 0.0
+
+
+def test_ac_blocks_pairs_stay_inside(orc):
+    # one block is the plain definition
+    rng = np.random.default_rng(5)
+    e = rng.standard_normal(777)
+    a, b = _ac_pair(e)
+    assert orc.autocorr_blocks(e.astype(np.float32).astype(np.float64), [777], 1) == \
+        pytest.approx(orc.autocorr(a, b, 1), abs=1e-12)
+    # blocks [1, 1, 1, 1] and [-1, -1, -1, -1]: mean 0, variance 1; every pair
+    # inside a block gives +1, the one pair across the boundary (-1) is not
+    # counted, so AC = 1 exactly
+    assert orc.autocorr_blocks([1, 1, 1, 1, -1, -1, -1, -1], [4, 4], 1) == 1.0
+    # the same errors as one block: 6 pairs of +1 and one of -1 -> 5/7
+    assert orc.autocorr_blocks([1, 1, 1, 1, -1, -1, -1, -1], [8], 1) == pytest.approx(5.0 / 7.0)

@@ -148,3 +148,35 @@ def test_target_psnr_mode_meets_target_on_samples(orc):
         # uniform-error start e0 = vr sqrt(3) 10^(-P/20) is within a factor 4
         e0 = vr * math.sqrt(3) * 10 ** (-target / 20)
         assert e0 / 16 <= r.e <= e0 * 4
+
+
+def test_ac_mode(orc):
+    """The AC-preferred mode (Sec. 7.2.2's autocorrelation mode): Table I with
+    M = -AC; the reported metric is the chosen setting's pooled lag-1 AC over
+    the sampled blocks, recomputed here from the error blocks themselves."""
+    x = _field(40, seed=17)
+    mn, mx, _ = orc.value_range(x)
+    vr = float(mx) - float(mn)
+    e = 1e-3 * vr
+    o = orc.make_tune_opts(3, block=16, rate=0.08, betas=[2.0, 3.0, 4.0])
+    r = orc.tune(x, e, vr, orc.METRIC_AC, opts=o)
+    assert r.n_trials >= 16 + 15
+    org, bd, _ = orc.sample_blocks(x.shape, 16, 0.08)
+    p = orc.make_params(3, anchor_stride=16, alpha=r.params.alpha, beta=r.params.beta)
+    for ll in range(4):
+        p.interp[ll], p.order[ll] = r.params.interp[ll], r.params.order[ll]
+    t = orc.block_trial(x, org, bd, p, e)
+    assert r.M == pytest.approx(orc.trial_metric(t, orc.METRIC_AC, vr), abs=0, rel=1e-15)
+    # the trial's AC is the pinned block-pooled definition applied to the
+    # blocks' own compression errors
+    errs, sizes = [], []
+    for o3 in org:
+        blk = np.ascontiguousarray(x[o3[0]:o3[0] + bd[0], o3[1]:o3[1] + bd[1],
+                                     o3[2]:o3[2] + bd[2]])
+        rec = orc.compress(blk, e, p)["recon"]
+        errs.append((rec.astype(np.float64) - blk.astype(np.float64)).ravel())
+        sizes.append(blk.size)
+    assert t.ac == pytest.approx(orc.autocorr_blocks(np.concatenate(errs), sizes, 1), abs=1e-15)
+    assert -1.0 <= r.M <= 1.0
+    with pytest.raises(ValueError):
+        orc.tune(x, e, vr, orc.METRIC_AC, target=0.1, opts=o)
