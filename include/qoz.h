@@ -53,7 +53,12 @@ typedef enum {
   QOZ_EUNSUPPORTED = 6   /* valid request outside what this build handles */
 } qoz_status;
 
-typedef enum { QOZ_METRIC_MAXERR = 0, QOZ_METRIC_PSNR = 1, QOZ_METRIC_SSIM = 2 } qoz_metric;
+typedef enum {
+  QOZ_METRIC_MAXERR = 0,
+  QOZ_METRIC_PSNR = 1,
+  QOZ_METRIC_SSIM = 2,
+  QOZ_METRIC_AC = 3  /* lag-1 error autocorrelation (Eq. ac), lower is better; no target mode */
+} qoz_metric;
 
 typedef struct {
   int32_t ndims;         /* 2 or 3 */
@@ -261,6 +266,7 @@ typedef struct {
   double psnr;           /* Eq. psnr: 20 log10(vrange / sqrt(mse)); +inf if mse = 0 */
   double ssim;           /* Eq. ssim: mean over windows (NaN if not requested / none) */
   int64_t ssim_windows;
+  double ac;             /* Eq. ac at lag 1 of the errors b - a, flattened (row-major) order */
 } qoz_metrics;
 
 /* Quality metrics of Sec. 3 between the original d_a and the reconstruction
@@ -270,6 +276,16 @@ typedef struct {
 qoz_status qoz_compute_metrics(const float* d_a, const float* d_b, qoz_shape shape,
                                double vrange, int32_t ssim_win, int32_t ssim_step,
                                qoz_metrics* out, void* stream);
+
+/* Eq. (ac): autocorrelation at lag >= 1 of the errors e_i = d_b[i] - d_a[i]
+ * over n values in the given (flattened) order: the mean over the n - lag
+ * pairs of (e_i - mu)(e_{i+lag} - mu), divided by sigma^2, with mu and
+ * sigma^2 the population mean and variance of all n errors.  One pass of
+ * compensated binary32 sums per thread, double across threads and on the
+ * host.  *ac = 0 when n <= lag or the variance vanishes (below 1e-6 of the
+ * mean square).  Synchronises `stream`. */
+qoz_status qoz_error_autocorr(const float* d_a, const float* d_b, int64_t n, int64_t lag,
+                              double* ac, void* stream);
 
 /* ---------------------------------------------------------------- tuning */
 

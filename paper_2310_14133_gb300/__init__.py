@@ -7,6 +7,7 @@ library has not been built: there is no CPU fallback.
 """
 
 from ._binding import (  # noqa: F401
+    METRIC_AC,
     METRIC_MAXERR,
     METRIC_PSNR,
     METRIC_SSIM,
@@ -34,6 +35,7 @@ from ._binding import (  # noqa: F401
     compute_metrics,
     decompress,
     deserialize,
+    error_autocorr,
     features,
     lib,
     library_path,

@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = os.path.join(_HERE, "_build", "libqoz.so")
 
 MAX_LEVELS = 8
-METRIC_MAXERR, METRIC_PSNR, METRIC_SSIM = 0, 1, 2
+METRIC_MAXERR, METRIC_PSNR, METRIC_SSIM, METRIC_AC = 0, 1, 2, 3
 STATUS = {0: "QOZ_OK", 1: "QOZ_EINVAL", 2: "QOZ_ENOMEM", 3: "QOZ_ECUDA", 4: "QOZ_ECORRUPT",
           5: "QOZ_ETIMEOUT", 6: "QOZ_EUNSUPPORTED"}
 
@@ -108,7 +108,7 @@ def tune(x: torch.Tensor, rel_eb: float, metric: int = 0, target: float = float(
 
 class Metrics(C.Structure):
     _fields_ = [("max_abs_err", C.c_double), ("mse", C.c_double), ("psnr", C.c_double),
-                ("ssim", C.c_double), ("ssim_windows", C.c_int64)]
+                ("ssim", C.c_double), ("ssim_windows", C.c_int64), ("ac", C.c_double)]
 
 
 _lib = None
@@ -145,6 +145,7 @@ def lib():
             "qoz_blob_deserialize": (i32, [P, C.c_size_t, P, P]),
             "qoz_blob_free": (None, [P]),
             "qoz_compute_metrics": (i32, [P, P, Shape, f64, i32, i32, P, P]),
+            "qoz_error_autocorr": (i32, [P, P, i64, i64, P, P]),
             "qoz_profile_enable": (i32, [i32]),
             "qoz_profile_stages": (i32, [C.c_uint32]),
             "qoz_tune": (i32, [P, Shape, f64, i32, f64, P, P, P]),
@@ -360,6 +361,16 @@ def compute_metrics(a: torch.Tensor, b: torch.Tensor, vrange: float, ssim_win: i
     _check(lib().qoz_compute_metrics(_dev_ptr(a), _dev_ptr(b), _shape_of(a), float(vrange),
                                      int(ssim_win), int(ssim_step), C.byref(m), _stream(stream)))
     return m
+
+
+def error_autocorr(a: torch.Tensor, b: torch.Tensor, lag: int = 1, stream=None) -> float:
+    """Eq. (ac) of the errors b - a at the given lag, flattened order."""
+    if a.numel() != b.numel():
+        raise ValueError("size mismatch")
+    v = C.c_double()
+    _check(lib().qoz_error_autocorr(_dev_ptr(a), _dev_ptr(b), a.numel(), int(lag), C.byref(v),
+                                    _stream(stream)))
+    return v.value
 
 
 BATCH_AUTOTUNE = 1

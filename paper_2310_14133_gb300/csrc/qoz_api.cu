@@ -562,21 +562,24 @@ qoz_status qoz_compute_metrics(const float* d_a, const float* d_b, qoz_shape sha
   configure_pool_once();
   const int ne = err_metric_blocks();
   const int ns = ssim_win > 0 ? ssim_parts(r.n, r.ndims == 3, ssim_win, ssim_step) : 0;
+  const int na = ac_parts();
   void* scratch = nullptr;
-  cudaError_t e = dev_alloc(&scratch, sizeof(double) * (2 * ne + ns), s);
+  cudaError_t e = dev_alloc(&scratch, sizeof(double) * (2 * ne + ns + na), s);
   if (e != cudaSuccess) return fail(QOZ_ENOMEM, "metrics scratch: %s", cudaGetErrorString(e));
   double* psse = (double*)scratch;
   double* pmax = psse + ne;
   double* pss = pmax + ne;
+  double* pac = pss + ns;
   e = launch_check(launch_err_metrics(d_a, d_b, r.N, psse, pmax, ne, s));
+  if (e == cudaSuccess) e = launch_check(launch_autocorr(d_a, d_b, r.N, 1, pac, s));
   const double c1 = (0.01 * vrange) * (0.01 * vrange);
   const double c2 = (0.03 * vrange) * (0.03 * vrange);
   if (e == cudaSuccess && ssim_win > 0)
     e = launch_check(launch_ssim(d_a, d_b, r.n, r.ndims == 3, ssim_win, ssim_step, c1, c2, pss,
                                  s));
-  std::vector<double> h(2 * ne + ns, 0.0);
+  std::vector<double> h(2 * ne + ns + na, 0.0);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(h.data(), scratch, sizeof(double) * (2 * ne + ns),
+    e = cudaMemcpyAsync(h.data(), scratch, sizeof(double) * (2 * ne + ns + na),
                         cudaMemcpyDeviceToHost, s);
   dev_free(scratch, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -593,6 +596,7 @@ qoz_status qoz_compute_metrics(const float* d_a, const float* d_b, qoz_shape sha
   out->psnr = out->mse == 0.0 ? INFINITY : 20.0 * std::log10(vrange / std::sqrt(out->mse));
   out->ssim = NAN;
   out->ssim_windows = 0;
+  out->ac = autocorr_from_parts(h.data() + 2 * ne + ns, r.N, 1);
   if (ssim_win > 0) {
     auto cnt = [&](long long n) { return n >= ssim_win ? (n - ssim_win) / ssim_step + 1 : 0; };
     const long long nw = (r.ndims == 3 ? cnt(r.n[0]) : 1) * cnt(r.n[1]) * cnt(r.n[2]);
@@ -601,6 +605,27 @@ qoz_status qoz_compute_metrics(const float* d_a, const float* d_b, qoz_shape sha
     out->ssim_windows = nw;
     out->ssim = nw > 0 ? 1.0 - ss / (double)nw : NAN;  // parts hold sums of 1 - SSIM_w
   }
+  return QOZ_OK;
+}
+
+qoz_status qoz_error_autocorr(const float* d_a, const float* d_b, int64_t n, int64_t lag,
+                              double* ac, void* stream) {
+  if (!d_a || !d_b || !ac) return fail(QOZ_EINVAL, "NULL argument");
+  if (n < 0 || lag < 1) return fail(QOZ_EINVAL, "n >= 0 and lag >= 1 required");
+  cudaStream_t s = (cudaStream_t)stream;
+  configure_pool_once();
+  const int na = ac_parts();
+  void* scratch = nullptr;
+  cudaError_t e = dev_alloc(&scratch, sizeof(double) * na, s);
+  if (e != cudaSuccess) return fail(QOZ_ENOMEM, "autocorrelation scratch");
+  e = launch_check(launch_autocorr(d_a, d_b, n, lag, (double*)scratch, s));
+  std::vector<double> h(na, 0.0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h.data(), scratch, sizeof(double) * na, cudaMemcpyDeviceToHost, s);
+  dev_free(scratch, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "autocorrelation");
+  *ac = autocorr_from_parts(h.data(), n, lag);
   return QOZ_OK;
 }
 

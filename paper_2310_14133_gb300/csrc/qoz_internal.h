@@ -171,6 +171,12 @@ cudaError_t launch_ssim(const float* a, const float* b, const long long dims[3],
                         int win, int step, double c1, double c2, double* part_diss,
                         cudaStream_t s);
 int ssim_parts(const long long dims[3], bool is3d, int win, int step);
+// Eq. (ac) at lag k over the flattened arrays: ac_parts() doubles of per-CTA
+// sums, combined by autocorr_from_parts on the host.
+int ac_parts();
+cudaError_t launch_autocorr(const float* a, const float* b, long long n, long long k,
+                            double* part, cudaStream_t s);
+double autocorr_from_parts(const double* h, long long n, long long k);
 
 // Entropy stage (qoz_entropy.cu): canonical Huffman coding of the codes.
 constexpr int kEntropyChunk = 4096;  // symbols per independently coded chunk

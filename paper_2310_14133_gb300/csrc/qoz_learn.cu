@@ -744,10 +744,10 @@ qoz_status qoz_tune_learned(const float* d_field, qoz_shape shape, double rel_eb
                             qoz_metric metric, double target, const qoz_tune_opts* opts,
                             const qoz_model* model, void* stream, qoz_tune_report* out) {
   if (!model || !out) return fail(QOZ_EINVAL, "NULL argument");
-  if (metric < QOZ_METRIC_MAXERR || metric > QOZ_METRIC_SSIM)
+  if (metric < QOZ_METRIC_MAXERR || metric > QOZ_METRIC_AC)
     return fail(QOZ_EINVAL, "unknown metric %d", metric);
   const bool target_mode = !std::isnan(target);
-  if (target_mode && metric == QOZ_METRIC_MAXERR)
+  if (target_mode && (metric == QOZ_METRIC_MAXERR || metric == QOZ_METRIC_AC))
     return fail(QOZ_EINVAL, "a target needs the PSNR or SSIM metric");
   cudaStream_t s = (cudaStream_t)stream;
   configure_pool_once();

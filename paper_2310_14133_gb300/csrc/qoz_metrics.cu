@@ -118,6 +118,40 @@ __global__ void __launch_bounds__(kErrThreads) err_kernel(const float* __restric
   }
 }
 
+// ---------------------------------------------------------------- Eq. (ac)
+// Lag-k autocorrelation of the errors e_i = b_i - a_i over the flattened
+// arrays: one pass accumulating sum e, sum e^2, sum e_i e_{i+k} over the
+// n - k pairs and the sums of the pairs' first and second members, each in
+// compensated binary32 per thread and double across threads; the host forms
+// the mean, the variance and the lag covariance from them.
+constexpr int kAcParts = 5;
+
+__global__ void __launch_bounds__(kErrThreads) ac_kernel(const float* __restrict__ a,
+                                                         const float* __restrict__ b,
+                                                         long long n, long long k,
+                                                         double* part) {
+  __shared__ double sh[32];
+  Kahan s1, s2, sk, head, tail;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nthr = (long long)gridDim.x * blockDim.x;
+  for (long long i = tid; i < n; i += nthr) {
+    const float e = __fsub_rn(__ldcs(b + i), __ldcs(a + i));
+    s1.add(e);
+    s2.add(__fmul_rn(e, e));
+    if (i + k < n) {
+      const float f = __fsub_rn(b[i + k], a[i + k]);
+      sk.add(__fmul_rn(e, f));
+      head.add(e);
+    }
+    if (i >= k) tail.add(e);
+  }
+  Kahan* acc[kAcParts] = {&s1, &s2, &sk, &head, &tail};
+  for (int j = 0; j < kAcParts; ++j) {
+    const double v = block_sum((double)acc[j]->s - (double)acc[j]->c, sh);
+    if (threadIdx.x == 0) part[(size_t)j * gridDim.x + blockIdx.x] = v;
+  }
+}
+
 // ---------------------------------------------------------------- SSIM, tiled
 constexpr int kTileThreads = 256;
 constexpr int kWX = 32;   // windows per CTA along x
@@ -368,6 +402,32 @@ cudaError_t launch_err_metrics(const float* a, const float* b, long long n, doub
                                double* part_max, int nparts, cudaStream_t s) {
   err_kernel<<<nparts, kErrThreads, 0, s>>>(a, b, n, part_sse, part_max); note_launch(1);
   return cudaGetLastError();
+}
+
+int ac_parts() { return kAcParts * kErrBlocks; }
+
+cudaError_t launch_autocorr(const float* a, const float* b, long long n, long long k,
+                            double* part, cudaStream_t s) {
+  ac_kernel<<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, k, part);
+  note_launch(1);
+  return cudaGetLastError();
+}
+
+// Eq. (ac) from the per-CTA sums (host, double): mu = S1 / n,
+// sigma^2 = S2 / n - mu^2, covariance = (Sk - mu (head + tail)) / P + mu^2
+// over the P = n - k pairs.  A variance below 1e-6 of the mean square (all
+// errors equal up to rounding) gives 0, as an exact zero variance does.
+double autocorr_from_parts(const double* h, long long n, long long k) {
+  double v[kAcParts] = {0, 0, 0, 0, 0};
+  for (int j = 0; j < kAcParts; ++j)
+    for (int i = 0; i < kErrBlocks; ++i) v[j] += h[(size_t)j * kErrBlocks + i];
+  const long long P = n - k;
+  if (n <= 0 || P <= 0) return 0.0;
+  const double mu = v[0] / (double)n, ms = v[1] / (double)n;
+  const double var = ms - mu * mu;
+  if (!(var > 1e-6 * ms)) return 0.0;
+  const double cov = (v[2] - mu * (v[3] + v[4])) / (double)P + mu * mu;
+  return cov / var;
 }
 
 cudaError_t launch_ssim(const float* a, const float* b, const long long dims[3], bool is3d,

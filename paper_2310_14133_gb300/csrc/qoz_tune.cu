@@ -35,7 +35,10 @@ constexpr int kTrialThreads = 512;
 constexpr int kTrialThreadsCoarse = 128;
 constexpr int kTHistLo = kRadius - 2048;
 constexpr int kTHistWin = 4096;
-constexpr int kOutStride = 8;  // per (candidate, block): l1, l1_cnt, unpred, sse, maxerr, ssim_sum, ssim_n, pad
+// per (candidate, block): l1, l1_cnt, unpred, sse, maxerr, ssim_sum, ssim_n,
+// copy-timeout flag, then the lag-1 error sums of Eq. (ac) in block order
+// (sum e, sum e^2, sum e_i e_{i+1}) and the block's first and last error
+constexpr int kOutStride = 16;
 
 struct TrialCand {
   unsigned char interp[kMaxLevels];
@@ -58,6 +61,7 @@ struct TrialArgs {
   int metrics;             // accumulate sse / max error / SSIM after the last level
   int ssim_win, ssim_step, is3d;
   double c1, c2;           // SSIM constants (used when bt is null)
+  int ac;                  // accumulate the lag-1 error sums of Eq. (ac) after the last level
   const BoundTable* bt;    // value range on the device: SSIM constants from its range
   int use_tma;             // full-resolution block by one bulk tensor copy (tensor map given)
   int pitch;               // row pitch of the block in shared memory (values)
@@ -120,6 +124,9 @@ constexpr unsigned kTrialWaitPolls = 1u << 24;
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 1 : 4)
     trial_kernel(const TrialArgs a, const __grid_constant__ CUtensorMap tmap) {
+  // the coarse variant runs only levels above the finest (no histogram, no
+  // metrics): that code is compiled out of it
+  constexpr bool kFull = THREADS >= kTrialThreads;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar;
   const int f = 1 << (a.stop_level - 1);
@@ -129,7 +136,7 @@ __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 1 : 4)
   unsigned char* base = smem + ((128u - (smem_u32(smem) & 127u)) & 127u);
   unsigned* SH = reinterpret_cast<unsigned*>(
       base + (((size_t)sizeof(float) * m0 * m1 * P + 15) & ~size_t(15)));
-  __shared__ float redf[THREADS / 32][5];     // l1 (s, c), sse (s, c), max error
+  __shared__ float redf[THREADS / 32][11];    // l1, sse, ac sums (s, c each), max error
   __shared__ unsigned redu[THREADS / 32][2];  // l1 count, unpredictable count
   __shared__ double redd[THREADS / 32][2];    // SSIM sum, window count
 
@@ -188,7 +195,7 @@ __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 1 : 4)
   float mx = 0.0f;
   int l1n = 0, unp = 0;
   const int st1 = P, st0 = m1 * P;
-  if (a.metrics) {
+  if (kFull && a.metrics) {
     // the block's anchors (never targets) reconstruct exactly: they add to
     // the squared and maximum error only through non-finite values
     const int as = 1 << (a.Ls - a.stop_level + 1);
@@ -265,13 +272,13 @@ __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 1 : 4)
             rec = xv;
             ++unp;
           }
-          if (a.metrics) {  // every non-anchor point is a target once
+          if (kFull && a.metrics) {  // every non-anchor point is a target once
             const float d = __fsub_rn(xv, rec);
             sse.add(__fmul_rn(d, d));
             const float ad = fabsf(d);
             if (ad != ad || ad > mx) mx = ad;
           }
-          if (a.hist) {
+          if (kFull && a.hist) {
             // lanes with equal codes add once (smooth data puts most of a
             // warp's codes in one or two bins)
             const unsigned peers = __match_any_sync(__activemask(), (unsigned)code);
@@ -291,7 +298,7 @@ __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 1 : 4)
   }
 
   double ss = 0.0, sn = 0.0;
-  if (a.metrics) {  // stop_level == 1: S is the whole block
+  if (kFull && a.metrics) {  // stop_level == 1: S is the whole block
     const int n1 = a.bd[1], n2 = a.bd[2];
     if (a.ssim_win > 0) {
       double c1 = a.c1, c2 = a.c2;
@@ -352,7 +359,37 @@ __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 1 : 4)
       }
     }
   }
-  if (a.hist) {
+  // Eq. (ac) sums over the block in its row-major order (stop_level == 1:
+  // S holds the whole reconstruction): e = reconstruction - original
+  KSum as1, as2, ask;
+  if (kFull && a.ac && a.metrics) {
+    const int n0 = a.bd[0], n1 = a.bd[1], n2 = a.bd[2];
+    const int nbp = n0 * n1 * n2;
+    double* o = a.out + ((size_t)cand * a.nblocks + blk) * kOutStride;
+    auto err_at = [&](int z, int y, int x) {
+      return __fsub_rn(S[(z * n1 + y) * P + x], xb[z * a.st0 + y * a.st1 + x]);
+    };
+    for (int i = threadIdx.x; i < nbp; i += THREADS) {
+      const int x = i % n2, r = i / n2, y = r % n1, z = r / n1;
+      const float e = err_at(z, y, x);
+      as1.add(e);
+      as2.add(__fmul_rn(e, e));
+      if (i + 1 < nbp) {
+        int x2 = x + 1, y2 = y, z2 = z;
+        if (x2 == n2) {
+          x2 = 0;
+          if (++y2 == n1) {
+            y2 = 0;
+            ++z2;
+          }
+        }
+        ask.add(__fmul_rn(e, err_at(z2, y2, x2)));
+      }
+      if (i == 0) o[11] = (double)e;
+      if (i == nbp - 1) o[12] = (double)e;
+    }
+  }
+  if (kFull && a.hist) {
     __syncthreads();
     for (int i = threadIdx.x; i < kTHistWin; i += blockDim.x)
       if (SH[i]) atomicAdd(&a.hist[(size_t)cand * 65536 + kTHistLo + i], SH[i]);
@@ -360,10 +397,15 @@ __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 1 : 4)
   // fixed-order block reduction: warps, then warp 0 over the warps' partials
   warp_ksum(l1);
   warp_ksum(sse);
+  if (kFull && a.ac) {
+    warp_ksum(as1);
+    warp_ksum(as2);
+    warp_ksum(ask);
+  }
   mx = warp_nan_max(mx);
   const unsigned l1c = __reduce_add_sync(0xffffffffu, (unsigned)l1n);
   const unsigned unc = __reduce_add_sync(0xffffffffu, (unsigned)unp);
-  if (a.ssim_win > 0) {
+  if (kFull && a.ssim_win > 0) {
     ss = warp_sum(ss);
     sn = warp_sum(sn);
   }
@@ -373,6 +415,12 @@ __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 1 : 4)
     redf[warp][2] = sse.s;
     redf[warp][3] = sse.c;
     redf[warp][4] = mx;
+    redf[warp][5] = as1.s;
+    redf[warp][6] = as1.c;
+    redf[warp][7] = as2.s;
+    redf[warp][8] = as2.c;
+    redf[warp][9] = ask.s;
+    redf[warp][10] = ask.c;
     redu[warp][0] = l1c;
     redu[warp][1] = unc;
     redd[warp][0] = ss;
@@ -391,8 +439,20 @@ __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 1 : 4)
     const float m = warp_nan_max(on ? redf[lane][4] : 0.0f);
     const unsigned c1 = __reduce_add_sync(0xffffffffu, on ? redu[lane][0] : 0u);
     const unsigned c2 = __reduce_add_sync(0xffffffffu, on ? redu[lane][1] : 0u);
+    KSum t8, t9, t10;
+    if (kFull && a.ac) {
+      t8.s = on ? redf[lane][5] : 0.0f;
+      t8.c = on ? redf[lane][6] : 0.0f;
+      t9.s = on ? redf[lane][7] : 0.0f;
+      t9.c = on ? redf[lane][8] : 0.0f;
+      t10.s = on ? redf[lane][9] : 0.0f;
+      t10.c = on ? redf[lane][10] : 0.0f;
+      warp_ksum(t8);
+      warp_ksum(t9);
+      warp_ksum(t10);
+    }
     double s5 = 0.0, s6 = 0.0;
-    if (a.ssim_win > 0) {
+    if (kFull && a.ssim_win > 0) {
       s5 = warp_sum(on ? redd[lane][0] : 0.0);
       s6 = warp_sum(on ? redd[lane][1] : 0.0);
     }
@@ -406,6 +466,11 @@ __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 1 : 4)
       o[5] = s5;
       o[6] = s6;
       o[7] = 0.0;
+      if (kFull && a.ac) {
+        o[8] = t8.value();
+        o[9] = t9.value();
+        o[10] = t10.value();
+      }
     }
   }
 }
@@ -917,6 +982,7 @@ class Tuner {
     a.metrics = full ? 1 : 0;
     a.ssim_win = (full && metric_ == QOZ_METRIC_SSIM) ? win_ : 0;
     a.ssim_step = step_;
+    a.ac = (full && metric_ == QOZ_METRIC_AC) ? 1 : 0;
     a.is3d = r_.ndims == 3;
     a.c1 = (0.01 * vr_) * (0.01 * vr_);
     a.c2 = (0.03 * vr_) * (0.03 * vr_);
@@ -1051,12 +1117,34 @@ class Tuner {
           t.M = mse == 0.0 ? INFINITY : 20.0 * std::log10(vr_ / std::sqrt(mse));
         } else if (metric_ == QOZ_METRIC_SSIM) {
           t.M = sn > 0 ? ss / sn : NAN;
+        } else if (metric_ == QOZ_METRIC_AC) {
+          t.M = -pooled_ac(&out[(size_t)c * sm_.nb * kOutStride]);
         } else {
           t.M = -mx;
         }
       }
     }
     return QOZ_OK;
+  }
+
+  // Eq. (ac) at lag 1 pooled over the blocks of one candidate: pairs inside
+  // each block (in its row-major order), mean and variance over all sampled
+  // points; 0 when the variance vanishes (below 1e-6 of the mean square).
+  double pooled_ac(const double* o) const {
+    double s1 = 0.0, s2 = 0.0, sk = 0.0, hd = 0.0, tl = 0.0;
+    for (int b = 0; b < sm_.nb; ++b) {
+      const double* q = o + (size_t)b * kOutStride;
+      s1 += q[8];
+      s2 += q[9];
+      sk += q[10];
+      hd += q[8] - q[12];
+      tl += q[8] - q[11];
+    }
+    const double n = (double)sm_.npts, P = (double)(sm_.npts - sm_.nb);
+    if (!(n > 0.0) || !(P > 0.0)) return 0.0;
+    const double mu = s1 / n, ms = s2 / n, var = ms - mu * mu;
+    if (!(var > 1e-6 * ms)) return 0.0;
+    return ((sk - mu * (hd + tl)) / P + mu * mu) / var;
   }
 
   int trials() const { return trials_; }
@@ -1200,10 +1288,10 @@ qoz_status tune_impl(const float* d_field, const qoz_shape& shape, double rel_eb
                      qoz_tune_report* out) {
   if (!d_field || !out) return fail(QOZ_EINVAL, "NULL argument");
   if (!(rel_eb > 0.0 && std::isfinite(rel_eb))) return fail(QOZ_EINVAL, "rel_eb must be > 0");
-  if (metric < QOZ_METRIC_MAXERR || metric > QOZ_METRIC_SSIM)
+  if (metric < QOZ_METRIC_MAXERR || metric > QOZ_METRIC_AC)
     return fail(QOZ_EINVAL, "unknown metric %d", metric);
   const bool target_mode = !std::isnan(target);
-  if (target_mode && metric == QOZ_METRIC_MAXERR)
+  if (target_mode && (metric == QOZ_METRIC_MAXERR || metric == QOZ_METRIC_AC))
     return fail(QOZ_EINVAL, "a target needs the PSNR or SSIM metric");
   Resolved r;
   qoz_status st = resolve(shape, nullptr, &r);
@@ -1375,10 +1463,10 @@ qoz_status verify_impl(const float* d_field, const qoz_shape& shape, double rel_
                        cudaStream_t s, qoz_tune_report* out) {
   if (!d_field || !out || !p_in) return fail(QOZ_EINVAL, "NULL argument");
   if (!(rel_eb > 0.0 && std::isfinite(rel_eb))) return fail(QOZ_EINVAL, "rel_eb must be > 0");
-  if (metric < QOZ_METRIC_MAXERR || metric > QOZ_METRIC_SSIM)
+  if (metric < QOZ_METRIC_MAXERR || metric > QOZ_METRIC_AC)
     return fail(QOZ_EINVAL, "unknown metric %d", metric);
   const bool target_mode = !std::isnan(target);
-  if (target_mode && metric == QOZ_METRIC_MAXERR)
+  if (target_mode && (metric == QOZ_METRIC_MAXERR || metric == QOZ_METRIC_AC))
     return fail(QOZ_EINVAL, "a target needs the PSNR or SSIM metric");
   Resolved r;
   qoz_status st = resolve(shape, p_in, &r);

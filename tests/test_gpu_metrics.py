@@ -146,3 +146,39 @@ def test_ssim_256_field_vs_oracle(q, orc):
     q.decompress(blob, y)
     blob.free()
     _check(q, orc, x, y.cpu().numpy(), 7, 2, vr=vr)
+
+
+# ---- Eq. (ac): autocorrelation of the compression errors
+
+@pytest.mark.parametrize("lag", [1, 2, 7, 64])
+def test_autocorr_matches_oracle(q, orc, lag):
+    import synth
+    a = synth.grf((40, 64, 96), 5.0 / 3.0, seed=31, n_modes=48).numpy()
+    rng = np.random.default_rng(lag)
+    # correlated errors of about 1e-3 (a short moving average), mean near zero
+    e = np.convolve(1e-3 * rng.standard_normal(a.size), [0.6, 0.3, 0.1], mode="same")
+    b = (a.ravel() + e).astype(np.float32).reshape(a.shape)
+    da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    ref = orc.autocorr(a, b, lag)
+    got = q.error_autocorr(da, db, lag)
+    assert got == pytest.approx(ref, abs=2e-6)
+    if lag == 1:
+        m = q.compute_metrics(da, db, 1.0)
+        assert m.ac == pytest.approx(ref, abs=2e-6)
+
+
+def test_autocorr_closed_forms(q, orc):
+    n = 1 << 20
+    a = torch.zeros(n, dtype=torch.float32, device="cuda")
+    alt = torch.tensor([1.0, -1.0], device="cuda").repeat(n // 2)
+    assert q.error_autocorr(a, alt, 1) == pytest.approx(-1.0, abs=1e-12)
+    assert q.error_autocorr(a, alt, 2) == pytest.approx(1.0, abs=1e-12)
+    # constant error: no variance, AC 0 (as the oracle's exact zero)
+    assert q.error_autocorr(a, torch.full_like(a, 0.25), 1) == 0.0
+    # lag at or past the end
+    assert q.error_autocorr(a[:5], alt[:5], 5) == 0.0
+    # ragged length, unaligned start
+    x = torch.randn(100003, device="cuda")
+    y = x + 1e-3 * torch.randn(100003, device="cuda")
+    ref = orc.autocorr(x[1:].cpu().numpy(), y[1:].cpu().numpy(), 3)
+    assert q.error_autocorr(x[1:], y[1:], 3) == pytest.approx(ref, abs=2e-6)

@@ -137,3 +137,18 @@ def test_verify_fixed_bound_matches_oracle_trial(q, orc):
     assert ver.abs_eb == 1e-3 * vr and ver.n_trials == 1
     assert ver.B == pytest.approx(t.B, rel=1e-12)
     assert ver.M == pytest.approx(orc.trial_metric(t, 1, vr), rel=1e-6)
+
+
+def test_ac_table1_mode(q, orc):
+    # AC-preferred mode: M = -AC (lag 1, pooled over the blocks), Table I with
+    # the 0.8 e / 1.2 e trials
+    x = _field(64, 24)
+    rep, ref = _compare(q, orc, x, 1e-3, 3, float("nan"), 16, 0.05, 2,
+                        [1.0, 1.25, 1.5, 1.75, 2.0], [2.0, 3.0, 4.0], m_rel=1e-5)
+    assert -1.0 <= rep.M <= 1.0
+
+
+def test_ac_target_is_rejected(q):
+    x = torch.from_numpy(_field(32, 25)).cuda()
+    with pytest.raises(q.QozError):
+        q.tune(x, 1e-3, q.METRIC_AC, 0.1, q.make_tune_opts())
