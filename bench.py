@@ -56,11 +56,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="compress",
-                    choices=["compress", "batch", "learned", "ssim"],
+                    choices=["compress", "batch", "learned", "ssim", "ac"],
                     help="compress: the single-field step (default); batch: 48 2-D + 48 "
                          "uneven 3-D fields through one batched plan; learned: train the "
                          "tuner network, then learned vs sampled tuning; ssim: SSIM targets "
-                         "0.99 / 0.999, network proposes, sampled trials verify")
+                         "0.99 / 0.999, network proposes, sampled trials verify; ac: the "
+                         "error-autocorrelation reduction and the AC-preferred tuning mode")
     ap.add_argument("--train", type=int, default=2000, help="learned: training fields")
     return ap.parse_args()
 
@@ -473,6 +474,64 @@ def run_ssim(args):
     print(json.dumps(line), flush=True)
     model.free()
 
+def run_ac(args):
+    """Eq. (ac) on the 512^3 step's field (--n to change the edge): the field
+    is tuned in the max-CR, PSNR-preferred and AC-preferred modes at the same
+    relative bound 1e-3, compressed, decompressed and scored (lag-1 AC of the
+    errors, PSNR, the serialized ratio).  value = GB/s of the lag-1 error
+    autocorrelation reduction (both arrays read once: 8 B per point) on the
+    AC mode's reconstruction, with its HBM roofline."""
+    import torch
+    import paper_2310_14133_gb300 as q
+    import synth
+    topts = q.make_tune_opts(**TUNE)
+    n = args.n
+    N = n ** 3
+    x = synth.config2_field(n, device="cuda")
+    rows = []
+    y = torch.empty_like(x)
+    for name, metric in (("max_cr", q.METRIC_MAXERR), ("psnr", q.METRIC_PSNR),
+                         ("ac", q.METRIC_AC)):
+        ms_tune, _ = _events_ms(lambda: q.tune(x, REL_EB, metric, float("nan"), topts), 3, 1)
+        rep = q.tune(x, REL_EB, metric, float("nan"), topts)
+        blob = q.compress_abs(x, rep.abs_eb, rep.params)
+        q.decompress(blob, y)
+        m = q.compute_metrics(x, y, rep.vmax - rep.vmin)
+        rows.append({"mode": name, "ms_tune": ms_tune, "n_trials": rep.n_trials,
+                     "sampled_M": rep.M, "ac_lag1": m.ac, "psnr": m.psnr,
+                     "ratio": 4.0 * N / blob.serialize().numel(),
+                     "theta": [rep.params.interp[0], rep.params.order[0], rep.params.alpha,
+                               rep.params.beta]})
+        blob.free()
+    steps = max(1, args.steps)
+    ms_call, _ = _events_ms(lambda: q.error_autocorr(x, y, 1), steps, max(3, args.warmup))
+    # the kernel alone, from the library's event timers around its launch
+    q.profile_read(reset=True)
+    q.profile_enable(True, stages=[q.STAGE_METRICS])
+    for _ in range(steps):
+        q.error_autocorr(x, y, 1)
+    q.profile_enable(False)
+    prof = q.profile_read(reset=True)
+    ms = prof.ms[q.STAGE_METRICS] / max(1, prof.calls[q.STAGE_METRICS])
+    peak, peak_kind = _peak_hbm()
+    gbs = 8.0 * N / (ms * 1e-3) / 1e9
+    line = {
+        "metric": "error autocorrelation GB/s (two FP32 arrays in), lag 1", "value": gbs,
+        "unit": "GB/s", "n_gpus": 1, "steps": steps, "warmup": max(3, args.warmup),
+        "ms_per_step": ms, "ms_per_call": ms_call, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{n}^3 FP32 k^-5/3 GRF + 8 tanh fronts (NYX-sized), rel bound "
+                               "1e-3; max-CR / PSNR / AC modes",
+                   "tuner_opts": TUNE, "parallelism": "single GPU",
+                   "l2": "two 512 MiB inputs > 126 MB L2; no flush needed"},
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                     "frac": gbs / peak, "traffic": None, "kernel": "ac_kernel",
+                     "algorithmic_bytes_per_launch": 8.0 * N, "peak_kind": peak_kind},
+        "rows": rows,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank = _env_int("RANK", 0)
@@ -489,6 +548,9 @@ def main():
         return
     if args.workload == "ssim":
         run_ssim(args)
+        return
+    if args.workload == "ac":
+        run_ac(args)
         return
 
     import torch

@@ -618,7 +618,10 @@ qoz_status qoz_error_autocorr(const float* d_a, const float* d_b, int64_t n, int
   void* scratch = nullptr;
   cudaError_t e = dev_alloc(&scratch, sizeof(double) * na, s);
   if (e != cudaSuccess) return fail(QOZ_ENOMEM, "autocorrelation scratch");
-  e = launch_check(launch_autocorr(d_a, d_b, n, lag, (double*)scratch, s));
+  {
+    ProfScope ps(QOZ_STAGE_METRICS, s);
+    e = launch_check(launch_autocorr(d_a, d_b, n, lag, (double*)scratch, s));
+  }
   std::vector<double> h(na, 0.0);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h.data(), scratch, sizeof(double) * na, cudaMemcpyDeviceToHost, s);
