@@ -131,7 +131,7 @@ def test_degenerate_shapes(q, orc, shape):
         run_parity(q, orc, x, 1e-2, interp=1, order=order, alpha=1.5, beta=2.0)
 
 
-@pytest.mark.parametrize("stride", [2, 4, 8, 16, 64, 128])
+@pytest.mark.parametrize("stride", [2, 4, 8, 16, 64, 128, 256])
 def test_anchor_strides(q, orc, stride):
     import synth
     x = synth.grf((40, 41, 90), 5.0 / 3.0, seed=5, n_modes=64).numpy()
