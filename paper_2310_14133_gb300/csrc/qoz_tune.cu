@@ -476,25 +476,46 @@ __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 1 : 4)
 }
 
 // Optimal prefix-code cost of one candidate's pooled histogram (the rate
-// estimate of Sec. 6.1): one CTA compacts the non-zero counts, sorts them
-// and runs the two-queue merge (leaves and merged nodes both come out in
-// non-decreasing order; every merge adds its weight).  Integer arithmetic:
-// the same total as the host computation.  More than kHuffMax distinct codes
-// are left to the host (flag 1).
+// estimate of Sec. 6.1): one CTA per candidate.  The cost is the sum of the
+// weights of the merged nodes of Huffman's construction, run here as the
+// two-queue merge (leaves and merged nodes both come out in non-decreasing
+// order) over runs of equal weight: while the smallest item's run holds two
+// or more items, pairing them is what the merge would do step by step, so
+// all pairs of the run are merged at once into one run of nodes.  Leaves
+// come sorted without a sort: counts up to kHuffSmall are bucketed by value
+// (multiplicities in shared memory), the few larger counts are sorted.
+// Integer arithmetic: the same total as the host computation.  More than
+// kHuffBig large counts or kHuffNodes live node runs are left to the host
+// (flag 1).
 constexpr int kHuffThreads = 1024;
-constexpr int kHuffMax = 4096;
+constexpr int kHuffSmall = 4096;
+constexpr int kHuffBig = 2048;
+constexpr int kHuffNodes = 4096;  // node runs alive at once (a ring)
+
+struct HuffCostSmem {
+  unsigned small[kHuffSmall + 1];        // multiplicity of each count 1..kHuffSmall
+  unsigned rc[kHuffSmall], rm[kHuffSmall];  // the non-empty buckets in count order
+  unsigned big[kHuffBig];                // counts above kHuffSmall (sorted in place)
+  unsigned long long nw[kHuffNodes];     // node runs: weight
+  unsigned nm[kHuffNodes];               // node runs: multiplicity
+};
 
 __global__ void __launch_bounds__(kHuffThreads)
     huffman_cost_kernel(const unsigned* __restrict__ hist, unsigned long long* bits, int* flag) {
-  __shared__ unsigned cnt[kHuffMax];
-  __shared__ unsigned node[kHuffMax];  // merged weights: at most the sampled points (< 2^32)
-  __shared__ int nsh;
+  extern __shared__ __align__(16) unsigned char hsm[];
+  HuffCostSmem& S = *reinterpret_cast<HuffCostSmem*>(hsm);
+  __shared__ int nbig, nruns;
+  __shared__ unsigned long long nsym;
+  __shared__ int wsum[32];
   const uint4* h4 = reinterpret_cast<const uint4*>(hist + (size_t)blockIdx.x * 65536);
-  const int t = threadIdx.x, lane = t & 31;
-  if (t == 0) nsh = 0;
+  const int t = threadIdx.x;
+  for (int i = t; i <= kHuffSmall; i += kHuffThreads) S.small[i] = 0u;
+  if (t == 0) {
+    nbig = 0;
+    nsym = 0ull;
+  }
   __syncthreads();
-  // coalesced 16-byte scan, kBatch loads in flight per thread; each warp
-  // appends its non-zero counts (any order: they are sorted next)
+  // coalesced 16-byte scan, kBatch loads in flight per thread
   constexpr int kVec = 65536 / 4 / kHuffThreads, kBatch = 4;
   for (int j0 = 0; j0 < kVec; j0 += kBatch) {
     uint4 v[kBatch];
@@ -503,36 +524,70 @@ __global__ void __launch_bounds__(kHuffThreads)
 #pragma unroll
     for (int j = 0; j < kBatch; ++j) {
       const unsigned q[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
-      const int nz = (q[0] != 0u) + (q[1] != 0u) + (q[2] != 0u) + (q[3] != 0u);
-      if (__ballot_sync(0xffffffffu, nz != 0) == 0u) continue;
-      int inc = nz;  // inclusive prefix over the warp
-      for (int off = 1; off < 32; off <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, inc, off);
-        if (lane >= off) inc += y;
-      }
-      int base = 0;
-      if (lane == 31) base = atomicAdd(&nsh, inc);
-      int k = __shfl_sync(0xffffffffu, base, 31) + inc - nz;
 #pragma unroll
-      for (int e = 0; e < 4; ++e)
-        if (q[e] != 0u) {
-          if (k < kHuffMax) cnt[k] = q[e];
-          ++k;
+      for (int e = 0; e < 4; ++e) {
+        const unsigned c = q[e];
+        if (c == 0u) continue;
+        atomicAdd(&nsym, 1ull);
+        if (c <= (unsigned)kHuffSmall) {
+          atomicAdd(&S.small[c], 1u);
+        } else {
+          const int k = atomicAdd(&nbig, 1);
+          if (k < kHuffBig) S.big[k] = c;
         }
+      }
     }
   }
   __syncthreads();
-  const int n = nsh;
-  if (n > kHuffMax) {
+  const int nb = nbig;
+  if (nb > kHuffBig) {
     if (t == 0) {
       flag[blockIdx.x] = 1;
       bits[blockIdx.x] = 0ull;
     }
     return;
   }
+  // the non-empty buckets, compacted in count order (a block-wide scan over
+  // four consecutive buckets per thread)
+  {
+    static_assert(kHuffSmall == 4 * kHuffThreads, "four buckets per thread");
+    const int c0 = 4 * t + 1;
+    int cnt = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) cnt += S.small[c0 + k] != 0u ? 1 : 0;
+    const int lane = t & 31, w = t >> 5;
+    int inc = cnt;
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, inc, off);
+      if (lane >= off) inc += y;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+      const int x = wsum[lane];
+      int wi = x;
+      for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, wi, off);
+        if (lane >= off) wi += y;
+      }
+      wsum[lane] = wi - x;
+      if (lane == 31) nruns = wi;
+    }
+    __syncthreads();
+    int pos = wsum[w] + inc - cnt;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const unsigned m = S.small[c0 + k];
+      if (m != 0u) {
+        S.rc[pos] = (unsigned)(c0 + k);
+        S.rm[pos] = m;
+        ++pos;
+      }
+    }
+  }
   int P = 1;
-  while (P < n) P <<= 1;
-  for (int i = n + t; i < P; i += kHuffThreads) cnt[i] = 0xffffffffu;
+  while (P < nb) P <<= 1;
+  for (int i = nb + t; i < P; i += kHuffThreads) S.big[i] = 0xffffffffu;
   __syncthreads();
   for (int size = 2; size <= P; size <<= 1)
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
@@ -540,49 +595,100 @@ __global__ void __launch_bounds__(kHuffThreads)
         const int j = i ^ stride;
         if (j > i) {
           const bool up = (i & size) == 0;
-          const unsigned a = cnt[i], b = cnt[j];
+          const unsigned a = S.big[i], b = S.big[j];
           if ((a > b) == up) {
-            cnt[i] = b;
-            cnt[j] = a;
+            S.big[i] = b;
+            S.big[j] = a;
           }
         }
       }
       __syncthreads();
     }
-  if (t == 0) {
-    unsigned long long total = 0ull;
-    if (n == 1) {
-      total = cnt[0];
-    } else if (n > 1) {
-      // queue heads in registers, the next leaf prefetched: each pick is a
-      // compare on registers (the sorted leaves are padded with 0xffffffff)
-      int li = 0, ni = 0, nn = 0;
-      unsigned hl = cnt[0], hl2 = cnt[1], hn = 0u;
-      for (int m = 1; m < n; ++m) {
-        unsigned ab[2];
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          if (ni < nn && (li >= n || hn < hl)) {
-            ab[k] = hn;
-            ++ni;
-            hn = ni < nn ? node[ni] : 0u;
-          } else {
-            ab[k] = hl;
-            ++li;
-            hl = hl2;
-            hl2 = li + 1 < P ? cnt[li + 1] : 0xffffffffu;
-          }
-        }
-        const unsigned sum = ab[0] + ab[1];
-        total += sum;
-        node[nn] = sum;
-        if (ni == nn) hn = sum;
-        ++nn;
+  if (t != 0) return;
+  // leaf runs in order: the bucketed counts, then the sorted large ones
+  const int nr = nruns;
+  int ri = 0, bi = 0;                    // next bucket run / big index
+  unsigned long long lw = 0ull;          // current leaf run (weight, items left)
+  unsigned long long lm = 0ull;
+  auto next_leaf_run = [&]() {
+    lm = 0ull;
+    if (ri < nr) {
+      lw = (unsigned long long)S.rc[ri];
+      lm = S.rm[ri];
+      ++ri;
+      return;
+    }
+    if (bi < nb) {
+      lw = S.big[bi];
+      lm = 0ull;
+      while (bi < nb && S.big[bi] == lw) {
+        ++lm;
+        ++bi;
       }
     }
-    bits[blockIdx.x] = total;
-    flag[blockIdx.x] = 0;
+  };
+  next_leaf_run();
+  unsigned long long items = nsym;
+  unsigned long long total = 0ull;
+  int bad = 0;
+  if (items == 1ull) {
+    total = lw;  // a lone symbol: one bit per occurrence
+  } else {
+    unsigned nh = 0u, nt = 0u;  // node-run ring [nh, nt), indices taken mod kHuffNodes
+    constexpr unsigned kMask = kHuffNodes - 1;
+    static_assert((kHuffNodes & (kHuffNodes - 1)) == 0, "ring size is a power of two");
+    auto push_node = [&](unsigned long long w, unsigned long long m) {
+      if (nt > nh && S.nw[(nt - 1u) & kMask] == w) {
+        S.nm[(nt - 1u) & kMask] += (unsigned)m;
+      } else if (nt - nh < (unsigned)kHuffNodes) {
+        S.nw[nt & kMask] = w;
+        S.nm[nt & kMask] = (unsigned)m;
+        ++nt;
+      } else {
+        bad = 1;
+      }
+    };
+    // takes one item of the smallest front; returns its weight
+    auto take_one = [&]() -> unsigned long long {
+      const bool node = nt > nh && (lm == 0ull || S.nw[nh & kMask] < lw);
+      unsigned long long w;
+      if (node) {
+        w = S.nw[nh & kMask];
+        if (--S.nm[nh & kMask] == 0u) ++nh;
+      } else {
+        w = lw;
+        if (--lm == 0ull) next_leaf_run();
+      }
+      return w;
+    };
+    while (items > 1ull && !bad) {
+      const bool node = nt > nh && (lm == 0ull || S.nw[nh & kMask] < lw);
+      const unsigned long long w = node ? S.nw[nh & kMask] : lw;
+      const unsigned long long m = node ? (unsigned long long)S.nm[nh & kMask] : lm;
+      if (m >= 2ull) {
+        // every pair of this run is among the two smallest items in turn
+        const unsigned long long k = m / 2ull;
+        total += 2ull * w * k;
+        if (node) {
+          S.nm[nh & kMask] -= (unsigned)(2ull * k);
+          if (S.nm[nh & kMask] == 0u) ++nh;
+        } else {
+          lm -= 2ull * k;
+          if (lm == 0ull) next_leaf_run();
+        }
+        push_node(2ull * w, k);
+        items -= k;
+      } else {
+        const unsigned long long a = take_one();
+        const unsigned long long b = take_one();
+        total += a + b;
+        push_node(a + b, 1ull);
+        items -= 1ull;
+      }
+    }
   }
+  bits[blockIdx.x] = bad ? 0ull : total;
+  flag[blockIdx.x] = bad;
 }
 
 // Algorithm 1 on the device, one level at a time: the level's candidates
@@ -1019,7 +1125,11 @@ class Tuner {
     unsigned long long* d_bits = reinterpret_cast<unsigned long long*>(d_bits_);
     int* d_flag = reinterpret_cast<int*>(d_bits + nc);
     if (e == cudaSuccess && full) {
-      huffman_cost_kernel<<<nc, kHuffThreads, 0, s_>>>(d_hist_, d_bits, d_flag);
+      static unsigned long long attr_done = 0;
+      e = ensure_smem_attr((const void*)huffman_cost_kernel, &attr_done, sizeof(HuffCostSmem));
+      if (e == cudaSuccess)
+        huffman_cost_kernel<<<nc, kHuffThreads, sizeof(HuffCostSmem), s_>>>(d_hist_, d_bits,
+                                                                            d_flag);
       note_launch(1);
       e = launch_check(cudaGetLastError());
     }

@@ -152,3 +152,14 @@ def test_ac_target_is_rejected(q):
     x = torch.from_numpy(_field(32, 25)).cuda()
     with pytest.raises(q.QozError):
         q.tune(x, 1e-3, q.METRIC_AC, 0.1, q.make_tune_opts())
+
+
+def test_bound_mode_many_codes(q, orc):
+    # a tiny bound on a noisy field: thousands of distinct codes per trial
+    # histogram, so the prefix-code cost runs on runs of equal counts and the
+    # large counts' sort; the sampled bit rate must still be exact
+    rng = np.random.default_rng(7)
+    x = _field(48, 26) + rng.standard_normal((48, 48, 48)).astype(np.float32)
+    rep, ref = _compare(q, orc, x, 1e-5, 0, float("nan"), 16, 0.3, 2,
+                        [1.0, 1.5, 2.0], [2.0, 4.0])
+    assert rep.B == ref.B
