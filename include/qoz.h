@@ -48,7 +48,7 @@ typedef enum {
   QOZ_EINVAL = 1,        /* invalid argument (shape, bound, parameters) */
   QOZ_ENOMEM = 2,        /* device or host allocation failed */
   QOZ_ECUDA = 3,         /* a CUDA call or kernel launch failed */
-  QOZ_ECORRUPT = 4,      /* serialized stream damaged (magic, size, CRC) */
+  QOZ_ECORRUPT = 4,      /* serialized stream damaged (magic, size, checksum) */
   QOZ_ETIMEOUT = 5,      /* a bounded device wait gave up */
   QOZ_EUNSUPPORTED = 6   /* valid request outside what this build handles */
 } qoz_status;
@@ -442,6 +442,14 @@ typedef struct {
 /* Turns per-stage event timing on or off (process-wide; off by default).
  * The launch counter always runs. */
 qoz_status qoz_profile_enable(int32_t enable);
+/* Index checks of the bounds-checking build (built with QOZ_DEBUG_BOUNDS):
+ * every checked shared- or global-memory index that falls outside its array
+ * is skipped instead of accessed, and the first one is recorded as
+ * (1 << 63) | (source line << 40) | (index & (2^40 - 1)).  *first_bad
+ * receives the record of the kernels that ran since the last reset (0: none);
+ * reset != 0 clears it.  Synchronises the device.  A product build returns
+ * QOZ_EUNSUPPORTED. */
+qoz_status qoz_debug_bounds(uint64_t* first_bad, int32_t reset);
 /* Selects the stages that record events while timing is on: bit i of mask
  * enables stage i (process-wide; all stages by default).  Each timed stage
  * adds two event records to its stream, so a caller timing a whole pipeline

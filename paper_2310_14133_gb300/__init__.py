@@ -33,6 +33,7 @@ from ._binding import (  # noqa: F401
     compress_abs,
     compress_batch,
     compute_metrics,
+    debug_bounds,
     decompress,
     deserialize,
     error_autocorr,

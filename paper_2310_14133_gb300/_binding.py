@@ -12,7 +12,9 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB = os.path.join(_HERE, "_build", "libqoz.so")
+# QOZ_LIBRARY may name another build of the same library (the bounds-checking
+# build of build.build(debug_bounds=True)); the default is the product build.
+_LIB = os.environ.get("QOZ_LIBRARY") or os.path.join(_HERE, "_build", "libqoz.so")
 
 MAX_LEVELS = 8
 METRIC_MAXERR, METRIC_PSNR, METRIC_SSIM, METRIC_AC = 0, 1, 2, 3
@@ -59,6 +61,14 @@ def profile_enable(on: bool = True, stages=None):
     mask = 0xFFFFFFFF if stages is None else sum(1 << int(i) for i in stages)
     _check(lib().qoz_profile_stages(mask))
     _check(lib().qoz_profile_enable(1 if on else 0))
+
+
+def debug_bounds(reset: bool = True) -> int:
+    """Record of the first index check that failed since the last reset (0:
+    none).  Raises QozError (QOZ_EUNSUPPORTED) on the product build."""
+    v = C.c_uint64()
+    _check(lib().qoz_debug_bounds(C.byref(v), 1 if reset else 0))
+    return v.value
 
 
 def profile_read(reset: bool = False) -> StageTimes:
@@ -148,6 +158,7 @@ def lib():
             "qoz_error_autocorr": (i32, [P, P, i64, i64, P, P]),
             "qoz_profile_enable": (i32, [i32]),
             "qoz_profile_stages": (i32, [C.c_uint32]),
+            "qoz_debug_bounds": (i32, [P, i32]),
             "qoz_tune": (i32, [P, Shape, f64, i32, f64, P, P, P]),
             "qoz_profile_read": (i32, [P, i32]),
             "qoz_batch_create": (i32, [P, i32, P, C.c_uint32, P]),

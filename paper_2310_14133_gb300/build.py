@@ -47,17 +47,29 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
+DEBUG_BUILD = os.path.join(HERE, "_build_debug")
+DEBUG_LIB = os.path.join(DEBUG_BUILD, "libqoz.so")
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
+          debug_bounds: bool = False) -> str:
+    """Compiles the library for sm_103a and returns its path.  debug_bounds
+    builds the bounds-checking variant (QOZ_DEBUG_BOUNDS: every checked index
+    outside its array is recorded and skipped, see qoz_debug_bounds) into its
+    own directory; the package loads it when QOZ_LIBRARY names it."""
     srcs = _sources()
     hdrs = _headers()
-    if not force and not _stale(LIB, srcs + hdrs + [__file__]):
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    bdir, lib_path = (DEBUG_BUILD, DEBUG_LIB) if debug_bounds else (BUILD, LIB)
+    if not force and not _stale(lib_path, srcs + hdrs + [__file__]):
+        return lib_path
+    os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
+    if debug_bounds:
+        extra = extra + ["-DQOZ_DEBUG_BOUNDS"]
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         if not force and not _stale(obj, [src] + hdrs + [__file__]):
             return obj, ""
         cmd = [nvcc] + NVCC_FLAGS + extra + ["-c", src, "-o", obj]
@@ -72,13 +84,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         for _, log in results:
             if log:
                 sys.stdout.write(log)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results]
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError(f"link failed:\n{p.stdout}\n{p.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -11,6 +11,32 @@
 
 namespace qoz {
 
+// Index checks of the bounds-checking build.  QOZ_IN(i, n) is true when
+// 0 <= i < n; with QOZ_DEBUG_BOUNDS defined a failing check also records
+// its source line and index (the first failure since the last reset, in
+// this translation unit's bounds_word) and the caller skips the access.  In
+// the product build it is the constant true and costs nothing.
+#ifdef QOZ_DEBUG_BOUNDS
+static __device__ unsigned long long bounds_word;
+__device__ __forceinline__ bool bounds_ok(long long i, long long n, int line) {
+  if (i >= 0 && i < n) return true;
+  atomicCAS(&bounds_word, 0ull,
+            (1ull << 63) | ((unsigned long long)(line & 0x7fffff) << 40) |
+                ((unsigned long long)i & 0xffffffffffull));
+  return false;
+}
+// Reads and optionally clears this translation unit's record (host).
+static inline unsigned long long bounds_take(bool reset) {
+  unsigned long long v = 0ull, z = 0ull;
+  cudaMemcpyFromSymbol(&v, bounds_word, sizeof(v));
+  if (reset) cudaMemcpyToSymbol(bounds_word, &z, sizeof(z));
+  return v;
+}
+#define QOZ_IN(i, n) ::qoz::bounds_ok((long long)(i), (long long)(n), __LINE__)
+#else
+#define QOZ_IN(i, n) true
+#endif
+
 constexpr int kMaxLevels = 8;
 constexpr int kRadius = 32768;
 constexpr int kHalo = 3;  // stencil reach at the finest level of a grid

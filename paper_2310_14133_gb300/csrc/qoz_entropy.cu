@@ -348,17 +348,19 @@ constexpr int kRowWords = kRun / 2 + 1;
 // before, so at most one word completes).
 __device__ __forceinline__ void put_bits(unsigned long long& acc, int& nacc, unsigned long long v,
                                          int L, uint32_t* out, long long& wi, bool& first,
-                                         bool shared_first) {
+                                         bool shared_first, long long nwc) {
   acc = (acc << L) | v;
   nacc += L;
   if (nacc >= 32) {
     nacc -= 32;
     const uint32_t w = (uint32_t)(acc >> nacc);
     acc &= (1ull << nacc) - 1ull;
-    if (first && shared_first)
-      atomicOr(out + wi, w);
-    else
-      out[wi] = w;
+    if (QOZ_IN(wi, nwc)) {
+      if (first && shared_first)
+        atomicOr(out + wi, w);
+      else
+        out[wi] = w;
+    }
     ++wi;
     first = false;
   }
@@ -398,6 +400,8 @@ __global__ void __launch_bounds__(32 * kEncWarps)
   start -= bits;
   if (bits == 0) return;
   uint32_t* out = words + offs[c];
+  const long long nwc = (long long)(offs[c + 1] - offs[c]);  // the chunk's words
+  (void)nwc;
   long long wi = (long long)(start >> 5);
   int nacc = (int)(start & 31);  // pending bits (leading zeros of the first word)
   unsigned long long acc = 0ull;
@@ -408,13 +412,13 @@ __global__ void __launch_bounds__(32 * kEncWarps)
     const int L = (int)(en & 63ull);
     const unsigned long long cv = en >> 6;
     if (LONG && L > 32) {  // the high part first
-      put_bits(acc, nacc, cv >> 32, L - 32, out, wi, first, shared_first);
-      put_bits(acc, nacc, cv & 0xffffffffull, 32, out, wi, first, shared_first);
+      put_bits(acc, nacc, cv >> 32, L - 32, out, wi, first, shared_first, nwc);
+      put_bits(acc, nacc, cv & 0xffffffffull, 32, out, wi, first, shared_first, nwc);
     } else {
-      put_bits(acc, nacc, cv, L, out, wi, first, shared_first);
+      put_bits(acc, nacc, cv, L, out, wi, first, shared_first, nwc);
     }
   }
-  if (nacc > 0) atomicOr(out + wi, (uint32_t)(acc << (32 - nacc)));
+  if (nacc > 0 && QOZ_IN(wi, nwc)) atomicOr(out + wi, (uint32_t)(acc << (32 - nacc)));
 }
 
 // Decoder tables in shared memory: 12-bit lookup (symbol << 8 | length, 0
@@ -641,3 +645,10 @@ cudaError_t huff_decode(const void* d_section, const uint32_t* d_words, long lon
 }
 
 }  // namespace qoz
+
+#ifdef QOZ_DEBUG_BOUNDS
+namespace qoz {
+// This translation unit's record of failed index checks (bounds-checking build).
+unsigned long long bounds_take_entropy(bool reset) { return bounds_take(reset); }
+}  // namespace qoz
+#endif

@@ -217,4 +217,12 @@ void huff_free(HuffEncoded* h, cudaStream_t s);
 cudaError_t huff_decode(const void* d_section, const uint32_t* d_words, long long nchunks,
                         long long N, uint16_t* d_codes, int* d_err, cudaStream_t s);
 
+#ifdef QOZ_DEBUG_BOUNDS
+// Records of failed index checks, one per translation unit that checks.
+unsigned long long bounds_take_level(bool reset);
+unsigned long long bounds_take_level_batch(bool reset);
+unsigned long long bounds_take_tune(bool reset);
+unsigned long long bounds_take_entropy(bool reset);
+#endif
+
 }  // namespace qoz

@@ -309,3 +309,10 @@ bool level_tma_maps(const LevelKey& k, const LevelLaunch& L, LevelTmaMaps* m) {
 }
 
 }  // namespace qoz
+
+#ifdef QOZ_DEBUG_BOUNDS
+namespace qoz {
+// This translation unit's record of failed index checks (bounds-checking build).
+unsigned long long bounds_take_level(bool reset) { return bounds_take(reset); }
+}  // namespace qoz
+#endif

@@ -147,3 +147,10 @@ cudaError_t launch_level_batch(const LevelKey& k, const LevelItem* d_items, cons
 }
 
 }  // namespace qoz
+
+#ifdef QOZ_DEBUG_BOUNDS
+namespace qoz {
+// This translation unit's record of failed index checks (bounds-checking build).
+unsigned long long bounds_take_level_batch(bool reset) { return bounds_take(reset); }
+}  // namespace qoz
+#endif

@@ -278,13 +278,16 @@ __device__ __forceinline__ void pass_line(const LevelLaunch& a, const Ctx& c, fl
       const int pos = p0 - 2 + 2 * k;
       if (PASS == 1 && (pos < 0 || pos >= TP)) {
         if constexpr (CBOX) {
-          w[k] = CR[G::cbidx(P == 0 ? pos : lr, P == 1 ? pos : lr, lx)];
+          const int ci = G::cbidx(P == 0 ? pos : lr, P == 1 ? pos : lr, lx);
+          w[k] = QOZ_IN(ci, G::kCB) ? CR[ci] : 0.0f;
         } else {
           const int kk = pos < 0 ? 0 : (pos == TP ? 1 : 2);
-          w[k] = CR[G::side_row(kk, lr) * G::HX + ((lx + 4) >> 1)];
+          const int ci = G::side_row(kk, lr) * G::HX + ((lx + 4) >> 1);
+          w[k] = QOZ_IN(ci, G::kCR) ? CR[ci] : 0.0f;
         }
       } else {
-        w[k] = S[rbase + pos * SP];
+        const int si = rbase + pos * SP;
+        w[k] = QOZ_IN(si, G::kS) ? S[si] : 0.0f;
       }
     }
 #pragma unroll
@@ -300,6 +303,8 @@ __device__ __forceinline__ void pass_line(const LevelLaunch& a, const Ctx& c, fl
         pred = predict(w[j], w[j + 1], w[j + 2], w[j + 3], ha3, hb1, hb3, interp_of<G>(c));
       }
       const int lz = P == 0 ? pos : lr, ly = P == 1 ? pos : lr;
+      if (!QOZ_IN(rbase + pos * SP, G::kS) || (inside && !QOZ_IN(G::cidx(lz, ly, lx), G::kC)))
+        continue;
       finish<DECOMP>(a, c, S, IN16, rbase + pos * SP, pred, inside, C16 + G::cidx(lz, ly, lx),
                      c.oz + lz, c.oy + ly, cx);
     }
@@ -336,6 +341,9 @@ __device__ __forceinline__ void pass_x_rows(const LevelLaunch& a, const Ctx& c, 
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int si = si0 + u * DS;
+      if (!QOZ_IN(si - 3, G::kS) || !QOZ_IN(si + 3, G::kS) ||
+          (inside && !QOZ_IN(ci0 + u * DC, G::kC)))
+        continue;
       const float pred = predict_full(S[si - 3], S[si - 1], S[si + 1], S[si + 3], interp_of<G>(c));
       const int uz = ALONG_Y ? lz : lz + u * SZ::step, uy = ALONG_Y ? ly + u * SY::step : ly;
       finish<DECOMP>(a, c, S, IN16, si, pred, inside, C16 + ci0 + u * DC, c.oz + uz, c.oy + uy,
@@ -371,6 +379,10 @@ __device__ __forceinline__ void pass_x(const LevelLaunch& a, const Ctx& c, float
     const int cz = c.oz + lz, cy = c.oy + ly, cx = c.ox + lx;
     if (!INTERIOR && (cz < 0 || cz >= c.g0 || cy < 0 || cy >= c.g1 || cx >= c.g2)) continue;
     const int si = G::row(lz, ly) * G::EX + lx + 4;
+    const bool inside = lz >= 0 && lz < G::TZ && ly >= 0 && ly < G::TY;
+    if (!QOZ_IN(si - 3, G::kS) || !QOZ_IN(si + 3, G::kS) ||
+        (inside && !QOZ_IN(G::cidx(lz, ly, lx), G::kC)))
+      continue;
     const float a3 = S[si - 3], a1 = S[si - 1], b1 = S[si + 1], b3 = S[si + 3];
     float pred;
     if (INTERIOR) {
@@ -379,7 +391,6 @@ __device__ __forceinline__ void pass_x(const LevelLaunch& a, const Ctx& c, float
       const bool hb1 = cx + 1 < c.g2, ha3 = cx >= 3, hb3 = cx + 3 < c.g2;
       pred = predict(a3, a1, b1, b3, ha3, hb1, hb3, interp_of<G>(c));
     }
-    const bool inside = lz >= 0 && lz < G::TZ && ly >= 0 && ly < G::TY;
     finish<DECOMP>(a, c, S, IN16, si, pred, inside, C16 + G::cidx(lz, ly, lx), cz, cy, cx);
   }
 }
@@ -475,6 +486,7 @@ __device__ __forceinline__ void level_tile(const LevelLaunch& a, unsigned char* 
     if (cz < 0 || cz >= c.g0 || cy < 0 || cy >= c.g1) continue;
     const bool hz = lz < 0 || lz >= TZ, hy = ly < 0 || ly >= TY;
     if ((hz && (cz & 1)) || (hy && (cy & 1))) continue;
+    if (!QOZ_IN(r * G::EX + G::EX - 1, G::kS)) continue;
     const unsigned rbase = (unsigned)cz * xs0 + (unsigned)cy * xs1;
     if (vec_rows) {
       // groups of four x: 16-byte copies of the field (8 bytes of codes)
@@ -525,6 +537,7 @@ __device__ __forceinline__ void level_tile(const LevelLaunch& a, unsigned char* 
     const int cz = c.oz + lz, cy = c.oy + ly;
     if (cz < 0 || cz >= c.g0 || cy < 0 || cy >= c.g1) continue;
     const unsigned cb = (unsigned)(cz >> 1) * cs0 + (unsigned)(cy >> 1) * cs1;
+    if (!QOZ_IN(r * G::HX + G::HX - 1, G::kCR)) continue;
     for (int j = lane; j < G::HX; j += 32) {
       const int cx = c.ox - 4 + 2 * j;
       if (cx < 0 || cx >= c.g2) continue;
@@ -535,7 +548,7 @@ __device__ __forceinline__ void level_tile(const LevelLaunch& a, unsigned char* 
     // the coarse codes fetched first now land in the code tile
 #pragma unroll
     for (int k = 0; k < kCCPer; ++k)
-      if (cc_slot[k] >= 0) C16[cc_slot[k]] = cc_val[k];
+      if (cc_slot[k] >= 0 && QOZ_IN(cc_slot[k], G::kC)) C16[cc_slot[k]] = cc_val[k];
   }
   cp_async_wait_all();
   __syncthreads();
@@ -544,7 +557,8 @@ __device__ __forceinline__ void level_tile(const LevelLaunch& a, unsigned char* 
     const int j = i % G::HX;
     const int r = i / G::HX;
     const int lz = G::ZLO + 2 * (r / G::NCY), ly = G::YLO + 2 * (r % G::NCY);
-    S[G::row(lz, ly) * G::EX + 2 * j] = CR[i];
+    const int si = G::row(lz, ly) * G::EX + 2 * j;
+    if (QOZ_IN(si, G::kS) && QOZ_IN(i, G::kCR)) S[si] = CR[i];
   }
   __syncthreads();
 
@@ -581,6 +595,10 @@ __device__ __forceinline__ void level_tile(const LevelLaunch& a, unsigned char* 
     if (cz >= c.g0 || cy >= c.g1 || cx >= c.g2) continue;
     const unsigned oi = (unsigned)cz * os0 + (unsigned)cy * os1 + (unsigned)cx;
     const bool full = cx + 8 <= c.g2;
+    if (!QOZ_IN(G::cidx(lz, ly, lx) + 7, G::kC) ||
+        !QOZ_IN(G::row(lz, ly) * G::EX + lx + 11, G::kS) ||
+        !QOZ_IN((long long)oi + (full ? 7 : c.g2 - 1 - cx), (long long)c.g0 * os0))
+      continue;
     if (!DECOMP) {
       const uint4 v = *reinterpret_cast<const uint4*>(C16 + G::cidx(lz, ly, lx));
       if (full && vec_codes) {
@@ -721,7 +739,8 @@ __device__ __forceinline__ void level_tile_tma(const LevelLaunch& a, unsigned ch
     const int j = i % G::HX;
     const int r = i / G::HX;
     const int lz = G::ZLO + 2 * (r / G::NCY), ly = G::YLO + 2 * (r % G::NCY);
-    S[G::row(lz, ly) * G::EX + 2 * j] = CB[G::cbidx(lz, ly, 2 * j - 4)];
+    const int si = G::row(lz, ly) * G::EX + 2 * j, bi = G::cbidx(lz, ly, 2 * j - 4);
+    if (QOZ_IN(si, G::kS) && QOZ_IN(bi, G::kCB)) S[si] = CB[bi];
   }
   // the tile's coarse codes into the code tile
   for (int i = threadIdx.x; i < G::kCC; i += THR) {
@@ -729,7 +748,8 @@ __device__ __forceinline__ void level_tile_tma(const LevelLaunch& a, unsigned ch
     const int t = i / G::CCX;
     const int iy = t % G::CCY;
     const int iz = t / G::CCY;
-    C16[G::cidx(2 * iz, 2 * iy, 2 * ix)] = CC[i];
+    const int ci = G::cidx(2 * iz, 2 * iy, 2 * ix);
+    if (QOZ_IN(ci, G::kC)) C16[ci] = CC[i];
   }
   __syncthreads();
 
@@ -773,6 +793,10 @@ __device__ __forceinline__ void level_tile_tma(const LevelLaunch& a, unsigned ch
       if (cz >= c.g0 || cy >= c.g1 || cx >= c.g2) continue;
       const unsigned oi = (unsigned)cz * os0 + (unsigned)cy * os1 + (unsigned)cx;
       const bool full = cx + 8 <= c.g2;
+      if (!QOZ_IN(G::cidx(lz, ly, lx) + 7, G::kC) ||
+          !QOZ_IN(G::row(lz, ly) * G::EX + lx + 11, G::kS) ||
+          !QOZ_IN((long long)oi + (full ? 7 : c.g2 - 1 - cx), (long long)c.g0 * os0))
+        continue;
       const uint4 v = *reinterpret_cast<const uint4*>(C16 + G::cidx(lz, ly, lx));
       if (!map_out) {
         if (full && vec_codes) {

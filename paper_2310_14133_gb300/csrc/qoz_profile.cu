@@ -94,6 +94,25 @@ qoz_status qoz_profile_enable(int32_t enable) {
   return QOZ_OK;
 }
 
+qoz_status qoz_debug_bounds(uint64_t* first_bad, int32_t reset) {
+  if (!first_bad) return fail(QOZ_EINVAL, "NULL argument");
+#ifdef QOZ_DEBUG_BOUNDS
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "bounds record");
+  const unsigned long long w[4] = {bounds_take_level(reset != 0),
+                                   bounds_take_level_batch(reset != 0),
+                                   bounds_take_tune(reset != 0), bounds_take_entropy(reset != 0)};
+  *first_bad = 0;
+  for (unsigned long long v : w)
+    if (v && !*first_bad) *first_bad = v;
+  return QOZ_OK;
+#else
+  *first_bad = 0;
+  (void)reset;
+  return fail(QOZ_EUNSUPPORTED, "not the bounds-checking build (QOZ_DEBUG_BOUNDS)");
+#endif
+}
+
 qoz_status qoz_profile_stages(uint32_t mask) {
   g_mask.store(mask);
   return QOZ_OK;

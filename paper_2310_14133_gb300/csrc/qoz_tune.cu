@@ -150,6 +150,10 @@ __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 1 : 4)
   // the bulk copy starts at the 16-byte boundary at or below the block's x
   // origin; the block itself then starts ox mod 4 values into the buffer
   float* S = reinterpret_cast<float*>(base) + (a.use_tma ? (ox & 3) : 0);
+  // values of the block buffer reachable from S (checked by the
+  // bounds-checking build)
+  const int nS = m0 * m1 * P - (a.use_tma ? (ox & 3) : 0);
+  (void)nS;
 
   if (a.use_tma) {
     if (threadIdx.x == 0) {
@@ -202,7 +206,8 @@ __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 1 : 4)
     const int n0 = (m0 - 1) / as + 1, n1a = (m1 - 1) / as + 1, n2a = (m2 - 1) / as + 1;
     for (int i = threadIdx.x; i < n0 * n1a * n2a; i += THREADS) {
       const int i2 = i % n2a, r = i / n2a;
-      const float v = S[(r / n1a) * as * st0 + (r % n1a) * as * st1 + i2 * as];
+      const int si = (r / n1a) * as * st0 + (r % n1a) * as * st1 + i2 * as;
+      const float v = QOZ_IN(si, nS) ? S[si] : 0.0f;
       const float d = __fsub_rn(v, v);
       sse.add(__fmul_rn(d, d));
       const float ad = fabsf(d);
@@ -250,6 +255,9 @@ __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 1 : 4)
           const int li = z * st0 + y * st1 + xx;
           const int ca = ax == 0 ? z : (ax == 1 ? y : xx);
           const bool hb1 = ca + h < na, ha3 = ca >= 3 * h, hb3 = ca + 3 * h < na;
+          if (!QOZ_IN(li, nS) || !QOZ_IN(li - h * sa, nS) || (hb1 && !QOZ_IN(li + h * sa, nS)) ||
+              (ha3 && !QOZ_IN(li - 3 * h * sa, nS)) || (hb3 && !QOZ_IN(li + 3 * h * sa, nS)))
+            continue;
           const float a1 = S[li - h * sa];
           const float b1 = hb1 ? S[li + h * sa] : 0.0f;
           const float a3 = ha3 ? S[li - 3 * h * sa] : 0.0f;
@@ -319,6 +327,8 @@ __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 1 : 4)
         const int r = wi / c2n;
         const int w1 = r % c1n;
         const int w0 = r / c1n;
+        if (!QOZ_IN((w0 * sp + wz - 1) * n1 * P + (w1 * sp + w - 1) * P + w2 * sp + w - 1, nS))
+          continue;
         // window moments in binary32, centred on the window means to keep the
         // variances well conditioned; the SSIM formula itself in double
         float sx = 0.0f, sy = 0.0f;
@@ -367,7 +377,8 @@ __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 1 : 4)
     const int nbp = n0 * n1 * n2;
     double* o = a.out + ((size_t)cand * a.nblocks + blk) * kOutStride;
     auto err_at = [&](int z, int y, int x) {
-      return __fsub_rn(S[(z * n1 + y) * P + x], xb[z * a.st0 + y * a.st1 + x]);
+      const int si = (z * n1 + y) * P + x;
+      return QOZ_IN(si, nS) ? __fsub_rn(S[si], xb[z * a.st0 + y * a.st1 + x]) : 0.0f;
     };
     for (int i = threadIdx.x; i < nbp; i += THREADS) {
       const int x = i % n2, r = i / n2, y = r % n1, z = r / n1;
@@ -1662,3 +1673,9 @@ extern "C" qoz_status qoz_tune_verify(const float* d_field, qoz_shape shape, dou
                           (cudaStream_t)stream, out);
 }
 
+#ifdef QOZ_DEBUG_BOUNDS
+namespace qoz {
+// This translation unit's record of failed index checks (bounds-checking build).
+unsigned long long bounds_take_tune(bool reset) { return bounds_take(reset); }
+}  // namespace qoz
+#endif
