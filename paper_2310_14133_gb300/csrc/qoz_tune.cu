@@ -488,13 +488,14 @@ __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 1 : 4)
 
 // Optimal prefix-code cost of one candidate's pooled histogram (the rate
 // estimate of Sec. 6.1): one CTA per candidate.  The cost is the sum of the
-// weights of the merged nodes of Huffman's construction, run here as the
+// weights of the merged nodes of Huffman's construction, run as the
 // two-queue merge (leaves and merged nodes both come out in non-decreasing
-// order) over runs of equal weight: while the smallest item's run holds two
-// or more items, pairing them is what the merge would do step by step, so
-// all pairs of the run are merged at once into one run of nodes.  Leaves
-// come sorted without a sort: counts up to kHuffSmall are bucketed by value
-// (multiplicities in shared memory), the few larger counts are sorted.
+// order).  Up to kHuffSmall used codes, the counts are sorted and merged one
+// by one with the queue heads in registers.  With more, the leaves come
+// sorted without a sort (counts up to kHuffSmall bucketed by value, the few
+// larger ones sorted) and the merge runs over runs of equal weight: while
+// the smallest item's run holds two or more items, pairing them is what the
+// merge would do step by step, so all pairs of the run are merged at once.
 // Integer arithmetic: the same total as the host computation.  More than
 // kHuffBig large counts or kHuffNodes live node runs are left to the host
 // (flag 1).
@@ -505,7 +506,15 @@ constexpr int kHuffNodes = 4096;  // node runs alive at once (a ring)
 
 struct HuffCostSmem {
   unsigned small[kHuffSmall + 1];        // multiplicity of each count 1..kHuffSmall
-  unsigned rc[kHuffSmall], rm[kHuffSmall];  // the non-empty buckets in count order
+  union {
+    struct {                             // up to kHuffSmall used codes: the counts
+      unsigned cnt[kHuffSmall];          // (sorted in place) and the merged weights
+      unsigned node[kHuffSmall];         // (at most the sampled points, < 2^32)
+    } sorted;
+    struct {                             // more used codes: the non-empty buckets
+      unsigned rc[kHuffSmall], rm[kHuffSmall];  // in count order
+    } runs;
+  } u;
   unsigned big[kHuffBig];                // counts above kHuffSmall (sorted in place)
   unsigned long long nw[kHuffNodes];     // node runs: weight
   unsigned nm[kHuffNodes];               // node runs: multiplicity
@@ -526,8 +535,97 @@ __global__ void __launch_bounds__(kHuffThreads)
     nsym = 0ull;
   }
   __syncthreads();
-  // coalesced 16-byte scan, kBatch loads in flight per thread
+  // coalesced 16-byte scan, kBatch loads in flight per thread: each warp
+  // appends its non-zero counts (any order: they are sorted next) and the
+  // total of used codes
   constexpr int kVec = 65536 / 4 / kHuffThreads, kBatch = 4;
+  const int lane = t & 31;
+  for (int j0 = 0; j0 < kVec; j0 += kBatch) {
+    uint4 v[kBatch];
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) v[j] = h4[(j0 + j) * kHuffThreads + t];
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+      const unsigned q[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+      const int nz = (q[0] != 0u) + (q[1] != 0u) + (q[2] != 0u) + (q[3] != 0u);
+      if (__ballot_sync(0xffffffffu, nz != 0) == 0u) continue;
+      int inc = nz;  // inclusive prefix over the warp
+      for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += y;
+      }
+      unsigned long long base = 0ull;
+      if (lane == 31) base = atomicAdd(&nsym, (unsigned long long)inc);
+      unsigned long long k = __shfl_sync(0xffffffffu, base, 31) + (unsigned long long)(inc - nz);
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (q[e] != 0u) {
+          if (k < (unsigned long long)kHuffSmall) S.u.sorted.cnt[k] = q[e];
+          ++k;
+        }
+    }
+  }
+  __syncthreads();
+  if (nsym <= (unsigned long long)kHuffSmall) {
+    // few used codes: sort the counts and run the two-queue merge with the
+    // queue heads in registers and the next leaf prefetched (the sorted
+    // leaves are padded with 0xffffffff)
+    unsigned* cnt = S.u.sorted.cnt;
+    unsigned* node = S.u.sorted.node;
+    const int n = (int)nsym;
+    int P = 1;
+    while (P < n) P <<= 1;
+    for (int i = n + t; i < P; i += kHuffThreads) cnt[i] = 0xffffffffu;
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1)
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int i = t; i < P; i += kHuffThreads) {
+          const int j = i ^ stride;
+          if (j > i) {
+            const bool up = (i & size) == 0;
+            const unsigned a = cnt[i], b = cnt[j];
+            if ((a > b) == up) {
+              cnt[i] = b;
+              cnt[j] = a;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    if (t != 0) return;
+    unsigned long long total = 0ull;
+    if (n == 1) {
+      total = cnt[0];
+    } else if (n > 1) {
+      int li = 0, ni = 0, nn = 0;
+      unsigned hl = cnt[0], hl2 = cnt[1], hn = 0u;
+      for (int m = 1; m < n; ++m) {
+        unsigned ab[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          if (ni < nn && (li >= n || hn < hl)) {
+            ab[k] = hn;
+            ++ni;
+            hn = ni < nn ? node[ni] : 0u;
+          } else {
+            ab[k] = hl;
+            ++li;
+            hl = hl2;
+            hl2 = li + 1 < P ? cnt[li + 1] : 0xffffffffu;
+          }
+        }
+        const unsigned sum = ab[0] + ab[1];
+        total += sum;
+        node[nn] = sum;
+        if (ni == nn) hn = sum;
+        ++nn;
+      }
+    }
+    bits[blockIdx.x] = total;
+    flag[blockIdx.x] = 0;
+    return;
+  }
+  // many used codes: a second scan buckets the counts by value
   for (int j0 = 0; j0 < kVec; j0 += kBatch) {
     uint4 v[kBatch];
 #pragma unroll
@@ -539,12 +637,11 @@ __global__ void __launch_bounds__(kHuffThreads)
       for (int e = 0; e < 4; ++e) {
         const unsigned c = q[e];
         if (c == 0u) continue;
-        atomicAdd(&nsym, 1ull);
         if (c <= (unsigned)kHuffSmall) {
           atomicAdd(&S.small[c], 1u);
         } else {
-          const int k = atomicAdd(&nbig, 1);
-          if (k < kHuffBig) S.big[k] = c;
+          const int kb = atomicAdd(&nbig, 1);
+          if (kb < kHuffBig) S.big[kb] = c;
         }
       }
     }
@@ -590,8 +687,8 @@ __global__ void __launch_bounds__(kHuffThreads)
     for (int k = 0; k < 4; ++k) {
       const unsigned m = S.small[c0 + k];
       if (m != 0u) {
-        S.rc[pos] = (unsigned)(c0 + k);
-        S.rm[pos] = m;
+        S.u.runs.rc[pos] = (unsigned)(c0 + k);
+        S.u.runs.rm[pos] = m;
         ++pos;
       }
     }
@@ -624,8 +721,8 @@ __global__ void __launch_bounds__(kHuffThreads)
   auto next_leaf_run = [&]() {
     lm = 0ull;
     if (ri < nr) {
-      lw = (unsigned long long)S.rc[ri];
-      lm = S.rm[ri];
+      lw = (unsigned long long)S.u.runs.rc[ri];
+      lm = S.u.runs.rm[ri];
       ++ri;
       return;
     }
