@@ -1,10 +1,14 @@
-// Per-stage timing with CUDA events and a count of kernel launches.
+// Per-stage timing with CUDA events, NVTX ranges and a count of kernel
+// launches.
 //
 // When enabled, each stage of compress / decompress records a pair of events
 // on the caller's stream; elapsed times are folded in when they are read
-// (qoz_profile_read synchronises on the recorded events).  The launch counter
-// is always on: every kernel launch of the library increments it.
+// (qoz_profile_read synchronises on the recorded events).  Every stage also
+// opens an NVTX range named after it (a no-op unless a tool is attached), so
+// a timeline shows the library's stages.  The launch counter is always on:
+// every kernel launch of the library increments it.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <atomic>
 #include <mutex>
@@ -59,7 +63,28 @@ void fold_pending_locked() {
 
 void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+// NVTX range names of the stages (the host-side span of each stage).
+const char* stage_name(int stage) {
+  static const char* const level[] = {"qoz level 1", "qoz level 2", "qoz level 3", "qoz level 4",
+                                      "qoz level 5", "qoz level 6", "qoz level 7", "qoz level 8"};
+  static const char* const dlevel[] = {"qoz decode level 1", "qoz decode level 2",
+                                       "qoz decode level 3", "qoz decode level 4",
+                                       "qoz decode level 5", "qoz decode level 6",
+                                       "qoz decode level 7", "qoz decode level 8"};
+  if (stage == QOZ_STAGE_RANGE) return "qoz value range";
+  if (stage == QOZ_STAGE_SETUP) return "qoz bounds + anchors";
+  if (stage > QOZ_STAGE_LEVEL && stage <= QOZ_STAGE_LEVEL + 8) return level[stage - QOZ_STAGE_LEVEL - 1];
+  if (stage == QOZ_STAGE_HIST) return "qoz histogram";
+  if (stage == QOZ_STAGE_FINAL) return "qoz unpredictable list";
+  if (stage > QOZ_STAGE_DLEVEL && stage <= QOZ_STAGE_DLEVEL + 8)
+    return dlevel[stage - QOZ_STAGE_DLEVEL - 1];
+  if (stage == QOZ_STAGE_METRICS) return "qoz metrics";
+  if (stage == QOZ_STAGE_TUNE) return "qoz tuner trials";
+  return "qoz stage";
+}
+
 ProfScope::ProfScope(int stage, cudaStream_t s) : stage_(stage), s_(s), a_(nullptr) {
+  nvtxRangePushA(stage_name(stage));
   if (!g_on.load(std::memory_order_relaxed) || stage < 0 || stage >= QOZ_PROF_STAGES) return;
   if (!((g_mask.load(std::memory_order_relaxed) >> stage) & 1u)) return;
   std::lock_guard<std::mutex> lk(g_mu);
@@ -71,6 +96,7 @@ ProfScope::ProfScope(int stage, cudaStream_t s) : stage_(stage), s_(s), a_(nullp
 }
 
 ProfScope::~ProfScope() {
+  nvtxRangePop();
   if (!a_) return;
   std::lock_guard<std::mutex> lk(g_mu);
   cudaEvent_t b = take_event();

@@ -10,6 +10,8 @@ runs in the CUDA library; this module only batches the calls.
 
 from __future__ import annotations
 
+import os
+
 import numpy as np
 import torch
 
@@ -25,20 +27,40 @@ def label_of(rep, alphas, betas):
     return [int(p.interp[0]), int(p.order[0]), ia, ib]
 
 
-def collect(samples, opts, metric=B.METRIC_MAXERR, stream=None):
+def collect(samples, opts, metric=B.METRIC_MAXERR, stream=None, cache=None):
     """samples: iterable of (field tensor, relative bound).  Returns the
-    feature rows (n x 64, CUDA float32) and labels (n x 4, CUDA int32)."""
+    feature rows (n x 64, CUDA float32) and labels (n x 4, CUDA int32).
+
+    cache: an .npz path.  Labels already stored there (rows in sample order)
+    are reused and only the samples after them are tuned; the file is
+    rewritten with all rows, so an interrupted collection resumes where it
+    stopped."""
     alphas = [opts.alphas[i] for i in range(opts.n_alpha)]
     betas = [opts.betas[i] for i in range(opts.n_beta)]
+    if not alphas or not betas:
+        raise ValueError("labels index the candidate lists: give opts explicit alphas and betas")
+    done_x, done_y = np.zeros((0, B.NFEATURES), np.float32), np.zeros((0, 4), np.int32)
+    if cache is not None and os.path.exists(cache):
+        d = np.load(cache)
+        done_x, done_y = d["features"], d["labels"]
     feats, labels = [], []
-    for x, rel in samples:
+    for i, (x, rel) in enumerate(samples):
+        if i < done_x.shape[0]:
+            continue
         f = torch.empty(B.NFEATURES, dtype=torch.float32, device="cuda")
         B.features(x, rel, opts, device_out=f, stream=stream)
         rep = B.tune(x, rel, metric, float("nan"), opts, stream=stream)
         feats.append(f)
         labels.append(label_of(rep, alphas, betas))
-    X = torch.stack(feats)
-    Y = torch.tensor(labels, dtype=torch.int32, device="cuda")
+    new_x = torch.stack(feats).cpu().numpy() if feats else np.zeros((0, B.NFEATURES), np.float32)
+    new_y = np.asarray(labels, dtype=np.int32).reshape(-1, 4)
+    all_x, all_y = np.concatenate([done_x, new_x]), np.concatenate([done_y, new_y])
+    if cache is not None and new_x.shape[0]:
+        tmp = cache + ".tmp.npz"
+        np.savez(tmp, features=all_x, labels=all_y)
+        os.replace(tmp, cache)
+    X = torch.from_numpy(all_x).cuda()
+    Y = torch.from_numpy(all_y).cuda()
     return X, Y
 
 

@@ -168,3 +168,20 @@ def test_tune_learned_follows_network(q, orc, shape):
     rep2 = q.tune_learned(x, 1e-2, m, metric=q.METRIC_PSNR, target=80.0, opts=opts)
     assert rep2.abs_eb == pytest.approx(vr * math.sqrt(3) * 10 ** (-4.0), rel=1e-12)
     m.free()
+
+
+def test_label_collection_resumes_from_cache(q, tmp_path):
+    # an interrupted collection (3 of 5 samples) resumes from its cache and
+    # gives the rows a fresh collection gives
+    from paper_2310_14133_gb300 import learn
+    opts = q.make_tune_opts(block=16, rate=0.05, n_orders=2, alphas=[1.0, 1.5, 2.0],
+                            betas=[2.0, 4.0])
+    samples = [(_field((40, 40, 40), 50 + i), 1e-3) for i in range(5)]
+    cache = str(tmp_path / "labels.npz")
+    X3, Y3 = learn.collect(samples[:3], opts, cache=cache)
+    assert X3.shape == (3, q.NFEATURES) and Y3.shape == (3, 4)
+    X5, Y5 = learn.collect(samples, opts, cache=cache)
+    Xf, Yf = learn.collect(samples, opts)
+    assert torch.equal(Y5, Yf) and torch.equal(X5, Xf)
+    d = np.load(cache)
+    assert d["features"].shape == (5, q.NFEATURES) and d["labels"].shape == (5, 4)
