@@ -64,7 +64,18 @@ def parse():
                          "error-autocorrelation reduction and the AC-preferred tuning mode; "
                          "ablation: SZ3-like / +AP / +S / +LIS / QoZ rate-distortion")
     ap.add_argument("--train", type=int, default=2000, help="learned: training fields")
+    ap.add_argument("--log", default=None,
+                    help="also append the JSON line to this JSONL file (one line per run)")
     return ap.parse_args()
+
+
+def emit(line, args):
+    """Prints the run's JSON line; with --log, also appends it to a JSONL file."""
+    text = json.dumps(line)
+    print(text, flush=True)
+    if getattr(args, "log", None):
+        with open(args.log, "a") as f:
+            f.write(text + "\n")
 
 
 class ClockSampler:
@@ -225,7 +236,7 @@ def run_reference(args, rank, world):
                          "sample": f"{sub}^3 sample per step, single-threaded C++ oracle"},
         "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line), flush=True)
+    emit(line, args)
 
 
 def cpu_baseline(x):
@@ -317,7 +328,7 @@ def run_batch(args):
         "clocks": clk,
         "e2e": None,
     }
-    print(json.dumps(line), flush=True)
+    emit(line, args)
     plan.free()
 
 
@@ -394,7 +405,7 @@ def run_learned(args):
                                 "fit_s": t_fit, "final_loss": losses[-1],
                                 "train_accuracy_per_head": acc},
     }
-    print(json.dumps(line), flush=True)
+    emit(line, args)
     model.free()
 
 
@@ -472,7 +483,7 @@ def run_ssim(args):
                    "tuner_opts": TUNE, "train_fields": args.train, "parallelism": "single GPU"},
         "rows": rows,
     }
-    print(json.dumps(line), flush=True)
+    emit(line, args)
     model.free()
 
 def run_ac(args):
@@ -530,7 +541,7 @@ def run_ac(args):
                      "algorithmic_bytes_per_launch": 8.0 * N, "peak_kind": peak_kind},
         "rows": rows,
     }
-    print(json.dumps(line), flush=True)
+    emit(line, args)
 
 
 def run_ablation(args):
@@ -602,7 +613,7 @@ def run_ablation(args):
                    "tuner_opts": TUNE, "parallelism": "single GPU"},
         "rows": rows,
     }
-    print(json.dumps(line), flush=True)
+    emit(line, args)
 
 
 def main():
@@ -796,10 +807,19 @@ def main():
         "clocks": clk,
         "e2e": e2e,
     }
+    # quality of the step's result, outside the timed region: decompress the
+    # blob of one more step and score it against the field
+    blob, rep = step()
+    y = q.decompress(blob)
+    m = q.compute_metrics(x, y, rep.vmax - rep.vmin, 7, 2)
+    line["quality"] = {"psnr": m.psnr, "ssim": m.ssim, "max_abs_err": m.max_abs_err,
+                       "abs_eb": rep.abs_eb, "ac_lag1": m.ac}
+    blob.free()
+    del y
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(x.cpu().numpy())
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        emit(line, args)
     if dist:
         dist.destroy_process_group()
 
