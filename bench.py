@@ -56,13 +56,17 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="compress",
-                    choices=["compress", "batch", "learned", "ssim", "ac", "ablation"],
+                    choices=["compress", "batch", "learned", "ssim", "ac", "ablation",
+                             "streams"],
                     help="compress: the single-field step (default); batch: 48 2-D + 48 "
                          "uneven 3-D fields through one batched plan; learned: train the "
                          "tuner network, then learned vs sampled tuning; ssim: SSIM targets "
                          "0.99 / 0.999, network proposes, sampled trials verify; ac: the "
                          "error-autocorrelation reduction and the AC-preferred tuning mode; "
-                         "ablation: SZ3-like / +AP / +S / +LIS / QoZ rate-distortion")
+                         "ablation: SZ3-like / +AP / +S / +LIS / QoZ rate-distortion; "
+                         "streams: the compress step from --streams host threads at once, "
+                         "each on its own CUDA stream")
+    ap.add_argument("--streams", type=int, default=3, help="streams: host threads / streams")
     ap.add_argument("--train", type=int, default=2000, help="learned: training fields")
     ap.add_argument("--log", default=None,
                     help="also append the JSON line to this JSONL file (one line per run)")
@@ -616,6 +620,112 @@ def run_ablation(args):
     emit(line, args)
 
 
+def run_streams(args):
+    """The compress step's whole-job throughput when S host threads issue
+    steps at once, each on its own CUDA stream, so that one step's
+    host-synchronised tuner (its launches are small and its read-back waits)
+    overlaps the other steps' HBM-bound levels.  The K timed steps are split
+    over the threads; one event before (every stream waits on it) and one
+    after (recorded once every stream's last event has been waited on)
+    bracket the whole span on the device.  The level-1 launches are timed by
+    the library's events on their own streams: with other streams' kernels
+    running beside them their durations include the sharing, so the
+    roofline fraction here is lower than on the single-stream line."""
+    import threading
+    import torch
+    import paper_2310_14133_gb300 as q
+    import synth
+    S = max(1, args.streams)
+    n = args.n
+    N = n ** 3
+    x = synth.config2_field(n, device="cuda")
+    topts = q.make_tune_opts(**TUNE)
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream() for _ in range(S)]
+    ends = [torch.cuda.Event() for _ in range(S)]
+    share = [args.steps // S + (1 if i < args.steps % S else 0) for i in range(S)]
+    start_ev = torch.cuda.Event(enable_timing=True)
+    errors = []
+
+    def step(st):
+        rep = q.tune(x, REL_EB, q.METRIC_MAXERR, float("nan"), topts, stream=st)
+        q.compress_abs(x, rep.abs_eb, rep.params, stream=st).free()
+
+    def worker(i, nsteps, gate, timed):
+        try:
+            torch.cuda.set_device(x.device)
+            st = streams[i]
+            with torch.cuda.stream(st):
+                gate.wait()
+                if timed:
+                    st.wait_event(start_ev)
+                for _ in range(nsteps):
+                    step(st)
+                ends[i].record(st)
+        except Exception as ex:  # reported after the join
+            errors.append(repr(ex))
+
+    def run(counts, timed):
+        gate = threading.Barrier(S + 1)
+        ths = [threading.Thread(target=worker, args=(i, counts[i], gate, timed))
+               for i in range(S)]
+        for t in ths:
+            t.start()
+        if timed:
+            start_ev.record(torch.cuda.current_stream())
+        gate.wait()
+        for t in ths:
+            t.join()
+        if errors:
+            raise RuntimeError("; ".join(errors))
+
+    run([max(3, args.warmup)] * S, False)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    q.profile_read(reset=True)
+    q.profile_enable(True, stages=[q.STAGE_LEVEL + 1])
+    clocks.start()
+    time.sleep(0.3)
+    cur = torch.cuda.current_stream()
+    end_ev = torch.cuda.Event(enable_timing=True)
+    run(share, True)
+    for e in ends:
+        cur.wait_event(e)
+    end_ev.record(cur)
+    torch.cuda.synchronize()
+    ms = start_ev.elapsed_time(end_ev)
+    clk = clocks.stop()
+    q.profile_enable(False)
+    prof = q.profile_read(reset=True)
+    ms_step = ms / args.steps
+    value = job_gbs(N, 1, ms_step * 1e-3)
+    lvl1_ms = prof.ms[q.STAGE_LEVEL + 1] / max(1, prof.calls[q.STAGE_LEVEL + 1])
+    peak, peak_kind = _peak_hbm()
+    achieved = LEVEL1_BYTES_PER_POINT * N / (lvl1_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {
+            "workload": f"{n}^3 FP32 k^-5/3 GRF + 8 tanh fronts (NYX-sized), rel bound 1e-3, "
+                        "max-CR mode",
+            "step": "qoz_tune + qoz_compress_abs with the tuned theta",
+            "streams": S, "steps_per_stream": share,
+            "l2": "input 512 MiB > 126 MB L2; no flush needed",
+            "parallelism": f"single GPU, {S} host threads x 1 CUDA stream each"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "level_tma_kernel (durations include other streams' kernels "
+                               "running beside it)",
+                     "algorithmic_bytes_per_launch": LEVEL1_BYTES_PER_POINT * N,
+                     "peak_kind": peak_kind},
+        "gpu_launches": int(prof.launches),
+        "clocks": clk,
+        "e2e": None,
+    }
+    emit(line, args)
+
+
 def main():
     args = parse()
     rank = _env_int("RANK", 0)
@@ -638,6 +748,9 @@ def main():
         return
     if args.workload == "ablation":
         run_ablation(args)
+        return
+    if args.workload == "streams":
+        run_streams(args)
         return
 
     import torch
