@@ -50,7 +50,7 @@ typedef enum {
   QOZ_ECUDA = 3,         /* a CUDA call or kernel launch failed */
   QOZ_ECORRUPT = 4,      /* serialized stream damaged (magic, size, checksum) */
   QOZ_ETIMEOUT = 5,      /* a bounded device wait gave up */
-  QOZ_EUNSUPPORTED = 6   /* valid request outside what this build handles */
+  QOZ_EUNSUPPORTED = 6   /* valid request that this compiled library does not handle */
 } qoz_status;
 
 typedef enum {
