@@ -539,7 +539,7 @@ def run_ac(args):
         "config": {"workload": f"{n}^3 FP32 k^-5/3 GRF + 8 tanh fronts (NYX-sized), rel bound "
                                "1e-3; max-CR / PSNR / AC modes",
                    "tuner_opts": TUNE, "parallelism": "single GPU",
-                   "l2": "two 512 MiB inputs > 126 MB L2; no flush needed"},
+                   "l2": f"two {4 * N / 2**20:.0f} MiB inputs > 126 MB L2; no flush needed"},
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                      "frac": gbs / peak, "traffic": None, "kernel": "ac_kernel",
                      "algorithmic_bytes_per_launch": 8.0 * N, "peak_kind": peak_kind},
@@ -711,7 +711,7 @@ def run_streams(args):
                         "max-CR mode",
             "step": "qoz_tune + qoz_compress_abs with the tuned theta",
             "streams": S, "steps_per_stream": share,
-            "l2": "input 512 MiB > 126 MB L2; no flush needed",
+            "l2": f"input {4 * N / 2**20:.0f} MiB > 126 MB L2; no flush needed",
             "parallelism": f"single GPU, {S} host threads x 1 CUDA stream each"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
@@ -900,7 +900,7 @@ def main():
                     "+ qoz_compress_abs with the tuned theta",
             "theta": {"interp": list(rep.params.interp[:5]), "order": list(rep.params.order[:5]),
                       "alpha": rep.params.alpha, "beta": rep.params.beta},
-            "l2": "input 512 MiB > 126 MB L2; no flush needed",
+            "l2": f"input {4 * N / 2**20:.0f} MiB > 126 MB L2; no flush needed",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
