@@ -109,9 +109,15 @@ qoz_status resolve(const qoz_shape& shape, const qoz_params* p, Resolved* r) {
   } else {
     for (int i = 0; i < 3; ++i) r->n[i] = shape.dims[i];
   }
-  r->N = r->n[0] * r->n[1] * r->n[2];
-  if (r->N >= (1LL << 32))
-    return fail(QOZ_EUNSUPPORTED, "fields of 2^32 points or more are not supported");
+  // the product is formed with a bound check per factor, so that extents whose
+  // product wraps around 64 bits (a corrupt header, say) are refused too
+  constexpr long long kMaxPoints = (1LL << 32) - 1;
+  r->N = 1;
+  for (int i = 0; i < 3; ++i) {
+    if (r->n[i] > kMaxPoints / r->N)
+      return fail(QOZ_EUNSUPPORTED, "fields of 2^32 points or more are not supported");
+    r->N *= r->n[i];
+  }
   qoz_params d;
   memset(&d, 0, sizeof(d));
   if (p) {

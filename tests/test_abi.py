@@ -43,3 +43,24 @@ def test_binding_marshals_without_gpu():
         assert "CUDA" in str(e)
     else:
         raise AssertionError("a CPU tensor must be rejected")
+
+
+def test_oversized_extents_are_refused_before_any_device_call():
+    # the validation runs on the host before the first CUDA call: extents
+    # whose product reaches 2^32, or wraps around 64 bits, give
+    # QOZ_EUNSUPPORTED (the field pointer is never dereferenced)
+    import ctypes as C
+    from paper_2310_14133_gb300 import _binding as b
+    lib = b.lib()
+    out = C.c_void_p()
+    fake = C.c_void_p(256)
+    for dims, nd in (((1 << 22, 1 << 22, 1 << 22), 3), ((1 << 32, 1, 1), 3),
+                     ((65536, 65536, 1), 3), ((1 << 40, 1 << 30, 0), 2),
+                     ((3, 1 << 62, 4), 3)):
+        s = b.Shape()
+        s.ndims = nd
+        for i, v in enumerate(dims):
+            s.dims[i] = v
+        st = lib.qoz_compress(fake, s, 1e-3, None, None, None, C.byref(out))
+        assert st == 6, (dims, st)
+        assert not out.value
