@@ -226,6 +226,18 @@ def _dev_ptr(t: torch.Tensor, dtype=torch.float32):
     return C.c_void_p(t.data_ptr())
 
 
+def _host_bytes(t: torch.Tensor, what: str):
+    """A host buffer the library writes or reads as raw bytes."""
+    if t.is_cuda or t.dtype != torch.uint8 or not t.is_contiguous():
+        raise ValueError(f"{what} must be a contiguous host uint8 tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _same_points(t: torch.Tensor, n: int, what: str):
+    if t.numel() != n:
+        raise ValueError(f"{what} holds {t.numel()} values, the field {n}")
+
+
 def _level_value(v, l):
     """Per-level value: a scalar applies to every level; a list gives level
     l+1 its entry l, its last entry repeating above its length."""
@@ -293,10 +305,11 @@ class Blob:
         _check(lib().qoz_blob_serialize(self._h, None, 0, C.byref(used), _stream(stream)))
         if out is None:
             out = torch.empty(used.value, dtype=torch.uint8, pin_memory=True)
+        ptr = _host_bytes(out, "out")
         if out.numel() < used.value:
             raise ValueError("output buffer too small")
-        _check(lib().qoz_blob_serialize(self._h, C.c_void_p(out.data_ptr()), out.numel(),
-                                        C.byref(used), _stream(stream)))
+        _check(lib().qoz_blob_serialize(self._h, ptr, out.numel(), C.byref(used),
+                                        _stream(stream)))
         return out[:used.value]
 
     def serialize_bound(self) -> int:
@@ -309,7 +322,7 @@ class Blob:
         """Enqueues the serialized stream into `out` (pinned host uint8) on the
         stream; complete once the stream is synchronized.  Returns its size."""
         used = C.c_size_t()
-        _check(lib().qoz_blob_serialize_async(self._h, C.c_void_p(out.data_ptr()), out.numel(),
+        _check(lib().qoz_blob_serialize_async(self._h, _host_bytes(out, "out"), out.numel(),
                                               C.byref(used), _stream(stream)))
         return used.value
 
@@ -328,6 +341,8 @@ class Blob:
 def compress(x: torch.Tensor, rel_eb: float, params: Params | None = None,
              recon: torch.Tensor | None = None, stream=None) -> Blob:
     h = C.c_void_p()
+    if recon is not None:
+        _same_points(recon, x.numel(), "recon")
     _check(lib().qoz_compress(_dev_ptr(x), _shape_of(x), float(rel_eb),
                               C.byref(params) if params is not None else None,
                               _dev_ptr(recon) if recon is not None else None,
@@ -338,6 +353,8 @@ def compress(x: torch.Tensor, rel_eb: float, params: Params | None = None,
 def compress_abs(x: torch.Tensor, abs_eb: float, params: Params | None = None,
                  recon: torch.Tensor | None = None, stream=None) -> Blob:
     h = C.c_void_p()
+    if recon is not None:
+        _same_points(recon, x.numel(), "recon")
     _check(lib().qoz_compress_abs(_dev_ptr(x), _shape_of(x), float(abs_eb),
                                   C.byref(params) if params is not None else None,
                                   _dev_ptr(recon) if recon is not None else None,
@@ -348,16 +365,16 @@ def compress_abs(x: torch.Tensor, abs_eb: float, params: Params | None = None,
 def decompress(blob: Blob, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     if out is None:
         out = torch.empty(blob.shape, dtype=torch.float32, device="cuda")
+    else:
+        _same_points(out, math.prod(blob.shape), "out")
     _check(lib().qoz_decompress(blob.handle, _dev_ptr(out), _stream(stream)))
     return out
 
 
 def deserialize(buf: torch.Tensor, stream=None) -> Blob:
     h = C.c_void_p()
-    if buf.is_cuda or buf.dtype != torch.uint8:
-        raise ValueError("expected a host uint8 buffer")
-    _check(lib().qoz_blob_deserialize(C.c_void_p(buf.data_ptr()), buf.numel(), _stream(stream),
-                                      C.byref(h)))
+    ptr = _host_bytes(buf, "buf")
+    _check(lib().qoz_blob_deserialize(ptr, buf.numel(), _stream(stream), C.byref(h)))
     b = Blob(h, ())
     inf = b.info()
     b.shape = tuple(int(inf.shape.dims[i]) for i in range(inf.shape.ndims))

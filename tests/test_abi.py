@@ -64,3 +64,22 @@ def test_oversized_extents_are_refused_before_any_device_call():
         st = lib.qoz_compress(fake, s, 1e-3, None, None, None, C.byref(out))
         assert st == 6, (dims, st)
         assert not out.value
+
+
+def test_binding_checks_buffers_before_the_library():
+    # sizes and host buffers are checked in the binding, so a wrong buffer
+    # raises instead of letting the library write past its end
+    import pytest
+    import torch
+    import paper_2310_14133_gb300 as q
+    from paper_2310_14133_gb300 import _binding as b
+    with pytest.raises(ValueError):
+        q.deserialize(torch.zeros(64, dtype=torch.uint8)[::2])       # not contiguous
+    with pytest.raises(ValueError):
+        q.deserialize(torch.zeros(16, dtype=torch.float32))          # not bytes
+    with pytest.raises(ValueError):
+        b._same_points(torch.zeros(7), 8, "out")
+    b._same_points(torch.zeros(2, 4), 8, "out")
+    with pytest.raises(ValueError):
+        b._host_bytes(torch.zeros(8, dtype=torch.int16), "out")
+    assert b._host_bytes(torch.zeros(8, dtype=torch.uint8), "out").value

@@ -326,3 +326,22 @@ def test_full_size_512(q, orc, eps):
     x = xg.cpu().numpy()
     del xg
     run_parity(q, orc, x, eps, interp=1, order=0, alpha=1.5, beta=4.0)
+
+
+def test_binding_rejects_wrong_sized_buffers(q):
+    # the checks raise in the binding before the library is called
+    x = torch.randn((8, 9, 10), device="cuda")
+    with pytest.raises(ValueError):
+        q.compress(x, 1e-3, recon=torch.empty(719, device="cuda"))
+    with pytest.raises(ValueError):
+        q.compress_abs(x, 1e-2, recon=torch.empty(721, device="cuda"))
+    blob = q.compress(x, 1e-3)
+    with pytest.raises(ValueError):
+        q.decompress(blob, torch.empty(10, device="cuda"))
+    with pytest.raises(ValueError):
+        blob.serialize(out=torch.empty(1 << 16, dtype=torch.uint8, device="cuda"))
+    with pytest.raises(ValueError):
+        blob.serialize_async(torch.empty(1 << 16, dtype=torch.uint8, device="cuda"))
+    y = q.decompress(blob, torch.empty(720, device="cuda"))  # any shape of the same size
+    assert y.numel() == 720
+    blob.free()
