@@ -132,8 +132,9 @@ qoz_status qoz_value_range_noalloc(const float* d_x, int64_t n, float* d_minmax,
 qoz_status qoz_compress(const float* d_field, qoz_shape shape, double rel_eb,
                         const qoz_params* p, float* d_recon, void* stream, qoz_blob** out);
 
-/* Same with an absolute bound e >= 0 (no value-range pass; the blob's
- * vmin/vmax are then 0). */
+/* Same with an absolute bound e >= 0, the error bound of Sec. 3 given
+ * directly instead of relative to the value range (Sec. 7.1.4): no
+ * value-range pass, and the blob's vmin/vmax are then 0. */
 qoz_status qoz_compress_abs(const float* d_field, qoz_shape shape, double abs_eb,
                             const qoz_params* p, float* d_recon, void* stream, qoz_blob** out);
 
@@ -142,11 +143,18 @@ qoz_status qoz_compress_abs(const float* d_field, qoz_shape shape, double abs_eb
  * d_out: caller-owned N floats.  Asynchronous on `stream`. */
 qoz_status qoz_decompress(const qoz_blob* b, float* d_out, void* stream);
 
+/* The blob's shape, parameters, bounds and counts, and the rate estimate of
+ * Sec. 6.1 (est_bits, est_ratio: the optimal prefix-code cost of the code
+ * histogram plus 32 bits per unpredictable value and per anchor), into *info
+ * (host).  Reads the histogram back: synchronises the blob's stream. */
 qoz_status qoz_blob_get_info(const qoz_blob* b, qoz_blob_info* info);
 
-/* Device views of the blob's arrays (owned by the blob).  d_unpred_idx are
- * linear indices sorted ascending, d_unpred_val the stored values; any output
- * pointer may be NULL. */
+/* Device views of the blob's arrays (owned by the blob; valid until
+ * qoz_blob_free): the quantization codes of Sec. 5.2.2 (q + 32768 per point
+ * in array order, 0 for an unpredictable point or an anchor), the
+ * unpredictable points (d_unpred_idx linear indices sorted ascending,
+ * d_unpred_val their exact values) and the anchors of Sec. 5.2.1 (compact
+ * grid, float32).  Any output pointer may be NULL. */
 qoz_status qoz_blob_arrays(const qoz_blob* b, const uint16_t** d_codes,
                            const int64_t** d_unpred_idx, const float** d_unpred_val,
                            int64_t* n_unpred, const float** d_anchors, int64_t* n_anchors);
@@ -157,7 +165,9 @@ qoz_status qoz_blob_arrays(const qoz_blob* b, const uint16_t** d_codes,
 qoz_status qoz_blob_copy_arrays(const qoz_blob* b, uint16_t* d_codes, int64_t* d_unpred_idx,
                                 float* d_unpred_val, float* d_anchors, void* stream);
 
-/* Copy the 65536-bin histogram of the non-anchor codes to h_hist (uint32). */
+/* Copy the 65536-bin histogram of the non-anchor codes, the counts the rate
+ * estimate of Sec. 6.1 is computed from, to h_hist (host, 65536 uint32), on
+ * `stream` (NULL: the blob's stream), which it then synchronises. */
 qoz_status qoz_blob_histogram(const qoz_blob* b, uint32_t* h_hist, void* stream);
 
 /* Serialized form (format 2): a 160-byte header (magic, version, shape,
@@ -203,6 +213,9 @@ qoz_status qoz_blob_deserialize(const void* h_buf, size_t size, void* stream, qo
  * was created on (that stream must still exist). */
 void qoz_blob_free(qoz_blob* b);
 
+/* The message of the calling thread's last failed call (thread-local; an
+ * empty string if none).  Owned by the library, valid until the thread's next
+ * call. */
 const char* qoz_last_error(void);
 
 /* ---------------------------------------------------------------- batches
@@ -420,7 +433,9 @@ qoz_status qoz_tune_learned_verified(const float* d_field, qoz_shape shape, doub
                                      const qoz_tune_opts* opts, const qoz_model* model,
                                      void* stream, qoz_tune_report* out);
 
-/* ---------------------------------------------------------------- profiling */
+/* ---------------------------------------------------------------- profiling
+ * Tooling with no counterpart in the paper: per-stage device timers, a
+ * launch counter and the bounds-checking build's record. */
 
 /* Stage ids of the per-stage timers. */
 #define QOZ_PROF_STAGES 32
