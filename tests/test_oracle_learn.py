@@ -180,3 +180,59 @@ def test_adam_first_step_closed_form():
     # t = 1: bias-corrected moments are g and g^2
     assert np.allclose(p, p0 - 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-13, atol=0)
     assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+def _one_path_net():
+    """Weights with one nonzero per layer: feature 3 -> hidden-1 unit 5 ->
+    hidden-2 unit 7 -> logit 10 (W1[5, 3] = 2, W2[7, 5] = 3, W3[10, 7] = 1,
+    biases 0 except b3[4] = 0.5), normalisation mean 1, deviation 2 on
+    feature 3.  Packing: W1 (128 x 64) row-major, b1, W2 (128 x 128), b2,
+    W3 (16 x 128), b3."""
+    P = np.zeros(orc.NPARAM)
+    o_w1, o_b1 = 0, 128 * 64
+    o_w2 = o_b1 + 128
+    o_b2 = o_w2 + 128 * 128
+    o_w3 = o_b2 + 128
+    o_b3 = o_w3 + 16 * 128
+    assert o_b3 + 16 == orc.NPARAM
+    P[o_w1 + 5 * 64 + 3] = 2.0
+    P[o_w2 + 7 * 128 + 5] = 3.0
+    P[o_w3 + 10 * 128 + 7] = 1.0
+    P[o_b3 + 4] = 0.5
+    mean, sd = np.zeros(64), np.ones(64)
+    mean[3], sd[3] = 1.0, 2.0
+    return P, mean, sd
+
+
+def test_forward_hand_worked_path():
+    # f3 = 5: z3 = (5 - 1) / 2 = 2, h1[5] = relu(2 * 2) = 4, h2[7] = relu(3 * 4)
+    # = 12, logit 10 = 12; logit 4 is its bias 0.5; the others 0.  f3 = -3:
+    # z3 = -2, h1[5] = relu(-4) = 0, so only the bias remains.  Any other
+    # feature has no path to the output.
+    P, mean, sd = _one_path_net()
+    X = np.zeros((3, 64))
+    X[0, 3] = 5.0
+    X[1, 3] = -3.0
+    X[2, :] = 100.0
+    X[2, 3] = 1.0          # z3 = 0: the other features alone
+    out = orc.mlp_forward(P, mean, sd, X)
+    want = np.zeros((3, 16))
+    want[:, 4] = 0.5
+    want[0, 10] = 12.0
+    assert np.array_equal(out, want)
+
+
+def test_adam_second_step_closed_form():
+    # g1 = 1, g2 = -1 (Kingma and Ba, Algorithm 1, beta1 0.9, beta2 0.999):
+    # m2 = 0.9 * 0.1 - 0.1 = -0.01, bias-corrected -0.01 / (1 - 0.81) = -1/19;
+    # v2 = 0.999 * 0.001 + 0.001 = 0.001999, bias-corrected 0.001999 /
+    # (1 - 0.998001) = 1.  So the second step moves the parameter by
+    # +lr / 19 / (1 + eps).
+    p = np.array([0.25])
+    m, v = np.zeros(1), np.zeros(1)
+    orc.adam_step(p, np.array([1.0]), m, v, 1, lr=0.01, eps=1e-8)
+    p1 = p.copy()
+    orc.adam_step(p, np.array([-1.0]), m, v, 2, lr=0.01, eps=1e-8)
+    assert m[0] == pytest.approx(-0.01, rel=1e-12)
+    assert v[0] == pytest.approx(0.001999, rel=1e-12)
+    assert p[0] - p1[0] == pytest.approx(0.01 / 19 / (1 + 1e-8), rel=1e-10)
