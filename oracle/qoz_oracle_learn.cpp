@@ -8,7 +8,11 @@
  * The paper's concluding section names better selection policies and
  * hyper-parameter auto-tuning as future work; it prints no features or
  * network.  What is computed here is this project's
- * definition, written plainly in double precision:
+ * definition, written plainly in double precision.  Parity unpinned against
+ * the paper, which fixes no number for it: the tests pin these definitions
+ * to closed forms (features of linear, quadratic and trilinear fields; a
+ * hand-worked forward pass; Adam's first two steps) and to finite
+ * differences of the loss.
  *
  * Features, over the sampled blocks of Sec. 6.1 (each block on its own; no
  * difference reaches across a block's faces), with e = rel_eb * vrange
