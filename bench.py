@@ -402,7 +402,7 @@ def run_learned(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": f"train {args.train} fields (recipe slope U[1,4], edges "
-                               "64..256, rel bound 1e-5..1e-2), test {n}^3 k^-5/3 seed 4",
+                               f"64..256, rel bound 1e-5..1e-2), test {n}^3 k^-5/3 seed 4",
                    "tuner_opts": TUNE, "parallelism": "single GPU"},
         "speedup_sampled_over_learned": speed, "cr_gain_over_default": gain,
         "rows": rows, "train": {"fields": int(X.shape[0]), "label_s": t_label,
