@@ -208,7 +208,7 @@ def _workload_host(n, sub):
         dev = "cpu"
     if dev == "cpu" and n > 256:
         n = sub  # generating the full field on the host would dominate
-    x = synth.config2_field(n, device=dev)[:sub, :sub, :sub].contiguous()
+    x = synth.grf_fronts_field(n, device=dev)[:sub, :sub, :sub].contiguous()
     return x.cpu().numpy()
 
 
@@ -286,7 +286,7 @@ def run_batch(args):
     import torch
     import paper_2310_14133_gb300 as q
     import synth
-    fields = [f.contiguous() for _, f in synth.config3_fields(48, 48, device="cuda")]
+    fields = [f.contiguous() for _, f in synth.mixed_batch_fields(48, 48, device="cuda")]
     shapes = [tuple(f.shape) for f in fields]
     nbytes = sum(4 * f.numel() for f in fields)
     npts = nbytes // 4
@@ -356,7 +356,7 @@ def run_learned(args):
 
     def train_samples():
         for i in range(args.train):
-            sp = synth.config4_train_spec(i)
+            sp = synth.training_field_spec(i)
             x = synth.grf(sp["dims"], sp["slope"], seed=sp["seed"], n_modes=64, device="cuda")
             yield x.contiguous(), sp["rel_eb"]
 
@@ -416,7 +416,7 @@ def run_learned(args):
 def _train_model(q, learn, synth, ntrain, topts):
     def train_samples():
         for i in range(ntrain):
-            sp = synth.config4_train_spec(i)
+            sp = synth.training_field_spec(i)
             x = synth.grf(sp["dims"], sp["slope"], seed=sp["seed"], n_modes=64, device="cuda")
             yield x.contiguous(), sp["rel_eb"]
 
@@ -427,7 +427,7 @@ def _train_model(q, learn, synth, ntrain, topts):
 
 
 def run_ssim(args):
-    """The 1024^3 k^-5/3 field with 64 vortex tubes (--n to change the edge) at
+    """The --n^3 k^-5/3 field with 64 vortex tubes (the 1024^3 case: --n 1024) at
     SSIM targets 0.99 and 0.999 (7^3 windows, step 2), bound capped at 1e-2 and
     1e-3 of the value range.  The network proposes the setting and the sampled trials
     set the bound (qoz_tune_learned_verified); the sampled tuner's target mode
@@ -441,7 +441,7 @@ def run_ssim(args):
     topts = q.make_tune_opts(**TUNE)
     model = _train_model(q, learn, synth, args.train, topts)
     n = args.n
-    x = synth.config5_field(n, device="cuda").contiguous()
+    x = synth.vortex_field(n, device="cuda").contiguous()
     N = x.numel()
     vr = None
     rows = []
@@ -503,7 +503,7 @@ def run_ac(args):
     topts = q.make_tune_opts(**TUNE)
     n = args.n
     N = n ** 3
-    x = synth.config2_field(n, device="cuda")
+    x = synth.grf_fronts_field(n, device="cuda")
     rows = []
     y = torch.empty_like(x)
     for name, metric in (("max_cr", q.METRIC_MAXERR), ("psnr", q.METRIC_PSNR),
@@ -638,7 +638,7 @@ def run_streams(args):
     S = max(1, args.streams)
     n = args.n
     N = n ** 3
-    x = synth.config2_field(n, device="cuda")
+    x = synth.grf_fronts_field(n, device="cuda")
     topts = q.make_tune_opts(**TUNE)
     torch.cuda.synchronize()
     streams = [torch.cuda.Stream() for _ in range(S)]
@@ -764,7 +764,7 @@ def main():
 
     n = args.n
     N = n ** 3
-    x = synth.config2_field(n, device="cuda")
+    x = synth.grf_fronts_field(n, device="cuda")
     torch.cuda.synchronize()
     topts = q.make_tune_opts(**TUNE)
     stream = torch.cuda.current_stream()

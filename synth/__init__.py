@@ -20,11 +20,11 @@ field once and hands the same bytes to both sides.
 """
 
 from .fields import (  # noqa: F401
-    config1_field,
-    config2_field,
-    config3_fields,
-    config4_train_spec,
-    config5_field,
+    grf_trend_field,
+    grf_fronts_field,
+    mixed_batch_fields,
+    training_field_spec,
+    vortex_field,
     fronts,
     grf,
     linear_trend,

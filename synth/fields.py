@@ -160,12 +160,12 @@ def vortex_tubes(dims, seed: int, count: int = 64, device="cpu",
 
 # ---------------------------------------------------------------- workloads
 
-def config1_field(n: int = 64, device="cpu") -> torch.Tensor:
+def grf_trend_field(n: int = 64, device="cpu") -> torch.Tensor:
     """n^3 k^-5/3 field (seed 1) plus a linear trend, values in about [-10, 10]."""
     return grf((n, n, n), 5.0 / 3.0, seed=1, device=device) + linear_trend((n, n, n), device)
 
 
-def config2_field(n: int = 512, device="cpu") -> torch.Tensor:
+def grf_fronts_field(n: int = 512, device="cpu") -> torch.Tensor:
     """n^3 k^-5/3 field (seed 2) plus 8 tanh fronts of width 2 cells (NYX-sized)."""
     dims = (n, n, n)
     return grf(dims, 5.0 / 3.0, seed=2, device=device) + fronts(dims, 2000, device=device)
@@ -174,7 +174,7 @@ def config2_field(n: int = 512, device="cpu") -> torch.Tensor:
 UNEVEN_CHOICES = (100, 128, 256, 384, 500)
 
 
-def config3_fields(count2d: int = 48, count3d: int = 48, device="cpu", shape2d=(1800, 3600)):
+def mixed_batch_fields(count2d: int = 48, count3d: int = 48, device="cpu", shape2d=(1800, 3600)):
     """Batch of CESM-ATM-shaped 2D fields (zonal bands + k^-3 noise, seeds
     3000+i) and uneven 3D k^-5/3 fields (dims from UNEVEN_CHOICES, seeds
     3100+i).  Yields (name, tensor) lazily."""
@@ -188,7 +188,7 @@ def config3_fields(count2d: int = 48, count3d: int = 48, device="cpu", shape2d=(
         yield f"grf3d_{i}", grf(dims, 5.0 / 3.0, seed=3100 + i, device=device)
 
 
-def config4_train_spec(index: int):
+def training_field_spec(index: int):
     """Training-field recipe i: slope ~ U[1, 4], edge from {64,96,128,192,256},
     relative bound log-uniform in [1e-5, 1e-2], seed 40000 + i."""
     rng = np.random.Generator(np.random.PCG64(40000 + index))
@@ -198,7 +198,7 @@ def config4_train_spec(index: int):
     return {"seed": 40000 + index, "slope": slope, "dims": (edge, edge, edge), "rel_eb": rel}
 
 
-def config5_field(n: int = 1024, device="cpu") -> torch.Tensor:
+def vortex_field(n: int = 1024, device="cpu") -> torch.Tensor:
     """n^3 k^-5/3 field (seed 5) with 64 Gaussian vortex tubes."""
     dims = (n, n, n)
     return grf(dims, 5.0 / 3.0, seed=5, device=device) + vortex_tubes(dims, 5, device=device)

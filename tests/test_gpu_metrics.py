@@ -138,7 +138,7 @@ def test_ssim_256_field_vs_oracle(q, orc):
     """A field of the SSIM workload's kind (GRF plus vortex tubes) at 256^3,
     compressed at a relative bound of 1e-3 and decompressed on the GPU."""
     import synth
-    x = synth.config5_field(256, device="cuda").cpu().numpy()
+    x = synth.vortex_field(256, device="cuda").cpu().numpy()
     vr = float(x.max()) - float(x.min())
     xd = torch.from_numpy(x).cuda()
     blob = q.compress(xd, 1e-3)

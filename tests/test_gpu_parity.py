@@ -66,11 +66,11 @@ def run_parity(q, orc, x, rel=1e-3, interp=1, order=0, alpha=1.5, beta=4.0, stri
     return ref, e
 
 
-def test_config1_plain_method(q, orc):
+def test_trend_field_plain_method(q, orc):
     """64^3 k^-5/3 field + trend, eps 1e-3, cubic, order z,y,x, alpha 1.5,
     beta 4: the plain-method configuration."""
     import synth
-    x = synth.config1_field(64).numpy()
+    x = synth.grf_trend_field(64).numpy()
     ref, e = run_parity(q, orc, x, 1e-3, interp=1, order=0, alpha=1.5, beta=4.0)
     err = np.abs(x.astype(np.float64) - ref["recon"].astype(np.float64))
     assert err.max() <= e
@@ -187,7 +187,7 @@ def test_value_range(q, orc):
 
 def test_metrics(q, orc):
     import synth
-    x = synth.config1_field(48).numpy()
+    x = synth.grf_trend_field(48).numpy()
     y = (x + np.random.default_rng(3).normal(0, 0.02, x.shape)).astype(np.float32)
     vr = float(x.max()) - float(x.min())
     m = q.compute_metrics(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), vr, 7, 2)
@@ -322,7 +322,7 @@ def test_full_size_512(q, orc, eps):
     plain-method-at-scale case, whole-field parity in the launch
     configuration the benchmark times."""
     import synth
-    xg = synth.config2_field(512, device="cuda")
+    xg = synth.grf_fronts_field(512, device="cuda")
     x = xg.cpu().numpy()
     del xg
     run_parity(q, orc, x, eps, interp=1, order=0, alpha=1.5, beta=4.0)

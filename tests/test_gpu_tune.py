@@ -100,7 +100,7 @@ def test_full_size_512_sampled_tuner(q, orc):
     """The plain-method-at-scale workload: 512^3 field with fronts, 0.5 %
     sampled 33^3 blocks, 12 interpolators, alpha 5 x beta 3, max-CR mode."""
     import synth
-    xg = synth.config2_field(512, device="cuda")
+    xg = synth.grf_fronts_field(512, device="cuda")
     x = xg.cpu().numpy()
     del xg
     rep, ref = _compare(q, orc, x, 1e-3, 0, float("nan"), 32, 0.005, 6,

@@ -43,8 +43,8 @@ def test_deviation_and_seed():
     assert not torch.equal(x, synth.grf((256, 256), 1.0, seed=4, n_modes=4096))
 
 
-def test_config1_field_range():
+def test_trend_field_range():
     # the 64^3 k^-5/3 field plus its linear trend: values in about [-10, 10]
-    x = synth.config1_field(64)
+    x = synth.grf_trend_field(64)
     assert tuple(x.shape) == (64, 64, 64)
     assert -16.0 < float(x.min()) < -4.0 and 4.0 < float(x.max()) < 16.0
