@@ -88,7 +88,7 @@ float predict_1d(const float* R, int64_t p, int64_t st, int64_t c, int64_t n, in
   return s * 0.5f;
 }
 
-/* Linear-scale quantization of one point (the quantizer SZ uses):
+/* Linear-scale quantization of one point (the quantizer SZ uses, Sec. 5.1):
  * bin width 2 e_l, bin index rounded half away from zero, reconstruction
  * pred + 2 e_l q.  A point is unpredictable when its bin index does not fit
  * in the code range, or when the reconstruction misses the bound (rounding,
