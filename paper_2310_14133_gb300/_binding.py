@@ -96,6 +96,9 @@ def make_tune_opts(block=0, rate=0.0, n_orders=0, alphas=None, betas=None, ssim_
                    ssim_step=0, anchor_stride=0) -> TuneOpts:
     """Zero / None fields take the library's defaults (the paper's)."""
     o = TuneOpts()
+    for name, vals in (("alphas", alphas), ("betas", betas)):
+        if len(vals or []) > 8:
+            raise ValueError(f"at most 8 {name} (got {len(vals)})")
     o.block, o.rate, o.n_orders = block, rate, n_orders
     for i, v in enumerate(alphas or []):
         o.alphas[i] = v
@@ -238,6 +241,16 @@ def _same_points(t: torch.Tensor, n: int, what: str):
         raise ValueError(f"{what} holds {t.numel()} values, the field {n}")
 
 
+def _u8(v, what: str) -> int:
+    """A per-level entry of the parameter block (one byte).  Values that do
+    not fit are refused here rather than wrapped; which values are valid is
+    the library's check."""
+    v = int(v)
+    if not 0 <= v <= 255:
+        raise ValueError(f"{what} {v} does not fit the parameter block")
+    return v
+
+
 def _level_value(v, l):
     """Per-level value: a scalar applies to every level; a list gives level
     l+1 its entry l, its last entry repeating above its length."""
@@ -252,8 +265,8 @@ def make_params(ndims: int, interp=1, order=0, alpha=1.0, beta=1.0, anchor_strid
     p = Params()
     p.anchor_stride = anchor_stride
     for l in range(MAX_LEVELS):
-        p.interp[l] = _level_value(interp, l)
-        p.order[l] = _level_value(order, l)
+        p.interp[l] = _u8(_level_value(interp, l), "interp")
+        p.order[l] = _u8(_level_value(order, l), "order")
     p.alpha, p.beta = float(alpha), float(beta)
     return p
 

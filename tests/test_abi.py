@@ -83,3 +83,23 @@ def test_binding_checks_buffers_before_the_library():
     with pytest.raises(ValueError):
         b._host_bytes(torch.zeros(8, dtype=torch.int16), "out")
     assert b._host_bytes(torch.zeros(8, dtype=torch.uint8), "out").value
+
+
+def test_parameter_builders_refuse_values_they_cannot_hold():
+    # per-level entries are bytes: out-of-range values are refused instead of
+    # wrapping into a valid one; validity itself (order < 6, ...) is the
+    # library's check and still reaches it
+    import pytest
+    import paper_2310_14133_gb300 as q
+    for bad in (256, -1, 300):
+        with pytest.raises(ValueError):
+            q.make_params(3, order=bad)
+        with pytest.raises(ValueError):
+            q.make_params(3, interp=[1, 1, bad])
+    assert q.make_params(3, order=6).order[0] == 6
+    with pytest.raises(ValueError):
+        q.make_tune_opts(alphas=[1.0] * 9)
+    with pytest.raises(ValueError):
+        q.make_tune_opts(betas=[2.0] * 9)
+    o = q.make_tune_opts(alphas=[1.0, 1.5], betas=[2.0])
+    assert o.n_alpha == 2 and o.n_beta == 1 and o.alphas[1] == 1.5
