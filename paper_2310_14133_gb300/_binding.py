@@ -436,6 +436,17 @@ def _params_array(params, shapes):
     return (Params * len(shapes))(*params)
 
 
+def _per_field(eb, n: int):
+    """One bound per field: a scalar applies to all n fields, a sequence must
+    hold exactly n."""
+    if isinstance(eb, (int, float)):
+        return [float(eb)] * n
+    ebs = [float(v) for v in eb]
+    if len(ebs) != n:
+        raise ValueError(f"{len(ebs)} bounds for {n} fields")
+    return ebs
+
+
 class Batch:
     """A batched-compression plan for a fixed list of field shapes."""
 
@@ -458,8 +469,7 @@ class Batch:
             if tuple(f.shape) != s:
                 raise ValueError(f"field shape {tuple(f.shape)} != plan shape {s}")
         ptrs = (C.c_void_p * n)(*[_dev_ptr(f).value for f in fields])
-        ebs = [float(eb)] * n if isinstance(eb, (int, float)) else [float(v) for v in eb]
-        eba = (C.c_double * n)(*ebs)
+        eba = (C.c_double * n)(*_per_field(eb, n))
         outs = (C.c_void_p * n)()
         _check(lib().qoz_batch_compress(self._h, ptrs, eba, 1 if relative else 0,
                                         _stream(stream), outs))

@@ -103,3 +103,12 @@ def test_parameter_builders_refuse_values_they_cannot_hold():
         q.make_tune_opts(betas=[2.0] * 9)
     o = q.make_tune_opts(alphas=[1.0, 1.5], betas=[2.0])
     assert o.n_alpha == 2 and o.n_beta == 1 and o.alphas[1] == 1.5
+
+
+def test_batch_bounds_per_field():
+    import pytest
+    from paper_2310_14133_gb300 import _binding as b
+    assert b._per_field(1e-3, 3) == [1e-3] * 3
+    assert b._per_field([1e-3, 2e-3], 2) == [1e-3, 2e-3]
+    with pytest.raises(ValueError):
+        b._per_field([1e-3, 2e-3], 3)
