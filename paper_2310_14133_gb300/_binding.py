@@ -541,7 +541,8 @@ class Model:
             if a is None:
                 return None
             a = np.ascontiguousarray(a, dtype=np.float32)
-            assert a.size == n
+            if a.size != n:
+                raise ValueError(f"expected {n} values, got {a.size}")
             return a
         p, m, s = arr(params, MLP_PARAMS), arr(mean, NFEATURES), arr(sd, NFEATURES)
         _check(lib().qoz_model_set(self._h, *(C.c_void_p(a.ctypes.data) if a is not None
@@ -564,6 +565,7 @@ class Model:
 
     def gradient(self, feats: torch.Tensor, labels: torch.Tensor, stream=None):
         feats = feats.reshape(-1, NFEATURES)
+        _same_points(labels, 4 * feats.shape[0], "labels (4 per feature row)")
         g = torch.empty(MLP_PARAMS, dtype=torch.float32, device="cuda")
         loss = C.c_float()
         _check(lib().qoz_model_gradient(self._h, _dev_ptr(feats), _dev_ptr(labels, torch.int32),
@@ -574,6 +576,7 @@ class Model:
     def train_step(self, feats: torch.Tensor, labels: torch.Tensor, lr: float, want_loss=False,
                    stream=None):
         feats = feats.reshape(-1, NFEATURES)
+        _same_points(labels, 4 * feats.shape[0], "labels (4 per feature row)")
         loss = C.c_float()
         _check(lib().qoz_model_train_step(self._h, _dev_ptr(feats), _dev_ptr(labels, torch.int32),
                                           feats.shape[0], C.c_float(lr),
