@@ -516,6 +516,8 @@ def features(x: torch.Tensor, rel_eb: float, opts=None, stream=None, device_out=
     h = None
     if device_out is None:
         h = np.zeros(NFEATURES, dtype=np.float64)
+    else:
+        _same_points(device_out, NFEATURES, "device_out")
     _check(lib().qoz_features(_dev_ptr(x), _shape_of(x), float(rel_eb),
                               C.byref(opts) if opts is not None else None,
                               C.c_void_p(h.ctypes.data) if h is not None else None,
