@@ -395,8 +395,9 @@ qoz_status qoz_model_forward(const qoz_model* m, const float* d_features, int64_
                              float* d_logits, void* stream);
 /* Gradient of the loss (device, QOZ_MLP_PARAMS floats; may be NULL) for n
  * rows with labels (n x 4 int32, device: interpolator, order, alpha index,
- * beta index); h_loss (may be NULL) receives the loss and then the call
- * synchronises. */
+ * beta index, each within its head); h_loss (may be NULL) receives the loss
+ * and then the call synchronises.  A label outside its head makes the loss
+ * NaN (it is never used as an index). */
 qoz_status qoz_model_gradient(qoz_model* m, const float* d_features, const int32_t* d_labels,
                               int64_t n, float* d_grad, float* h_loss, void* stream);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on the

@@ -376,11 +376,14 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_kernel(
     float l = 0.0f;
     if (s0 + s < B) {
       const int lab = labels[(s0 + s) * 4 + hd];
+      // a label outside its head is not read through: the loss becomes NaN
+      // (the batch is invalid) and the head's gradient lacks the label term
+      const bool lab_ok = lab >= 0 && lab < len;
       float mx = sm.o[s][off];
       for (int j = 1; j < len; ++j) mx = fmaxf(mx, sm.o[s][off + j]);
       float se = 0.0f;
       for (int j = 0; j < len; ++j) se += expf(sm.o[s][off + j] - mx);
-      l = (logf(se) + mx) - sm.o[s][off + lab];
+      l = (logf(se) + mx) - (lab_ok ? sm.o[s][off + lab] : __int_as_float(0x7fc00000));
       for (int j = 0; j < len; ++j)
         sm.dout[s][off + j] = (expf(sm.o[s][off + j] - mx) / se - (j == lab ? 1.0f : 0.0f)) * invB;
     } else {
