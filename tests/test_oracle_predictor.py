@@ -318,3 +318,23 @@ def test_nonfinite_points_unpredictable(orc):
     assert np.array_equal(y.view(np.uint32), r["recon"].view(np.uint32))
     fin = np.isfinite(x)
     assert np.all(np.abs(x[fin].astype(np.float64) - y[fin]) <= e)
+
+
+def test_value_range_finite_values_only(orc):
+    # Sec. 7.1.4's value range is over the finite values: min and max equal
+    # numpy's over the finite subset wherever the non-finite values sit
+    # (first, last, between), and a field with none gives 0, 0 and count 0
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal(1000).astype(np.float32)
+    for pos in (0, 999, 500):
+        y = x.copy()
+        y[pos] = np.nan
+        y[(pos + 7) % 1000] = -np.inf
+        y[(pos + 13) % 1000] = np.inf
+        fin = np.isfinite(y)
+        mn, mx, cnt = orc.value_range(y)
+        assert cnt == 997 and mn == y[fin].min() and mx == y[fin].max()
+    mn, mx, cnt = orc.value_range(np.full(16, np.nan, np.float32))
+    assert (mn, mx, cnt) == (0.0, 0.0, 0)
+    mn, mx, cnt = orc.value_range(np.array([np.inf, 2.5, -np.inf], np.float32))
+    assert (mn, mx, cnt) == (2.5, 2.5, 1)
