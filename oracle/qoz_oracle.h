@@ -49,7 +49,8 @@ int64_t orc_value_range(const float* x, int64_t n, float* out_min, float* out_ma
  * l = 1..L, written to el[l-1].  alpha^(l-1) by repeated multiplication. */
 void orc_level_bounds(double e, double alpha, double beta, int L, double* el);
 
-/* Permutation table entry: axes of order index `ord` for ndims axes. */
+/* Permutation table entry: axes of order index `ord` for ndims axes (the
+ * dimension orders of Sec. 5.2, enumerated lexicographically). */
 void orc_order_axes(int ndims, int ord, int* axes);
 
 /* Multi-level interpolation predictor + linear-scale quantizer (Sec. 5).
@@ -65,17 +66,19 @@ int orc_compress(const float* x, int ndims, const int64_t* dims, double e,
                  int64_t* unpred_idx, float* unpred_val, int64_t cap, int64_t* n_unpred,
                  orc_level_stats* stats);
 
-/* Mirror of orc_compress: rebuilds the field from codes, anchors and the
- * sorted unpredictable list. */
+/* Mirror of orc_compress (decompression, Sec. 5.1): rebuilds the field from
+ * codes, anchors and the sorted unpredictable list. */
 int orc_decompress(const uint16_t* codes, int ndims, const int64_t* dims, double e,
                    const orc_params* p, const float* anchors,
                    const int64_t* unpred_idx, const float* unpred_val, int64_t n_unpred,
                    float* out);
 
-/* Number of anchor points (all coordinates multiples of the stride). */
+/* Number of anchor points (Sec. 5.2.1: all coordinates multiples of the
+ * stride). */
 int64_t orc_anchor_count(int ndims, const int64_t* dims, int anchor_stride);
 
-/* 65536-bin histogram of the quant codes of non-anchor points. */
+/* 65536-bin histogram of the quant codes of non-anchor points: the counts
+ * the rate estimate of Sec. 6.1 is computed from. */
 void orc_histogram(const uint16_t* codes, int ndims, const int64_t* dims,
                    int anchor_stride, uint64_t* hist);
 
@@ -83,10 +86,12 @@ void orc_histogram(const uint16_t* codes, int ndims, const int64_t* dims,
  * counts hist[0..K-1]; a single used symbol costs 1 bit per occurrence. */
 uint64_t orc_huffman_bits(const uint64_t* hist, int K);
 
-/* Entropy stage (qoz_oracle_entropy.cpp): Huffman code lengths of hist[0..K-1]
- * with the stated tie rule (returns the longest length, 0 if no symbol is
- * used); canonical codes from the lengths; chunked MSB-first encoding (returns
- * the total 32-bit words, < 0 on error); decoding (0 on success). */
+/* Entropy stage (qoz_oracle_entropy.cpp), the Huffman coding whose size the
+ * rate estimate of Sec. 6.1 stands for: Huffman code lengths of
+ * hist[0..K-1] with the stated tie rule (returns the longest length, 0 if no
+ * symbol is used); canonical codes from the lengths (RFC 1951 Sec. 3.2.2);
+ * chunked MSB-first encoding (returns the total 32-bit words, < 0 on error);
+ * decoding (0 on success). */
 int orc_huffman_lengths(const uint64_t* hist, int K, uint8_t* len);
 void orc_canonical_codes(const uint8_t* len, int K, uint64_t* code);
 int64_t orc_huffman_encode(const uint16_t* sym, int64_t n, int chunk, const uint8_t* len,
@@ -99,7 +104,8 @@ int orc_huffman_decode(const uint32_t* words, const uint64_t* offs, int64_t n, i
  * + 32 bits per anchor. */
 double orc_estimate_bits(const uint64_t* hist, int64_t n_unpred, int64_t n_anchors);
 
-/* Metrics, Sec. 3 */
+/* Metrics, Sec. 3: maximum absolute error; mean squared error (the MSE of
+ * Eq. (psnr)). */
 double orc_max_abs_err(const float* a, const float* b, int64_t n);
 double orc_mse(const float* a, const float* b, int64_t n);
 /* Eq. (ac): autocorrelation at lag k of the errors e_i = b_i - a_i over the
@@ -107,11 +113,13 @@ double orc_mse(const float* a, const float* b, int64_t n);
  * divided by sigma^2, mu and sigma^2 the population mean and variance of all
  * n errors; 0 when sigma^2 = 0 or n <= k. */
 double orc_autocorr(const float* a, const float* b, int64_t n, int64_t k);
-/* The same over errors cut into blocks (block j = e[starts[j] .. starts[j+1])):
- * pairs stay inside a block, mu and sigma^2 are over all errors. */
+/* Eq. (ac) over errors cut into blocks (block j = e[starts[j] ..
+ * starts[j+1])), as the tuner scores its sampled blocks (Sec. 6.1): pairs
+ * stay inside a block, mu and sigma^2 are over all errors. */
 double orc_autocorr_blocks(const double* e, const int64_t* starts, int64_t nblocks, int64_t k);
+/* Eq. (psnr): 20 log10(vrange / sqrt(MSE)), +inf when the MSE is 0. */
 double orc_psnr(const float* a, const float* b, int64_t n, double vrange);
-/* Mean SSIM over all box windows of edge `win` placed every `step` points
+/* Eq. (ssim): mean SSIM over all box windows of edge `win` placed every `step` points
  * that lie fully inside the array; c1 = (0.01 vrange)^2, c2 = (0.03 vrange)^2.
  * Returns the number of windows in *n_windows and the SUM of window SSIMs in
  * *sum (either may be NULL); the return value is the mean (NaN if none). */
@@ -168,15 +176,16 @@ typedef struct {
 int64_t orc_sample_blocks(int ndims, const int64_t* dims, int b, double rate,
                           int64_t* origins, int64_t cap, int64_t* block_dims, int64_t* stride);
 
-/* Trial compression of the sampled blocks with params p (anchor stride of
- * the blocks = p->anchor_stride) at absolute bound e, down to stop_level. */
+/* Trial compression of the sampled blocks (Sec. 6.1) with params p (anchor
+ * stride of the blocks = p->anchor_stride) at absolute bound e, down to
+ * stop_level. */
 int orc_block_trial(const float* x, int ndims, const int64_t* dims,
                     const int64_t* origins, int64_t nblocks, const int64_t* block_dims,
                     const orc_params* p, double e, int stop_level, int ssim_win, int ssim_step,
                     double vrange, orc_trial* out);
 
-/* Metric value of a trial, higher is better: PSNR (dB), SSIM, -AC (lag 1,
- * pooled over the blocks) or -max error. */
+/* Metric value of a trial, higher is better (the M of Sec. 6.3): PSNR (dB),
+ * SSIM, -AC (lag 1, pooled over the blocks) or -max error. */
 double orc_trial_metric(const orc_trial* t, int metric, double vrange);
 
 /* Table I comparison of the incumbent I = (b1, m1) with the challenger
@@ -201,8 +210,9 @@ int orc_tune(const float* x, int ndims, const int64_t* dims, double e_user, doub
 #define ORC_NOUT 16
 #define ORC_NPARAM (ORC_H * ORC_NFEAT + ORC_H + ORC_H * ORC_H + ORC_H + ORC_NOUT * ORC_H + ORC_NOUT)
 
-/* The 64 features of the sampled blocks (origins / block_dims as written by
- * orc_sample_blocks). */
+/* Learned tuner (this project's definition; the paper's concluding section
+ * leaves it to future work): the 64 features of the sampled blocks
+ * (origins / block_dims as written by orc_sample_blocks). */
 int orc_features(const float* x, int ndims, const int64_t* dims, double rel_eb, double vrange,
                  const int64_t* origins, int64_t nblocks, const int64_t* block_dims,
                  double* out);
@@ -213,7 +223,8 @@ void orc_mlp_forward(const double* params, const double* mean, const double* sd,
  * NULL) receives its gradient (ORC_NPARAM values, packed like params). */
 double orc_mlp_loss_grad(const double* params, const double* mean, const double* sd,
                          const double* X, const int32_t* labels, int64_t B, double* grad);
-/* One Adam step (t = 1 for the first step). */
+/* One Adam step (Kingma and Ba, bias-corrected moments; t = 1 for the first
+ * step). */
 void orc_adam_step(double* params, const double* grad, double* m, double* v, int64_t n,
                    int64_t t, double lr, double beta1, double beta2, double eps);
 
