@@ -1,5 +1,12 @@
 // C ABI of the library (include/qoz.h): argument checks, device memory,
 // stream-ordered orchestration of the kernels, the compressed-blob format.
+//
+// A compression runs the steps of the paper in order: the value range and
+// the bound e = eps * vrange (Sec. 7.1.4), the level-wise bounds (Eq. (ebl)),
+// the anchor points (Sec. 5.2.1), then the interpolation levels from the
+// coarsest to the finest with the linear-scale quantizer (Sec. 5.1, 5.2),
+// and the code histogram of the rate estimate (Sec. 6.1).  Decompression
+// mirrors it; the metrics follow Sec. 3.
 #include <cuda_runtime.h>
 
 #include <cmath>

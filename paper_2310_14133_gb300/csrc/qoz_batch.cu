@@ -1,4 +1,5 @@
-// Batched compression plans (qoz_batch_* in include/qoz.h).
+// Batched compression plans (qoz_batch_* in include/qoz.h): the single-field
+// method (Sec. 5.1, 5.2, Eq. (ebl)) applied to many fields at once.
 //
 // A plan fixes the shapes and parameters of nfields fields.  A run issues
 //   table uploads -> init -> value range -> bound tables -> anchors ->

@@ -1,4 +1,6 @@
-// Serialized blob format and array export.
+// Serialized blob format and array export.  The code section holds the
+// Huffman coding of the quantization codes whose size the rate estimate of
+// Sec. 6.1 stands for (canonical codes as in RFC 1951 Sec. 3.2.2).
 //
 // Layout (little-endian): a 160-byte header, then the anchors (float32), the
 // unpredictable indices (int64) and values (float32), and the code section,
