@@ -110,6 +110,12 @@ def lib():
             "orc_trial_metric": (f64, [P, i32, f64]),
             "orc_table1": (i32, [f64, f64, f64, f64, f64, f64, P]),
             "orc_tune": (i32, [P, i32, P, f64, f64, i32, f64, P, P]),
+            "orc_ab_candidate": (None, [P, i32, P, P]),
+            "orc_select_fixed": (i32, [i32, P, P, i32, RETRIAL_FN, P]),
+            "orc_target_scale": (f64, [f64, f64]),
+            "orc_target_rate": (f64, [f64, f64, f64, f64, f64]),
+            "orc_secant_step": (i32, [f64, f64, f64, f64, f64, f64, f64, P]),
+            "orc_target_pick": (i32, [i32, P, P, f64, f64]),
             "orc_features": (i32, [P, i32, P, f64, f64, P, i64, P, P]),
             "orc_mlp_forward": (None, [P, P, P, P, i64, P]),
             "orc_mlp_loss_grad": (f64, [P, P, P, P, P, i64, P]),
@@ -369,6 +375,60 @@ def table1(b1, m1, b2, m2, b2p=float("nan"), m2p=float("nan")):
     sc = C.c_double(0.0)
     r = lib().orc_table1(b1, m1, b2, m2, b2p, m2p, C.byref(sc))
     return int(r), float(sc.value)
+
+
+RETRIAL_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int, C.c_double,
+                         C.POINTER(C.c_double), C.POINTER(C.c_double))
+
+
+def ab_candidate(opts, k):
+    """(alpha, beta) of candidate k of the tuner's search."""
+    a, b = C.c_double(), C.c_double()
+    lib().orc_ab_candidate(C.byref(opts), int(k), C.byref(a), C.byref(b))
+    return float(a.value), float(b.value)
+
+
+def select_fixed(B, M, maxerr_mode=False, retrial=None):
+    """Sec. 6.3.2 keep-best over candidates in order.  retrial(k, scale) ->
+    (B', M') supplies solution II's second point when Table I asks for it.
+    Returns the kept index."""
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    M = np.ascontiguousarray(M, dtype=np.float64)
+
+    def cb(_ctx, k, scale, pb, pm):
+        if retrial is None:
+            return 1
+        b, m = retrial(int(k), float(scale))
+        pb[0], pm[0] = float(b), float(m)
+        return 0
+
+    fn = RETRIAL_FN(cb)
+    r = lib().orc_select_fixed(len(B), _ptr(B), _ptr(M), 1 if maxerr_mode else 0, fn, None)
+    if r < 0:
+        raise ValueError("orc_select_fixed failed")
+    return int(r)
+
+
+def target_scale(M, target):
+    return float(lib().orc_target_scale(float(M), float(target)))
+
+
+def target_rate(B, M, B2, M2, target):
+    return float(lib().orc_target_rate(float(B), float(M), float(B2), float(M2), float(target)))
+
+
+def secant_step(ea, ma, eb, mb, target, e0, e_user):
+    """Returns the next bound of the target mode's secant, or None (no step)."""
+    en = C.c_double(0.0)
+    r = lib().orc_secant_step(float(ea), float(ma), float(eb), float(mb), float(target),
+                              float(e0), float(e_user), C.byref(en))
+    return float(en.value) if r else None
+
+
+def target_pick(e, M, target, e_user):
+    e = np.ascontiguousarray(e, dtype=np.float64)
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    return int(lib().orc_target_pick(len(e), _ptr(e), _ptr(M), float(target), float(e_user)))
 
 
 def make_tune_opts(ndims: int, block=None, rate=None, n_orders=None, alphas=None, betas=None,

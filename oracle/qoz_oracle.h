@@ -197,6 +197,32 @@ double orc_trial_metric(const orc_trial* t, int metric, double vrange);
 int orc_table1(double b1, double m1, double b2, double m2, double b2p, double m2p,
                double* second_scale);
 
+/* Sec. 6.3.2 keep-best over n candidates taken in order (alpha ascending,
+ * then beta), from each one's rate B[k] and metric M[k] at the user's bound.
+ * The incumbent is solution I, the new candidate solution II; when Table I
+ * needs II's second point (0.8 e in case 3, 1.2 e in case 4) retrial(ctx, k,
+ * scale, &B', &M') supplies it (nonzero return: failure).  maxerr_mode
+ * compares B alone (strictly lower replaces).  Returns the kept index, or -1
+ * on failure. */
+/* Candidate k (0 .. n_alpha n_beta - 1) of the (alpha, beta) search: alpha
+ * ascending in the outer loop, beta in the inner one. */
+void orc_ab_candidate(const orc_tune_opts* o, int k, double* alpha, double* beta);
+typedef int (*orc_retrial_fn)(void* ctx, int k, double scale, double* b, double* m);
+int orc_select_fixed(int n, const double* B, const double* M, int maxerr_mode,
+                     orc_retrial_fn retrial, void* ctx);
+
+/* Target mode (this project's reading of a target PSNR / SSIM): scale of a
+ * candidate's second point (1.2 if M meets the target, else 0.8); the rate
+ * at the target on the line through the two points; one secant step on
+ * (log e, M) clamped to [e0/16, e_user] (returns 0: no step); the final
+ * pick: the largest tried bound <= e_user that met the target, else the
+ * smallest tried bound. */
+double orc_target_scale(double M, double target);
+double orc_target_rate(double B, double M, double B2, double M2, double target);
+int orc_secant_step(double ea, double ma, double eb, double mb, double target, double e0,
+                    double e_user, double* e_next);
+int orc_target_pick(int n, const double* e, const double* M, double target, double e_user);
+
 /* Whole tuner.  metric: ORC_METRIC_*; target NaN selects the paper's
  * fixed-bound mode (max-error metric: maximise compression ratio; PSNR / SSIM:
  * Table I comparisons at e); a finite target selects the target mode. */

@@ -199,6 +199,82 @@ int orc_table1(double b1, double m1, double b2, double m2, double b2p, double m2
   return m1 >= m_line ? 0 : 1;
 }
 
+/* Candidate k of the (alpha, beta) search: alpha ascending in the outer
+ * loop, beta in the inner one (reading A10's visiting order). */
+void orc_ab_candidate(const orc_tune_opts* o, int k, double* alpha, double* beta) {
+  *alpha = o->alphas[k / o->n_beta];
+  *beta = o->betas[k % o->n_beta];
+}
+
+/* Sec. 6.3.2: the setting kept over the candidates taken in order.  The
+ * incumbent is solution I and each new candidate solution II; when Table I
+ * asks for a second point of II (case 3: 0.8 e, case 4: 1.2 e) it comes from
+ * retrial.  In the max-error (max-CR) mode only B counts (Sec. 7.2.2): a
+ * candidate replaces the incumbent when its rate is strictly lower. */
+int orc_select_fixed(int n, const double* B, const double* M, int maxerr_mode,
+                     orc_retrial_fn retrial, void* ctx) {
+  if (n <= 0) return -1;
+  int best = 0;
+  for (int k = 1; k < n; ++k) {
+    bool replace;
+    if (maxerr_mode) {
+      replace = B[k] < B[best];
+    } else {
+      double scale = 0.0;
+      int r = orc_table1(B[best], M[best], B[k], M[k], NAN, NAN, &scale);
+      if (r < 0) {
+        double b2 = 0.0, m2 = 0.0;
+        if (!retrial || retrial(ctx, k, scale, &b2, &m2) != 0) return -1;
+        r = orc_table1(B[best], M[best], B[k], M[k], b2, m2, &scale);
+      }
+      replace = r == 1;
+    }
+    if (replace) best = k;
+  }
+  return best;
+}
+
+/* Target mode (reading A11): the second point of a candidate is taken at
+ * 1.2 e0 when the first already meets the target (a larger bound lowers the
+ * rate), else at 0.8 e0. */
+double orc_target_scale(double M, double target) { return M >= target ? 1.2 : 0.8; }
+
+/* Bit rate where the line through (B, M) and (B2, M2) reaches the target;
+ * with equal metrics the lower rate if the target is met, else +inf. */
+double orc_target_rate(double B, double M, double B2, double M2, double target) {
+  if (M2 == M) return M >= target ? (B < B2 ? B : B2) : INFINITY;
+  return B + (target - M) * (B2 - B) / (M2 - M);
+}
+
+/* One secant step on (log e, M) through the last two points a and b toward
+ * M = target, clamped to [e0 / 16, e_user].  Returns 0 (no step) when the
+ * two metrics are equal or the step lands on b's bound. */
+int orc_secant_step(double ea, double ma, double eb, double mb, double target, double e0,
+                    double e_user, double* e_next) {
+  if (ma == mb) return 0;
+  const double le = std::log(eb) + (target - mb) * (std::log(ea) - std::log(eb)) / (ma - mb);
+  double en = std::exp(le);
+  if (en > e_user) en = e_user;
+  if (en < e0 / 16.0) en = e0 / 16.0;
+  if (en == eb) return 0;
+  *e_next = en;
+  return 1;
+}
+
+/* The bound finally used: the largest tried bound (not above e_user) whose
+ * metric met the target; when none did, the smallest tried bound. */
+int orc_target_pick(int n, const double* e, const double* M, double target, double e_user) {
+  int pick = -1;
+  for (int k = 0; k < n; ++k)
+    if (M[k] >= target && e[k] <= e_user && (pick < 0 || e[k] > e[pick])) pick = k;
+  if (pick < 0) {
+    pick = 0;
+    for (int k = 1; k < n; ++k)
+      if (e[k] < e[pick]) pick = k;
+  }
+  return pick;
+}
+
 int orc_tune(const float* x, int ndims, const int64_t* dims, double e_user, double vrange,
              int metric, double target, const orc_tune_opts* o, orc_tune_result* out) {
   std::memset(out, 0, sizeof(*out));
@@ -274,101 +350,90 @@ int orc_tune(const float* x, int ndims, const int64_t* dims, double e_user, doub
     fp.order[l - 1] = bp.order[src - 1];
   }
 
-  /* ---- alpha / beta search, Sec. 6.3 ---- */
-  double best_a = o->alphas[0], best_b = o->betas[0];
-  double best_B = 0.0, best_M = 0.0, best_score = INFINITY, best_e = e0;
-  bool have = false;
+  /* ---- alpha / beta search, Sec. 6.3: every candidate at e0, alpha
+   * ascending then beta ---- */
+  const int nc = o->n_alpha * o->n_beta;
+  std::vector<orc_params> cp(nc);
+  std::vector<double> cB(nc), cM(nc);
+  double best_B = 0.0, best_M = 0.0, best_e = e0;
+  int sel = 0;
   struct TP {
     double e, B, M;
   };
   std::vector<TP> best_pts;
-  for (int ia = 0; ia < o->n_alpha; ++ia)
-    for (int ib = 0; ib < o->n_beta; ++ib) {
-      orc_params p = bp;
-      p.alpha = o->alphas[ia];
-      p.beta = o->betas[ib];
+  for (int k = 0; k < nc; ++k) {
+    cp[k] = bp;
+    orc_ab_candidate(o, k, &cp[k].alpha, &cp[k].beta);
+    if (target_mode) continue;
+    orc_trial t;
+    if (trial(cp[k], e0, 1, &t) != 0) return 1;
+    cB[k] = t.B;
+    cM[k] = orc_trial_metric(&t, metric, vrange);
+  }
+  if (!target_mode) {
+    /* Table I keep-best; a second point of solution II is one more trial */
+    struct Ctx {
+      decltype(trial)* run;
+      const std::vector<orc_params>* cp;
+      double e0;
+      int metric;
+      double vrange;
+    } ctx{&trial, &cp, e0, metric, vrange};
+    auto retrial = [](void* c, int k, double scale, double* b, double* m) -> int {
+      Ctx* x = static_cast<Ctx*>(c);
+      orc_trial t2;
+      if ((*x->run)((*x->cp)[k], scale * x->e0, 1, &t2) != 0) return 1;
+      *b = t2.B;
+      *m = orc_trial_metric(&t2, x->metric, x->vrange);
+      return 0;
+    };
+    sel = orc_select_fixed(nc, cB.data(), cM.data(), metric == ORC_METRIC_MAXERR ? 1 : 0,
+                           retrial, &ctx);
+    if (sel < 0) return 1;
+    best_B = cB[sel];
+    best_M = cM[sel];
+  } else {
+    /* each candidate's bit rate at the target, from two sampled points;
+     * the lowest (first on ties) is kept */
+    double best_score = INFINITY;
+    bool have = false;
+    for (int k = 0; k < nc; ++k) {
       orc_trial t;
-      if (trial(p, e0, 1, &t) != 0) return 1;
-      const double B = t.B;
-      const double M = orc_trial_metric(&t, metric, vrange);
-      if (!target_mode) {
-        bool replace;
-        if (!have) {
-          replace = true;
-        } else if (metric == ORC_METRIC_MAXERR) {
-          replace = B < best_B;
-        } else {
-          double scale = 0.0;
-          int r = orc_table1(best_B, best_M, B, M, NAN, NAN, &scale);
-          if (r < 0) {
-            orc_trial t2;
-            if (trial(p, scale * e0, 1, &t2) != 0) return 1;
-            r = orc_table1(best_B, best_M, B, M, t2.B, orc_trial_metric(&t2, metric, vrange),
-                           &scale);
-          }
-          replace = r == 1;
-        }
-        if (replace) {
-          have = true;
-          best_a = p.alpha;
-          best_b = p.beta;
-          best_B = B;
-          best_M = M;
-        }
-      } else {
-        /* bit rate at the target, on the line through two sampled points */
-        const double sc = M >= target ? 1.2 : 0.8;
-        orc_trial t2;
-        if (trial(p, sc * e0, 1, &t2) != 0) return 1;
-        const double B2 = t2.B, M2 = orc_trial_metric(&t2, metric, vrange);
-        double Bstar;
-        if (M2 == M) {
-          Bstar = M >= target ? (B < B2 ? B : B2) : INFINITY;
-        } else {
-          Bstar = B + (target - M) * (B2 - B) / (M2 - M);
-        }
-        if (!have || Bstar < best_score) {
-          have = true;
-          best_score = Bstar;
-          best_a = p.alpha;
-          best_b = p.beta;
-          best_pts = {{e0, B, M}, {sc * e0, B2, M2}};
-        }
+      if (trial(cp[k], e0, 1, &t) != 0) return 1;
+      const double B = t.B, M = orc_trial_metric(&t, metric, vrange);
+      const double sc = orc_target_scale(M, target);
+      orc_trial t2;
+      if (trial(cp[k], sc * e0, 1, &t2) != 0) return 1;
+      const double B2 = t2.B, M2 = orc_trial_metric(&t2, metric, vrange);
+      const double Bstar = orc_target_rate(B, M, B2, M2, target);
+      if (!have || Bstar < best_score) {
+        have = true;
+        best_score = Bstar;
+        sel = k;
+        best_pts = {{e0, B, M}, {sc * e0, B2, M2}};
       }
     }
-  fp.alpha = best_a;
-  fp.beta = best_b;
+  }
+  fp.alpha = cp[sel].alpha;
+  fp.beta = cp[sel].beta;
 
   if (target_mode) {
     /* secant on (log e, M) for the chosen setting, at most 4 more trials */
-    orc_params p = bp;
-    p.alpha = best_a;
-    p.beta = best_b;
     for (int it = 0; it < 4; ++it) {
       const TP a = best_pts[best_pts.size() - 2];
       const TP b = best_pts[best_pts.size() - 1];
-      if (a.M == b.M) break;
-      const double le = std::log(b.e) + (target - b.M) * (std::log(a.e) - std::log(b.e)) /
-                                            (a.M - b.M);
-      double en = std::exp(le);
-      if (en > e_user) en = e_user;
-      if (en < e0 / 16.0) en = e0 / 16.0;
-      if (en == b.e) break;
+      double en = 0.0;
+      if (!orc_secant_step(a.e, a.M, b.e, b.M, target, e0, e_user, &en)) break;
       orc_trial t;
-      if (trial(p, en, 1, &t) != 0) return 1;
+      if (trial(cp[sel], en, 1, &t) != 0) return 1;
       best_pts.push_back({en, t.B, orc_trial_metric(&t, metric, vrange)});
     }
-    /* the largest tried bound that met the target, else the smallest tried */
-    int pick = -1;
-    for (size_t k = 0; k < best_pts.size(); ++k)
-      if (best_pts[k].M >= target && best_pts[k].e <= e_user &&
-          (pick < 0 || best_pts[k].e > best_pts[pick].e))
-        pick = (int)k;
-    if (pick < 0) {
-      pick = 0;
-      for (size_t k = 1; k < best_pts.size(); ++k)
-        if (best_pts[k].e < best_pts[pick].e) pick = (int)k;
+    std::vector<double> pe(best_pts.size()), pm(best_pts.size());
+    for (size_t k = 0; k < best_pts.size(); ++k) {
+      pe[k] = best_pts[k].e;
+      pm[k] = best_pts[k].M;
     }
+    const int pick = orc_target_pick((int)best_pts.size(), pe.data(), pm.data(), target, e_user);
     best_e = best_pts[pick].e;
     if (best_e > e_user) best_e = e_user;
     best_B = best_pts[pick].B;

@@ -180,3 +180,161 @@ def test_ac_mode(orc):
     assert -1.0 <= r.M <= 1.0
     with pytest.raises(ValueError):
         orc.tune(x, e, vr, orc.METRIC_AC, target=0.1, opts=o)
+
+
+# ---- the tuner's selection rules on hand-worked numbers (Sec. 6.3.2, Table I)
+
+class _Retrials:
+    """Second points of solution II, keyed by (candidate, scale); every call
+    is recorded so that a test can require exactly the calls Table I asks for."""
+
+    def __init__(self, table):
+        self.table = table
+        self.calls = []
+
+    def __call__(self, k, scale):
+        key = (k, round(scale, 6))
+        self.calls.append(key)
+        return self.table[key]
+
+
+def test_select_fixed_case3_keeps_incumbent_above_line(orc):
+    # I = (2.5, 57) incumbent, II = (2.0, 50): B_I > B_II and M_I > M_II is
+    # case 3, so II runs again at 0.8 e and lands at (3.0, 60); the line
+    # through II's two points is 55 at B_I = 2.5 and M_I = 57 lies above it.
+    rt = _Retrials({(1, 0.8): (3.0, 60.0)})
+    assert orc.select_fixed([2.5, 2.0], [57.0, 50.0], retrial=rt) == 0
+    assert rt.calls == [(1, 0.8)]
+
+
+def test_select_fixed_case4_challenger_replaces_below_line(orc):
+    # I = (2.5, 55), II = (3.0, 60): case 4, II again at 1.2 e -> (2.0, 52);
+    # the line is 56 at B_I = 2.5 and M_I = 55 lies below it: II is kept.
+    rt = _Retrials({(1, 1.2): (2.0, 52.0)})
+    assert orc.select_fixed([2.5, 3.0], [55.0, 60.0], retrial=rt) == 1
+    assert rt.calls == [(1, 1.2)]
+
+
+def test_select_fixed_equal_rate_second_point(orc):
+    # case 3 whose second point has II's own rate: I is compared with the
+    # better of II's two metrics (58), and 57 < 58 keeps II.
+    rt = _Retrials({(1, 0.8): (2.0, 58.0)})
+    assert orc.select_fixed([2.5, 2.0], [57.0, 50.0], retrial=rt) == 1
+
+
+def test_select_fixed_sequence(orc):
+    """Six candidates in order, each compared with the incumbent of its turn:
+    k1 dominates k0 (case 2); k2 ties k1 (case 1 keeps the incumbent); k3 is
+    case 3 and stays below the incumbent's point on II's line (59.5 < 60);
+    k4 is case 4 with the line at 59.6 < 60; k5 dominates (case 2)."""
+    B = [3.0, 2.0, 2.0, 1.8, 2.4, 1.5]
+    M = [55.0, 60.0, 60.0, 58.0, 62.0, 61.0]
+    rt = _Retrials({(3, 0.8): (2.2, 61.0), (4, 1.2): (2.1, 60.2)})
+    assert orc.select_fixed(B, M, retrial=rt) == 5
+    assert rt.calls == [(3, 0.8), (4, 1.2)]
+    # without k5 the incumbent after k1 survives
+    rt = _Retrials({(3, 0.8): (2.2, 61.0), (4, 1.2): (2.1, 60.2)})
+    assert orc.select_fixed(B[:5], M[:5], retrial=rt) == 1
+
+
+def test_select_fixed_maxerr_mode_rate_only(orc):
+    # the max-CR mode compares rates alone; equal rates keep the first
+    B = [3.0, 2.0, 2.0, 2.5, 1.9, 1.9]
+    M = [0.0, -1.0, 5.0, 9.0, -9.0, 9.0]
+    assert orc.select_fixed(B, M, maxerr_mode=True) == 4
+
+
+def test_target_mode_helpers(orc):
+    # second point: above the target a larger bound, below it a smaller one
+    assert orc.target_scale(61.0, 60.0) == 1.2
+    assert orc.target_scale(60.0, 60.0) == 1.2
+    assert orc.target_scale(59.0, 60.0) == 0.8
+    # rate at the target on the line through (2.0, 58) and (2.5, 62): 2.25
+    assert orc.target_rate(2.0, 58.0, 2.5, 62.0, 60.0) == pytest.approx(2.25, rel=1e-15)
+    assert orc.target_rate(2.0, 61.0, 2.5, 61.0, 60.0) == 2.0
+    assert math.isinf(orc.target_rate(2.0, 59.0, 2.5, 59.0, 60.0))
+
+
+def test_secant_step(orc):
+    # (e, M) = (1, 58) and (0.5, 66), target 60: log e moves a quarter of the
+    # way from 0.5 toward 1 in log scale, e = 0.5^(1/4)
+    assert orc.secant_step(1.0, 58.0, 0.5, 66.0, 60.0, 1.0, 2.0) == pytest.approx(
+        0.5 ** 0.25, rel=1e-14)
+    # clamped to the user bound, and to e0 / 16
+    assert orc.secant_step(1.0, 58.0, 0.5, 66.0, 60.0, 1.0, 0.7) == 0.7
+    assert orc.secant_step(1.0, 60.0, 0.5, 61.0, 100.0, 1.0, 2.0) == 1.0 / 16.0
+    # no step: equal metrics, or a step that lands on the last bound
+    assert orc.secant_step(1.0, 60.0, 0.5, 60.0, 65.0, 1.0, 2.0) is None
+    assert orc.secant_step(0.5, 66.0, 1.0, 62.0, 50.0, 1.0, 1.0) is None
+
+
+def test_target_pick(orc):
+    e = [1.0, 1.2, 0.8, 0.9]
+    M = [59.0, 58.0, 61.0, 60.5]
+    # meeting 60 dB: 0.8 and 0.9 (1.2 is above the user bound 1.0) -> 0.9
+    assert orc.target_pick(e, M, 60.0, 1.0) == 3
+    assert orc.target_pick(e, M, 60.0, 0.85) == 2
+    # nobody meets 70 dB: the smallest bound
+    assert orc.target_pick(e, M, 70.0, 1.0) == 2
+    # equal bounds that both meet the target: the first
+    assert orc.target_pick([0.9, 0.9], [61.0, 62.0], 60.0, 1.0) == 0
+
+
+@pytest.mark.parametrize("metric,eb,seed", [("PSNR", 1e-3, 11), ("SSIM", 1e-2, 21),
+                                            ("AC", 1e-3, 17)])
+def test_fixed_mode_replays_table1_loop(orc, metric, eb, seed):
+    """orc_tune's fixed-bound mode against a replay of Sec. 6.3.2 from its
+    parts: each (alpha, beta) trial in alpha-then-beta order, Table I with the
+    incumbent as solution I and the new candidate as II, II's second trial at
+    the bound scale Table I names.  The replay must take at least one second
+    trial, so that swapping I and II or the 0.8 / 1.2 factors changes it."""
+    met = getattr(orc, "METRIC_" + metric)
+    x = _field(40, seed=seed)
+    mn, mx, _ = orc.value_range(x)
+    vr = float(mx) - float(mn)
+    e = eb * vr
+    o = orc.make_tune_opts(3, block=16, rate=0.08, betas=[2.0, 3.0, 4.0])
+    r = orc.tune(x, e, vr, met, opts=o)
+    org, bd, _ = orc.sample_blocks(x.shape, 16, 0.08)
+    win = 7 if metric == "SSIM" else 0
+    alphas = [1.0, 1.25, 1.5, 1.75, 2.0]
+    betas = [2.0, 3.0, 4.0]
+
+    def run(a, b, ee):
+        p = orc.make_params(3, anchor_stride=16, alpha=a, beta=b)
+        for ll in range(4):
+            p.interp[ll], p.order[ll] = r.params.interp[ll], r.params.order[ll]
+        t = orc.block_trial(x, org, bd, p, ee, ssim_win=win, ssim_step=2, vrange=vr)
+        return t.B, orc.trial_metric(t, met, vr)
+
+    cands = [(a, b) for a in alphas for b in betas]
+    pts = [run(a, b, e) for a, b in cands]
+    best, second = 0, 0
+    for k in range(1, len(cands)):
+        (bi, mi), (bk, mk) = pts[best], pts[k]
+        d, sc = orc.table1(bi, mi, bk, mk)
+        if d < 0:
+            second += 1
+            b2, m2 = run(*cands[k], sc * e)
+            d, _ = orc.table1(bi, mi, bk, mk, b2, m2)
+        if d == 1:
+            best = k
+    assert second >= 1
+    assert (r.params.alpha, r.params.beta) == cands[best]
+    assert r.B == pts[best][0] and r.M == pts[best][1]
+    assert r.e == e
+    # Algorithm 1 (4 levels x 4 candidates), the 15 candidates, the second trials
+    assert r.n_trials == 16 + 15 + second
+
+
+def test_select_fixed_tie_on_line_keeps_incumbent(orc):
+    # II's points (2.0, 50) and (3.0, 60) put the line at exactly 55 at
+    # B_I = 2.5; I at 55 lies on it, and a tie keeps the incumbent
+    rt = _Retrials({(1, 0.8): (3.0, 60.0)})
+    assert orc.select_fixed([2.5, 2.0], [55.0, 50.0], retrial=rt) == 0
+
+
+def test_ab_candidates_alpha_outer_beta_inner(orc):
+    o = orc.make_tune_opts(3, alphas=[1.0, 1.5, 2.0], betas=[2.0, 4.0])
+    got = [orc.ab_candidate(o, k) for k in range(6)]
+    assert got == [(1.0, 2.0), (1.0, 4.0), (1.5, 2.0), (1.5, 4.0), (2.0, 2.0), (2.0, 4.0)]
