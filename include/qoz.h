@@ -112,7 +112,9 @@ qoz_status qoz_value_range(const float* d_x, int64_t n, float* h_min, float* h_m
  * Asynchronous on `stream`; calls no cudaMalloc, cudaFree or other
  * allocating routine.  The first call on a device looks up the scratch
  * array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  All calls share the one array, which keeps the
+ * before any stream capture.  The address is kept per device context: after
+ * cudaDeviceReset the next call looks it up again (make that call before
+ * any capture too).  All calls share the one array, which keeps the
  * last call's contents: calls whose work overlaps on the GPU (different
  * streams, or several host threads) race and must be serialised by the
  * caller.  The paper has no counterpart to this entry point. */
@@ -140,8 +142,19 @@ qoz_status qoz_compress_abs(const float* d_field, qoz_shape shape, double abs_eb
 
 /* Decompress (mirror of Sec. 5.1): anchors, then the same passes with
  * recon = pred + 2 e_l (code - 32768), or the stored value where code = 0.
- * d_out: caller-owned N floats.  Asynchronous on `stream`. */
+ * d_out: caller-owned N floats.  Asynchronous on `stream`, so problems the
+ * kernels find in the blob are not in the returned status: a code-0 point
+ * whose index is missing from the unpredictable list (a corrupt blob whose
+ * checksum still matched) is written as 0.0f and flagged in the blob;
+ * qoz_blob_check reads the flag. */
 qoz_status qoz_decompress(const qoz_blob* b, float* d_out, void* stream);
+
+/* Status of the blob's last decompression (this library's check; the paper
+ * has no counterpart): synchronises `stream` (NULL: the blob's stream) and
+ * returns QOZ_ECORRUPT when a code-0 point had no unpredictable-list entry
+ * or its coded stream did not decode, QOZ_OK otherwise.  The flags are
+ * cleared at the start of every qoz_decompress. */
+qoz_status qoz_blob_check(const qoz_blob* b, void* stream);
 
 /* The blob's shape, parameters, bounds and counts, and the rate estimate of
  * Sec. 6.1 (est_bits, est_ratio: the optimal prefix-code cost of the code

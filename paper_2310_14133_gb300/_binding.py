@@ -152,6 +152,7 @@ def lib():
             "qoz_blob_arrays": (i32, [P, P, P, P, P, P, P]),
             "qoz_blob_copy_arrays": (i32, [P, P, P, P, P, P]),
             "qoz_blob_histogram": (i32, [P, P, P]),
+            "qoz_blob_check": (i32, [P, P]),
             "qoz_blob_serialize": (i32, [P, P, C.c_size_t, P, P]),
             "qoz_blob_serialize_async": (i32, [P, P, C.c_size_t, P, P]),
             "qoz_blob_serialize_bound": (i32, [P, P]),
@@ -307,6 +308,11 @@ class Blob:
                                           C.c_void_p(ui.data_ptr()), C.c_void_p(uv.data_ptr()),
                                           C.c_void_p(an.data_ptr()), _stream(stream)))
         return codes, ui, uv, an
+
+    def check(self, stream=None) -> None:
+        """Raises QozError(QOZ_ECORRUPT) when the last decompression met a
+        code-0 point without an unpredictable-list entry (synchronises)."""
+        _check(lib().qoz_blob_check(self._h, _stream(stream)))
 
     def histogram(self, stream=None) -> torch.Tensor:
         h = torch.zeros(65536, dtype=torch.int32)

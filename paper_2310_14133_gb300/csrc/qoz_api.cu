@@ -441,8 +441,11 @@ qoz_status decompress_impl(const qoz_blob* b, float* d_out, cudaStream_t s) {
   if (e != cudaSuccess) return fail(QOZ_ENOMEM, "decompress scratch: %s", cudaGetErrorString(e));
   BoundTable* d_bt = (BoundTable*)scratch;
   char* coarse = (char*)scratch + 256;
-  e = launch_check(launch_bound_table(nullptr, nullptr, nullptr, 0, 0, b->abs_eb, r.p.alpha,
-                                      r.p.beta, r.L, d_bt, s));
+  // the decode flags start clean for every decompression (qoz_blob_check)
+  e = cudaMemsetAsync(b->d_err, 0, sizeof(int), s);
+  if (e == cudaSuccess)
+    e = launch_check(launch_bound_table(nullptr, nullptr, nullptr, 0, 0, b->abs_eb, r.p.alpha,
+                                        r.p.beta, r.L, d_bt, s));
   UnpredList ul{nullptr, nullptr, nullptr, 0};
   if (e == cudaSuccess)
     e = run_levels(true, r, nullptr, b->d_codes, b->d_anchors, coarse, cl, d_out, d_bt, ul,
@@ -539,6 +542,21 @@ qoz_status qoz_blob_arrays(const qoz_blob* b, const uint16_t** d_codes,
   if (n_unpred) *n_unpred = b->nu;
   if (d_anchors) *d_anchors = b->d_anchors;
   if (n_anchors) *n_anchors = b->na;
+  return QOZ_OK;
+}
+
+qoz_status qoz_blob_check(const qoz_blob* b, void* stream) {
+  if (!b) return fail(QOZ_EINVAL, "NULL blob");
+  HostStage* hs = host_stage();
+  if (!hs) return fail(QOZ_ENOMEM, "pinned staging buffer");
+  cudaStream_t s = stream ? (cudaStream_t)stream : b->stream;
+  cudaError_t e = cudaMemcpyAsync(&hs->err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "blob status read-back");
+  if (hs->err & 1)
+    return fail(QOZ_ECORRUPT, "a code-0 point has no entry in the unpredictable list");
+  if (hs->err & 4) return fail(QOZ_ECORRUPT, "the coded stream does not decode");
+  if (hs->err & 2) return fail(QOZ_ETIMEOUT, "a tile's bulk copy did not complete");
   return QOZ_OK;
 }
 

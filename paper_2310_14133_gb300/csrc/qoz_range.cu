@@ -6,10 +6,12 @@
 // bound_table_kernel folds the triples and evaluates e and e_l in double,
 // rounding each table entry to binary32 once, so the predictor's launches
 // can follow without a host round trip.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cfloat>
 #include <mutex>
+#include <utility>
 
 #include "../../include/qoz.h"
 #include "qoz_host.h"
@@ -384,7 +386,46 @@ __global__ void __launch_bounds__(kTableThreads)
 }
 
 std::mutex g_scratch_mu;
-RangeScratch* g_scratch_ptr[64] = {nullptr};
+// The scratch's device address per device, with the id of the context it was
+// taken in: a device reset destroys the context (and the module with the
+// array), and the context created next has another id, so the address is
+// looked up again.
+struct ScratchSlot {
+  RangeScratch* ptr;
+  unsigned long long ctx_id;
+};
+ScratchSlot g_scratch_slot[64] = {};
+
+// Id of the calling thread's current context (0 when the driver entry points
+// are unavailable), through the runtime's driver entry-point lookup so that
+// the library does not link the driver library.
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static const std::pair<GetCurrent, GetId> fns = [] {
+    void* a = nullptr;
+    void* b = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    const bool ok =
+        cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 4000, cudaEnableDefault, &q1) ==
+            cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &q2) ==
+            cudaSuccess &&
+        q2 == cudaDriverEntryPointSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      return std::pair<GetCurrent, GetId>(nullptr, nullptr);
+    }
+    return std::pair<GetCurrent, GetId>(reinterpret_cast<GetCurrent>(a),
+                                        reinterpret_cast<GetId>(b));
+  }();
+  if (!fns.first || !fns.second) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (fns.first(&ctx) != CUDA_SUCCESS || !ctx || fns.second(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 }  // namespace
 }  // namespace qoz
@@ -403,16 +444,20 @@ extern "C" qoz_status qoz_value_range_noalloc(const float* d_x, int64_t n, float
   if (dev < 0 || dev >= 64) return fail(QOZ_EUNSUPPORTED, "device ordinal %d", dev);
   RangeScratch* sc;
   {
-    // once per device, with that device current: the device address of the
-    // static scratch (its host-side name is not a device address)
+    // once per device context, with that device current: the device address
+    // of the static scratch (its host-side name is not a device address);
+    // the lookup itself sets the context up when none is current yet, so
+    // the context's id is taken after it
     std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
+    ScratchSlot& slot = g_scratch_slot[dev];
+    if (!slot.ptr || slot.ctx_id == 0 || slot.ctx_id != current_context_id()) {
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_range_scratch);
       if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
-      g_scratch_ptr[dev] = static_cast<RangeScratch*>(p);
+      slot.ptr = static_cast<RangeScratch*>(p);
+      slot.ctx_id = current_context_id();
     }
-    sc = g_scratch_ptr[dev];
+    sc = slot.ptr;
   }
   cudaStream_t s = (cudaStream_t)stream;
   // every partial slot the fold reads is written by this call (the range
