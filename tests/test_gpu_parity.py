@@ -98,6 +98,27 @@ def test_orders_bulk_copy_shapes(q, orc, order, shape):
     run_parity(q, orc, x, 1e-3, interp=order % 2, order=order, alpha=1.5, beta=2.0)
 
 
+@pytest.mark.parametrize("order", range(6))
+@pytest.mark.parametrize("shape", [(40, 72, 200), (100, 44, 96)])
+def test_level1_persistent_orders(q, orc, order, shape):
+    # rows of 200 / 96 values keep every array's rows on 16-byte boundaries,
+    # so level 1 runs on the persistent bulk-copy kernel: tiles on every edge
+    # and inside, ragged tails on z, y and x, both interpolators
+    import synth
+    x = synth.grf(shape, 5.0 / 3.0, seed=40 + order, n_modes=96).numpy()
+    for interp in (0, 1):
+        run_parity(q, orc, x, 1e-3, interp=interp, order=order, alpha=1.25, beta=3.0)
+
+
+def test_level1_many_tiles_per_cta(q, orc):
+    # 256^3: thousands of tiles over the resident CTAs, so each CTA reuses
+    # both pipeline stages and both code buffers many times
+    import synth
+    x = synth.grf((256, 256, 256), 5.0 / 3.0, seed=77, n_modes=128).numpy()
+    for order in (3, 4):
+        run_parity(q, orc, x, 1e-4, interp=1, order=order, alpha=1.5, beta=2.0)
+
+
 def test_mixed_levels(q, orc):
     import synth
     x = synth.grf((70, 45, 99), 2.5, seed=3, n_modes=64).numpy()
@@ -344,4 +365,79 @@ def test_binding_rejects_wrong_sized_buffers(q):
         blob.serialize_async(torch.empty(1 << 16, dtype=torch.uint8, device="cuda"))
     y = q.decompress(blob, torch.empty(720, device="cuda"))  # any shape of the same size
     assert y.numel() == 720
+    blob.free()
+
+
+def test_decompress_flags_missing_unpredictable_entry(q):
+    """A code-0 point whose index is missing from the unpredictable list (a
+    corrupt blob that no checksum caught) decompresses to 0.0 and is
+    reported by qoz_blob_check as QOZ_ECORRUPT; an intact blob checks OK."""
+    import ctypes as C
+    x = torch.randn((16, 24, 40), device="cuda").cumsum(2)
+    x[3, 4, 5] = float("nan")
+    x[9, 1, 33] = float("inf")
+    blob = q.compress(x, 1e-3)
+    y = q.decompress(blob)
+    blob.check()
+    pidx = C.c_void_p()
+    n = C.c_int64()
+    q.lib().qoz_blob_arrays(blob.handle, None, C.byref(pidx), None, C.byref(n), None, None)
+    assert n.value >= 2
+
+    class _Dev:
+        __cuda_array_interface__ = {"shape": (n.value,), "typestr": "<i8",
+                                    "data": (pidx.value, False), "version": 3}
+
+    idx = torch.as_tensor(_Dev(), device="cuda")
+    lost = int(idx[0].item())
+    idx[0] = -1                      # still sorted; the first listed point loses its entry
+    y = q.decompress(blob)
+    with pytest.raises(q.QozError) as ei:
+        blob.check()
+    assert ei.value.status == 4
+    assert y.view(-1)[lost].item() == 0.0
+    idx[0] = lost                    # restored: decompression is clean again
+    q.decompress(blob, out=y)
+    blob.check()
+    blob.free()
+
+
+def test_full_size_1024_benchmark_configuration(q, orc):
+    """The 1024^3 headline field (4 GiB) in the launch configuration the
+    benchmark times: the sampled tuner's setting (max-CR mode, 0.5 % of the
+    field in 33^3 blocks, 12 interpolators, alpha x beta), then the
+    compression at the tuner's absolute bound; codes, lists, anchors and
+    both reconstructions bit-exact against the oracle with the same setting
+    and bound."""
+    import synth
+    xg = synth.grf_fronts_field(1024, device="cuda")
+    topts = q.make_tune_opts(block=32, rate=0.005, n_orders=6,
+                             alphas=[1.0, 1.25, 1.5, 1.75, 2.0], betas=[2.0, 3.0, 4.0])
+    rep = q.tune(xg, 1e-3, q.METRIC_MAXERR, float("nan"), topts)
+    x = xg.cpu().numpy()
+    mn, mx, _ = orc.value_range(x)
+    assert rep.abs_eb == 1e-3 * (float(mx) - float(mn))
+    interp = [int(v) for v in rep.params.interp[:5]]
+    order = [int(v) for v in rep.params.order[:5]]
+    recon = torch.empty_like(xg)
+    blob = q.compress_abs(xg, rep.abs_eb, rep.params, recon=recon)
+    codes, ui, uv, an = blob.arrays()
+    hist = blob.histogram()
+    torch.cuda.synchronize()
+    op = orc.make_params(3, interp=interp, order=order, alpha=rep.params.alpha,
+                         beta=rep.params.beta)
+    ref = orc.compress(x, rep.abs_eb, op)
+    assert np.array_equal(codes.cpu().numpy().view(np.uint16), ref["codes"]), "codes"
+    del codes
+    assert np.array_equal(an.cpu().numpy().view(np.uint32), ref["anchors"].view(np.uint32))
+    assert np.array_equal(ui.cpu().numpy(), ref["unpred_idx"])
+    assert np.array_equal(uv.cpu().numpy().view(np.uint32), ref["unpred_val"].view(np.uint32))
+    rb = ref["recon"].view(np.uint32)
+    assert np.array_equal(recon.cpu().numpy().view(np.uint32), rb), "compress-side recon"
+    del recon
+    out = q.decompress(blob)
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), rb), "decompressed field"
+    blob.check()
+    oh = orc.histogram(ref["codes"], op.anchor_stride)
+    assert np.array_equal(hist.numpy().astype(np.uint64), oh), "histogram"
     blob.free()
