@@ -155,7 +155,7 @@ using L1Geo = l1::Geo<A0, A1, A2, l1::tile_for(A0).tz, l1::tile_for(A0).ty, l1::
 
 template <int A0, int A1, int A2, int IP>
 __global__ void __launch_bounds__(l1::kThr, l1::kCtasPerSm)
-    level1_kernel(const LevelLaunch a, int nt1, int nt2, int ntiles,
+    level1_kernel(const __grid_constant__ LevelLaunch a, int nt1, int nt2, int ntiles,
                   const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mrc,
                   const __grid_constant__ CUtensorMap mcc,
                   const __grid_constant__ CUtensorMap mout) {
@@ -254,8 +254,74 @@ bool try_launch_l1(const LevelLaunch& a, cudaStream_t s, cudaError_t* err) {
   return true;
 }
 
+template <int A0, int A1, int A2, int IP>
+__global__ void __launch_bounds__(l1::kThr, l1::kCtasPerSm)
+    level1_dec_kernel(const __grid_constant__ LevelLaunch a, int nt1, int nt2, int ntiles,
+                      const __grid_constant__ CUtensorMap mcode,
+                      const __grid_constant__ CUtensorMap mrc) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mbar[1];
+  l1::decompress_tiles<L1Geo<A0, A1, A2, IP>, IP>(a, smem, mbar, nt1, nt2, ntiles, &mcode, &mrc);
+}
+
+// Level 1 of a 3-D decompression on the persistent kernel, under the same
+// bulk-copy rules (16-byte rows of the code array: x extent a multiple of 8);
+// false (nothing launched) otherwise.
+template <int A0, int A1, int A2, int IP>
+bool try_launch_l1_dec(const LevelLaunch& a, cudaStream_t s, cudaError_t* err) {
+  using G = L1Geo<A0, A1, A2, IP>;
+  if (!l1_enabled() || !tma_enabled() || !a.decompress || a.is2d || a.level != 1 ||
+      a.xs[2] != 1 || !a.cin || !a.rc || !a.rout)
+    return false;
+  if (!aligned16(a.cin) || !aligned16(a.rc)) return false;
+  if (a.xs[1] % 8 || a.xs[0] % 8 || a.cs[1] % 8 || a.cs[0] % 8) return false;
+  const unsigned long long g2 = a.g[2], g1 = a.g[1], g0 = a.g[0];
+  const unsigned long long c2 = (g2 + 1) / 2, c1 = (g1 + 1) / 2, c0 = (g0 + 1) / 2;
+  CUtensorMap mcode, mrc;
+  {
+    const unsigned long long d[3] = {g2, g1, g0};
+    const unsigned long long st[2] = {2ull * a.xs[1], 2ull * a.xs[0]};
+    const unsigned bx[3] = {(unsigned)G::ECX, (unsigned)G::EY, (unsigned)G::EZ};
+    if (!encode_tensor_map_3d(&mcode, CU_TENSOR_MAP_DATA_TYPE_UINT16, a.cin, d, st, bx))
+      return false;
+  }
+  {
+    const unsigned long long d[3] = {c2, c1, c0};
+    const unsigned long long st[2] = {4ull * a.cs[1], 4ull * a.cs[0]};
+    const unsigned bx[3] = {(unsigned)G::CBX, (unsigned)G::CBY, (unsigned)G::CBZ};
+    if (!encode_tensor_map_3d(&mrc, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, a.rc, d, st, bx)) return false;
+  }
+  static unsigned long long done = 0;
+  constexpr size_t smem = G::kDecSmem;
+  static_assert((smem + 1024 + 64) * l1::kCtasPerSm <= 228 * 1024, "CTAs per SM");
+  const void* fn = (const void*)level1_dec_kernel<A0, A1, A2, IP>;
+  cudaError_t e = ensure_smem_attr(fn, &done, smem);
+  if (e != cudaSuccess) {
+    *err = e;
+    return true;
+  }
+  const long long nt0 = (a.g[0] + G::TZ - 1) / G::TZ;
+  const long long nt1 = (a.g[1] + G::TY - 1) / G::TY;
+  const long long nt2 = (a.g[2] + G::TX - 1) / G::TX;
+  const long long nt = nt0 * nt1 * nt2;
+  if (nt > 0x7fffffffLL) {
+    *err = cudaErrorInvalidConfiguration;
+    return true;
+  }
+  const long long slots = (long long)l1::kCtasPerSm * sm_count();
+  const unsigned grid = (unsigned)(nt < slots ? nt : (slots > 0 ? slots : 1));
+  level1_dec_kernel<A0, A1, A2, IP><<<grid, l1::kThr, smem, s>>>(a, (int)nt1, (int)nt2, (int)nt,
+                                                                 mcode, mrc);
+  note_launch(1);
+  *err = cudaGetLastError();
+  return true;
+}
+
 template <int A0, int A1, int A2>
 bool try_l1_order(const LevelLaunch& a, cudaStream_t s, cudaError_t* err) {
+  if (a.decompress)
+    return a.interp == 1 ? try_launch_l1_dec<A0, A1, A2, 1>(a, s, err)
+                         : try_launch_l1_dec<A0, A1, A2, 0>(a, s, err);
   return a.interp == 1 ? try_launch_l1<A0, A1, A2, 1>(a, s, err)
                        : try_launch_l1<A0, A1, A2, 0>(a, s, err);
 }
@@ -298,6 +364,10 @@ bool try_tma_order(const LevelLaunch& a, cudaStream_t s, cudaError_t* err) {
 template <int A0, int A1, int A2, int TZ, int TY, int TX, bool DECOMP, bool HIST>
 cudaError_t launch_one(const LevelLaunch& a, cudaStream_t s) {
   using G = Geo<A0, A1, A2, TZ, TY, TX>;
+  if constexpr (DECOMP && TZ > 1) {  // level 1 of a 3-D decompression
+    cudaError_t te = cudaSuccess;
+    if (try_l1_order<A0, A1, A2>(a, s, &te)) return te;
+  }
   if constexpr (!DECOMP && HIST) {  // level 1 of a compression (the histogram launch)
     cudaError_t te = cudaSuccess;
     if constexpr (TZ > 1) {

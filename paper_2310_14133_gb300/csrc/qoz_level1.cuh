@@ -46,7 +46,10 @@ namespace qoz {
 namespace l1 {
 
 constexpr int kThr = 256;
-constexpr int kCtasPerSm = 4;
+#ifndef QOZ_L1_CTAS
+#define QOZ_L1_CTAS 4
+#endif
+constexpr int kCtasPerSm = QOZ_L1_CTAS;  // resident CTAs per SM (a build-time choice)
 constexpr int kHistLo = kRadius - 512;  // shared histogram window [32768 - 512, 32768 + 512)
 constexpr int kHistWin = 1024;
 constexpr unsigned kPolls = 1u << 24;   // mbarrier polls before a tile gives up
@@ -63,6 +66,7 @@ struct Geo {
   static constexpr int HY = A0 == 1 ? 0 : 3;
   static constexpr int XL = A0 == 2 ? 0 : 4;
   static constexpr int EZ = TZ + 2 * HZ, EY = TY + 2 * HY, EX = TX + 2 * XL;
+  static constexpr unsigned a128(unsigned v) { return (v + 127u) & ~127u; }
   static constexpr int kS = EZ * EY * EX;
   __host__ __device__ static constexpr int sidx(int z, int y, int x) {
     return ((z + HZ) * EY + (y + HY)) * EX + x + XL;
@@ -83,6 +87,20 @@ struct Geo {
   }
   static constexpr int kC = TZ * TY * TX;
   __host__ __device__ static constexpr int cidx(int z, int y, int x) { return (z * TY + y) * TX + x; }
+  // decompression's code box: the codes over the field box's extent, its x
+  // range widened to [-8, TX + 8) (16-byte rows of 16-bit codes) where x has
+  // a halo
+  static constexpr int XC = XL ? 8 : 0;
+  static constexpr int ECX = TX + 2 * XC;
+  static constexpr int kCode = EZ * EY * ECX;
+  __host__ __device__ static constexpr int xidx(int z, int y, int x) {
+    return ((z + HZ) * EY + (y + HY)) * ECX + x + XC;
+  }
+  // decompression's shared memory: field box | code box | coarse box
+  static constexpr unsigned dCode = a128(4u * kS);
+  static constexpr unsigned dCB = dCode + a128(2u * kCode);
+  static constexpr unsigned kDecTxBytes = 2u * kCode + 4u * kCB;
+  static constexpr unsigned kDecSmem = 128u + dCB + a128(4u * kCB);
   // role of physical axis P in pass PASS
   template <int PASS, int P>
   __host__ __device__ static constexpr int role() {
@@ -92,7 +110,6 @@ struct Geo {
   }
   // shared memory: the tile's input (field box | coarse box | coarse
   // codes), its code buffer, the histogram window
-  static constexpr unsigned a128(unsigned v) { return (v + 127u) & ~127u; }
   static constexpr unsigned oCB = a128(4u * kS);
   static constexpr unsigned oCC = oCB + a128(4u * kCB);
   static constexpr unsigned kStage = oCC + a128(2u * kCC);
@@ -157,15 +174,15 @@ __device__ __forceinline__ bool qfast(float x, float p, const Ctx& c, float& r, 
 // Slow path of one point: the reference quantizer; an unpredictable point
 // keeps its value, gets code 0 and, when it is a valid point of this tile
 // (store), joins the list at its field index (cz, cy, cx).  Returns (bits of
-// the reconstruction, code).  Arguments by value: nothing of the caller's
-// state has to live in memory for the call.
-__device__ __noinline__ uint2 qslow(const LevelLaunch& a, float el, float two_e, float inv,
-                                    float x, float p, bool store, int cz, int cy, int cx,
-                                    int g0, int g1, int g2) {
+// the reconstruction, code).  The bound and the extents are read again from
+// the launch: the rare call holds few of the caller's registers.
+__device__ __noinline__ uint2 qslow(const LevelLaunch& a, float x, float p, bool store, int cz,
+                                    int cy, int cx) {
   uint16_t cd;
   float rr;
-  if (quantize(x, p, el, two_e, inv, &cd, &rr)) return make_uint2(__float_as_uint(rr), cd);
-  if (store && cz >= 0 && cz < g0 && cy >= 0 && cy < g1 && cx >= 0 && cx < g2) {
+  if (quantize(x, p, a.bt->el[0], a.bt->two_e[0], a.bt->inv[0], &cd, &rr))
+    return make_uint2(__float_as_uint(rr), cd);
+  if (store && cz >= 0 && cz < a.g[0] && cy >= 0 && cy < a.g[1] && cx >= 0 && cx < a.g[2]) {
     const long long xi = (long long)((unsigned long long)cz * a.xs[0] +
                                      (unsigned long long)cy * a.xs[1] +
                                      (unsigned long long)cx * a.xs[2]);
@@ -185,8 +202,7 @@ __device__ __forceinline__ void quant1(const LevelLaunch& a, const Ctx& c, float
     code = cb & 0xffffu;
     return;
   }
-  const uint2 v = qslow(a, c.el, c.two_e, c.inv, x, p, store, c.oz + lz, c.oy + ly, c.ox + lx,
-                        c.g0, c.g1, c.g2);
+  const uint2 v = qslow(a, x, p, store, c.oz + lz, c.oy + ly, c.ox + lx);
   r = __uint_as_float(v.x);
   code = v.y;
 }
@@ -199,6 +215,32 @@ __device__ __forceinline__ void quant2(const LevelLaunch& a, const Ctx& c, float
   quant1(a, c, x.x, p.x, store, lz, ly, lx, r.x, k0);
   quant1(a, c, x.y, p.y, store, lz, ly, lx + 1, r.y, k1);
   code2 = k0 | (k1 << 16);
+}
+
+// Decompression of one point whose code is 0: the stored value from the
+// sorted unpredictable list (0 and a flag when it is missing; 0 for a halo
+// position outside the field, which no valid point reads).
+__device__ __noinline__ float dslow(const LevelLaunch& a, int cz, int cy, int cx) {
+  if (cz < 0 || cz >= a.g[0] || cy < 0 || cy >= a.g[1] || cx < 0 || cx >= a.g[2]) return 0.0f;
+  const long long xi = (long long)((unsigned long long)cz * a.xs[0] +
+                                   (unsigned long long)cy * a.xs[1] +
+                                   (unsigned long long)cx * a.xs[2]);
+  float v;
+  if (!unpred_lookup(a.uidx, a.uval, a.nu, xi, &v)) {
+    v = 0.0f;
+    if (a.err) atomicOr(a.err, 1);
+  }
+  return v;
+}
+
+// Reconstruction from a code (Sec. 5.1 mirrored): p + (code - 32768) 2 e_l,
+// the same operations as qoz::dequantize; (float)(code - 32768) is read from
+// the bits of 2^23 + code.
+__device__ __forceinline__ float deq1(const LevelLaunch& a, const Ctx& c, unsigned code, float p,
+                                      int lz, int ly, int lx) {
+  if (code == 0u) return dslow(a, c.oz + lz, c.oy + ly, c.ox + lx);
+  const float q = __fsub_rn(__uint_as_float(0x4B000000u | code), kCodeBias);
+  return __fadd_rn(p, __fmul_rn(q, c.two_e));
 }
 
 // ---- segment length of a line pass: minimises rounds x per-item work
@@ -218,8 +260,10 @@ __host__ __device__ constexpr int seg_for(int NT, int lanes) {
   return best;
 }
 
-// ---- a pass along z or y.  R is the other of z and y.
-template <class G, int PASS, int IP, bool BORDER, bool WREC>
+// ---- a pass along z or y.  R is the other of z and y.  Compression
+// (DEC false): CC / C16 are the tile's coarse codes and its code buffer.
+// Decompression: CC is the code box and C16 is unused.
+template <class G, int PASS, int IP, bool BORDER, bool WREC, bool DEC>
 __device__ __forceinline__ void line_pass(const LevelLaunch& a, const Ctx& c, float* S,
                                           const float* CB, const uint16_t* CC, uint16_t* C16) {
   constexpr int P = PASS == 1 ? G::A0 : (PASS == 2 ? G::A1 : G::A2);
@@ -236,7 +280,8 @@ __device__ __forceinline__ void line_pass(const LevelLaunch& a, const Ctx& c, fl
   constexpr int SEG = seg_for(NT, NR * NXC);
   constexpr int NSEG = NT / SEG;
   constexpr int items = NSEG * NR * NXC;
-  constexpr int SP = P == 0 ? G::EY * G::EX : G::EX;       // field box stride along P
+  constexpr int SP = P == 0 ? G::EY * G::EX : G::EX;    // field box stride along P
+  constexpr int XP = P == 0 ? G::EY * G::ECX : G::ECX;  // code box stride along P
   const int gP = P == 0 ? c.g0 : c.g1;
   const int oP = P == 0 ? c.oz : c.oy;
 
@@ -249,12 +294,13 @@ __device__ __forceinline__ void line_pass(const LevelLaunch& a, const Ctx& c, fl
     const int lx = XK == kAny ? 4 * xc : 4 * xc - 4;
     const int p0 = seg * 2 * SEG;
     const int sb = P == 0 ? G::sidx(0, lr, lx) : G::sidx(lr, 0, lx);
+    const int xb = P == 0 ? G::xidx(0, lr, lx) : G::xidx(lr, 0, lx);
     const int lz_of = P == 0 ? 0 : lr, ly_of = P == 0 ? lr : 0;  // R's contribution
     const bool r_in = lr >= 0 && lr < TR;
     const bool x_in = XK == kAny || (lx >= 0 && lx < G::TX);
     const bool inside = r_in && x_in;
     if constexpr (XK == kAny) {
-      // four targets per position, two pairs
+      // four targets per position
       float4 w[SEG + 3];
 #pragma unroll
       for (int k = 0; k < SEG + 3; ++k)
@@ -263,7 +309,6 @@ __device__ __forceinline__ void line_pass(const LevelLaunch& a, const Ctx& c, fl
       for (int j = 0; j < SEG; ++j) {
         const int pos = p0 + 2 * j + 1;
         float4* tp = reinterpret_cast<float4*>(S + sb + pos * SP);
-        const float4 xv = *tp;
         const int cP = oP + pos;
         float2 plo, phi;
         plo.x = pred1<IP, BORDER>(w[j].x, w[j + 1].x, w[j + 2].x, w[j + 3].x, cP, gP);
@@ -271,13 +316,22 @@ __device__ __forceinline__ void line_pass(const LevelLaunch& a, const Ctx& c, fl
         phi.x = pred1<IP, BORDER>(w[j].z, w[j + 1].z, w[j + 2].z, w[j + 3].z, cP, gP);
         phi.y = pred1<IP, BORDER>(w[j].w, w[j + 1].w, w[j + 2].w, w[j + 3].w, cP, gP);
         const int lz = P == 0 ? pos : lz_of, ly = P == 0 ? ly_of : pos;
-        float2 rlo, rhi;
-        unsigned clo, chi;
-        quant2(a, c, make_float2(xv.x, xv.y), plo, inside, lz, ly, lx, rlo, clo);
-        quant2(a, c, make_float2(xv.z, xv.w), phi, inside, lz, ly, lx + 2, rhi, chi);
-        if (WREC) *tp = make_float4(rlo.x, rlo.y, rhi.x, rhi.y);
-        if (inside)
-          *reinterpret_cast<uint2*>(C16 + G::cidx(lz, ly, lx)) = make_uint2(clo, chi);
+        if constexpr (DEC) {
+          const uint2 cw = *reinterpret_cast<const uint2*>(CC + xb + pos * XP);
+          *tp = make_float4(deq1(a, c, cw.x & 0xffffu, plo.x, lz, ly, lx),
+                            deq1(a, c, cw.x >> 16, plo.y, lz, ly, lx + 1),
+                            deq1(a, c, cw.y & 0xffffu, phi.x, lz, ly, lx + 2),
+                            deq1(a, c, cw.y >> 16, phi.y, lz, ly, lx + 3));
+        } else {
+          const float4 xv = *tp;
+          float2 rlo, rhi;
+          unsigned clo, chi;
+          quant2(a, c, make_float2(xv.x, xv.y), plo, inside, lz, ly, lx, rlo, clo);
+          quant2(a, c, make_float2(xv.z, xv.w), phi, inside, lz, ly, lx + 2, rhi, chi);
+          if (WREC) *tp = make_float4(rlo.x, rlo.y, rhi.x, rhi.y);
+          if (inside)
+            *reinterpret_cast<uint2*>(C16 + G::cidx(lz, ly, lx)) = make_uint2(clo, chi);
+        }
       }
     } else {
       // two targets per position (x = lx and lx + 2)
@@ -301,7 +355,7 @@ __device__ __forceinline__ void line_pass(const LevelLaunch& a, const Ctx& c, fl
           float* sp = S + sb + pos * SP;
           sp[0] = w[k].x;
           sp[2] = w[k].y;
-          if (inside) {
+          if (!DEC && inside) {
             const int lz = P == 0 ? pos : lz_of, ly = P == 0 ? ly_of : pos;
             const unsigned cc = *reinterpret_cast<const unsigned*>(CC + G::ccidx(lz, ly, lx));
             uint16_t* cp = C16 + G::cidx(lz, ly, lx);
@@ -313,22 +367,27 @@ __device__ __forceinline__ void line_pass(const LevelLaunch& a, const Ctx& c, fl
 #pragma unroll
       for (int j = 0; j < SEG; ++j) {
         const int pos = p0 + 2 * j + 1;
-        float4* tp = reinterpret_cast<float4*>(S + sb + pos * SP);
-        const float4 xv = *tp;
-        float p0v, p1v;
+        float* sp = S + sb + pos * SP;
         const int cP = oP + pos;
-        p0v = pred1<IP, BORDER>(w[j].x, w[j + 1].x, w[j + 2].x, w[j + 3].x, cP, gP);
-        p1v = pred1<IP, BORDER>(w[j].y, w[j + 1].y, w[j + 2].y, w[j + 3].y, cP, gP);
+        const float p0v = pred1<IP, BORDER>(w[j].x, w[j + 1].x, w[j + 2].x, w[j + 3].x, cP, gP);
+        const float p1v = pred1<IP, BORDER>(w[j].y, w[j + 1].y, w[j + 2].y, w[j + 3].y, cP, gP);
         const int lz = P == 0 ? pos : lz_of, ly = P == 0 ? ly_of : pos;
-        float r0, r1;
-        unsigned k0, k1;
-        quant1(a, c, xv.x, p0v, inside, lz, ly, lx, r0, k0);
-        quant1(a, c, xv.z, p1v, inside, lz, ly, lx + 2, r1, k1);
-        if (WREC) *tp = make_float4(r0, xv.y, r1, xv.w);
-        if (inside) {
-          uint16_t* cp = C16 + G::cidx(lz, ly, lx);
-          cp[0] = (uint16_t)k0;
-          cp[2] = (uint16_t)k1;
+        if constexpr (DEC) {
+          const uint2 cw = *reinterpret_cast<const uint2*>(CC + xb + pos * XP);
+          sp[0] = deq1(a, c, cw.x & 0xffffu, p0v, lz, ly, lx);
+          sp[2] = deq1(a, c, cw.y & 0xffffu, p1v, lz, ly, lx + 2);
+        } else {
+          const float4 xv = *reinterpret_cast<const float4*>(sp);
+          float r0, r1;
+          unsigned k0, k1;
+          quant1(a, c, xv.x, p0v, inside, lz, ly, lx, r0, k0);
+          quant1(a, c, xv.z, p1v, inside, lz, ly, lx + 2, r1, k1);
+          if (WREC) *reinterpret_cast<float4*>(sp) = make_float4(r0, xv.y, r1, xv.w);
+          if (inside) {
+            uint16_t* cp = C16 + G::cidx(lz, ly, lx);
+            cp[0] = (uint16_t)k0;
+            cp[2] = (uint16_t)k1;
+          }
         }
       }
     }
@@ -336,7 +395,7 @@ __device__ __forceinline__ void line_pass(const LevelLaunch& a, const Ctx& c, fl
 }
 
 // ---- a pass along x: each item takes the odd x 8c + 1, + 3, + 5, + 7 of one row.
-template <class G, int PASS, int IP, bool BORDER, bool WREC>
+template <class G, int PASS, int IP, bool BORDER, bool WREC, bool DEC>
 __device__ __forceinline__ void x_pass(const LevelLaunch& a, const Ctx& c, float* S,
                                        const float* CB, const uint16_t* CC, uint16_t* C16) {
   constexpr bool FROM_CB = PASS == 1;  // the order takes x first
@@ -359,8 +418,8 @@ __device__ __forceinline__ void x_pass(const LevelLaunch& a, const Ctx& c, float
     const int base = G::sidx(lz, ly, lx0);
     const bool inside = lz >= 0 && lz < G::TZ && ly >= 0 && ly < G::TY;
     float4* t4 = reinterpret_cast<float4*>(S + base);
-    const float4 v0 = t4[0], v1 = t4[1];
     float e[7];  // even x at lx0 - 2, lx0, ..., lx0 + 10
+    float4 v0, v1;
     if (FROM_CB) {
       const int cbi = G::cbidx(lz, ly, lx0);
       const float4 cm = *reinterpret_cast<const float4*>(CB + cbi);
@@ -372,8 +431,14 @@ __device__ __forceinline__ void x_pass(const LevelLaunch& a, const Ctx& c, float
       e[4] = cm.w;
       e[5] = cn.x;
       e[6] = cn.y;
+      if (!DEC) {
+        v0 = t4[0];
+        v1 = t4[1];
+      }
     } else {
       const float4 vm = t4[-1], v2 = t4[2];
+      v0 = t4[0];
+      v1 = t4[1];
       e[0] = vm.z;
       e[1] = v0.x;
       e[2] = v0.z;
@@ -382,76 +447,113 @@ __device__ __forceinline__ void x_pass(const LevelLaunch& a, const Ctx& c, float
       e[5] = v2.x;
       e[6] = v2.z;
     }
-    const float tv[4] = {v0.y, v0.w, v1.y, v1.w};
     float r[4];
-    unsigned k[4];
+    if constexpr (DEC) {
+      const uint4 cw = *reinterpret_cast<const uint4*>(CC + G::xidx(lz, ly, lx0));
+      const unsigned cd[4] = {cw.x >> 16, cw.y >> 16, cw.z >> 16, cw.w >> 16};
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int lx = lx0 + 2 * q + 1;
-      const float p = pred1<IP, BORDER>(e[q], e[q + 1], e[q + 2], e[q + 3], c.ox + lx, c.g2);
-      quant1(a, c, tv[q], p, inside, lz, ly, lx, r[q], k[q]);
+      for (int q = 0; q < 4; ++q) {
+        const int lx = lx0 + 2 * q + 1;
+        const float p = pred1<IP, BORDER>(e[q], e[q + 1], e[q + 2], e[q + 3], c.ox + lx, c.g2);
+        r[q] = deq1(a, c, cd[q], p, lz, ly, lx);
+      }
+    } else {
+      const float tv[4] = {v0.y, v0.w, v1.y, v1.w};
+      unsigned k[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int lx = lx0 + 2 * q + 1;
+        const float p = pred1<IP, BORDER>(e[q], e[q + 1], e[q + 2], e[q + 3], c.ox + lx, c.g2);
+        quant1(a, c, tv[q], p, inside, lz, ly, lx, r[q], k[q]);
+      }
+      if (inside) {
+        uint16_t* cp = C16 + G::cidx(lz, ly, lx0);
+        if (FROM_CB) {
+          const uint2 cc = *reinterpret_cast<const uint2*>(CC + G::ccidx(lz, ly, lx0));
+          uint4 o;
+          o.x = __byte_perm(cc.x, k[0], 0x5410);
+          o.y = __byte_perm(cc.x, k[1], 0x5432);
+          o.z = __byte_perm(cc.y, k[2], 0x5410);
+          o.w = __byte_perm(cc.y, k[3], 0x5432);
+          *reinterpret_cast<uint4*>(cp) = o;
+        } else {
+          cp[1] = (uint16_t)k[0];
+          cp[3] = (uint16_t)k[1];
+          cp[5] = (uint16_t)k[2];
+          cp[7] = (uint16_t)k[3];
+        }
+      }
     }
-    if (WREC || FROM_CB) {
+    if (WREC || FROM_CB || DEC) {
       t4[0] = make_float4(e[1], r[0], e[2], r[1]);
       t4[1] = make_float4(e[3], r[2], e[4], r[3]);
-    }
-    if (inside) {
-      uint16_t* cp = C16 + G::cidx(lz, ly, lx0);
-      if (FROM_CB) {
-        const uint2 cc = *reinterpret_cast<const uint2*>(CC + G::ccidx(lz, ly, lx0));
-        uint4 o;
-        o.x = __byte_perm(cc.x, k[0], 0x5410);
-        o.y = __byte_perm(cc.x, k[1], 0x5432);
-        o.z = __byte_perm(cc.y, k[2], 0x5410);
-        o.w = __byte_perm(cc.y, k[3], 0x5432);
-        *reinterpret_cast<uint4*>(cp) = o;
-      } else {
-        cp[1] = (uint16_t)k[0];
-        cp[3] = (uint16_t)k[1];
-        cp[5] = (uint16_t)k[2];
-        cp[7] = (uint16_t)k[3];
-      }
     }
   }
 }
 
-template <class G, int PASS, int IP, bool BORDER, bool WREC>
+template <class G, int PASS, int IP, bool BORDER, bool WREC, bool DEC>
 __device__ __forceinline__ void run_pass_b(const LevelLaunch& a, const Ctx& c, float* S,
                                            const float* CB, const uint16_t* CC, uint16_t* C16) {
   constexpr int P = PASS == 1 ? G::A0 : (PASS == 2 ? G::A1 : G::A2);
   if constexpr (P == 2)
-    x_pass<G, PASS, IP, BORDER, WREC>(a, c, S, CB, CC, C16);
+    x_pass<G, PASS, IP, BORDER, WREC, DEC>(a, c, S, CB, CC, C16);
   else
-    line_pass<G, PASS, IP, BORDER, WREC>(a, c, S, CB, CC, C16);
+    line_pass<G, PASS, IP, BORDER, WREC, DEC>(a, c, S, CB, CC, C16);
 }
 
 // A pass needs the border stencils only when the tile comes within 4 points
 // of the grid's edge along the pass axis; elsewhere every target's four
 // neighbours exist.
-template <class G, int PASS, int IP, bool WREC>
+template <class G, int PASS, int IP, bool WREC, bool DEC>
 __device__ __forceinline__ void run_pass(const LevelLaunch& a, const Ctx& c, float* S,
                                          const float* CB, const uint16_t* CC, uint16_t* C16) {
   constexpr int P = PASS == 1 ? G::A0 : (PASS == 2 ? G::A1 : G::A2);
   const int o = P == 0 ? c.oz : (P == 1 ? c.oy : c.ox);
   const int g = P == 0 ? c.g0 : (P == 1 ? c.g1 : c.g2);
   if (o >= 4 && o + G::T(P) + 4 <= g)
-    run_pass_b<G, PASS, IP, false, WREC>(a, c, S, CB, CC, C16);
+    run_pass_b<G, PASS, IP, false, WREC, DEC>(a, c, S, CB, CC, C16);
   else
-    run_pass_b<G, PASS, IP, true, WREC>(a, c, S, CB, CC, C16);
+    run_pass_b<G, PASS, IP, true, WREC, DEC>(a, c, S, CB, CC, C16);
 }
 
-template <class G, int IP>
+template <class G, int IP, bool DEC>
 __device__ __forceinline__ void run_tile(const LevelLaunch& a, const Ctx& c, float* S,
                                          const float* CB, const uint16_t* CC, uint16_t* C16,
                                          bool want_rec) {
-  run_pass<G, 1, IP, true>(a, c, S, CB, CC, C16);
+  run_pass<G, 1, IP, true, DEC>(a, c, S, CB, CC, C16);
   __syncthreads();
-  run_pass<G, 2, IP, true>(a, c, S, CB, CC, C16);
+  run_pass<G, 2, IP, true, DEC>(a, c, S, CB, CC, C16);
   __syncthreads();
-  if (want_rec)
-    run_pass<G, 3, IP, true>(a, c, S, CB, CC, C16);
+  if (want_rec || DEC)
+    run_pass<G, 3, IP, true, DEC>(a, c, S, CB, CC, C16);
   else
-    run_pass<G, 3, IP, false>(a, c, S, CB, CC, C16);
+    run_pass<G, 3, IP, false, DEC>(a, c, S, CB, CC, C16);
+}
+
+// The tile's reconstruction (field box interior) into the compact output
+// rows of the level's grid, four x per item.
+template <class G>
+__device__ __forceinline__ void store_tile(const LevelLaunch& a, const Ctx& c, const float* S) {
+  const unsigned os0 = (unsigned)a.os[0], os1 = (unsigned)a.os[1];
+  const bool vec = (a.os[1] % 4) == 0 && (a.os[0] % 4) == 0 &&
+                   (reinterpret_cast<uintptr_t>(a.rout) & 15) == 0;
+  for (int g = threadIdx.x; g < G::kC / 4; g += kThr) {
+    const int lx = (g % (G::TX / 4)) * 4;
+    const int t = g / (G::TX / 4);
+    const int ly = t % G::TY, lz = t / G::TY;
+    const int cz = c.oz + lz, cy = c.oy + ly, cx = c.ox + lx;
+    if (cz >= c.g0 || cy >= c.g1 || cx >= c.g2) continue;
+    const float4 v = *reinterpret_cast<const float4*>(S + G::sidx(lz, ly, lx));
+    const unsigned oi = (unsigned)cz * os0 + (unsigned)cy * os1 + (unsigned)cx;
+    if (vec && cx + 4 <= c.g2) {
+      *reinterpret_cast<float4*>(a.rout + oi) = v;
+    } else {
+      a.rout[oi] = v.x;
+      if (cx + 1 < c.g2) a.rout[oi + 1] = v.y;
+      if (cx + 2 < c.g2) a.rout[oi + 2] = v.z;
+      if (cx + 3 < c.g2) a.rout[oi + 3] = v.w;
+    }
+  }
 }
 
 // Issues the three bulk copies of a tile into a stage (one thread).
@@ -537,31 +639,11 @@ __device__ __forceinline__ void compress_tiles(const LevelLaunch& a, unsigned ch
     }
     // every point of the tile lies inside the field
     const bool full = c.oz + G::TZ <= c.g0 && c.oy + G::TY <= c.g1 && c.ox + G::TX <= c.g2;
-    run_tile<G, IP>(a, c, S, CB, CC, C16, want_rec);
+    run_tile<G, IP, false>(a, c, S, CB, CC, C16, want_rec);
     fence_proxy_async_smem();  // code tile written: visible to the bulk store
     __syncthreads();
     if (want_rec) {
-      // the tile's reconstruction (the caller asked for it), four x per item
-      const unsigned os0 = (unsigned)a.os[0], os1 = (unsigned)a.os[1];
-      const bool vec = (a.os[1] % 4) == 0 && (a.os[0] % 4) == 0 &&
-                       (reinterpret_cast<uintptr_t>(a.rout) & 15) == 0;
-      for (int g = threadIdx.x; g < G::kC / 4; g += kThr) {
-        const int lx = (g % (G::TX / 4)) * 4;
-        const int t = g / (G::TX / 4);
-        const int ly = t % G::TY, lz = t / G::TY;
-        const int cz = c.oz + lz, cy = c.oy + ly, cx = c.ox + lx;
-        if (cz >= c.g0 || cy >= c.g1 || cx >= c.g2) continue;
-        const float4 v = *reinterpret_cast<const float4*>(S + G::sidx(lz, ly, lx));
-        const unsigned oi = (unsigned)cz * os0 + (unsigned)cy * os1 + (unsigned)cx;
-        if (vec && cx + 4 <= c.g2) {
-          *reinterpret_cast<float4*>(a.rout + oi) = v;
-        } else {
-          a.rout[oi] = v.x;
-          if (cx + 1 < c.g2) a.rout[oi + 1] = v.y;
-          if (cx + 2 < c.g2) a.rout[oi + 2] = v.z;
-          if (cx + 3 < c.g2) a.rout[oi + 3] = v.w;
-        }
-      }
+      store_tile<G>(a, c, S);  // the caller asked for the reconstruction
       __syncthreads();
     }
     if (threadIdx.x == 0) {
@@ -600,6 +682,59 @@ __device__ __forceinline__ void compress_tiles(const LevelLaunch& a, unsigned ch
   for (int k = threadIdx.x; k < kHistWin; k += kThr)
     if (SH[k]) atomicAdd(&a.hist[kHistLo + k], SH[k]);
   if (threadIdx.x == 0) bulk_wait_read0();
+}
+
+// The level-1 decompression of a 3-D field: per tile, the codes over the
+// tile and its halo and the coarse box arrive by bulk copies (the field box
+// is filled by the passes themselves); the next tile's copies are issued
+// once the passes are done, while the CTA writes the tile's reconstruction.
+template <class G, int IP>
+__device__ __forceinline__ void decompress_tiles(const LevelLaunch& a, unsigned char* smem_raw,
+                                                 uint64_t* mbar, int nt1, int nt2, int ntiles,
+                                                 const CUtensorMap* mcode,
+                                                 const CUtensorMap* mrc) {
+  unsigned char* sm = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  float* S = reinterpret_cast<float*>(sm);
+  const uint16_t* CODE = reinterpret_cast<const uint16_t*>(sm + G::dCode);
+  const float* CB = reinterpret_cast<const float*>(sm + G::dCB);
+  Ctx c;
+  c.g0 = (int)a.g[0];
+  c.g1 = (int)a.g[1];
+  c.g2 = (int)a.g[2];
+  c.el = a.bt->el[0];
+  c.two_e = a.bt->two_e[0];
+  c.inv = a.bt->inv[0];
+  auto issue = [&](int tile) {
+    const int tx = tile % nt2;
+    const int r = tile / nt2;
+    const int ox = tx * G::TX, oy = (r % nt1) * G::TY, oz = (r / nt1) * G::TZ;
+    mbar_expect_tx(&mbar[0], G::kDecTxBytes);
+    tma_load_3d(sm + G::dCode, mcode, ox - G::XC, oy - G::HY, oz - G::HZ, &mbar[0]);
+    tma_load_3d(sm + G::dCB, mrc, ox / 2 - 4, oy / 2 - 1, oz / 2 - 1, &mbar[0]);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&mbar[0], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) issue(blockIdx.x);
+  int i = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+    const bool landed = wait_polls(&mbar[0], (unsigned)i & 1u, kPolls);
+    if (!__syncthreads_and(landed)) {
+      if (threadIdx.x == 0 && a.err) atomicOr(a.err, 2);
+      return;
+    }
+    const int tx = tile % nt2;
+    const int r = tile / nt2;
+    c.ox = tx * G::TX;
+    c.oy = (r % nt1) * G::TY;
+    c.oz = (r / nt1) * G::TZ;
+    run_tile<G, IP, true>(a, c, S, CB, CODE, nullptr, true);
+    __syncthreads();  // the passes are done with the code box and the coarse box
+    if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) issue(tile + (int)gridDim.x);
+    store_tile<G>(a, c, S);
+  }
 }
 
 }  // namespace l1
