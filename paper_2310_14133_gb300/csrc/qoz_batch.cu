@@ -57,7 +57,7 @@ struct qoz_batch {
   std::vector<long long> cap;
   std::vector<Coarse> cl;
   // scratch: [bt | cnt | hs] per field (one read-back), lists, coarse grids
-  size_t off_bt = 0, off_cnt = 0, off_hs = 0;
+  size_t off_bt = 0, off_cnt = 0, off_hs = 0, off_err = 0;
   std::vector<size_t> off_uidx, off_uval, off_coarse;
   size_t scratch_bytes = 0;
   char* d_scratch = nullptr;
@@ -82,7 +82,7 @@ struct qoz_batch {
   BatchFieldDesc* h_desc = nullptr;
   LevelItem* h_items = nullptr;
   LevelTmaMaps* h_maps = nullptr;
-  char* h_back = nullptr;  // read-back of [bt | cnt | hs]
+  char* h_back = nullptr;  // read-back of [bt | cnt | hs | err]
   size_t back_bytes = 0;
   // graph
   cudaStream_t cap_stream = nullptr;
@@ -103,6 +103,9 @@ unsigned long long* cnt_of(qoz_batch* p, int f) {
   return reinterpret_cast<unsigned long long*>(p->d_scratch + p->off_cnt) + f;
 }
 int* hs_of(qoz_batch* p, int f) { return reinterpret_cast<int*>(p->d_scratch + p->off_hs) + f; }
+// Per-field status of a run: bit 2 = a level tile's bulk copy did not
+// complete (zeroed by the run's init kernel, read back with the counts).
+int* err_of(qoz_batch* p, int f) { return reinterpret_cast<int*>(p->d_scratch + p->off_err) + f; }
 
 // The level launch of (field f, level l) with the plan-owned pointers
 // (coarse grids, bound table, list); the per-run pointers (field, anchors,
@@ -266,14 +269,22 @@ bool fill_tables(qoz_batch* p, const float* const* x, const double* eb, int rel,
     d.hist = outs[f]->d_hist;
     d.ul = UnpredList{(long long*)(p->d_scratch + p->off_uidx[f]),
                       (float*)(p->d_scratch + p->off_uval[f]), cnt_of(p, f), p->cap[f]};
-    d.err = outs[f]->d_err;
+    d.err = err_of(p, f);
     d.host_sort = hs_of(p, f);
   }
+  const bool inject_wait = fault_injected("tma_wait");
   for (size_t i = 0; i < p->items.size(); ++i) {
     LevelItem it = p->items[i];
     const int f = p->refs[i].field, l = p->refs[i].level;
     const Resolved& r = p->r[f];
     it.L.x = x[f];
+    it.L.err = err_of(p, f);
+    if (l == 1 && inject_wait) {
+      // host fault injection: a barrier phase that expects bytes no copy
+      // brings, so the tile's bounded wait runs out after 4096 polls
+      it.L.extra_tx = 16;
+      it.L.wait_polls = 4096;
+    }
     if (l == r.L) it.L.rc = outs[f]->d_anchors;
     if (l == 1) {
       it.L.cout = outs[f]->d_codes;
@@ -500,6 +511,8 @@ qoz_status qoz_batch_create(const qoz_shape* shapes, int32_t nfields, const qoz_
   o += up(sizeof(unsigned long long) * nfields);
   p->off_hs = o;
   o += up(sizeof(int) * nfields);
+  p->off_err = o;
+  o += up(sizeof(int) * nfields);
   p->back_bytes = o - p->off_bt;
   p->off_uidx.resize(nfields);
   p->off_uval.resize(nfields);
@@ -585,7 +598,8 @@ qoz_status qoz_batch_compress(qoz_batch* p, const float* const* d_fields, const 
     if ((e = dev_alloc((void**)&b->d_codes, sizeof(uint16_t) * r.N, s)) != cudaSuccess ||
         (e = dev_alloc((void**)&b->d_anchors, sizeof(float) * b->na, s)) != cudaSuccess ||
         (e = dev_alloc((void**)&b->d_hist, sizeof(unsigned) * 65536, s)) != cudaSuccess ||
-        (e = dev_alloc((void**)&b->d_err, sizeof(int), s)) != cudaSuccess) {
+        (e = dev_alloc((void**)&b->d_err, sizeof(int), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(b->d_err, 0, sizeof(int), s)) != cudaSuccess) {
       free_blobs(outs, p->nf);
       return fail(QOZ_ENOMEM, "blob allocation: %s", cudaGetErrorString(e));
     }
@@ -626,6 +640,13 @@ qoz_status qoz_batch_compress(qoz_batch* p, const float* const* d_fields, const 
   const unsigned long long* cnt =
       reinterpret_cast<const unsigned long long*>(p->h_back + (p->off_cnt - p->off_bt));
   const int* hs = reinterpret_cast<const int*>(p->h_back + (p->off_hs - p->off_bt));
+  const int* errs = reinterpret_cast<const int*>(p->h_back + (p->off_err - p->off_bt));
+  for (int f = 0; f < p->nf; ++f)
+    if (errs[f] & 2) {
+      free_blobs(outs, p->nf);
+      return fail(QOZ_ETIMEOUT, "field %d: a tile's bulk copy did not complete (flag %d)", f,
+                  errs[f]);
+    }
   for (int f = 0; f < p->nf && st == QOZ_OK; ++f) {
     qoz_blob* b = outs[f];
     const long long count = (long long)cnt[f];

@@ -715,7 +715,7 @@ __device__ __forceinline__ void level_tile_tma(const LevelLaunch& a, unsigned ch
   if (threadIdx.x == 0) {
     constexpr unsigned kBytes = (unsigned)(sizeof(float) * (G::kS + G::kCB) +
                                            sizeof(uint16_t) * G::kCC);
-    mbar_expect_tx(mbar, kBytes + (unsigned)a.extra_tx);
+    mbar_expect_tx(mbar, kBytes);
     tma_load_3d(S, map_x, c.ox - 4, c.oy - G::HY, c.oz - G::HZ, mbar);
     tma_load_3d(CB, map_rc, c.ox / 2 - 4, c.oy / 2 - 2, c.oz / 2 - 2, mbar);
     tma_load_3d(CC, map_cc, c.ox / 2, c.oy / 2, c.oz / 2, mbar);
@@ -723,13 +723,27 @@ __device__ __forceinline__ void level_tile_tma(const LevelLaunch& a, unsigned ch
   if (HIST)
     for (int i = threadIdx.x; i < kTmaHistWin; i += THR) SH[i] = 0;
   bool landed = false;
-  const unsigned polls = a.wait_polls > 0 ? (unsigned)a.wait_polls : kTmaWaitPolls;
-  for (unsigned it = 0; it < polls; ++it)
+  for (unsigned it = 0; it < kTmaWaitPolls; ++it)
     if (mbar_try_wait(mbar, 0)) {
       landed = true;
       break;
     }
-  if (!__syncthreads_and(landed)) {
+  landed = __syncthreads_and(landed) != 0;
+  if (landed && a.extra_tx > 0) {
+    // host fault injection: once the copies have landed, the barrier's next
+    // phase expects bytes that never come, and its bounded wait runs out
+    // with no copy in flight
+    if (threadIdx.x == 0) mbar_expect_tx(mbar, (unsigned)a.extra_tx);
+    const unsigned polls = a.wait_polls > 0 ? (unsigned)a.wait_polls : kTmaWaitPolls;
+    bool done = false;
+    for (unsigned it = 0; it < polls; ++it)
+      if (mbar_try_wait(mbar, 1)) {
+        done = true;
+        break;
+      }
+    landed = __syncthreads_and(done) != 0;
+  }
+  if (!landed) {
     if (threadIdx.x == 0 && a.err) atomicOr(a.err, 2);
     return;
   }

@@ -194,3 +194,25 @@ def test_batch_rejects_bad_input(q):
     with pytest.raises(q.QozError):
         q.Batch([(10, 10, 10, 10)])
     plan.free()
+
+
+def test_batch_bulk_copy_wait_times_out_cleanly(q, orc, monkeypatch):
+    """A bulk-copy tile whose barrier never completes fails the whole batch
+    with QOZ_ETIMEOUT (host fault injection: the barrier's second phase
+    expects bytes no copy brings; the copies themselves have landed), and
+    the next run of the same plan, graph and all, is exact again."""
+    fields = _fields(11, BULK_SHAPES)
+    qps, ops = _params(q, orc, BULK_SHAPES, 12)
+    plan = q.Batch(BULK_SHAPES, qps)
+    monkeypatch.setenv("QOZ_FAULT", "tma_wait")
+    with pytest.raises(q.QozError) as ei:
+        plan.compress(fields, 1e-3)
+    assert ei.value.status == 5
+    monkeypatch.delenv("QOZ_FAULT")
+    blobs = plan.compress(fields, 1e-3)
+    for x, b, op in zip(fields, blobs, ops):
+        xn = x.cpu().numpy()
+        mn, mx, _ = orc.value_range(xn)
+        _vs_oracle(orc, b, xn, 1e-3 * (float(mx) - float(mn)), op)
+        b.free()
+    plan.free()
