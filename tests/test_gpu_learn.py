@@ -185,3 +185,50 @@ def test_label_collection_resumes_from_cache(q, tmp_path):
     assert torch.equal(Y5, Yf) and torch.equal(X5, Xf)
     d = np.load(cache)
     assert d["features"].shape == (5, q.NFEATURES) and d["labels"].shape == (5, 4)
+
+
+def test_tune_learned_verified_against_oracle(q, orc):
+    """The network proposes the setting (one interpolator and order for every
+    level, alpha, beta) and the sampled trials verify it in the PSNR-target
+    mode: its bound, rate and metric follow the oracle's target-mode steps on
+    that setting (trials at e0 and at 1.2 e0 or 0.8 e0, the secant on log e,
+    the final pick), and the setting is the network's."""
+    x = _field((96, 100, 120), seed=7)
+    P, mean, sd = _net(11)
+    m = q.Model()
+    m.set(P, mean, sd)
+    alphas, betas = [1.0, 1.25, 1.5, 1.75, 2.0], [2.0, 3.0, 4.0]
+    opts = q.make_tune_opts(block=16, rate=0.05, alphas=alphas, betas=betas)
+    target = 70.0
+    prop = q.tune_learned(x, 1e-2, m, opts=opts)
+    rep = q.tune_learned_verified(x, 1e-2, m, metric=q.METRIC_PSNR, target=target, opts=opts)
+    assert list(rep.params.interp[:5]) == list(prop.params.interp[:5])
+    assert list(rep.params.order[:5]) == list(prop.params.order[:5])
+    assert (rep.params.alpha, rep.params.beta) == (prop.params.alpha, prop.params.beta)
+    xn = x.cpu().numpy()
+    mn, mx, _ = orc.value_range(xn)
+    vr = float(mx) - float(mn)
+    org, bd, _ = orc.sample_blocks(xn.shape, 16, 0.05)
+    assert org.shape[0] > 1
+    op = orc.make_params(3, interp=int(prop.params.interp[0]), order=int(prop.params.order[0]),
+                         alpha=prop.params.alpha, beta=prop.params.beta, anchor_stride=16)
+    e_user = 1e-2 * vr
+    e0 = min(vr * math.sqrt(3.0) * 10.0 ** (-target / 20.0), e_user)
+
+    def trial(e):
+        t = orc.block_trial(xn, org, bd, op, e, vrange=vr)
+        return e, t.B, orc.trial_metric(t, orc.METRIC_PSNR, vr)
+
+    pts = [trial(e0)]
+    pts.append(trial(orc.target_scale(pts[0][2], target) * e0))
+    for _ in range(4):
+        en = orc.secant_step(pts[-2][0], pts[-2][2], pts[-1][0], pts[-1][2], target, e0, e_user)
+        if en is None:
+            break
+        pts.append(trial(en))
+    k = orc.target_pick([p[0] for p in pts], [p[2] for p in pts], target, e_user)
+    assert rep.abs_eb == pytest.approx(pts[k][0], rel=1e-5)
+    assert rep.B == pytest.approx(pts[k][1], rel=1e-5)
+    assert rep.M == pytest.approx(pts[k][2], rel=1e-6)
+    assert rep.M >= target
+    m.free()
