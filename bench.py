@@ -1,8 +1,8 @@
 """Benchmark: QoZ compression throughput on GB300.
 
-Workload (N=1): one 512^3 FP32 field, k^-5/3 Gaussian random field plus 8
-tanh fronts (NYX-sized, the plain-method-at-scale case), value-range
-relative bound 1e-3.  One step = the sampled tuner (0.5 % of the field in
+Workload (N=1): one 1024^3 FP32 field (4 GiB), k^-5/3 Gaussian random field
+plus 8 tanh fronts, value-range relative bound 1e-3 (--n 512 gives the
+NYX-sized plain-method-at-scale case).  One step = the sampled tuner (0.5 % of the field in
 33^3 blocks, 12 interpolators by Algorithm 1, alpha in {1..2} x beta in
 {2, 3, 4}, maximum compression ratio under the bound) followed by the
 compression with the tuned parameters: value range, anchors, the five
@@ -20,14 +20,14 @@ sample of the same workload.
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import os
-import re
 import subprocess
 import sys
 import threading
 import time
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
-    ap.add_argument("--n", type=int, default=512, help="edge of the cubic field")
+    ap.add_argument("--n", type=int, default=1024, help="edge of the cubic field")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="compress",
@@ -162,29 +162,6 @@ def _peak_hbm():
         return 6800.0, "fallback"
 
 
-def _kernel_source_hash():
-    h = hashlib.sha256()
-    for f in ("qoz_level_impl.cuh", "qoz_level.cu", "qoz_device.cuh", "qoz_internal.h"):
-        with open(os.path.join(ROOT, "paper_2310_14133_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
-
-
-def _traffic_from_profile(n):
-    """Per-launch DRAM bytes of the level-1 compress kernel from the committed
-    ncu summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "level1_compress_512.md")
-    try:
-        txt = open(path).read()
-    except OSError:
-        return None
-    m = re.search(r"kernel_source_hash:\s*(\w+)", txt)
-    t = re.search(r"dram_bytes_per_point:\s*([0-9.]+)", txt)
-    if not m or not t or m.group(1) != _kernel_source_hash():
-        return None
-    return float(t.group(1)) * n ** 3
-
-
 def _oracle_step(oracle, x):
     """The oracle as it stands: sampled tuner (max-CR mode), then compression
     with the tuned parameters, value range and rate estimate included."""
@@ -243,18 +220,70 @@ def run_reference(args, rank, world):
     emit(line, args)
 
 
-def cpu_baseline(x):
-    """The oracle as it stands, on a bounded sample: one tune + compress of
-    the benchmark field itself (several seconds of single-threaded work)."""
+def _oracle_worker(args):
+    """One process of the all-core baseline: the oracle's tune + compress of
+    block k of a shared-memory array of blocks (warm-up call: k < 0 only
+    loads the oracle)."""
+    from multiprocessing import shared_memory
     import oracle
     oracle.build()
+    name, k, b, nb = args
+    if k < 0:
+        return 0.0
+    shm = shared_memory.SharedMemory(name=name)
+    try:
+        blk = np.array(np.ndarray((nb, b, b, b), np.float32, buffer=shm.buf)[k])
+    finally:
+        shm.close()
     t0 = time.perf_counter()
-    _oracle_step(oracle, x)
-    dt = time.perf_counter() - t0
-    return {"value": 4.0 * x.size / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"one tune + compress of the {x.shape[0]}^3 benchmark field "
-                      f"(rel bound 1e-3, max-CR mode), single-threaded, {dt:.1f} s"}
+    _oracle_step(oracle, blk)
+    return time.perf_counter() - t0
 
+
+def cpu_baseline(x):
+    """The oracle as it stands, on bounded samples of the benchmark field:
+    single-threaded, one tune + compress of its 512^3 corner; and on all host
+    cores, one process per core, each running tune + compress of its own
+    256^3 block (spawned processes: no fork after CUDA initialisation)."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    sub = min(512, x.shape[0])
+    corner = np.ascontiguousarray(x[:sub, :sub, :sub])
+    t0 = time.perf_counter()
+    _oracle_step(oracle, corner)
+    dt1 = time.perf_counter() - t0
+    single = {"value": 4.0 * corner.size / dt1 / 1e9, "unit": "GB/s", "cores": 1,
+              "kind": "oracle",
+              "sample": f"one tune + compress of the {sub}^3 corner of the {x.shape[0]}^3 "
+                        f"benchmark field (rel bound 1e-3, max-CR mode), one thread, {dt1:.1f} s"}
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    from multiprocessing import shared_memory
+    b = min(256, x.shape[0])
+    per = max(1, x.shape[0] // b)
+    shm = shared_memory.SharedMemory(create=True, size=4 * cores * b ** 3)
+    try:
+        arr = np.ndarray((cores, b, b, b), np.float32, buffer=shm.buf)
+        for k in range(cores):
+            i, j, l = (k // (per * per)) % per, (k // per) % per, k % per
+            arr[k] = x[i * b:(i + 1) * b, j * b:(j + 1) * b, l * b:(l + 1) * b]
+        del arr
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(cores) as pool:
+            pool.map(_oracle_worker, [(shm.name, -1, b, cores)] * cores)  # imports, library
+            t0 = time.perf_counter()
+            pool.map(_oracle_worker, [(shm.name, k, b, cores) for k in range(cores)])
+            dtn = time.perf_counter() - t0
+    finally:
+        shm.close()
+        shm.unlink()
+    nbytes = 4.0 * cores * b ** 3
+    blocks = range(cores)
+    return {"value": nbytes / dtn / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(blocks)} blocks of {b}^3 of the benchmark field, one process "
+                      f"per host core, each running the oracle's tune + compress (rel bound "
+                      f"1e-3, max-CR mode), {dtn:.1f} s wall",
+            "single_core": single}
 
 
 def _events_ms(fn, reps, warm):
@@ -371,6 +400,10 @@ def run_learned(args):
 
     n = args.n
     x = synth.grf((n, n, n), 5.0 / 3.0, seed=4, device="cuda").contiguous()
+    # the value range both tuners start from (timed on its own so that the
+    # step after it, features -> setting against sampled trials, can be told
+    # apart)
+    ms_range, _ = _events_ms(lambda: q.value_range(x), 5, 2)
     rows = []
     for P in (60.0, 80.0, 100.0):
         rel = math.sqrt(3.0) * 10.0 ** (-P / 20.0)
@@ -395,6 +428,9 @@ def run_learned(args):
                                        rl.params.beta]})
     ratio = math.exp(sum(math.log(r["cr_learned"] / r["cr_sampled"]) for r in rows) / len(rows))
     speed = math.exp(sum(math.log(r["ms_sampled"] / r["ms_learned"]) for r in rows) / len(rows))
+    speed_after_range = math.exp(sum(
+        math.log(max(r["ms_sampled"] - ms_range, 1e-6) / max(r["ms_learned"] - ms_range, 1e-6))
+        for r in rows) / len(rows))
     gain = math.exp(sum(math.log(r["cr_learned"] / r["cr_default"]) for r in rows) / len(rows))
     line = {
         "metric": "learned vs sampled tune: CR ratio (geometric mean over 60/80/100 dB bounds)",
@@ -404,7 +440,10 @@ def run_learned(args):
         "config": {"workload": f"train {args.train} fields (recipe slope U[1,4], edges "
                                f"64..256, rel bound 1e-5..1e-2), test {n}^3 k^-5/3 seed 4",
                    "tuner_opts": TUNE, "parallelism": "single GPU"},
-        "speedup_sampled_over_learned": speed, "cr_gain_over_default": gain,
+        "speedup_sampled_over_learned": speed,
+        "speedup_after_value_range": speed_after_range,
+        "value_range_ms": ms_range,
+        "cr_gain_over_default": gain,
         "rows": rows, "train": {"fields": int(X.shape[0]), "label_s": t_label,
                                 "fit_s": t_fit, "final_loss": losses[-1],
                                 "train_accuracy_per_head": acc},
@@ -702,13 +741,27 @@ def run_streams(args):
     lvl1_ms = prof.ms[q.STAGE_LEVEL + 1] / max(1, prof.calls[q.STAGE_LEVEL + 1])
     peak, peak_kind = _peak_hbm()
     achieved = LEVEL1_BYTES_PER_POINT * N / (lvl1_ms * 1e-3) / 1e9
+
+    # decompression of one step's blob through the public API: 2N code bytes
+    # in, 4N field bytes out (the lists and anchors are a few KB)
+    dblob, _ = step()
+    dinfo = dblob.info()
+    yd = torch.empty_like(x)
+
+    def dec():
+        q.decompress(dblob, out=yd)
+
+    dec_ms, _ = _events_ms(dec, args.steps, 3)
+    dblob.free()
+    del yd
+    dec_bytes = 6.0 * N + 12.0 * dinfo.n_unpredictable + 4.0 * dinfo.n_anchors
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {
-            "workload": f"{n}^3 FP32 k^-5/3 GRF + 8 tanh fronts (NYX-sized), rel bound 1e-3, "
-                        "max-CR mode",
+            "workload": f"{n}^3 FP32 k^-5/3 GRF + 8 tanh fronts"
+                        f"{' (NYX-sized)' if n == 512 else ''}, rel bound 1e-3, max-CR mode",
             "step": "qoz_tune + qoz_compress_abs with the tuned theta",
             "streams": S, "steps_per_stream": share,
             "l2": f"input {4 * N / 2**20:.0f} MiB > 126 MB L2; no flush needed",
@@ -823,7 +876,23 @@ def main():
     tune_ms = parts.ms[q.STAGE_TUNE] / args.steps
     peak, peak_kind = _peak_hbm()
     achieved = LEVEL1_BYTES_PER_POINT * N / (lvl1_ms * 1e-3) / 1e9
-    traffic = _traffic_from_profile(n)
+
+    # decompression of one step's blob through the public API: 2N code bytes
+    # in, 4N field bytes out (the lists and anchors are a few KB)
+    dblob, _ = step()
+    dinfo = dblob.info()
+    yd = torch.empty_like(x)
+
+    def dec():
+        q.decompress(dblob, out=yd)
+
+    dec_ms, _ = _events_ms(dec, args.steps, 3)
+    dblob.free()
+    del yd
+    dec_bytes = 6.0 * N + 12.0 * dinfo.n_unpredictable + 4.0 * dinfo.n_anchors
+    # DRAM bytes of the dominant kernel come from an ncu capture of a smaller
+    # case, summarised under profiles/; this run has no counter of its own
+    traffic = None
 
     e2e = None
     if not args.no_e2e:
@@ -894,8 +963,8 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {
-            "workload": f"{n}^3 FP32 k^-5/3 GRF + 8 tanh fronts (NYX-sized), rel bound 1e-3, "
-                        "max-CR mode",
+            "workload": f"{n}^3 FP32 k^-5/3 GRF + 8 tanh fronts"
+                        f"{' (NYX-sized)' if n == 512 else ''}, rel bound 1e-3, max-CR mode",
             "step": "qoz_tune (0.5% sampled 33^3 blocks, 12 interpolators, alpha 5 x beta 3) "
                     "+ qoz_compress_abs with the tuned theta",
             "theta": {"interp": list(rep.params.interp[:5]), "order": list(rep.params.order[:5]),
@@ -907,8 +976,25 @@ def main():
                      "kernel": "level_tma_kernel (level 1 of the compression, histogram fused)",
                      "algorithmic_bytes_per_launch": LEVEL1_BYTES_PER_POINT * N,
                      "peak_kind": peak_kind},
+        "roofline_pq": {"bound": "hbm", "achieved": 6.0 * N / (pq_ms * 1e-3) / 1e9, "peak": peak,
+                        "unit": "GB/s", "frac": 6.0 * N / (pq_ms * 1e-3) / 1e9 / peak,
+                        "traffic": None,
+                        "kernel": "predictor + quantizer: every level launch of one compression "
+                                  "(CUDA events per level, summed)",
+                        "algorithmic_bytes_per_step": 6.0 * N, "peak_kind": peak_kind},
+        "decompress": {"value": 4.0 * N / (dec_ms * 1e-3) / 1e9, "unit": "GB/s (FP32 out)",
+                       "ms": dec_ms,
+                       "roofline": {"bound": "hbm", "achieved": dec_bytes / (dec_ms * 1e-3) / 1e9,
+                                    "peak": peak, "unit": "GB/s",
+                                    "frac": dec_bytes / (dec_ms * 1e-3) / 1e9 / peak,
+                                    "traffic": None,
+                                    "algorithmic_bytes": dec_bytes, "peak_kind": peak_kind},
+                       "timing": "CUDA events around qoz_decompress of the step's blob "
+                                 "(bound table, all levels, lists), median of --steps calls"},
         "breakdown_ms": {"tune_trials": tune_ms, "range": range_ms, "levels_total": pq_ms,
                          "level1": lvl1_ms,
+                         "per_level": [parts.ms[q.STAGE_LEVEL + l] / args.steps
+                                       for l in range(1, 6)],
                          "pq_input_gbs": 4.0 * N / (pq_ms * 1e-3) / 1e9,
                          "pq_frac_6N": 6.0 * N / (pq_ms * 1e-3) / 1e9 / peak},
         "compression": {"est_ratio": info.est_ratio,

@@ -255,7 +255,7 @@ bool try_launch_l1(const LevelLaunch& a, cudaStream_t s, cudaError_t* err) {
 }
 
 template <int A0, int A1, int A2, int IP>
-__global__ void __launch_bounds__(l1::kThr, l1::kCtasPerSm)
+__global__ void __launch_bounds__(l1::kThr, l1::kDecCtasPerSm)
     level1_dec_kernel(const __grid_constant__ LevelLaunch a, int nt1, int nt2, int ntiles,
                       const __grid_constant__ CUtensorMap mcode,
                       const __grid_constant__ CUtensorMap mrc) {
@@ -293,7 +293,7 @@ bool try_launch_l1_dec(const LevelLaunch& a, cudaStream_t s, cudaError_t* err) {
   }
   static unsigned long long done = 0;
   constexpr size_t smem = G::kDecSmem;
-  static_assert((smem + 1024 + 64) * l1::kCtasPerSm <= 228 * 1024, "CTAs per SM");
+  static_assert((smem + 1024 + 64) * l1::kDecCtasPerSm <= 228 * 1024, "CTAs per SM");
   const void* fn = (const void*)level1_dec_kernel<A0, A1, A2, IP>;
   cudaError_t e = ensure_smem_attr(fn, &done, smem);
   if (e != cudaSuccess) {
@@ -308,7 +308,7 @@ bool try_launch_l1_dec(const LevelLaunch& a, cudaStream_t s, cudaError_t* err) {
     *err = cudaErrorInvalidConfiguration;
     return true;
   }
-  const long long slots = (long long)l1::kCtasPerSm * sm_count();
+  const long long slots = (long long)l1::kDecCtasPerSm * sm_count();
   const unsigned grid = (unsigned)(nt < slots ? nt : (slots > 0 ? slots : 1));
   level1_dec_kernel<A0, A1, A2, IP><<<grid, l1::kThr, smem, s>>>(a, (int)nt1, (int)nt2, (int)nt,
                                                                  mcode, mrc);
