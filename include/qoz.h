@@ -461,6 +461,8 @@ qoz_status qoz_tune_learned_verified(const float* d_field, qoz_shape shape, doub
 #define QOZ_STAGE_DLEVEL 12    /* + l (l = 1..8): decompress, level l */
 #define QOZ_STAGE_METRICS 21
 #define QOZ_STAGE_TUNE 22      /* sampled-block trials of the tuner */
+#define QOZ_STAGE_FEATURES 23  /* learned tuner: the features of the sampled blocks */
+#define QOZ_STAGE_FORWARD 24   /* learned tuner: the network's forward pass and read-back */
 
 typedef struct {
   double ms[QOZ_PROF_STAGES];      /* accumulated device time per stage (CUDA events) */

@@ -34,6 +34,8 @@ from ._binding import (  # noqa: F401
     STAGE_METRICS,
     STAGE_SETUP,
     STAGE_TUNE,
+    STAGE_FEATURES,
+    STAGE_FORWARD,
     BATCH_AUTOTUNE,
     BATCH_NO_GRAPH,
     Batch,

@@ -48,6 +48,7 @@ class BlobInfo(C.Structure):
 PROF_STAGES = 32
 STAGE_RANGE, STAGE_SETUP, STAGE_LEVEL, STAGE_HIST, STAGE_FINAL = 0, 1, 2, 11, 12
 STAGE_DLEVEL, STAGE_METRICS, STAGE_TUNE = 12, 21, 22
+STAGE_FEATURES, STAGE_FORWARD = 23, 24
 
 
 class StageTimes(C.Structure):

@@ -479,15 +479,25 @@ __global__ void __launch_bounds__(128)
   unsigned long long bp = 0;  // bit position in the chunk
   const long long b = c * kEntropyChunk;
   const long long e = b + kEntropyChunk < n ? b + kEntropyChunk : n;
-  long long cw = -1;
-  unsigned long long win = 0ull;  // the 64 bits from word cw on
+  // words cw and cw + 1 form the decoding window; the next four are loaded
+  // ahead into a register queue, so that moving the window on waits for no
+  // load (a code is at most 58 bits, so a code moves it by at most two words)
+  long long cw = 0;
+  unsigned long long wa = word_at(0), wb = word_at(1);
+  unsigned long long q0 = word_at(2), q1 = word_at(3), q2 = word_at(4), q3 = word_at(5);
   uint32_t grp[4] = {0u, 0u, 0u, 0u};  // eight decoded codes, stored as one 16-byte vector
   for (long long i = b; i < e; ++i) {
     const long long wk = (long long)(bp >> 5);
-    if (wk != cw) {
-      win = (word_at(wk) << 32) | word_at(wk + 1);
-      cw = wk;
+    while (cw < wk) {
+      wa = wb;
+      wb = q0;
+      q0 = q1;
+      q1 = q2;
+      q2 = q3;
+      q3 = word_at((unsigned long long)(cw + 6));
+      ++cw;
     }
+    const unsigned long long win = (wa << 32) | wb;  // the 64 bits from word cw on
     const unsigned long long top = win << (bp & 31);  // >= 33 valid bits
     const uint32_t ent = T.lut[top >> (64 - kLut)];
     int L = (int)(ent & 0xffu);

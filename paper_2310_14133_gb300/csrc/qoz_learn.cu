@@ -54,7 +54,6 @@ __constant__ int kHeadLen[4] = {2, 6, 5, 3};
 
 // ------------------------------------------------------------- features
 constexpr int kFeatThreads = 256;
-constexpr int kFeatChunk = 8192;     // block points per CTA
 constexpr int kNSum = 14;            // s1, s2, d1[3], d2[3], lin[3], cub[3]
 constexpr int kNCnt = 12 + 48;       // n, n1[3], n2[3], nint[3], ng, nl, gh[24], lh[24]
 
@@ -69,6 +68,7 @@ struct FeatArgs {
   const int* origins;      // 3 per block (embedded)
   int bd0, bd1, bd2;
   int is2d;
+  int chunk;               // block points per CTA (a multiple of kFeatThreads)
   int chunks;              // CTAs per block
   float inv_e, inv_e2;     // (float)(1 / e), (float)(1 / e^2)
   long long c_index;       // the value that shifts the second moment
@@ -95,7 +95,7 @@ __device__ __forceinline__ int grad_bin(float t) {
   return clamp_bin(half + 12);
 }
 
-// Compensated binary32 sum (Kahan).
+// Compensated binary32 sum (Kahan); the value is s - c.
 struct KSumF {
   float s = 0.f, c = 0.f;
   __device__ __forceinline__ void add(float v) {
@@ -104,12 +104,45 @@ struct KSumF {
     c = __fsub_rn(__fsub_rn(t, s), y);
     s = t;
   }
-  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
-__global__ void __launch_bounds__(kFeatThreads) feature_kernel(const FeatArgs a) {
+// A binary32 pair hi + lo (about 48 significant bits) for combining the
+// per-thread compensated sums without binary64 arithmetic (1/64 of the
+// binary32 rate on this part): Knuth's TwoSum on the leading parts, the
+// trailing parts added to its error, then Fast2Sum renormalisation.
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  const float lo = __fadd_rn(__fadd_rn(a.lo, b.lo), err);
+  const float hi = __fadd_rn(s, lo);
+  return DF{hi, __fsub_rn(lo, __fsub_rn(hi, s))};
+}
+
+__device__ __forceinline__ DF df_shfl_xor(DF v, int off) {
+  return DF{__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off)};
+}
+
+// One bin increment per distinct bin of the warp (bin < 0: no increment);
+// every lane of the warp calls it.
+__device__ __forceinline__ void warp_bin_add(unsigned* h, int bin) {
+  const unsigned peers = __match_any_sync(0xffffffffu, bin);
+  if (bin >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[bin], __popc(peers));
+}
+
+// Each CTA walks `chunk` points of one sampled block (the points of a block
+// in row-major order, kFeatThreads apart per thread, coordinates carried
+// from one point to the next by a mixed-radix add), accumulates the moment,
+// difference and interpolation-error sums as compensated binary32 sums and
+// the two histograms in shared memory, and writes one partial.
+template <bool is2d>
+__global__ void __launch_bounds__(kFeatThreads, 4) feature_kernel(const FeatArgs a) {
   __shared__ unsigned sc[kNCnt];
-  __shared__ double sred[kFeatThreads / 32][kNSum];
+  __shared__ DF sred[kFeatThreads / 32][kNSum];
   for (int i = threadIdx.x; i < kNCnt; i += blockDim.x) sc[i] = 0u;
   __syncthreads();
   const int blk = blockIdx.y;
@@ -117,167 +150,187 @@ __global__ void __launch_bounds__(kFeatThreads) feature_kernel(const FeatArgs a)
   const int st0 = (int)(a.n1 * a.n2), st1 = (int)a.n2;  // field < 2^32 points: fits int
   const float* blk_base = a.x + (long long)a.origins[3 * blk] * a.n1 * a.n2 +
                           (long long)a.origins[3 * blk + 1] * a.n2 + a.origins[3 * blk + 2];
-  const double cshift = (double)__ldg(a.x + a.c_index);
+  const float cshift = __ldg(a.x + a.c_index);
   const int bpts = bd0 * bd1 * bd2;
-  const int p0 = blockIdx.x * kFeatChunk;
-  const int p1 = min(bpts, p0 + kFeatChunk);
-  const bool is2d = a.is2d;
+  const int p0 = blockIdx.x * a.chunk;
+  const int p1 = min(bpts, p0 + a.chunk);
+  const int iters = (p1 - p0 + kFeatThreads - 1) / kFeatThreads;
   const int bdv[3] = {bd0, bd1, bd2};
   const int stv[3] = {st0, st1, 1};
-  double m1 = 0.0, m2 = 0.0;
-  KSumF d1[3], d2[3], lin[3], cub[3];
+  KSumF m1, m2, d1[3], d2[3], lin[3], cub[3];
   unsigned n = 0, n1[3] = {0, 0, 0}, n2[3] = {0, 0, 0}, nint[3] = {0, 0, 0}, ng = 0, nl = 0;
-  for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-    int c[3];
-    c[2] = p % bd2;
-    const int r = p / bd2;
-    c[1] = r % bd1;
-    c[0] = r / bd1;
-    const float* pt = blk_base + (long long)c[0] * st0 + (long long)c[1] * st1 + c[2];
-    const float v = pt[0];
-    const double u = (double)v - cshift;
-    m1 += u;
-    m2 += u * u;
-    ++n;
-    bool fwd = true, bwd = true;
-    float gs = 0.0f;
+  int p = p0 + threadIdx.x;
+  int c[3];
+  c[2] = p % bd2;
+  c[1] = (p / bd2) % bd1;
+  c[0] = (p / bd2) / bd1;
+  // kFeatThreads in the block's mixed radix (each digit below its radix)
+  const int k2 = kFeatThreads % bd2, k1 = (kFeatThreads / bd2) % bd1,
+            k0 = (kFeatThreads / bd2) / bd1;
+  for (int it = 0; it < iters; ++it, p += kFeatThreads) {
+    const bool valid = p < p1;
+    int gbin = -1, lbin = -1;
+    if (valid) {
+      const float* pt = blk_base + (long long)c[0] * st0 + (long long)c[1] * st1 + c[2];
+      const float v = pt[0];
+      const float u = __fsub_rn(v, cshift);
+      m1.add(u);
+      m2.add(__fmul_rn(u, u));
+      ++n;
+      bool fwd = true, bwd = true;
+      float gs = 0.0f;
 #pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-      if (is2d && ax == 0) continue;
-      const int k = is2d ? ax - 1 : ax;
-      const int sa = stv[ax], ca = c[ax], ba = bdv[ax];
-      const bool hasf = ca + 1 < ba, hasb = ca >= 1;
-      fwd = fwd && hasf;
-      bwd = bwd && hasb;
-      if (hasf) {
-        const float xf = pt[sa];
-        const float df = __fsub_rn(xf, v);
-        d1[k].add(fabsf(df));
-        ++n1[k];
-        gs = __fadd_rn(gs, __fmul_rn(df, df));
-        if (hasb) {
-          d2[k].add(fabsf(__fsub_rn(__fadd_rn(xf, pt[-sa]), __fmul_rn(2.0f, v))));
-          ++n2[k];
+      for (int ax = 0; ax < 3; ++ax) {
+        if (is2d && ax == 0) continue;
+        const int k = is2d ? ax - 1 : ax;
+        const int sa = stv[ax], ca = c[ax], ba = bdv[ax];
+        const bool hasf = ca + 1 < ba, hasb = ca >= 1;
+        fwd = fwd && hasf;
+        bwd = bwd && hasb;
+        if (hasf) {
+          const float xf = pt[sa];
+          const float df = __fsub_rn(xf, v);
+          d1[k].add(fabsf(df));
+          ++n1[k];
+          gs = __fadd_rn(gs, __fmul_rn(df, df));
+          if (hasb) {
+            d2[k].add(fabsf(__fsub_rn(__fadd_rn(xf, pt[-sa]), __fmul_rn(2.0f, v))));
+            ++n2[k];
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const int h = 1 << j;
+          if ((ca & (2 * h - 1)) != h || ca - 3 * h < 0 || ca + 3 * h > ba - 1) continue;
+          const float a3 = pt[-3 * h * sa], a1 = pt[-h * sa], b1 = pt[h * sa],
+                      b3 = pt[3 * h * sa];
+          const float s1 = __fadd_rn(a1, b1);
+          lin[j].add(fabsf(__fsub_rn(v, __fmul_rn(s1, 0.5f))));
+          cub[j].add(fabsf(__fsub_rn(
+              v, __fmul_rn(__fsub_rn(__fmul_rn(9.0f, s1), __fadd_rn(a3, b3)), 0.0625f))));
+          ++nint[j];
         }
       }
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const int h = 1 << j;
-        if ((ca & (2 * h - 1)) != h || ca - 3 * h < 0 || ca + 3 * h > ba - 1) continue;
-        const float a3 = pt[-3 * h * sa], a1 = pt[-h * sa], b1 = pt[h * sa], b3 = pt[3 * h * sa];
-        const float s1 = __fadd_rn(a1, b1);
-        lin[j].add(fabsf(__fsub_rn(v, __fmul_rn(s1, 0.5f))));
-        cub[j].add(fabsf(
-            __fsub_rn(v, __fmul_rn(__fsub_rn(__fmul_rn(9.0f, s1), __fadd_rn(a3, b3)), 0.0625f))));
-        ++nint[j];
+      if (fwd) {
+        gbin = grad_bin(__fmul_rn(gs, a.inv_e2));
+        ++ng;
+      }
+      if (bwd) {
+        float pred;
+        if (!is2d) {
+          const float sa = __fadd_rn(__fadd_rn(pt[-st0], pt[-st1]), pt[-1]);
+          const float sb = __fadd_rn(__fadd_rn(pt[-st0 - st1], pt[-st0 - 1]), pt[-st1 - 1]);
+          pred = __fadd_rn(__fsub_rn(sa, sb), pt[-st0 - st1 - 1]);
+        } else {
+          pred = __fsub_rn(__fadd_rn(pt[-st1], pt[-1]), pt[-st1 - 1]);
+        }
+        lbin = res_bin(__fmul_rn(fabsf(__fsub_rn(v, pred)), a.inv_e));
+        ++nl;
       }
     }
-    if (fwd) {
-      atomicAdd(&sc[12 + grad_bin(__fmul_rn(gs, a.inv_e2))], 1u);
-      ++ng;
-    }
-    if (bwd) {
-      float pred;
-      if (!is2d) {
-        const float sa = __fadd_rn(__fadd_rn(pt[-st0], pt[-st1]), pt[-1]);
-        const float sb = __fadd_rn(__fadd_rn(pt[-st0 - st1], pt[-st0 - 1]), pt[-st1 - 1]);
-        pred = __fadd_rn(__fsub_rn(sa, sb), pt[-st0 - st1 - 1]);
-      } else {
-        pred = __fsub_rn(__fadd_rn(pt[-st1], pt[-1]), pt[-st1 - 1]);
-      }
-      atomicAdd(&sc[36 + res_bin(__fmul_rn(fabsf(__fsub_rn(v, pred)), a.inv_e))], 1u);
-      ++nl;
-    }
+    warp_bin_add(sc + 12, gbin);
+    warp_bin_add(sc + 36, lbin);
+    c[2] += k2;
+    int cy = c[2] >= bd2;
+    c[2] -= cy ? bd2 : 0;
+    c[1] += k1 + cy;
+    cy = c[1] >= bd1;
+    c[1] -= cy ? bd1 : 0;
+    c[0] += k0 + cy;
   }
-  double sum[kNSum];
-  sum[0] = m1;
-  sum[1] = m2;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    sum[2 + k] = d1[k].value();
-    sum[5 + k] = d2[k].value();
-    sum[8 + k] = lin[k].value();
-    sum[11 + k] = cub[k].value();
-  }
-  // counts (exact)
-  atomicAdd(&sc[0], n);
-  for (int k = 0; k < 3; ++k) {
-    atomicAdd(&sc[1 + k], n1[k]);
-    atomicAdd(&sc[4 + k], n2[k]);
-    atomicAdd(&sc[7 + k], nint[k]);
-  }
-  atomicAdd(&sc[10], ng);
-  atomicAdd(&sc[11], nl);
-  // sums: warp trees, then warps in order
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  // counts (exact): warp sums, then one atomic per warp
+  unsigned cnt[12] = {n, n1[0], n1[1], n1[2], n2[0], n2[1], n2[2], nint[0], nint[1], nint[2],
+                      ng, nl};
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    const unsigned v = __reduce_add_sync(0xffffffffu, cnt[i]);
+    if (l == 0) atomicAdd(&sc[i], v);
+  }
+  // sums: warp trees, then warps in order
+  const KSumF ks[kNSum] = {m1,     m2,     d1[0],  d1[1],  d1[2],  d2[0],  d2[1],
+                           d2[2],  lin[0], lin[1], lin[2], cub[0], cub[1], cub[2]};
 #pragma unroll
   for (int i = 0; i < kNSum; ++i) {
-    double v = sum[i];
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    DF v{ks[i].s, -ks[i].c};
+    for (int off = 16; off > 0; off >>= 1) v = df_add(v, df_shfl_xor(v, off));
     if (l == 0) sred[w][i] = v;
   }
   __syncthreads();
   FeatPart* out = a.parts + (long long)blockIdx.y * a.chunks + blockIdx.x;
   if (threadIdx.x < kNSum) {
-    double v = 0.0;
-    for (int k = 0; k < kFeatThreads / 32; ++k) v += sred[k][threadIdx.x];
-    out->sum[threadIdx.x] = v;
+    DF v = sred[0][threadIdx.x];
+    for (int k = 1; k < kFeatThreads / 32; ++k) v = df_add(v, sred[k][threadIdx.x]);
+    out->sum[threadIdx.x] = (double)v.hi + (double)v.lo;
   }
   for (int i = threadIdx.x; i < kNCnt; i += blockDim.x) out->cnt[i] = sc[i];
 }
 
-// Fold the partials (one thread per accumulated quantity, partials in
-// order), then one thread evaluates the 64 features.
-constexpr int kFinalThreads = 128;
-static_assert(kNSum + kNCnt <= kFinalThreads, "one thread per quantity");
+// Fold the partials: one warp per accumulated quantity, its lanes striding
+// over the partials, combined by a fixed shuffle tree (a fixed order for the
+// double sums; the counts are exact); then one thread per feature.
+constexpr int kFinalThreads = 1024;
+constexpr int kFinalWarps = kFinalThreads / 32;
+static_assert(NF <= kFinalThreads, "one thread per feature");
 
 __global__ void __launch_bounds__(kFinalThreads)
     feature_final_kernel(const FeatPart* parts, int nparts, double rel_eb, double vrange,
                          double e, double npoints, int ndims, double* fd, float* ff) {
   __shared__ double s[kNSum];
   __shared__ unsigned long long c[kNCnt];
-  const int t = threadIdx.x;
-  if (t < kNSum) {
-    double v = 0.0;
-    for (int p = 0; p < nparts; ++p) v += parts[p].sum[t];
-    s[t] = v;
-  } else if (t < kNSum + kNCnt) {
-    unsigned long long v = 0ull;
-    for (int p = 0; p < nparts; ++p) v += parts[p].cnt[t - kNSum];
-    c[t - kNSum] = v;
+  const int t = threadIdx.x, w = t >> 5, l = t & 31;
+  for (int q = w; q < kNSum + kNCnt; q += kFinalWarps) {
+    if (q < kNSum) {
+      double v = 0.0;
+      for (int p = l; p < nparts; p += 32) v += parts[p].sum[q];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (l == 0) s[q] = v;
+    } else {
+      unsigned long long v = 0ull;
+      for (int p = l; p < nparts; p += 32) v += parts[p].cnt[q - kNSum];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (l == 0) c[q - kNSum] = v;
+    }
   }
   __syncthreads();
-  if (t != 0) return;
-  double f[NF];
-  for (int i = 0; i < NF; ++i) f[i] = 0.0;
-  const double n = (double)c[0];
-  double var = 0.0;
-  if (c[0]) {
-    const double m = s[0] / n;
-    var = s[1] / n - m * m;
-    if (var < 0.0) var = 0.0;
+  if (t >= NF) return;
+  const int i = t;
+  double f = 0.0;
+  if (i == 0) {
+    f = log10(rel_eb);
+  } else if (i == 1) {
+    double var = 0.0;
+    if (c[0]) {
+      const double n = (double)c[0];
+      const double m = s[0] / n;
+      var = s[1] / n - m * m;
+      if (var < 0.0) var = 0.0;
+    }
+    const double sigma = sqrt(var);
+    f = (sigma > 0.0 && vrange > 0.0) ? log10(vrange / sigma) : 0.0;
+  } else if (i == 2) {
+    f = ndims / 3.0;
+  } else if (i == 3) {
+    f = log2(npoints) / 30.0;
+  } else if (i < 7) {  // mean |first difference| per axis
+    const int k = i - 4;
+    if (k < ndims && c[1 + k]) f = log2(1.0 + (s[2 + k] / (double)c[1 + k]) / e);
+  } else if (i < 10) {  // mean |second difference| per axis
+    const int k = i - 7;
+    if (k < ndims && c[4 + k]) f = log2(1.0 + (s[5 + k] / (double)c[4 + k]) / e);
+  } else if (i < 34) {  // gradient-magnitude histogram
+    if (c[10]) f = (double)c[12 + (i - 10)] / (double)c[10];
+  } else if (i < 58) {  // Lorenzo-residual histogram
+    if (c[11]) f = (double)c[36 + (i - 34)] / (double)c[11];
+  } else if (i < 61) {  // linear interpolation error per stride
+    const int j = i - 58;
+    if (c[7 + j]) f = log2(1.0 + (s[8 + j] / (double)c[7 + j]) / e);
+  } else {  // cubic interpolation error per stride
+    const int j = i - 61;
+    if (c[7 + j]) f = log2(1.0 + (s[11 + j] / (double)c[7 + j]) / e);
   }
-  const double sigma = sqrt(var);
-  f[0] = log10(rel_eb);
-  f[1] = (sigma > 0.0 && vrange > 0.0) ? log10(vrange / sigma) : 0.0;
-  f[2] = ndims / 3.0;
-  f[3] = log2(npoints) / 30.0;
-  for (int k = 0; k < ndims; ++k) {
-    f[4 + k] = c[1 + k] ? log2(1.0 + (s[2 + k] / (double)c[1 + k]) / e) : 0.0;
-    f[7 + k] = c[4 + k] ? log2(1.0 + (s[5 + k] / (double)c[4 + k]) / e) : 0.0;
-  }
-  for (int i = 0; i < 24; ++i) {
-    f[10 + i] = c[10] ? (double)c[12 + i] / (double)c[10] : 0.0;
-    f[34 + i] = c[11] ? (double)c[36 + i] / (double)c[11] : 0.0;
-  }
-  for (int j = 0; j < 3; ++j) {
-    f[58 + j] = c[7 + j] ? log2(1.0 + (s[8 + j] / (double)c[7 + j]) / e) : 0.0;
-    f[61 + j] = c[7 + j] ? log2(1.0 + (s[11 + j] / (double)c[7 + j]) / e) : 0.0;
-  }
-  for (int i = 0; i < NF; ++i) {
-    if (fd) fd[i] = f[i];
-    if (ff) ff[i] = (float)f[i];
-  }
+  if (fd) fd[i] = f;
+  if (ff) ff[i] = (float)f;
 }
 
 // ------------------------------------------------------------- network
@@ -323,9 +376,13 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_kernel(
   // are combined by a fixed shuffle tree
   const int warp = t >> 5, lane = t & 31;
   constexpr int kWarps = kMlpThreads / 32;
+  // inference walks only the CTA's valid samples (one for a single field);
+  // training keeps every slot, the padded ones computed from z = 0, so the
+  // gradient sums below read no unwritten shared memory
+  const int ns = TRAIN ? kMlpS : (int)(B - s0 < kMlpS ? B - s0 : kMlpS);
   for (int o = warp; o < NH; o += kWarps) {
     const float w0 = W1[o * NF + lane], w1 = W1[o * NF + 32 + lane];
-    for (int s = 0; s < kMlpS; ++s) {
+    for (int s = 0; s < ns; ++s) {
       float v = __fadd_rn(__fmul_rn(w0, sm.z[s][lane]), __fmul_rn(w1, sm.z[s][32 + lane]));
       for (int off = 16; off > 0; off >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, off));
       if (lane == 0) {
@@ -339,7 +396,7 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_kernel(
     float w[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) w[j] = W2[o * NH + 32 * j + lane];
-    for (int s = 0; s < kMlpS; ++s) {
+    for (int s = 0; s < ns; ++s) {
       float v = 0.0f;
 #pragma unroll
       for (int j = 0; j < 4; ++j) v = __fadd_rn(v, __fmul_rn(w[j], sm.h1[s][32 * j + lane]));
@@ -355,7 +412,7 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_kernel(
     float w[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) w[j] = W3[o * NH + 32 * j + lane];
-    for (int s = 0; s < kMlpS; ++s) {
+    for (int s = 0; s < ns; ++s) {
       float v = 0.0f;
 #pragma unroll
       for (int j = 0; j < 4; ++j) v = __fadd_rn(v, __fmul_rn(w[j], sm.h2[s][32 * j + lane]));
@@ -571,10 +628,21 @@ qoz_status features_impl(const float* d_field, const qoz_shape& shape, double re
   const double e = e0 > 0.0 ? e0 : 1.0;
   Sampling sm = sample_blocks(r, o.block, o.rate, o.anchor_stride);
   const long long bpts = (long long)sm.bd[0] * sm.bd[1] * sm.bd[2];
-  const int chunks = (int)((bpts + kFeatChunk - 1) / kFeatChunk);
+  // points per CTA: enough CTAs for about two waves at four CTAs per SM,
+  // at least eight points per thread
+  int nsm = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    nsm = 1;
+  const long long want = 8LL * nsm;
+  const long long per_block = std::max(1LL, (want + sm.nb - 1) / sm.nb);
+  long long chunk = (bpts + per_block - 1) / per_block;
+  chunk = std::max<long long>(8LL * kFeatThreads, (chunk + kFeatThreads - 1) / kFeatThreads *
+                                                      kFeatThreads);
+  const int chunks = (int)((bpts + chunk - 1) / chunk);
   const long long nparts = (long long)chunks * sm.nb;
   if (sm.nb > 65535) return fail(QOZ_EUNSUPPORTED, "too many sampled blocks");
-  if (bpts > 0x7fffffffLL) return fail(QOZ_EUNSUPPORTED, "sampled block too large");
+  if (bpts > 0x7fff0000LL) return fail(QOZ_EUNSUPPORTED, "sampled block too large");
   void* scratch = nullptr;
   const size_t ob = ((size_t)sm.origins.size() * sizeof(int) + 255) & ~(size_t)255;
   cudaError_t ce = dev_alloc(&scratch, ob + sizeof(FeatPart) * nparts, s);
@@ -583,6 +651,7 @@ qoz_status features_impl(const float* d_field, const qoz_shape& shape, double re
   FeatPart* parts = (FeatPart*)((char*)scratch + ob);
   ce = cudaMemcpyAsync(d_org, sm.origins.data(), sizeof(int) * sm.origins.size(),
                        cudaMemcpyHostToDevice, s);
+  ProfScope ps(QOZ_STAGE_FEATURES, s);
   if (ce == cudaSuccess) {
     FeatArgs a;
     a.x = d_field;
@@ -593,13 +662,17 @@ qoz_status features_impl(const float* d_field, const qoz_shape& shape, double re
     a.bd1 = sm.bd[1];
     a.bd2 = sm.bd[2];
     a.is2d = r.ndims == 2;
+    a.chunk = (int)chunk;
     a.chunks = chunks;
     a.inv_e = (float)(1.0 / e);
     a.inv_e2 = (float)(1.0 / (e * e));
     // the second moment is shifted by the first sampled value
     a.c_index = ((long long)sm.origins[0] * r.n[1] + sm.origins[1]) * r.n[2] + sm.origins[2];
     a.parts = parts;
-    feature_kernel<<<dim3(chunks, sm.nb), kFeatThreads, 0, s>>>(a);
+    if (a.is2d)
+      feature_kernel<true><<<dim3(chunks, sm.nb), kFeatThreads, 0, s>>>(a);
+    else
+      feature_kernel<false><<<dim3(chunks, sm.nb), kFeatThreads, 0, s>>>(a);
     note_launch(1);
     ce = cudaGetLastError();
   }
@@ -769,6 +842,7 @@ qoz_status qoz_tune_learned(const float* d_field, qoz_shape shape, double rel_eb
   st = features_impl(d_field, shape, rel_eb, &o, nullptr, d_buf, s, &vr, &vmin, &vmax, &sm);
   float logits[NO];
   if (st == QOZ_OK) {
+    ProfScope ps(QOZ_STAGE_FORWARD, s);
     cudaError_t e = launch_mlp<false>(model, d_buf, nullptr, 1, d_buf + NF, s);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(logits, d_buf + NF, sizeof(logits), cudaMemcpyDeviceToHost, s);

@@ -330,6 +330,31 @@ __device__ __forceinline__ void line_pass(const LevelLaunch& a, const Ctx& c, fl
     const bool r_in = lr >= 0 && lr < TR;
     const bool x_in = XK == kAny || (lx >= 0 && lx < G::TX);
     const bool inside = r_in && x_in;
+    // bounds-checking build: the item's first and last index in every buffer
+    // it touches (the constant true otherwise)
+    {
+      const int lzf = P == 0 ? p0 : lz_of, lyf = P == 0 ? ly_of : p0;
+      const int lzl = P == 0 ? p0 + 2 * SEG - 1 : lz_of, lyl = P == 0 ? ly_of : p0 + 2 * SEG - 1;
+      // pass 1 reads its window from the coarse box and touches the field box
+      // only at this segment's own positions; later passes read a window of
+      // field-box positions two beyond the segment on each side
+      const int slo = FROM_CB ? p0 : p0 - 2, shi = FROM_CB ? p0 + 2 * SEG - 1 : p0 + 2 * SEG + 2;
+      if (!QOZ_IN(sb + slo * SP, G::kS) || !QOZ_IN(sb + shi * SP + 3, G::kS)) continue;
+      if (DEC && (!QOZ_IN(xb + (p0 + 1) * XP, G::kCode) ||
+                  !QOZ_IN(xb + (p0 + 2 * SEG - 1) * XP + 3, G::kCode)))
+        continue;
+      if (FROM_CB &&
+          (!QOZ_IN(P == 0 ? G::cbidx(p0 - 2, lr, lx) : G::cbidx(lr, p0 - 2, lx), G::kCB) ||
+           !QOZ_IN((P == 0 ? G::cbidx(p0 + 2 * SEG + 2, lr, lx)
+                           : G::cbidx(lr, p0 + 2 * SEG + 2, lx)) + 1, G::kCB)))
+        continue;
+      if (!DEC && inside &&
+          (!QOZ_IN(G::cidx(lzf, lyf, lx), G::kC) ||
+           !QOZ_IN(G::cidx(lzl, lyl, lx) + 3, G::kC) ||
+           (FROM_CB && (!QOZ_IN(G::ccidx(lzf, lyf, lx), G::kCC) ||
+                        !QOZ_IN(G::ccidx(lzl, lyl, lx) + 1, G::kCC)))))
+        continue;
+    }
     if constexpr (XK == kAny) {
       // four targets per position
       float4 w[SEG + 3];
@@ -452,6 +477,17 @@ __device__ __forceinline__ void x_pass(const LevelLaunch& a, const Ctx& c, float
     const int lx0 = 8 * xc;
     const int base = G::sidx(lz, ly, lx0);
     const bool inside = lz >= 0 && lz < G::TZ && ly >= 0 && ly < G::TY;
+    // bounds-checking build: the item's first and last index in each buffer
+    if (!QOZ_IN(base - (FROM_CB ? 0 : 4), G::kS) || !QOZ_IN(base + (FROM_CB ? 7 : 11), G::kS))
+      continue;
+    if (FROM_CB && (!QOZ_IN(G::cbidx(lz, ly, lx0) - 1, G::kCB) ||
+                    !QOZ_IN(G::cbidx(lz, ly, lx0) + 5, G::kCB)))
+      continue;
+    if (DEC && !QOZ_IN(G::xidx(lz, ly, lx0) + 7, G::kCode)) continue;
+    if (!DEC && inside &&
+        (!QOZ_IN(G::cidx(lz, ly, lx0) + 7, G::kC) ||
+         (FROM_CB && !QOZ_IN(G::ccidx(lz, ly, lx0) + 3, G::kCC))))
+      continue;
     float4* t4 = reinterpret_cast<float4*>(S + base);
     float e[7];  // even x at lx0 - 2, lx0, ..., lx0 + 10
     float4 v0, v1;
@@ -584,6 +620,7 @@ __device__ __forceinline__ void store_tile(const LevelLaunch& a, const Ctx& c, c
     const int ly = t % G::TY, lz = t / G::TY;
     const int cz = c.oz + lz, cy = c.oy + ly, cx = c.ox + lx;
     if (cz >= c.g0 || cy >= c.g1 || cx >= c.g2) continue;
+    if (!QOZ_IN(G::sidx(lz, ly, lx) + 3, G::kS)) continue;
     const float4 v = *reinterpret_cast<const float4*>(S + G::sidx(lz, ly, lx));
     const unsigned oi = (unsigned)cz * os0 + (unsigned)cy * os1 + (unsigned)cx;
     if (vec && cx + 4 <= c.g2) {

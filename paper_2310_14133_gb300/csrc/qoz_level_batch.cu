@@ -104,9 +104,11 @@ Info info_h(int is2d, int order3, int v) {
     case 1: return v ? info_of<0, 2, 1, 4, 32, 64, HIST>() : info_of<0, 2, 1, 8, 16, 64, HIST>();
     case 2: return v ? info_of<1, 0, 2, 32, 4, 64, HIST>() : info_of<1, 0, 2, 16, 8, 64, HIST>();
     case 3: return v ? info_of<1, 2, 0, 32, 4, 64, HIST>() : info_of<1, 2, 0, 16, 8, 64, HIST>();
-    case 4: return v ? info_of<2, 0, 1, 12, 12, 48, HIST>() : info_of<2, 0, 1, 12, 16, 32, HIST>();
+    // x first: no 48-wide tile (its instances spilled 116-136 bytes at the
+    // 64-register cap of two 512-thread CTAs per SM)
+    case 4: return v ? info_of<2, 0, 1, 16, 12, 32, HIST>() : info_of<2, 0, 1, 12, 16, 32, HIST>();
     default:
-      return v ? info_of<2, 1, 0, 12, 12, 48, HIST>() : info_of<2, 1, 0, 12, 16, 32, HIST>();
+      return v ? info_of<2, 1, 0, 16, 12, 32, HIST>() : info_of<2, 1, 0, 12, 16, 32, HIST>();
   }
 }
 

@@ -232,3 +232,59 @@ def test_tune_learned_verified_against_oracle(q, orc):
     assert rep.M == pytest.approx(pts[k][2], rel=1e-6)
     assert rep.M >= target
     m.free()
+
+
+def _stretched_field(n, axis, stretch, slope, seed, modes=64):
+    """A Gaussian random field whose wavenumbers along `axis` are divided by
+    `stretch`: smooth along that axis, rough along the others (test input:
+    the recipe's random Fourier modes with one axis stretched)."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    d = torch.randn(modes, 3, generator=g, dtype=torch.float64)
+    d = d / d.norm(dim=1, keepdim=True)
+    kmag = torch.exp(torch.rand(modes, generator=g, dtype=torch.float64) * math.log(n / 4.0))
+    k = d * kmag[:, None]
+    k[:, axis] /= stretch
+    amp = kmag ** ((1.0 - slope) / 2.0)
+    phase = torch.rand(modes, generator=g, dtype=torch.float64) * 2.0 * math.pi
+    c = torch.arange(n, dtype=torch.float64, device="cuda") / n
+    f = torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
+    for m in range(modes):
+        arg = (2.0 * math.pi * (k[m, 0] * c[:, None, None] + k[m, 1] * c[None, :, None]
+                                + k[m, 2] * c[None, None, :]) + phase[m])
+        f += amp[m] * torch.cos(arg)
+    f *= 3.0 / f.std()
+    return f.float().contiguous()
+
+
+def test_trained_network_gains_over_default_setting(q):
+    """What the trained network gains: labelled by the sampled tuner on a few
+    hundred small fields, each smooth along a random axis, the network picks
+    for a held-out field that is smooth along z a setting that compresses it
+    better than the fixed default (cubic, dimension order z, y, x,
+    alpha = beta = 1), at the same bound."""
+    from paper_2310_14133_gb300 import learn
+    opts = q.make_tune_opts(block=16, rate=0.05, alphas=[1.0, 1.25, 1.5, 1.75, 2.0],
+                            betas=[2.0, 3.0, 4.0])
+    rng = np.random.default_rng(3)
+
+    def samples():
+        for i in range(240):
+            axis = int(rng.integers(0, 3))
+            stretch = float(rng.choice([1.0, 4.0, 8.0]))
+            slope = float(rng.uniform(1.5, 3.0))
+            rel = float(10.0 ** rng.uniform(-4.0, -2.0))
+            yield _stretched_field(48, axis, stretch, slope, 1000 + i), rel
+
+    X, Y = learn.collect(samples(), opts)
+    m = q.Model(seed=4)
+    learn.fit(m, X, Y, epochs=200, batch=64, lr=3e-3)
+    x = _stretched_field(96, 0, 8.0, 2.0, 77)
+    rel = 1e-3
+    rl = q.tune_learned(x, rel, m, opts=opts)
+    crs = {}
+    for name, p in (("learned", rl.params), ("default", q.make_params(3))):
+        b = q.compress_abs(x, rl.abs_eb, p)
+        crs[name] = b.info().est_ratio
+        b.free()
+    assert crs["learned"] > 1.02 * crs["default"], crs
+    m.free()
