@@ -601,8 +601,7 @@ qoz_status qoz_compute_metrics(const float* d_a, const float* d_b, qoz_shape sha
   double* pmax = psse + ne;
   double* pss = pmax + ne;
   double* pac = pss + ns;
-  e = launch_check(launch_err_metrics(d_a, d_b, r.N, psse, pmax, ne, s));
-  if (e == cudaSuccess) e = launch_check(launch_autocorr(d_a, d_b, r.N, 1, pac, s));
+  e = launch_check(launch_err_metrics(d_a, d_b, r.N, psse, pmax, pac, s));
   const double c1 = (0.01 * vrange) * (0.01 * vrange);
   const double c2 = (0.03 * vrange) * (0.03 * vrange);
   if (e == cudaSuccess && ssim_win > 0)

@@ -163,8 +163,11 @@ cudaError_t launch_sort_pairs(long long* idx, float* val, long long n, long long
 size_t sort_pairs_scratch(long long n);
 
 // Metrics (qoz_metrics.cu)
+// One pass: err_metric_blocks() partials each of the squared-error sum and
+// the max |a - b|, and ac_parts() doubles of lag-1 autocorrelation sums (the
+// layout autocorr_from_parts reads).
 cudaError_t launch_err_metrics(const float* a, const float* b, long long n, double* part_sse,
-                               double* part_max, int nparts, cudaStream_t s);
+                               double* part_max, double* part_ac, cudaStream_t s);
 int err_metric_blocks();
 // SSIM partial sums of (1 - SSIM_w), one per part; ssim_parts() gives the count.
 cudaError_t launch_ssim(const float* a, const float* b, const long long dims[3], bool is3d,

@@ -27,7 +27,7 @@ namespace qoz {
 namespace {
 
 constexpr int kErrThreads = 512;
-constexpr int kErrBlocks = 152 * 4;
+constexpr int kErrBlocks = 152 * 2;
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -69,52 +69,163 @@ struct Kahan {
   }
 };
 
-__device__ __forceinline__ void err_point(float av, float bv, float& mxf, double& mxd,
-                                          int& nans, Kahan& sse) {
-  const float d = __fsub_rn(av, bv);
-  const float ad = fabsf(d);
-  if (ad != ad) {
-    ++nans;
-  } else if (ad >= mxf) {  // candidate: the exact maximum always passes this test
-    mxf = ad;
-    mxd = fmax(mxd, fabs((double)av - (double)bv));
+// Max and NaN bookkeeping of one error e = fl(b - a) (|e| = |fl(a - b)|).
+// fl is monotone, so the exact maximum of |b - a| has the largest |e|; among
+// equal |e| it has the largest t, the rounding error of the subtraction
+// (Knuth's TwoSum, exact in binary32) signed towards |e|, since the exact
+// |b - a| is |e| + t.  The leader's inputs are kept and its difference is
+// taken in binary64 at the end, as the definition does.  Only a new or tied
+// leader (rare after a thread's first few elements) takes the branch; start
+// with mxf = -1 so that the first element leads.  (Differences beyond the
+// binary32 range all round to infinity; the first of them leads.)
+struct ErrMax {
+  float mxf = -1.0f, mxt = 0.0f, ma = 0.0f, mb = 0.0f;
+  __device__ __forceinline__ void add(float av, float bv, float e) {
+    const float ad = fabsf(e);  // NaN never leads
+    if (ad >= mxf) {
+      const float bp = __fsub_rn(e, bv);
+      const float ap = __fsub_rn(e, bp);
+      const float t = __fadd_rn(__fsub_rn(bv, ap), __fsub_rn(-av, bp));
+      const float tt = e < 0.0f ? -t : t;
+      if (ad > mxf || tt > mxt) {
+        mxf = ad;
+        mxt = tt;
+        ma = av;
+        mb = bv;
+      }
+    }
   }
-  sse.add(__fmul_rn(d, d));
-}
+  __device__ __forceinline__ double value() const {
+    return mxf < 0.0f ? 0.0 : fabs((double)mb - (double)ma);
+  }
+};
 
-__global__ void __launch_bounds__(kErrThreads) err_kernel(const float* __restrict__ a,
-                                                          const float* __restrict__ b,
-                                                          long long n, double* part_sse,
-                                                          double* part_max) {
-  __shared__ double sh[32];
-  float mxf = 0.f;
-  double mxd = 0.0;
+constexpr int kAcParts = 5;
+
+// One pass over a and b for the metrics call: the exact max |a - b|, the sum
+// of squared errors and the lag-1 autocorrelation sums of e = b - a (sum e,
+// sum e^2, sum e_i e_{i+1}, and sum e without its last / first element).
+// With 16-byte aligned inputs a thread takes four consecutive errors per
+// step, adds their terms pairwise and each of the three partials to a
+// compensated binary32 sum; the error after its fourth comes from the next
+// lane by a shuffle, or by a load for the warp's last lane.  Part layout:
+// part_sse[g], part_max[g], part_ac[j * g + cta].
+struct ErrAcc {
+  ErrMax mx;
+  Kahan s1, s2, sk;
   int nans = 0;
-  Kahan sse;
+  // four consecutive errors of (u, v); nx the one after them (has_next)
+  __device__ __forceinline__ void step4(const float4& u, const float4& v, float e0, float nx,
+                                        bool has_next) {
+    const float e1 = __fsub_rn(v.y, u.y), e2 = __fsub_rn(v.z, u.z), e3 = __fsub_rn(v.w, u.w);
+    const float q = __fadd_rn(__fadd_rn(__fmul_rn(e0, e0), __fmul_rn(e1, e1)),
+                              __fadd_rn(__fmul_rn(e2, e2), __fmul_rn(e3, e3)));
+    if (q != q) ++nans;  // a square is NaN only for a NaN error
+    const float am = fmaxf(fmaxf(fabsf(e0), fabsf(e1)), fmaxf(fabsf(e2), fabsf(e3)));
+    if (am >= mx.mxf) {
+      mx.add(u.x, v.x, e0);
+      mx.add(u.y, v.y, e1);
+      mx.add(u.z, v.z, e2);
+      mx.add(u.w, v.w, e3);
+    }
+    s1.add(__fadd_rn(__fadd_rn(e0, e1), __fadd_rn(e2, e3)));
+    s2.add(q);
+    const float k3 = has_next ? __fmul_rn(e3, nx) : 0.0f;
+    sk.add(__fadd_rn(__fadd_rn(__fmul_rn(e0, e1), __fmul_rn(e1, e2)),
+                     __fadd_rn(__fmul_rn(e2, e3), k3)));
+  }
+  __device__ __forceinline__ void step1(float av, float bv, float e) {
+    if (e != e) ++nans;
+    mx.add(av, bv, e);
+    s1.add(e);
+    s2.add(__fmul_rn(e, e));
+  }
+};
+
+__global__ void __launch_bounds__(kErrThreads, 2) err_kernel(const float* __restrict__ a,
+                                                             const float* __restrict__ b,
+                                                             long long n, double* part_sse,
+                                                             double* part_max, double* part_ac) {
+  __shared__ double sh[32];
+  ErrAcc acc;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nthr = (long long)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
   const bool vec = ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15) == 0;
   long long i0 = 0;
   if (vec) {
     const long long n4 = n >> 2;
     const float4* a4 = reinterpret_cast<const float4*>(a);
     const float4* b4 = reinterpret_cast<const float4*>(b);
-    for (long long i = tid; i < n4; i += nthr) {
-      const float4 u = __ldcs(a4 + i), v = __ldcs(b4 + i);
-      err_point(u.x, v.x, mxf, mxd, nans, sse);
-      err_point(u.y, v.y, mxf, mxd, nans, sse);
-      err_point(u.z, v.z, mxf, mxd, nans, sse);
-      err_point(u.w, v.w, mxf, mxd, nans, sse);
+    // i - lane is the warp's first vector, so the trip counts are
+    // warp-uniform. Full steps (all 32 lanes in range) load the next step's
+    // vectors before this step's arithmetic; at most one partial step per
+    // warp follows.
+    long long i = tid;
+    float4 un = make_float4(0.f, 0.f, 0.f, 0.f), vn = un;
+    if (i - lane < n4 - 31) {
+      un = __ldcs(a4 + i);
+      vn = __ldcs(b4 + i);
+    }
+    for (; i - lane < n4 - 31; i += nthr) {
+      const float4 u = un, v = vn;
+      if (i + nthr - lane < n4 - 31) {
+        un = __ldcs(a4 + i + nthr);
+        vn = __ldcs(b4 + i + nthr);
+      }
+      const float e0 = __fsub_rn(v.x, u.x);
+      float nx = __shfl_down_sync(0xffffffffu, e0, 1);
+      bool has_next = true;
+      if (lane == 31) {
+        const long long j = 4 * i + 4;
+        has_next = j < n;
+        nx = has_next ? __fsub_rn(b[j], a[j]) : 0.0f;
+      }
+      acc.step4(u, v, e0, nx, has_next);
+    }
+    if (i - lane < n4) {
+      const bool ok = i < n4;
+      float4 u = make_float4(0.f, 0.f, 0.f, 0.f), v = u;
+      if (ok) {
+        u = __ldcs(a4 + i);
+        v = __ldcs(b4 + i);
+      }
+      const float e0 = __fsub_rn(v.x, u.x);
+      float nx = __shfl_down_sync(0xffffffffu, e0, 1);
+      if (ok) {
+        const long long j = 4 * i + 4;
+        const bool has_next = j < n;
+        if (has_next && (lane == 31 || i + 1 >= n4)) nx = __fsub_rn(b[j], a[j]);
+        acc.step4(u, v, e0, nx, has_next);
+      }
     }
     i0 = n4 << 2;
   }
-  for (long long i = i0 + tid; i < n; i += nthr) err_point(a[i], b[i], mxf, mxd, nans, sse);
-  const double s = block_sum((double)sse.s - (double)sse.c, sh);
-  const double m = block_max(mxd, sh);
-  const double nn = block_sum((double)nans, sh);  // a NaN difference makes the max NaN
+  for (long long i = i0 + tid; i < n; i += nthr) {
+    const float av = a[i], bv = b[i];
+    const float e = __fsub_rn(bv, av);
+    acc.step1(av, bv, e);
+    if (i + 1 < n) acc.sk.add(__fmul_rn(e, __fsub_rn(b[i + 1], a[i + 1])));
+  }
+  // the pair sums' members: all errors but the last (head), all but the first (tail)
+  Kahan head = acc.s1, tail = acc.s1;
+  if (tid == 0 && n > 0) {
+    tail.add(-__fsub_rn(b[0], a[0]));
+    head.add(-__fsub_rn(b[n - 1], a[n - 1]));
+  }
+  const double ss = block_sum((double)acc.s2.s - (double)acc.s2.c, sh);
+  const double m = block_max(acc.mx.value(), sh);
+  const double nn = block_sum((double)acc.nans, sh);  // a NaN difference makes the max NaN
   if (threadIdx.x == 0) {
-    part_sse[blockIdx.x] = s;
+    part_sse[blockIdx.x] = ss;
     part_max[blockIdx.x] = nn > 0.0 ? __longlong_as_double(0x7ff8000000000000LL) : m;
+    part_ac[1 * gridDim.x + blockIdx.x] = ss;
+  }
+  const Kahan* ks[4] = {&acc.s1, &acc.sk, &head, &tail};
+  const int slot[4] = {0, 2, 3, 4};
+  for (int j = 0; j < 4; ++j) {
+    const double v = block_sum((double)ks[j]->s - (double)ks[j]->c, sh);
+    if (threadIdx.x == 0) part_ac[(size_t)slot[j] * gridDim.x + blockIdx.x] = v;
   }
 }
 
@@ -124,7 +235,6 @@ __global__ void __launch_bounds__(kErrThreads) err_kernel(const float* __restric
 // n - k pairs and the sums of the pairs' first and second members, each in
 // compensated binary32 per thread and double across threads; the host forms
 // the mean, the variance and the lag covariance from them.
-constexpr int kAcParts = 5;
 
 __global__ void __launch_bounds__(kErrThreads) ac_kernel(const float* __restrict__ a,
                                                          const float* __restrict__ b,
@@ -163,9 +273,10 @@ template <int WIN, int STEP>
 struct SsimGeo {
   static constexpr int EX = STEP * (kWX - 1) + WIN;   // input columns per plane tile
   static constexpr int EY = STEP * (kWY - 1) + WIN;   // input rows per plane tile
-  static constexpr int EXP = EX | 1;                  // odd row pitch
-  static constexpr int NIN = EY * EX;
-  static constexpr int LPT = (NIN + kTileThreads - 1) / kTileThreads;
+  static constexpr int EX4 = (EX + 3) / 4;            // 16-byte chunks per input row
+  static constexpr int EXP = (4 * EX4) | 1;           // odd row pitch holding whole chunks
+  static constexpr int NCH = EY * EX4;                // chunks per plane tile
+  static constexpr int LPT = (NCH + kTileThreads - 1) / kTileThreads;
   static constexpr int SPAN = STEP * (kG - 1) + WIN;  // points one x task reads
   static constexpr int NXT = EY * (kWX / kG);         // x tasks per plane
   static_assert(kWX * kWY == kTileThreads, "one thread per (wy, wx) window column");
@@ -177,12 +288,15 @@ struct SsimSmem {
   using G = SsimGeo<WIN, STEP>;
   float xs[G::EY * G::EXP];
   float ys[G::EY * G::EXP];
-  float h[5][G::EY][kWX];
-  float ring[IS3D ? WIN : 1][5][kTileThreads];
+  float h[5][G::EY][kWX + 1];   // padded: the x pass's lanes write down a column
+  // z sums: per-plane sums of the last WIN planes, or with step 2 the last
+  // three sums of plane pairs (2k, 2k + 1)
+  static constexpr int kRing = !IS3D ? 1 : (STEP == 2 && WIN == 7 ? 3 : WIN);
+  float ring[kRing][5][kTileThreads];
 };
 
 template <int WIN, int STEP, bool IS3D>
-__global__ void __launch_bounds__(kTileThreads) ssim_tile_kernel(
+__global__ void __launch_bounds__(kTileThreads, 4) ssim_tile_kernel(
     const float* __restrict__ a, const float* __restrict__ b, long long n1, long long n2,
     long long c0, long long c1n, long long c2n, float k1, float k2, double* part) {
   using G = SsimGeo<WIN, STEP>;
@@ -204,34 +318,50 @@ __global__ void __launch_bounds__(kTileThreads) ssim_tile_kernel(
   const int wyl = t / kWX, wxl = t % kWX;
   const bool col_ok = (y0 / STEP + wyl) < c1n && (x0 / STEP + wxl) < c2n;
 
-  float px[G::LPT], py[G::LPT];
+  // The plane tile moves in 16-byte chunks: a chunk inside the field (rows
+  // on 16-byte boundaries) is one vector load per array, one crossing the
+  // field's last column takes scalar loads, the rest is zero.
+  const bool vec = ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15) == 0 &&
+                   (n2 & 3) == 0;
+  float4 px[G::LPT], py[G::LPT];
   auto load_plane = [&](int p) {
     const long long zb = (z0 + p) * plane;
 #pragma unroll
     for (int i = 0; i < G::LPT; ++i) {
       const int e = t + i * kTileThreads;
-      const int r = e / G::EX, cc = e - (e / G::EX) * G::EX;
-      const long long y = y0 + r, x = x0 + cc;
-      px[i] = 0.f;
-      py[i] = 0.f;
-      if (e < G::NIN && y < n1 && x < n2) {
+      const int r = e / G::EX4, c4 = e - (e / G::EX4) * G::EX4;
+      const long long y = y0 + r, x = x0 + 4 * c4;
+      px[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      py[i] = px[i];
+      if (e < G::NCH && y < n1 && x < n2) {
         const long long idx = zb + y * n2 + x;
-        px[i] = __ldg(a + idx);
-        py[i] = __ldg(b + idx);
+        if (vec && x + 3 < n2) {
+          px[i] = __ldg(reinterpret_cast<const float4*>(a + idx));
+          py[i] = __ldg(reinterpret_cast<const float4*>(b + idx));
+        } else {
+          px[i].x = __ldg(a + idx);
+          py[i].x = __ldg(b + idx);
+          if (x + 1 < n2) px[i].y = __ldg(a + idx + 1), py[i].y = __ldg(b + idx + 1);
+          if (x + 2 < n2) px[i].z = __ldg(a + idx + 2), py[i].z = __ldg(b + idx + 2);
+          if (x + 3 < n2) px[i].w = __ldg(a + idx + 3), py[i].w = __ldg(b + idx + 3);
+        }
       }
     }
   };
 
   float diss = 0.f;
+  float prev[5] = {0.f, 0.f, 0.f, 0.f, 0.f};   // the last even plane's sums (step 2)
   load_plane(0);
   for (int p = 0; p < nplanes; ++p) {
 #pragma unroll
     for (int i = 0; i < G::LPT; ++i) {
       const int e = t + i * kTileThreads;
-      if (e < G::NIN) {
-        const int r = e / G::EX, cc = e - (e / G::EX) * G::EX;
-        sm.xs[r * G::EXP + cc] = px[i];
-        sm.ys[r * G::EXP + cc] = py[i];
+      if (e < G::NCH) {
+        const int r = e / G::EX4, c4 = e - (e / G::EX4) * G::EX4;
+        float* xd = sm.xs + r * G::EXP + 4 * c4;
+        float* yd = sm.ys + r * G::EXP + 4 * c4;
+        xd[0] = px[i].x, xd[1] = px[i].y, xd[2] = px[i].z, xd[3] = px[i].w;
+        yd[0] = py[i].x, yd[1] = py[i].y, yd[2] = py[i].z, yd[3] = py[i].w;
       }
     }
     __syncthreads();
@@ -242,27 +372,65 @@ __global__ void __launch_bounds__(kTileThreads) ssim_tile_kernel(
       const int r = t % G::EY, g = t / G::EY;
       const float* xr = sm.xs + r * G::EXP + g * (kG * STEP);
       const float* yr = sm.ys + r * G::EXP + g * (kG * STEP);
-      float acc[kG][5];
-#pragma unroll
-      for (int k = 0; k < kG; ++k)
-#pragma unroll
-        for (int m = 0; m < 5; ++m) acc[k][m] = 0.f;
-#pragma unroll
-      for (int j = 0; j < G::SPAN; ++j) {
+      auto moments = [&](int j, float mo[5]) {
         const float xv = xr[j], yv = yr[j];
         const float u = __fsub_rn(xv, c);
         const float d = __fsub_rn(yv, xv);
-        const float mo[5] = {u, d, __fmul_rn(u, u), __fmul_rn(d, d), __fmul_rn(u, d)};
+        mo[0] = u;
+        mo[1] = d;
+        mo[2] = __fmul_rn(u, u);
+        mo[3] = __fmul_rn(d, d);
+        mo[4] = __fmul_rn(u, d);
+      };
+      if constexpr (STEP == 2 && WIN == 7) {
+        // window k = the pairs (2k, 2k+1), (2k+2, 2k+3), (2k+4, 2k+5) and
+        // point 2k+6; each pair is formed once and serves up to three windows
+        float pr[3][5];  // the last three pairs, oldest first
+        float ev[5];
+#pragma unroll
+        for (int j = 0; j < G::SPAN; ++j) {
+          float mo[5];
+          moments(j, mo);
+          if (j % 2 == 0) {
+            if (j >= 6) {
+              const int k = (j - 6) / 2;
+#pragma unroll
+              for (int m = 0; m < 5; ++m)
+                sm.h[m][r][g * kG + k] =
+                    __fadd_rn(__fadd_rn(__fadd_rn(pr[0][m], pr[1][m]), pr[2][m]), mo[m]);
+            }
+#pragma unroll
+            for (int m = 0; m < 5; ++m) ev[m] = mo[m];
+          } else {
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+              pr[0][m] = pr[1][m];
+              pr[1][m] = pr[2][m];
+              pr[2][m] = __fadd_rn(ev[m], mo[m]);
+            }
+          }
+        }
+      } else {
+        float acc[kG][5];
 #pragma unroll
         for (int k = 0; k < kG; ++k)
-          if (j >= STEP * k && j < STEP * k + WIN)
 #pragma unroll
-            for (int m = 0; m < 5; ++m) acc[k][m] = __fadd_rn(acc[k][m], mo[m]);
+          for (int m = 0; m < 5; ++m) acc[k][m] = 0.f;
+#pragma unroll
+        for (int j = 0; j < G::SPAN; ++j) {
+          float mo[5];
+          moments(j, mo);
+#pragma unroll
+          for (int k = 0; k < kG; ++k)
+            if (j >= STEP * k && j < STEP * k + WIN)
+#pragma unroll
+              for (int m = 0; m < 5; ++m) acc[k][m] = __fadd_rn(acc[k][m], mo[m]);
+        }
+#pragma unroll
+        for (int k = 0; k < kG; ++k)
+#pragma unroll
+          for (int m = 0; m < 5; ++m) sm.h[m][r][g * kG + k] = acc[k][m];
       }
-#pragma unroll
-      for (int k = 0; k < kG; ++k)
-#pragma unroll
-        for (int m = 0; m < 5; ++m) sm.h[m][r][g * kG + k] = acc[k][m];
     }
     __syncthreads();
 
@@ -270,13 +438,33 @@ __global__ void __launch_bounds__(kTileThreads) ssim_tile_kernel(
     float s[5];
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
-      float v = 0.f;
+      float v = sm.h[m][STEP * wyl][wxl];
 #pragma unroll
-      for (int j = 0; j < WIN; ++j) v = __fadd_rn(v, sm.h[m][STEP * wyl + j][wxl]);
+      for (int j = 1; j < WIN; ++j) v = __fadd_rn(v, sm.h[m][STEP * wyl + j][wxl]);
       s[m] = v;
     }
     bool window = true;
-    if constexpr (IS3D) {
+    if constexpr (IS3D && STEP == 2 && WIN == 7) {
+      // window k spans planes 2k .. 2k + 6: the pairs formed at planes
+      // 2k + 1, 2k + 3, 2k + 5 and plane 2k + 6 itself
+      if (p & 1) {
+        const int slot = (p >> 1) % 3;
+#pragma unroll
+        for (int m = 0; m < 5; ++m) sm.ring[slot][m][t] = __fadd_rn(prev[m], s[m]);
+        window = false;
+      } else {
+        window = p >= 6;
+        const int h0 = (p >> 1) % 3, h1 = (h0 + 1) % 3, h2 = (h0 + 2) % 3;
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+          prev[m] = s[m];
+          if (window)
+            s[m] = __fadd_rn(
+                __fadd_rn(__fadd_rn(sm.ring[h0][m][t], sm.ring[h1][m][t]), sm.ring[h2][m][t]),
+                s[m]);
+        }
+      }
+    } else if constexpr (IS3D) {
       const int slot = p % WIN;
 #pragma unroll
       for (int m = 0; m < 5; ++m) sm.ring[slot][m][t] = s[m];
@@ -399,8 +587,9 @@ int ssim_parts(const long long dims[3], bool is3d, int win, int step) {
 }
 
 cudaError_t launch_err_metrics(const float* a, const float* b, long long n, double* part_sse,
-                               double* part_max, int nparts, cudaStream_t s) {
-  err_kernel<<<nparts, kErrThreads, 0, s>>>(a, b, n, part_sse, part_max); note_launch(1);
+                               double* part_max, double* part_ac, cudaStream_t s) {
+  err_kernel<<<kErrBlocks, kErrThreads, 0, s>>>(a, b, n, part_sse, part_max, part_ac);
+  note_launch(1);
   return cudaGetLastError();
 }
 
