@@ -188,14 +188,16 @@ qoz_status qoz_blob_histogram(const qoz_blob* b, uint32_t* h_hist, void* stream)
  * indices (int64) and values (float32), then the code section: the codes of
  * all N points (anchors carry code 0) in canonical Huffman code, the entropy
  * stage the rate estimate of Sec. 6.1 stands for.  The code section holds a
- * 288-byte fixed part (used symbols, longest code, chunk size 4096, chunk and
+ * 288-byte fixed part (used symbols, longest code, chunk size, chunk and
  * word counts, number of codes per length 0..63), the used symbols in
  * (length, symbol) order, the n_chunks + 1 word offsets (uint64) and the
  * stream (uint32 words; each chunk starts on a word, codes most significant
  * bit first from each word's most significant bit).  Code lengths follow
  * Huffman's construction with ties going to the leaf queue; codes are
- * RFC 1951's canonical assignment.  Every part is padded to 8 bytes.  The
- * checksum is a 64-bit sum of splitmix64-mixed 8-byte words.
+ * RFC 1951's canonical assignment.  The writer takes the largest chunk size
+ * of 256, 512, 1024, 2048 and 4096 codes that gives at least 8192 chunks
+ * (else 256); a reader accepts any multiple of 8 up to 4096.  Every part is padded
+ * to 8 bytes.  The checksum is a 64-bit sum of splitmix64-mixed 8-byte words.
  *
  * The stream's length depends on the code table, which is built on the
  * device: serialization synchronises `stream` once to learn it.  With

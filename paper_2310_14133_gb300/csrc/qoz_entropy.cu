@@ -13,7 +13,9 @@
 //     depth, a lone symbol gets length 1;
 //   - canonical codes (RFC 1951 Sec. 3.2.2): consecutive integers in
 //     (length, symbol) order;
-//   - stream: chunks of kEntropyChunk symbols, each starting on a 32-bit
+//   - stream: chunks of C symbols (entropy_chunk: the largest power of two
+//     from 256 to 4096 that gives at least 8192 chunks, recorded in the
+//     section's fixed part), each starting on a 32-bit
 //     word, codes most significant bit first, words filled from their most
 //     significant bit, the tail of a chunk's last word zero.
 //
@@ -21,11 +23,14 @@
 // symbols, a global workspace beyond); the encoder counts each chunk's words,
 // scans them into word offsets and writes the chunks (one warp per chunk,
 // each lane a run of consecutive symbols); the decoder walks one chunk per
-// thread with a 12-bit lookup table and the canonical search for longer
-// codes, checking every index against the stream it was given.
+// thread with a 12-bit lookup table and, for longer codes, the canonical
+// codes' interval ends, checking every index against the stream it was
+// given.  Smaller fields get smaller chunks so that their decode still
+// spreads over thousands of threads.
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <type_traits>
 
 #include "../../include/qoz.h"
 #include "qoz_host.h"
@@ -38,6 +43,10 @@ constexpr int kSymbols = 65536;
 constexpr int kTabThreads = 1024;
 constexpr int kHuffSmemSym = 4096;  // used symbols handled in shared memory
 constexpr int kLut = 12;            // bits of the decoder's lookup table
+constexpr int kDecSmemSym = 12288;  // symbols the decoder keeps in shared memory
+constexpr int kDecThreads = 128;    // decoder: one chunk per thread
+constexpr int kRingWords = 64;      // decoder: stream words staged per thread
+constexpr int kRingGroup = 16;      // decoder: words per asynchronous refill
 
 // Workspace of the table kernel (device memory).
 struct HuffWork {
@@ -70,8 +79,8 @@ __device__ __forceinline__ void bitonic_sort(unsigned long long* k, int P) {
 }
 
 __global__ void __launch_bounds__(kTabThreads)
-    huff_table_kernel(const unsigned* __restrict__ hist, long long extra0, HuffWork* w,
-                      HuffFixed* fx, uint16_t* sym_out) {
+    huff_table_kernel(const unsigned* __restrict__ hist, long long extra0, int chunk,
+                      HuffWork* w, HuffFixed* fx, uint16_t* sym_out) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int nsh, maxlen_sh, err_sh;
   __shared__ unsigned bl[64];
@@ -209,7 +218,7 @@ __global__ void __launch_bounds__(kTabThreads)
     }
     fx->n_sym = (uint32_t)n;
     fx->max_len = (uint32_t)maxlen;
-    fx->chunk = (uint32_t)kEntropyChunk;
+    fx->chunk = (uint32_t)chunk;
     fx->flags = 0u;
     for (int b = 0; b < 64; ++b) fx->bl_count[b] = b <= maxlen ? bl[b] : 0u;
     w->err = 0;
@@ -226,8 +235,6 @@ __global__ void __launch_bounds__(kTabThreads)
 
 // Words of each chunk (one warp per chunk; the lanes read the chunk's codes
 // as consecutive 16-byte vectors and sum their code lengths).
-constexpr int kRun = kEntropyChunk / 32;  // symbols of one lane's run (encoder)
-constexpr int kVecPerChunk = kEntropyChunk / 8;
 
 __device__ __forceinline__ void load8(const uint16_t* __restrict__ sym, long long i, long long n,
                                       uint32_t v[4]) {
@@ -248,15 +255,15 @@ __device__ __forceinline__ void load8(const uint16_t* __restrict__ sym, long lon
 
 __global__ void __launch_bounds__(256)
     huff_count_kernel(const uint16_t* __restrict__ sym, long long n,
-                      const unsigned char* __restrict__ len, long long nchunks,
+                      const unsigned char* __restrict__ len, long long nchunks, int chunk,
                       unsigned long long* __restrict__ offs, int* err) {
   const long long c = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (c >= nchunks) return;
-  const long long base = c * kEntropyChunk;
+  const long long base = c * chunk;
   unsigned bits = 0;
   bool missing = false;  // a code the table has no entry for
-  for (int j = 0; j < kVecPerChunk / 32; ++j) {
+  for (int j = 0; j < chunk / 256; ++j) {
     const long long i = base + 8ll * (j * 32 + lane);
     if (i >= n) break;
     uint32_t v[4];
@@ -337,12 +344,11 @@ __global__ void __launch_bounds__(1024)
 
 // The chunks' bits (one warp per chunk).  The chunk's codes are read as
 // consecutive 16-byte vectors and transposed through shared memory into one
-// run of kRun consecutive codes per lane (rows padded to 65 words: the
+// run of kRun consecutive codes per lane (rows padded by one word: the
 // lanes' reads fall in distinct banks).  A lane places its run from its bit
 // offset in the chunk; words the run covers whole are stored, the first and
 // last (shared with the neighbouring runs) are OR-ed into the zeroed stream.
-constexpr int kEncWarps = 4;  // 33 KB of static shared memory per CTA
-constexpr int kRowWords = kRun / 2 + 1;
+constexpr int kEncWarps = 4;  // 33 KB of static shared memory per CTA at 4096
 
 // Appends L <= 32 bits to the lane's accumulator (nacc < 32 pending bits
 // before, so at most one word completes).
@@ -366,16 +372,19 @@ __device__ __forceinline__ void put_bits(unsigned long long& acc, int& nacc, uns
   }
 }
 
-template <bool LONG>
+template <bool LONG, int CHUNK>
 __global__ void __launch_bounds__(32 * kEncWarps)
     huff_encode_kernel(const uint16_t* __restrict__ sym, long long n,
                        const unsigned long long* __restrict__ entry, long long nchunks,
                        const unsigned long long* __restrict__ offs, uint32_t* words) {
+  constexpr int kRun = CHUNK / 32;  // symbols of one lane's run
+  constexpr int kVecPerChunk = CHUNK / 8;
+  constexpr int kRowWords = kRun / 2 + 1;
   __shared__ uint32_t stage[kEncWarps][32 * kRowWords];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long c = (long long)blockIdx.x * kEncWarps + warp;
   if (c >= nchunks) return;
-  const long long base = c * kEntropyChunk;
+  const long long base = c * CHUNK;
   uint32_t* st = stage[warp];
   for (int j = 0; j < kVecPerChunk / 32; ++j) {
     const int q = j * 32 + lane;  // vector q holds codes 8q .. 8q + 7 of the chunk
@@ -427,16 +436,57 @@ __global__ void __launch_bounds__(32 * kEncWarps)
 struct DecTables {
   uint32_t lut[1 << kLut];
   unsigned long long first_code[64];
+  // end of length L's codes, left-justified in 64 bits: canonical codes of
+  // increasing length occupy consecutive intervals, so a code's length is
+  // the first L whose end exceeds the next 64 stream bits
+  unsigned long long end[64];
   unsigned first_index[64];
   unsigned count[64];
 };
 
-__global__ void __launch_bounds__(128)
+// A code longer than kLut bits at bit pos of its chunk, x the 32 stream bits
+// from pos on: the length from the canonical intervals while the code fits
+// in x, then bit by bit from the stream.  Returns (length, symbol), the
+// symbol negative when no code matches.
+__device__ __noinline__ int2 decode_long(const DecTables& T, uint32_t x, unsigned long long pos,
+                                         const uint32_t* __restrict__ W, unsigned long long nw,
+                                         int maxlen, unsigned nsym,
+                                         const uint16_t* __restrict__ syms) {
+  const unsigned long long top = (unsigned long long)x << 32;
+  const int lim = maxlen < 32 ? maxlen : 32;
+  int L = kLut + 1;
+  while (L <= lim && top >= T.end[L]) ++L;
+  if (L <= lim) {
+    const unsigned long long d = (unsigned long long)(x >> (32 - L)) - T.first_code[L];
+    if (d < T.count[L] && T.first_index[L] + d < nsym)
+      return make_int2(L, (int)syms[T.first_index[L] + d]);
+    return make_int2(L, -1);
+  }
+  L = lim;
+  unsigned long long v = L > 0 ? (unsigned long long)(x >> (32 - L)) : 0ull;
+  while (L < maxlen) {
+    ++L;
+    const unsigned long long q = pos + (unsigned long long)(L - 1);
+    const uint32_t w = (q >> 5) < nw ? W[q >> 5] : 0u;
+    v = (v << 1) | ((w >> (31 - (q & 31))) & 1u);
+    if (v >= T.first_code[L] && v - T.first_code[L] < T.count[L]) {
+      const unsigned long long k = T.first_index[L] + (v - T.first_code[L]);
+      return make_int2(L, k < nsym ? (int)syms[k] : -1);
+    }
+  }
+  return make_int2(L, -1);
+}
+
+__global__ void __launch_bounds__(kDecThreads)
     huff_decode_kernel(const uint32_t* __restrict__ words,
                        const unsigned long long* __restrict__ offs, long long nchunks,
-                       long long n, const HuffFixed* __restrict__ fx,
-                       const uint16_t* __restrict__ syms, uint16_t* __restrict__ out, int* err) {
+                       int chunk, long long n, const HuffFixed* __restrict__ fx,
+                       const uint16_t* __restrict__ syms, unsigned nss,
+                       uint16_t* __restrict__ out, int* err) {
   __shared__ DecTables T;
+  // dynamic: the threads' word rings, then nss <= n_sym symbols
+  extern __shared__ __align__(16) uint32_t ring_all[];
+  uint16_t* ssym = reinterpret_cast<uint16_t*>(ring_all + kDecThreads * (kRingWords + 1));
   const int t = threadIdx.x;
   const int maxlen = (int)fx->max_len;
   const unsigned nsym = fx->n_sym;
@@ -450,95 +500,154 @@ __global__ void __launch_bounds__(128)
       T.first_index[b] = idx;
       T.count[b] = b >= 1 && b <= maxlen ? fx->bl_count[b] : 0u;
       idx += T.count[b];
+      const unsigned long long lim = c + T.count[b];
+      T.end[b] = b == 0 ? 0ull : (lim >= (1ull << b) ? ~0ull : lim << (64 - b));
     }
   }
   __syncthreads();
-  // lookup entries of the codes with length <= kLut
-  for (unsigned i = t; i < nsym; i += blockDim.x) {
+  // lookup entries, one per kLut-bit prefix: the code whose interval holds
+  // the prefix (symbol << 8 | length) if its length is at most kLut; for a
+  // prefix of longer codes 0x80 | the shortest length among them; 0 for a
+  // prefix of no code
+  for (int k = t; k < (1 << kLut); k += blockDim.x) {
+    const unsigned long long top = (unsigned long long)k << (64 - kLut);
     int L = 1;
-    while (L <= maxlen && i >= T.first_index[L] + T.count[L]) ++L;
-    if (L > kLut) continue;
-    const unsigned long long cv = T.first_code[L] + (i - T.first_index[L]);
-    const unsigned lo = (unsigned)(cv << (kLut - L)), hi = (unsigned)((cv + 1) << (kLut - L));
-    for (unsigned k = lo; k < hi && k < (1u << kLut); ++k)
-      T.lut[k] = ((uint32_t)syms[i] << 8) | (uint32_t)L;
+    while (L <= maxlen && top >= T.end[L]) ++L;
+    if (L > maxlen) continue;
+    if (L > kLut) {
+      T.lut[k] = 0x80u | (uint32_t)L;
+      continue;
+    }
+    const unsigned long long d = (top >> (64 - L)) - T.first_code[L];
+    if (d < T.count[L] && T.first_index[L] + d < nsym)
+      T.lut[k] = ((uint32_t)syms[T.first_index[L] + d] << 8) | (uint32_t)L;
   }
+  // the first nss symbols (the long codes' among them) in shared memory
+  for (unsigned k = t; k < nss; k += blockDim.x) ssym[k] = syms[k];
   __syncthreads();
   const long long c = blockIdx.x * (long long)blockDim.x + t;
   if (c >= nchunks) return;
   const unsigned long long w0 = offs[c], w1 = offs[c + 1];
-  if (w1 < w0) {
+  if (w1 < w0 || w1 - w0 > 0xffffffffull) {
     atomicOr(err, 4);
     return;
   }
-  const unsigned long long nbits = (w1 - w0) * 32ull;
+  const unsigned nw = (unsigned)(w1 - w0);  // the chunk's words
   const uint32_t* W = words + w0;
-  auto word_at = [&](unsigned long long k) -> unsigned long long {
-    return k < w1 - w0 ? (unsigned long long)W[k] : 0ull;
-  };
-  unsigned long long bp = 0;  // bit position in the chunk
-  const long long b = c * kEntropyChunk;
-  const long long e = b + kEntropyChunk < n ? b + kEntropyChunk : n;
-  // words cw and cw + 1 form the decoding window; the next four are loaded
-  // ahead into a register queue, so that moving the window on waits for no
-  // load (a code is at most 58 bits, so a code moves it by at most two words)
-  long long cw = 0;
-  unsigned long long wa = word_at(0), wb = word_at(1);
-  unsigned long long q0 = word_at(2), q1 = word_at(3), q2 = word_at(4), q3 = word_at(5);
-  uint32_t grp[4] = {0u, 0u, 0u, 0u};  // eight decoded codes, stored as one 16-byte vector
-  for (long long i = b; i < e; ++i) {
-    const long long wk = (long long)(bp >> 5);
-    while (cw < wk) {
-      wa = wb;
-      wb = q0;
-      q0 = q1;
-      q1 = q2;
-      q2 = q3;
-      q3 = word_at((unsigned long long)(cw + 6));
-      ++cw;
+  // The chunk's words pass through this thread's ring of kRingWords words
+  // in shared memory (four groups of kRingGroup), filled by asynchronous
+  // copies a group at a time: when the window's second word enters group m,
+  // group m + 2 is issued into the slots of group m - 2 and group m is
+  // waited for (two groups may stay in flight).  Words past the chunk's end
+  // read as zero.
+  uint32_t* ring = ring_all + t * (kRingWords + 1);
+  const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
+  auto issue_group = [&](unsigned g) {
+#pragma unroll
+    for (int k = 0; k < kRingGroup; ++k) {
+      const unsigned wi = kRingGroup * g + k;
+      const bool in = wi < nw;
+      const uint32_t* src = in ? W + wi : words;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(
+                       ring_s + 4 * (wi & (kRingWords - 1))),
+                   "l"(src), "r"(in ? 4 : 0)
+                   : "memory");
     }
-    const unsigned long long win = (wa << 32) | wb;  // the 64 bits from word cw on
-    const unsigned long long top = win << (bp & 31);  // >= 33 valid bits
-    const uint32_t ent = T.lut[top >> (64 - kLut)];
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  issue_group(0);
+  issue_group(1);
+  issue_group(2);
+  asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+  // the window: words wcur and wcur + 1 (w0r, w1r), sh bits of w0r consumed
+  unsigned wcur = 0;
+  uint32_t w0r = ring[0], w1r = ring[1];
+  int sh = 0;
+  // the window moves on by one word when adv (without a branch but for the
+  // rare refill)
+  auto advance = [&](bool adv) {
+    w0r = adv ? w1r : w0r;
+    wcur += adv ? 1u : 0u;
+    const unsigned nx = wcur + 1;
+    if (adv && (nx & (kRingGroup - 1)) == 0) {
+      issue_group(nx / kRingGroup + 2);
+      asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+    }
+    const uint32_t nxt = ring[nx & (kRingWords - 1)];
+    w1r = adv ? nxt : w1r;
+  };
+  // one code: the 32 stream bits from the window's position and the lookup
+  // table; a longer code's length from the canonical interval ends, starting
+  // at the shortest length under its prefix, its symbol from shared memory;
+  // codes beyond 32 bits and prefixes of no code out of line
+  const int lim = maxlen < 32 ? maxlen : 32;
+  auto decode = [&](int& sym) -> bool {
+    const uint32_t x = __funnelshift_l(w1r, w0r, (unsigned)sh);
+    const uint32_t ent = T.lut[x >> (32 - kLut)];
     int L = (int)(ent & 0xffu);
-    int s;
-    if (L) {
-      s = (int)(ent >> 8);
-    } else {
-      // canonical search over the longer lengths, bit by bit from the stream
-      unsigned long long v = top >> (64 - kLut);
-      s = -1;
-      L = kLut;
-      while (L < maxlen) {
-        ++L;
-        const unsigned long long q = bp + (unsigned long long)(L - 1);
-        v = (v << 1) | ((word_at(q >> 5) >> (31 - (q & 31))) & 1ull);
-        if (v >= T.first_code[L] && v - T.first_code[L] < T.count[L]) {
-          const unsigned long long k = T.first_index[L] + (v - T.first_code[L]);
-          if (k < nsym) s = syms[k];
-          break;
-        }
+    sym = (int)(ent >> 8);
+    if (L & 0x80) {
+      L &= 0x7f;
+      if (L <= lim) {
+        const unsigned long long top = (unsigned long long)x << 32;
+        while (L < lim && top >= T.end[L]) ++L;
+        const unsigned long long d = (unsigned long long)(x >> (32 - L)) - T.first_code[L];
+        const unsigned long long k = T.first_index[L] + d;
+        if (top < T.end[L] && d < T.count[L] && k < nsym)
+          sym = k < nss ? (int)ssym[k] : (int)syms[k];
+        else
+          L = 0;
+      } else {
+        L = 0;
       }
-      if (s < 0) {
+    }
+    if (L == 0) {
+      const int2 r = decode_long(T, x, 32ull * wcur + (unsigned long long)sh, W, nw, maxlen,
+                                 nsym, syms);
+      L = r.x;
+      sym = r.y;
+      if (sym < 0) return false;
+      if (L > 32) {  // a code longer than a word: the window moves twice
+        L -= 32;
+        advance(true);
+      }
+    }
+    sh += L;
+    const bool adv = sh >= 32;
+    sh -= adv ? 32 : 0;
+    advance(adv);
+    return true;
+  };
+  const long long b = c * chunk;
+  const int cnt = (int)(b + chunk < n ? chunk : n - b);
+  uint16_t* o = out + b;
+  int i = 0;
+  for (; i + 8 <= cnt; i += 8) {  // chunks start on multiples of eight codes
+    uint32_t g[4];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      int sym;
+      if (!decode(sym)) {
         atomicOr(err, 4);
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
         return;
       }
+      g[k >> 1] = (k & 1) ? (g[k >> 1] | ((uint32_t)sym << 16)) : (uint32_t)sym;
     }
-    bp += (unsigned long long)L;
-    if (bp > nbits) {
+    *reinterpret_cast<uint4*>(o + i) = make_uint4(g[0], g[1], g[2], g[3]);
+  }
+  for (; i < cnt; ++i) {
+    int sym;
+    if (!decode(sym)) {
       atomicOr(err, 4);
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
       return;
     }
-    const int g = (int)(i - b) & 7;  // chunks start on multiples of eight codes
-    grp[g >> 1] |= (uint32_t)s << (16 * (g & 1));
-    if (g == 7) {
-      *reinterpret_cast<uint4*>(out + (i - 7)) = make_uint4(grp[0], grp[1], grp[2], grp[3]);
-      grp[0] = grp[1] = grp[2] = grp[3] = 0u;
-    }
+    o[i] = (uint16_t)sym;
   }
-  const long long tail = (e - b) & 7;  // the last partial group
-  for (long long k = 0; k < tail; ++k)
-    out[e - tail + k] = (uint16_t)(grp[k >> 1] >> (16 * (k & 1)));
+  // the codes must end inside the chunk's words
+  if (32ull * wcur + (unsigned long long)sh > 32ull * nw) atomicOr(err, 4);
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
 }  // namespace
@@ -554,7 +663,8 @@ void huff_free(HuffEncoded* h, cudaStream_t s) {
 
 qoz_status huff_encode(const qoz_blob* b, cudaStream_t s, HuffEncoded* h, bool sizes_only) {
   memset(h, 0, sizeof(*h));
-  h->n_chunks = (b->N + kEntropyChunk - 1) / kEntropyChunk;
+  h->chunk = entropy_chunk(b->N);
+  h->n_chunks = (b->N + h->chunk - 1) / h->chunk;
   // the section's fixed part and symbol list, then the chunk offsets
   h->sym_bytes = pad8_bytes(sizeof(uint16_t) * kSymbols);
   const size_t sec = sizeof(HuffFixed) + h->sym_bytes + sizeof(unsigned long long) * (h->n_chunks + 1);
@@ -575,14 +685,15 @@ qoz_status huff_encode(const qoz_blob* b, cudaStream_t s, HuffEncoded* h, bool s
   if (e == cudaSuccess)
     e = ensure_smem_attr((const void*)huff_table_kernel, &attr_done, kTabSmem);
   if (e == cudaSuccess) {
-    huff_table_kernel<<<1, kTabThreads, kTabSmem, s>>>(b->d_hist, b->na, w, fx, syms);
+    huff_table_kernel<<<1, kTabThreads, kTabSmem, s>>>(b->d_hist, b->na, h->chunk, w, fx, syms);
     note_launch(1);
     e = launch_check(cudaGetLastError());
   }
   const long long nch = h->n_chunks;
   const unsigned grid = (unsigned)((nch * 32 + 255) / 256);
   if (e == cudaSuccess && nch > 0) {
-    huff_count_kernel<<<grid, 256, 0, s>>>(b->d_codes, b->N, w->len, nch, offs, &w->err);
+    huff_count_kernel<<<grid, 256, 0, s>>>(b->d_codes, b->N, w->len, nch, h->chunk, offs,
+                                           &w->err);
     note_launch(1);
     e = launch_check(cudaGetLastError());
   }
@@ -621,12 +732,23 @@ qoz_status huff_encode(const qoz_blob* b, cudaStream_t s, HuffEncoded* h, bool s
     e = cudaMemsetAsync(h->d_words, 0, sizeof(uint32_t) * (size_t)h->n_words + 8, s);
     if (e == cudaSuccess) {
       const unsigned eg = (unsigned)((nch + kEncWarps - 1) / kEncWarps);
+      auto enc = [&](auto lng, auto ck) {
+        huff_encode_kernel<decltype(lng)::value, decltype(ck)::value>
+            <<<eg, 32 * kEncWarps, 0, s>>>(b->d_codes, b->N, w->code, nch, offs, h->d_words);
+      };
+      auto by_chunk = [&](auto lng) {
+        switch (h->chunk) {
+          case 256: enc(lng, std::integral_constant<int, 256>()); break;
+          case 512: enc(lng, std::integral_constant<int, 512>()); break;
+          case 1024: enc(lng, std::integral_constant<int, 1024>()); break;
+          case 2048: enc(lng, std::integral_constant<int, 2048>()); break;
+          default: enc(lng, std::integral_constant<int, 4096>()); break;
+        }
+      };
       if (hf.max_len > 32)
-        huff_encode_kernel<true><<<eg, 32 * kEncWarps, 0, s>>>(b->d_codes, b->N, w->code, nch,
-                                                                offs, h->d_words);
+        by_chunk(std::true_type());
       else
-        huff_encode_kernel<false><<<eg, 32 * kEncWarps, 0, s>>>(b->d_codes, b->N, w->code, nch,
-                                                                 offs, h->d_words);
+        by_chunk(std::false_type());
       note_launch(1);
       e = launch_check(cudaGetLastError());
     }
@@ -641,15 +763,25 @@ qoz_status huff_encode(const qoz_blob* b, cudaStream_t s, HuffEncoded* h, bool s
 }
 
 cudaError_t huff_decode(const void* d_section, const uint32_t* d_words, long long nchunks,
-                        long long N, uint16_t* d_codes, int* d_err, cudaStream_t s) {
+                        int chunk, unsigned n_sym, long long N, uint16_t* d_codes, int* d_err,
+                        cudaStream_t s) {
   if (nchunks <= 0) return cudaSuccess;
   const HuffFixed* fx = static_cast<const HuffFixed*>(d_section);
   const uint16_t* syms =
       reinterpret_cast<const uint16_t*>(static_cast<const char*>(d_section) + sizeof(HuffFixed));
   const unsigned long long* offs = reinterpret_cast<const unsigned long long*>(
       static_cast<const char*>(d_section) + sizeof(HuffFixed) + pad8_bytes(sizeof(uint16_t) * kSymbols));
-  const unsigned grid = (unsigned)((nchunks + 127) / 128);
-  huff_decode_kernel<<<grid, 128, 0, s>>>(d_words, offs, nchunks, N, fx, syms, d_codes, d_err);
+  // symbols held in shared memory: all of them up to kDecSmemSym, the first
+  // kDecSmemSym otherwise; beside them the threads' word rings
+  const unsigned nss = n_sym < (unsigned)kDecSmemSym ? n_sym : (unsigned)kDecSmemSym;
+  constexpr size_t kRingBytes = sizeof(uint32_t) * kDecThreads * (kRingWords + 1);
+  static unsigned long long attr_done = 0;
+  cudaError_t e = ensure_smem_attr((const void*)huff_decode_kernel, &attr_done,
+                                   kRingBytes + sizeof(uint16_t) * kDecSmemSym);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)((nchunks + kDecThreads - 1) / kDecThreads);
+  huff_decode_kernel<<<grid, kDecThreads, kRingBytes + sizeof(uint16_t) * nss, s>>>(
+      d_words, offs, nchunks, chunk, N, fx, syms, nss, d_codes, d_err);
   note_launch(1);
   return cudaGetLastError();
 }

@@ -182,7 +182,16 @@ cudaError_t launch_autocorr(const float* a, const float* b, long long n, long lo
 double autocorr_from_parts(const double* h, long long n, long long k);
 
 // Entropy stage (qoz_entropy.cu): canonical Huffman coding of the codes.
-constexpr int kEntropyChunk = 4096;  // symbols per independently coded chunk
+constexpr int kEntropyChunk = 4096;     // largest chunk: symbols per independently coded chunk
+constexpr int kEntropyChunkMin = 256;   // smallest chunk a stream is written with
+// Chunk size for N codes: the largest power of two from 256 to 4096 that
+// still gives at least 8192 chunks (one decoding thread per chunk), else
+// 256; a reader accepts any multiple of 8 up to 4096.
+inline int entropy_chunk(long long N) {
+  int c = kEntropyChunk;
+  while (c > kEntropyChunkMin && (N + c - 1) / c < 8192) c >>= 1;
+  return c;
+}
 constexpr int kMaxCodeLen = 58;      // longest code the coder handles
 
 // Fixed part of the serialized code section (288 bytes): counts, then the
@@ -201,6 +210,7 @@ inline size_t pad8_bytes(size_t v) { return (v + 7) & ~(size_t)7; }
 // the n_words stream words.
 struct HuffEncoded {
   HuffFixed fixed;
+  int chunk;  // symbols per chunk
   long long n_chunks, n_words;
   size_t sym_bytes;
   void* d_work;
@@ -218,7 +228,8 @@ void huff_free(HuffEncoded* h, cudaStream_t s);
 // out as huff_encode's; bit 2 of *d_err reports a stream that does not
 // decode.
 cudaError_t huff_decode(const void* d_section, const uint32_t* d_words, long long nchunks,
-                        long long N, uint16_t* d_codes, int* d_err, cudaStream_t s);
+                        int chunk, unsigned n_sym, long long N, uint16_t* d_codes, int* d_err,
+                        cudaStream_t s);
 
 #ifdef QOZ_DEBUG_BOUNDS
 // Records of failed index checks, one per translation unit that checks.

@@ -326,7 +326,7 @@ qoz_status qoz_blob_serialize_bound(const qoz_blob* b, size_t* bound) {
   if (!b || !bound) return fail(QOZ_EINVAL, "NULL argument");
   // an optimal prefix code averages under 17 bits on a 65536-symbol
   // alphabet; each chunk adds at most one partly filled word
-  const long long nch = (b->N + kEntropyChunk - 1) / kEntropyChunk;
+  const long long nch = (b->N + kEntropyChunkMin - 1) / kEntropyChunkMin;  // at most
   const long long words = (b->N * 17 + 31) / 32 + nch;
   *bound = layout_of(b->na, b->nu, 65536, nch, words).total;
   return QOZ_OK;
@@ -336,9 +336,10 @@ qoz_status qoz_blob_serialize_bound(const qoz_blob* b, size_t* bound) {
 // counts, a complete prefix code (Kraft's equality) and the symbol order.
 static bool code_section_ok(const HuffFixed& f, long long N, const unsigned char* sym_bytes,
                      size_t avail) {
-  const long long nch = (N + kEntropyChunk - 1) / kEntropyChunk;
-  if (f.chunk != (uint32_t)kEntropyChunk || f.flags != 0 || (long long)f.n_chunks != nch)
+  if (f.chunk < 8 || f.chunk > (uint32_t)kEntropyChunk || f.chunk % 8 != 0 || f.flags != 0)
     return false;
+  const long long nch = (N + f.chunk - 1) / f.chunk;
+  if ((long long)f.n_chunks != nch) return false;
   if (f.n_sym > 65536 || f.max_len > (uint32_t)kMaxCodeLen || f.bl_count[0] != 0) return false;
   if ((N > 0) != (f.n_sym > 0)) return false;
   unsigned long long sum = 0, kraft = 0;
@@ -449,6 +450,7 @@ qoz_status qoz_blob_deserialize(const void* h_buf, size_t size, void* stream, qo
   HuffEncoded hc;
   memset(&hc, 0, sizeof(hc));
   hc.fixed = f;
+  hc.chunk = (int)f.chunk;
   hc.n_chunks = (long long)f.n_chunks;
   hc.n_words = (long long)f.n_words;
   hc.sym_bytes = pad8_bytes(sizeof(uint16_t) * 65536);
@@ -490,7 +492,8 @@ qoz_status qoz_blob_deserialize(const void* h_buf, size_t size, void* stream, qo
     e = cudaMemcpyAsync(hc.d_words, in + L.words, sizeof(uint32_t) * hc.n_words,
                         cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
-    e = launch_check(huff_decode(hc.d_section, hc.d_words, hc.n_chunks, b->N, b->d_codes,
+    e = launch_check(huff_decode(hc.d_section, hc.d_words, hc.n_chunks, hc.chunk, f.n_sym, b->N,
+                                 b->d_codes,
                                  b->d_err, s));
   Part parts[7];
   const int np = e == cudaSuccess ? parts_of(b, hc, L, parts) : 0;

@@ -15,6 +15,15 @@ pytestmark = pytest.mark.gpu
 HEADER = 160
 FIXED = 288
 CHUNK = 4096
+
+
+def writer_chunk(n):
+    """The writer's chunk size for n codes: the largest of 4096, 2048, 1024,
+    512 and 256 that gives at least 8192 chunks, else 256."""
+    c = 4096
+    while c > 256 and -(-n // c) < 8192:
+        c //= 2
+    return c
 # header fields (byte offsets): counts, checksum, code-section size
 OFF_ANCHORS, OFF_CHECKSUM, OFF_CODE_BYTES = 120, 136, 144
 
@@ -58,12 +67,13 @@ def parse(buf):
                 total=wo + pad8(4 * n_words))
 
 
-def expected(orc, codes):
+def expected(orc, codes, chunk=None):
     """The oracle's table and stream for the codes of all points."""
+    chunk = writer_chunk(codes.size) if chunk is None else chunk
     h = np.bincount(codes.ravel(), minlength=65536).astype(np.uint64)
     ln, mx = orc.huffman_lengths(h)
     cd = orc.canonical_codes(ln)
-    words, offs = orc.huffman_encode(codes.ravel(), ln, cd, chunk=CHUNK)
+    words, offs = orc.huffman_encode(codes.ravel(), ln, cd, chunk=chunk)
     used = np.nonzero(ln)[0]
     order = sorted(used, key=lambda s: (int(ln[s]), int(s)))
     bl = np.bincount(ln[used], minlength=64).astype(np.uint32)
@@ -75,7 +85,7 @@ def check_section(orc, q, blob, buf):
     codes = blob.arrays()[0].cpu().numpy().view(np.uint16)
     sec = parse(buf)
     ref = expected(orc, codes)
-    assert sec["chunk"] == CHUNK and sec["flags"] == 0
+    assert sec["chunk"] == writer_chunk(codes.size) and sec["flags"] == 0
     assert sec["n_sym"] == ref["syms"].size and sec["max_len"] == ref["mx"]
     assert np.array_equal(sec["bl"], ref["bl"]), "codes per length"
     assert np.array_equal(sec["syms"], ref["syms"]), "symbol order"
@@ -146,17 +156,19 @@ def _checksum(b):
         return int(np.sum(mix(w ^ mix(np.arange(w.size, dtype=np.uint64))), dtype=np.uint64))
 
 
-def test_gpu_decodes_oracle_stream(q, orc):
-    # replace the GPU's code section by one the oracle wrote (chunk size and
-    # layout as specified), fix the checksum, and decode on the GPU
+@pytest.mark.parametrize("chunk", [CHUNK, 512, 200])
+def test_gpu_decodes_oracle_stream(q, orc, chunk):
+    # replace the GPU's code section by one the oracle wrote (layout as
+    # specified; a reader takes any chunk size that is a multiple of 8 up to
+    # 4096), fix the checksum, and decode on the GPU
     import synth
     x = synth.grf((36, 40, 70), 5.0 / 3.0, seed=21, n_modes=48).cuda()
     blob = q.compress(x, 1e-3)
     buf = bytes(blob.serialize().numpy())
     codes = blob.arrays()[0].cpu().numpy().view(np.uint16)
-    ref = expected(orc, codes)
+    ref = expected(orc, codes, chunk)
     sec = parse(buf)
-    fixed = struct.pack("<IIIIQQ", ref["syms"].size, ref["mx"], CHUNK, 0, ref["offs"].size - 1,
+    fixed = struct.pack("<IIIIQQ", ref["syms"].size, ref["mx"], chunk, 0, ref["offs"].size - 1,
                         ref["words"].size) + ref["bl"].tobytes()
     body = fixed + ref["syms"].tobytes()
     body += bytes(pad8(len(body)) - len(body))
@@ -202,6 +214,13 @@ def test_corrupt_code_sections(q):
         expect_corrupt(b)
     # truncated inside the stream words
     expect_corrupt(raw[: len(raw) - 12])
+    # chunk sizes a reader does not take (checksum made valid, so the code
+    # section's own check rejects them)
+    for bad in (12, 8192, 0):
+        b = bytearray(raw)
+        struct.pack_into("<I", b, sec["code_off"] + 8, bad)
+        struct.pack_into("<Q", b, OFF_CHECKSUM, _checksum(bytes(b)))
+        expect_corrupt(b)
     blob.free()
 
 
