@@ -1013,7 +1013,7 @@ def main():
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "level_tma_kernel (level 1 of the compression, histogram fused)",
+                     "kernel": "level1_kernel (level 1 of the compression: persistent CTAs, bulk tensor copies, histogram counted in the passes)",
                      "algorithmic_bytes_per_launch": LEVEL1_BYTES_PER_POINT * N,
                      "peak_kind": peak_kind},
         "roofline_pq": {"bound": "hbm", "achieved": 6.0 * N / (pq_ms * 1e-3) / 1e9, "peak": peak,

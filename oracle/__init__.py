@@ -256,9 +256,21 @@ def canonical_codes(lengths):
 ENTROPY_CHUNK = 4096
 
 
-def huffman_encode(symbols, lengths, codes, chunk: int = ENTROPY_CHUNK):
-    """(words uint32, offs uint64) of the chunked MSB-first stream."""
+def entropy_chunk(n: int) -> int:
+    """The stream's chunk size for n codes (reading A21 of the entropy
+    stage): the largest of 4096, 2048, 1024, 512 and 256 codes that still
+    gives at least 8192 chunks, else 256."""
+    c = ENTROPY_CHUNK
+    while c > 256 and -(-n // c) < 8192:
+        c //= 2
+    return c
+
+
+def huffman_encode(symbols, lengths, codes, chunk: int | None = None):
+    """(words uint32, offs uint64) of the chunked MSB-first stream; chunk
+    None takes entropy_chunk of the symbol count."""
     s = np.ascontiguousarray(symbols, dtype=np.uint16).ravel()
+    chunk = entropy_chunk(s.size) if chunk is None else int(chunk)
     ln = np.ascontiguousarray(lengths, dtype=np.uint8)
     cd = np.ascontiguousarray(codes, dtype=np.uint64)
     nch = (s.size + chunk - 1) // chunk
@@ -272,7 +284,8 @@ def huffman_encode(symbols, lengths, codes, chunk: int = ENTROPY_CHUNK):
     return words[:w].copy(), offs
 
 
-def huffman_decode(words, offs, n: int, lengths, codes, chunk: int = ENTROPY_CHUNK):
+def huffman_decode(words, offs, n: int, lengths, codes, chunk: int | None = None):
+    chunk = entropy_chunk(n) if chunk is None else int(chunk)
     w = np.ascontiguousarray(words, dtype=np.uint32)
     o = np.ascontiguousarray(offs, dtype=np.uint64)
     ln = np.ascontiguousarray(lengths, dtype=np.uint8)

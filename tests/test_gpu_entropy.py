@@ -17,13 +17,6 @@ FIXED = 288
 CHUNK = 4096
 
 
-def writer_chunk(n):
-    """The writer's chunk size for n codes: the largest of 4096, 2048, 1024,
-    512 and 256 that gives at least 8192 chunks, else 256."""
-    c = 4096
-    while c > 256 and -(-n // c) < 8192:
-        c //= 2
-    return c
 # header fields (byte offsets): counts, checksum, code-section size
 OFF_ANCHORS, OFF_CHECKSUM, OFF_CODE_BYTES = 120, 136, 144
 
@@ -69,7 +62,7 @@ def parse(buf):
 
 def expected(orc, codes, chunk=None):
     """The oracle's table and stream for the codes of all points."""
-    chunk = writer_chunk(codes.size) if chunk is None else chunk
+    chunk = orc.entropy_chunk(codes.size) if chunk is None else chunk
     h = np.bincount(codes.ravel(), minlength=65536).astype(np.uint64)
     ln, mx = orc.huffman_lengths(h)
     cd = orc.canonical_codes(ln)
@@ -85,7 +78,7 @@ def check_section(orc, q, blob, buf):
     codes = blob.arrays()[0].cpu().numpy().view(np.uint16)
     sec = parse(buf)
     ref = expected(orc, codes)
-    assert sec["chunk"] == writer_chunk(codes.size) and sec["flags"] == 0
+    assert sec["chunk"] == orc.entropy_chunk(codes.size) and sec["flags"] == 0
     assert sec["n_sym"] == ref["syms"].size and sec["max_len"] == ref["mx"]
     assert np.array_equal(sec["bl"], ref["bl"]), "codes per length"
     assert np.array_equal(sec["syms"], ref["syms"]), "symbol order"

@@ -132,3 +132,22 @@ def test_round_trip(n, chunk, seed):
     assert int(offs[-1]) <= (total + 31) // 32 + (offs.size - 1)
     out = orc.huffman_decode(words, offs, n, ln, code, chunk=chunk)
     assert np.array_equal(out, sym)
+
+
+def test_chunk_size_rule(orc):
+    """The writer's chunk size (reading A21): the largest of 4096 .. 256 codes
+    that still gives 8192 chunks, else 256; worked by hand at the sizes of
+    the workloads (48^3, 256^3, 512^3, 1024^3) and at the switch points."""
+    assert orc.entropy_chunk(0) == 256
+    assert orc.entropy_chunk(48 ** 3) == 256          # 432 chunks
+    assert orc.entropy_chunk(256 * 8192) == 256       # exactly 8192 chunks of 256
+    assert orc.entropy_chunk(512 * 8191) == 256       # 8191 chunks of 512: too few
+    assert orc.entropy_chunk(512 * 8191 + 1) == 512   # 8192 chunks, the last one short
+    assert orc.entropy_chunk(256 ** 3) == 2048        # 8192 chunks of 2048
+    assert orc.entropy_chunk(512 ** 3) == 4096
+    assert orc.entropy_chunk(1024 ** 3) == 4096
+    # the default stream of a small symbol list is one chunk of the rule's size
+    ln = np.array([1, 1], dtype=np.uint8)
+    words, offs = orc.huffman_encode(np.array([0, 1, 1, 0] * 100, np.uint16), ln,
+                                     orc.canonical_codes(ln))
+    assert offs.size == 400 // 256 + 2 and offs[-1] == words.size
