@@ -121,6 +121,175 @@ __device__ __forceinline__ float warp_nan_max(float v) {
 // flag then reports it).
 constexpr unsigned kTrialWaitPolls = 1u << 24;
 
+// One pass of a trial, its geometry fixed at compile time: Bk is physical
+// axis k's role in the pass (0: an axis the level's order visits before the
+// pass axis, every h; 1: the pass axis, targets at h mod 2h; 2: an axis
+// visited after it, every 2h), IP the interpolator.  Every target of the
+// pass, flattened (x fastest) so that all lanes work; the quotients come
+// from a binary32 reciprocal, which is exact for dividends below 70000 and
+// divisors below 4100 (checked exhaustively), else from integer division.
+struct TrialPass {
+  float* S;
+  int nS;
+  int m0, m1, m2, st0, st1, h;
+  float el, two_e, inv;
+  bool score, metrics, hist;
+  unsigned* SH;     // histogram window
+  unsigned* ghist;  // the candidate's global histogram (codes outside the window)
+};
+
+struct TrialAcc {
+  KSum l1, sse;
+  float mx = 0.0f;
+  int l1n = 0, unp = 0;
+};
+
+constexpr float kQTwo23 = 8388608.0f;     // 2^23
+constexpr float kQCodeBias = 8421376.0f;  // 2^23 + 32768
+
+template <int THREADS, bool kFull, int B0, int B1, int B2, int IP>
+__device__ __forceinline__ void trial_pass(const TrialPass& t, TrialAcc& acc) {
+  static_assert((B0 == 1) + (B1 == 1) + (B2 == 1) == 1, "one pass axis");
+  constexpr int AX = B0 == 1 ? 0 : (B1 == 1 ? 1 : 2);
+  const int h = t.h, h2 = 2 * h;
+  const int s0 = B0 == 1 ? h : 0, s1 = B1 == 1 ? h : 0, s2 = B2 == 1 ? h : 0;
+  const int d0 = B0 == 0 ? h : h2, d1 = B1 == 0 ? h : h2, d2 = B2 == 0 ? h : h2;
+  const int c0n = t.m0 - 1 >= s0 ? (t.m0 - 1 - s0) / d0 + 1 : 0;
+  const int c1n = t.m1 - 1 >= s1 ? (t.m1 - 1 - s1) / d1 + 1 : 0;
+  const int c2n = t.m2 - 1 >= s2 ? (t.m2 - 1 - s2) / d2 + 1 : 0;
+  const int sa = AX == 0 ? t.st0 : (AX == 1 ? t.st1 : 1);
+  const int na = AX == 0 ? t.m0 : (AX == 1 ? t.m1 : t.m2);
+  const int hs = h * sa;
+  const int nrow = c0n * c1n;
+  const int items = nrow * c2n;
+  const bool fdiv = items < 70000 && c2n < 4100 && c1n < 4100;
+  const float rc2 = 1.0f / (float)(c2n > 0 ? c2n : 1);
+  const float rc1 = 1.0f / (float)(c1n > 0 ? c1n : 1);
+  float* S = t.S;
+  const int nS = t.nS;
+  (void)nS;
+  const int lane = threadIdx.x & 31;
+  // a target's position, its field value and its prediction
+  struct Tgt {
+    int li;
+    float xv, pred;
+    bool ok;
+  };
+  auto fetch = [&](int it) -> Tgt {
+    const int row =
+        fdiv ? __float2int_rz(__fmul_rn(__fadd_rn(__int2float_rn(it), 0.5f), rc2)) : it / c2n;
+    const int i2 = it - row * c2n;
+    const int i0 =
+        fdiv ? __float2int_rz(__fmul_rn(__fadd_rn(__int2float_rn(row), 0.5f), rc1)) : row / c1n;
+    const int i1 = row - i0 * c1n;
+    const int z = s0 + i0 * d0, y = s1 + i1 * d1, xx = s2 + i2 * d2;
+    Tgt g;
+    g.li = z * t.st0 + y * t.st1 + xx;
+    const int ca = AX == 0 ? z : (AX == 1 ? y : xx);
+    const bool hb1 = ca + h < na, ha3 = ca >= 3 * h, hb3 = ca + 3 * h < na;
+    g.ok = QOZ_IN(g.li, nS) && QOZ_IN(g.li - hs, nS) && (!hb1 || QOZ_IN(g.li + hs, nS)) &&
+           (!ha3 || QOZ_IN(g.li - 3 * hs, nS)) && (!hb3 || QOZ_IN(g.li + 3 * hs, nS));
+    if (!g.ok) {
+      g.xv = g.pred = 0.0f;
+      return g;
+    }
+    const float a1 = S[g.li - hs];
+    const float b1 = hb1 ? S[g.li + hs] : 0.0f;
+    const float a3 = ha3 ? S[g.li - 3 * hs] : 0.0f;
+    const float b3 = hb3 ? S[g.li + 3 * hs] : 0.0f;
+    g.pred = predict(a3, a1, b1, b3, ha3, hb1, hb3, IP);
+    g.xv = S[g.li];  // not yet predicted: still the field value
+    return g;
+  };
+  auto finish = [&](const Tgt& g) {
+    const float xv = g.xv, pred = g.pred;
+    if (t.score) {
+      const float ad = fabsf(__fsub_rn(xv, pred));
+      if (isfinite(ad)) {
+        acc.l1.add(ad);
+        ++acc.l1n;
+      }
+    }
+    // the quantizer's fast path: m = floor(|d| inv + 0.5) from a
+    // round-toward-minus-infinity add of 2^23, the code from the bits of
+    // q + 2^23 + 32768; whenever it accepts a point its result is the
+    // reference quantizer's, which decides every other point
+    const float d = __fsub_rn(xv, pred);
+    const float u = __fadd_rn(__fmul_rn(fabsf(d), t.inv), 0.5f);
+    const float m = __fsub_rn(__fadd_rd(u, kQTwo23), kQTwo23);
+    const float cf = __fadd_rn(copysignf(m, d), kQCodeBias);
+    float rec = __fadd_rn(pred, __fmul_rn(__fsub_rn(cf, kQCodeBias), t.two_e));
+    unsigned code = __float_as_uint(cf) & 0xffffu;
+    if (!((u < 32768.0f) & (fabsf(__fsub_rn(xv, rec)) <= t.el))) {
+      uint16_t c16;
+      float rr;
+      if (quantize(xv, pred, t.el, t.two_e, t.inv, &c16, &rr)) {
+        code = c16;
+        rec = rr;
+      } else {
+        code = 0;
+        rec = xv;
+        ++acc.unp;
+      }
+    }
+    S[g.li] = rec;
+    if (kFull && t.metrics) {  // every non-anchor point is a target once
+      const float e = __fsub_rn(xv, rec);
+      acc.sse.add(__fmul_rn(e, e));
+      const float ae = fabsf(e);
+      if (ae != ae || ae > acc.mx) acc.mx = ae;
+    }
+    if (kFull && t.hist) {
+      // lanes with equal codes add once (smooth data puts most of a warp's
+      // codes in one or two bins)
+      const unsigned peers = __match_any_sync(__activemask(), code);
+      if (lane == __ffs(peers) - 1) {
+        const unsigned kk = code - (unsigned)kTHistLo;
+        const unsigned n = (unsigned)__popc(peers);
+        if (kk < (unsigned)kTHistWin)
+          atomicAdd(&t.SH[kk], n);
+        else
+          atomicAdd(&t.ghist[code], n);
+      }
+    }
+  };
+  for (int it = threadIdx.x; it < items; it += THREADS) {
+    const Tgt g = fetch(it);
+    if (g.ok) finish(g);
+  }
+}
+
+// The pass for role code b0 * 9 + b1 * 3 + b2 and interpolator ip (uniform
+// over the CTA).
+template <int THREADS, bool kFull>
+__device__ __forceinline__ void trial_pass_dispatch(int roles, int ip, const TrialPass& t,
+                                                    TrialAcc& acc) {
+#define QOZ_TRIAL_PASS(B0, B1, B2)                                 \
+  case B0 * 9 + B1 * 3 + B2:                                       \
+    if (ip == 1)                                                   \
+      trial_pass<THREADS, kFull, B0, B1, B2, 1>(t, acc);           \
+    else                                                           \
+      trial_pass<THREADS, kFull, B0, B1, B2, 0>(t, acc);           \
+    break;
+  switch (roles) {
+    QOZ_TRIAL_PASS(1, 0, 0)
+    QOZ_TRIAL_PASS(1, 0, 2)
+    QOZ_TRIAL_PASS(1, 2, 0)
+    QOZ_TRIAL_PASS(1, 2, 2)
+    QOZ_TRIAL_PASS(0, 1, 0)
+    QOZ_TRIAL_PASS(0, 1, 2)
+    QOZ_TRIAL_PASS(2, 1, 0)
+    QOZ_TRIAL_PASS(2, 1, 2)
+    QOZ_TRIAL_PASS(0, 0, 1)
+    QOZ_TRIAL_PASS(0, 2, 1)
+    QOZ_TRIAL_PASS(2, 0, 1)
+    QOZ_TRIAL_PASS(2, 2, 1)
+    default:
+      break;
+  }
+#undef QOZ_TRIAL_PASS
+}
+
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 1 : 4)
     trial_kernel(const TrialArgs a, const __grid_constant__ CUtensorMap tmap) {
@@ -195,9 +364,8 @@ __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 1 : 4)
     __syncthreads();
   }
 
-  KSum l1, sse;
-  float mx = 0.0f;
-  int l1n = 0, unp = 0;
+  KSum sse0;         // the anchors' squared errors
+  float mx0 = 0.0f;  // and their maximum
   const int st1 = P, st0 = m1 * P;
   if (kFull && a.metrics) {
     // the block's anchors (never targets) reconstruct exactly: they add to
@@ -209,101 +377,51 @@ __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 1 : 4)
       const int si = (r / n1a) * as * st0 + (r % n1a) * as * st1 + i2 * as;
       const float v = QOZ_IN(si, nS) ? S[si] : 0.0f;
       const float d = __fsub_rn(v, v);
-      sse.add(__fmul_rn(d, d));
+      sse0.add(__fmul_rn(d, d));
       const float ad = fabsf(d);
-      if (ad != ad || ad > mx) mx = ad;
+      if (ad != ad || ad > mx0) mx0 = ad;
     }
   }
+  TrialAcc acc;
   for (int l = a.Ls; l >= a.stop_level; --l) {
     const int h = 1 << (l - a.stop_level);
-    const float el = C.el[l - 1], two_e = C.two_e[l - 1], inv = C.inv[l - 1];
     const int interp = C.interp[l - 1];
-    const int ax0 = C.axes[l - 1][0], ax1 = C.axes[l - 1][1], ax2 = C.axes[l - 1][2];
+    const int ax0 = C.axes[l - 1][0], ax1 = C.axes[l - 1][1];
+    TrialPass tp;
+    tp.S = S;
+    tp.nS = nS;
+    tp.m0 = m0;
+    tp.m1 = m1;
+    tp.m2 = m2;
+    tp.st0 = st0;
+    tp.st1 = st1;
+    tp.h = h;
+    tp.el = C.el[l - 1];
+    tp.two_e = C.two_e[l - 1];
+    tp.inv = C.inv[l - 1];
+    tp.score = l == a.score_level;
+    tp.metrics = kFull && a.metrics;
+    tp.hist = kFull && a.hist != nullptr;
+    tp.SH = SH;
+    tp.ghist = a.hist ? a.hist + (size_t)cand * 65536 : nullptr;
     for (int k = 0; k < 3; ++k) {
-      const int ax = k == 0 ? ax0 : (k == 1 ? ax1 : ax2);
-      // position of each physical axis in the order
+      // position of each physical axis in the order: before the pass axis
+      // (0), the pass axis (1), after it (2)
       const int j0 = ax0 == 0 ? 0 : (ax1 == 0 ? 1 : 2);
       const int j1 = ax0 == 1 ? 0 : (ax1 == 1 ? 1 : 2);
       const int j2 = ax0 == 2 ? 0 : (ax1 == 2 ? 1 : 2);
-      // axes before the pass axis: every h; the pass axis: h mod 2h; after: every 2h
-      const int s0 = j0 == k ? h : 0, s1 = j1 == k ? h : 0, s2 = j2 == k ? h : 0;
-      const int d0 = j0 < k ? h : 2 * h, d1 = j1 < k ? h : 2 * h, d2 = j2 < k ? h : 2 * h;
-      const int c0n = m0 - 1 >= s0 ? (m0 - 1 - s0) / d0 + 1 : 0;
-      const int c1n = m1 - 1 >= s1 ? (m1 - 1 - s1) / d1 + 1 : 0;
-      const int c2n = m2 - 1 >= s2 ? (m2 - 1 - s2) / d2 + 1 : 0;
-      const int sa = ax == 0 ? st0 : (ax == 1 ? st1 : 1);
-      const int na = ax == 0 ? m0 : (ax == 1 ? m1 : m2);
-      // every target of the pass, flattened (x fastest) so that all lanes
-      // work; the quotients come from a binary32 reciprocal, which is exact
-      // for dividends below 70000 and divisors below 4100 (checked
-      // exhaustively), else from integer division
-      const int nrow = c0n * c1n;
-      const int items = nrow * c2n;
-      const bool fdiv = items < 70000 && c2n < 4100 && c1n < 4100;
-      const float rc2 = 1.0f / (float)(c2n > 0 ? c2n : 1);
-      const float rc1 = 1.0f / (float)(c1n > 0 ? c1n : 1);
-      for (int it = threadIdx.x; it < items; it += THREADS) {
-        const int row =
-            fdiv ? __float2int_rz(__fmul_rn(__fadd_rn(__int2float_rn(it), 0.5f), rc2)) : it / c2n;
-        const int i2 = it - row * c2n;
-        const int i0 =
-            fdiv ? __float2int_rz(__fmul_rn(__fadd_rn(__int2float_rn(row), 0.5f), rc1)) : row / c1n;
-        const int i1 = row - i0 * c1n;
-        const int z = s0 + i0 * d0, y = s1 + i1 * d1;
-        {
-          const int xx = s2 + i2 * d2;
-          const int li = z * st0 + y * st1 + xx;
-          const int ca = ax == 0 ? z : (ax == 1 ? y : xx);
-          const bool hb1 = ca + h < na, ha3 = ca >= 3 * h, hb3 = ca + 3 * h < na;
-          if (!QOZ_IN(li, nS) || !QOZ_IN(li - h * sa, nS) || (hb1 && !QOZ_IN(li + h * sa, nS)) ||
-              (ha3 && !QOZ_IN(li - 3 * h * sa, nS)) || (hb3 && !QOZ_IN(li + 3 * h * sa, nS)))
-            continue;
-          const float a1 = S[li - h * sa];
-          const float b1 = hb1 ? S[li + h * sa] : 0.0f;
-          const float a3 = ha3 ? S[li - 3 * h * sa] : 0.0f;
-          const float b3 = hb3 ? S[li + 3 * h * sa] : 0.0f;
-          const float pred = predict(a3, a1, b1, b3, ha3, hb1, hb3, interp);
-          const float xv = S[li];  // not yet predicted: still the field value
-          if (l == a.score_level) {
-            const float ad = fabsf(__fsub_rn(xv, pred));
-            if (isfinite(ad)) {
-              l1.add(ad);
-              ++l1n;
-            }
-          }
-          uint16_t code;
-          float rec;
-          if (quantize(xv, pred, el, two_e, inv, &code, &rec)) {
-            S[li] = rec;
-          } else {
-            code = 0;
-            rec = xv;
-            ++unp;
-          }
-          if (kFull && a.metrics) {  // every non-anchor point is a target once
-            const float d = __fsub_rn(xv, rec);
-            sse.add(__fmul_rn(d, d));
-            const float ad = fabsf(d);
-            if (ad != ad || ad > mx) mx = ad;
-          }
-          if (kFull && a.hist) {
-            // lanes with equal codes add once (smooth data puts most of a
-            // warp's codes in one or two bins)
-            const unsigned peers = __match_any_sync(__activemask(), (unsigned)code);
-            if (lane == __ffs(peers) - 1) {
-              const unsigned kk = (unsigned)code - (unsigned)kTHistLo;
-              const unsigned n = (unsigned)__popc(peers);
-              if (kk < (unsigned)kTHistWin)
-                atomicAdd(&SH[kk], n);
-              else
-                atomicAdd(&a.hist[(size_t)cand * 65536 + code], n);
-            }
-          }
-        }
-      }
+      const int b0 = j0 == k ? 1 : (j0 < k ? 0 : 2);
+      const int b1 = j1 == k ? 1 : (j1 < k ? 0 : 2);
+      const int b2 = j2 == k ? 1 : (j2 < k ? 0 : 2);
+      trial_pass_dispatch<THREADS, kFull>(b0 * 9 + b1 * 3 + b2, interp, tp, acc);
       __syncthreads();
     }
   }
+  KSum& l1 = acc.l1;
+  KSum& sse = acc.sse;
+  ksum_merge(sse, sse0.s, sse0.c);  // the anchors' terms (zero unless non-finite)
+  float mx = nan_max(acc.mx, mx0);
+  const int l1n = acc.l1n, unp = acc.unp;
 
   double ss = 0.0, sn = 0.0;
   if (kFull && a.metrics) {  // stop_level == 1: S is the whole block
