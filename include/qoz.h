@@ -271,8 +271,9 @@ typedef struct {
   int32_t graph;               /* 1 once the run sequence is a CUDA graph */
   int32_t autotuned;           /* 1 once the tile variants were timed */
   int32_t level1_groups;       /* number of level-1 launches */
-  int32_t level1_variant[16];  /* variant chosen for each (first 16): 0, 1 row-copy tiles, 2 bulk copies */
-  double level1_ms[16][3];     /* timed duration of each variant (autotune; 1e30: not possible), else 0 */
+  int32_t level1_variant[16];  /* variant chosen for each (first 16): 0, 1 row-copy tiles, 2 bulk
+                                  copies one tile per CTA, 3 persistent bulk-copy CTAs (3-D) */
+  double level1_ms[16][4];     /* timed duration of each variant (autotune; 1e30: not possible), else 0 */
   int64_t ctas_per_run;        /* CTAs of all batched level launches */
 } qoz_batch_info;
 qoz_status qoz_batch_get_info(const qoz_batch* plan, qoz_batch_info* info);

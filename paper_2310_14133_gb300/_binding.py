@@ -429,7 +429,7 @@ class BatchInfo(C.Structure):
     _fields_ = [("nfields", C.c_int32), ("n_groups", C.c_int32),
                 ("launches_per_run", C.c_int32), ("graph", C.c_int32),
                 ("autotuned", C.c_int32), ("level1_groups", C.c_int32),
-                ("level1_variant", C.c_int32 * 16), ("level1_ms", (C.c_double * 3) * 16),
+                ("level1_variant", C.c_int32 * 16), ("level1_ms", (C.c_double * 4) * 16),
                 ("ctas_per_run", C.c_int64)]
 
 

@@ -168,11 +168,17 @@ qoz_status build_launches(qoz_batch* p, const std::vector<int>& l1_variant) {
     }
     for (LevelKey k : keys) {
       if (l == 1) {
+        // default: the persistent bulk-copy kernel for 3-D fields, the
+        // one-tile-per-CTA bulk copies for 2-D ones (which have no
+        // persistent kernel: 3 falls back to 2)
         k.variant = l1_index < (int)l1_variant.size()
                         ? l1_variant[l1_index]
-                        : (p->no_bulk ? 0 : kLevelVariantBulk);
-        if (k.variant == kLevelVariantBulk && p->no_bulk) k.variant = 0;
-        if (k.variant == kLevelVariantBulk) p->any_bulk = true;
+                        : (p->no_bulk ? 0 : kLevelVariantPersist);
+        if (k.variant == kLevelVariantPersist && k.is2d) k.variant = kLevelVariantBulk;
+        if ((k.variant == kLevelVariantBulk || k.variant == kLevelVariantPersist) && p->no_bulk)
+          k.variant = 0;
+        if (k.variant == kLevelVariantBulk || k.variant == kLevelVariantPersist)
+          p->any_bulk = true;
         ++l1_index;
       }
       Group g;
@@ -294,7 +300,8 @@ bool fill_tables(qoz_batch* p, const float* const* x, const double* eb, int rel,
     it.vec = it.L.xs[2] == 1 && (it.L.xs[1] % 4) == 0 && (it.L.xs[0] % 4) == 0 &&
              (reinterpret_cast<uintptr_t>(it.L.x) & 15) == 0;
     p->h_items[i] = it;
-    if (p->refs[i].key.variant == kLevelVariantBulk)
+    if (p->refs[i].key.variant == kLevelVariantBulk ||
+        p->refs[i].key.variant == kLevelVariantPersist)
       maps_ok = maps_ok && level_tma_maps(p->refs[i].key, it.L, &p->h_maps[i]);
   }
   return maps_ok;
@@ -614,7 +621,10 @@ qoz_status qoz_batch_compress(qoz_batch* p, const float* const* d_fields, const 
     p->no_bulk = true;
     std::vector<int> l1;
     for (const Group& g : p->groups)
-      if (g.level == 1) l1.push_back(g.key.variant == kLevelVariantBulk ? 0 : g.key.variant);
+      if (g.level == 1)
+        l1.push_back(g.key.variant == kLevelVariantBulk || g.key.variant == kLevelVariantPersist
+                         ? 0
+                         : g.key.variant);
     st = build_launches(p, l1);
     if (st == QOZ_OK) st = upload_maps(p);
     if (st == QOZ_OK) st = prepare_kernels(p);

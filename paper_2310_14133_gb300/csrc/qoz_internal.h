@@ -67,8 +67,10 @@ struct LevelItem {
 };
 // Kernel instance of a batched launch: 2-D or 3-D, the level's order, whether
 // the launch accumulates the histogram (level 1), the level's interpolator
-// and the tile variant (0, 1: row copies; 2: bulk tensor copies, level 1
-// only, which needs the tensor maps of each item).
+// and the tile variant (0, 1: row copies; 2: bulk tensor copies, one tile per
+// CTA; 3: the persistent bulk-copy kernel of 3-D level 1, its CTAs walking
+// the tiles of all the launch's items; 2 and 3 are level 1 only and need the
+// tensor maps of each item; a 2-D key takes 2 for 3).
 struct LevelKey {
   bool is2d;
   int order3;
@@ -76,8 +78,9 @@ struct LevelKey {
   int interp;
   int variant;
 };
-constexpr int kLevelVariants = 3;
+constexpr int kLevelVariants = 4;
 constexpr int kLevelVariantBulk = 2;
+constexpr int kLevelVariantPersist = 3;
 // Tensor maps of one item of a bulk-copy launch (device memory).
 struct alignas(64) LevelTmaMaps {
   CUtensorMap x, rc, cc, out;

@@ -487,7 +487,54 @@ cudaError_t launch_anchor_batch(const BatchFieldDesc* d, int nfields, cudaStream
   return cudaGetLastError();
 }
 
+// Tensor maps of the persistent level-1 kernel's tiles (the single-field
+// launch's boxes, l1::Geo) for a 3-D order whose first axis is a0; false when
+// an input array does not meet the bulk-copy rules.
+static bool encode_l1_maps(const LevelLaunch& a, int a0, LevelTmaMaps* m) {
+  if (!tma_enabled() || a.decompress || a.is2d || a.level != 1 || a.xs[2] != 1 || !a.cin ||
+      !a.rc || !a.cout)
+    return false;
+  if (!aligned16(a.x) || !aligned16(a.rc) || !aligned16(a.cin)) return false;
+  if (a.xs[1] % 4 || a.xs[0] % 4 || a.cs[1] % 8 || a.cs[0] % 8) return false;
+  const l1::Tile3 t = l1::tile_for(a0);
+  const unsigned hz = a0 == 0 ? 0 : 3, hy = a0 == 1 ? 0 : 3, xl = a0 == 2 ? 0 : 4;
+  const unsigned long long g2 = a.g[2], g1 = a.g[1], g0 = a.g[0];
+  const unsigned long long c2 = (g2 + 1) / 2, c1 = (g1 + 1) / 2, c0 = (g0 + 1) / 2;
+  memset(m, 0, sizeof(*m));
+  {
+    const unsigned long long d[3] = {g2, g1, g0};
+    const unsigned long long st[2] = {4ull * a.xs[1], 4ull * a.xs[0]};
+    const unsigned bx[3] = {t.tx + 2 * xl, t.ty + 2 * hy, t.tz + 2 * hz};
+    if (!encode_tensor_map_3d(&m->x, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, a.x, d, st, bx)) return false;
+  }
+  {
+    const unsigned long long d[3] = {c2, c1, c0};
+    const unsigned long long st[2] = {4ull * a.cs[1], 4ull * a.cs[0]};
+    const unsigned bx[3] = {(unsigned)t.tx / 2 + 8, (unsigned)t.ty / 2 + 3, (unsigned)t.tz / 2 + 3};
+    if (!encode_tensor_map_3d(&m->rc, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, a.rc, d, st, bx)) return false;
+  }
+  {
+    const unsigned long long d[3] = {c2, c1, c0};
+    const unsigned long long st[2] = {2ull * a.cs[1], 2ull * a.cs[0]};
+    const unsigned bx[3] = {(unsigned)t.tx / 2, (unsigned)t.ty / 2, (unsigned)t.tz / 2};
+    if (!encode_tensor_map_3d(&m->cc, CU_TENSOR_MAP_DATA_TYPE_UINT16, a.cin, d, st, bx)) return false;
+  }
+  // the code tile's bulk store when the code array's rows start on 16 bytes
+  // (else the kernel stores the codes itself)
+  m->use_out = 0;
+  if (aligned16(a.cout) && a.os[1] % 8 == 0 && a.os[0] % 8 == 0) {
+    const unsigned long long d[3] = {g2, g1, g0};
+    const unsigned long long st[2] = {2ull * a.os[1], 2ull * a.os[0]};
+    const unsigned bx[3] = {(unsigned)t.tx, (unsigned)t.ty, (unsigned)t.tz};
+    m->use_out =
+        encode_tensor_map_3d(&m->out, CU_TENSOR_MAP_DATA_TYPE_UINT16, a.cout, d, st, bx) ? 1 : 0;
+  }
+  return true;
+}
+
 bool level_tma_maps(const LevelKey& k, const LevelLaunch& L, LevelTmaMaps* m) {
+  if (k.variant == kLevelVariantPersist && !k.is2d)
+    return encode_l1_maps(L, kOrderAxis0[k.order3], m);
   const int a0 = k.is2d ? 0 : kOrderAxis0[k.order3];
   const TmaTile t = tma_tile_for(k.is2d, a0);
   return encode_level_maps(L, t.tz, t.ty, t.tx, halo_z(a0), halo_y(a0), m);

@@ -196,7 +196,7 @@ __device__ __forceinline__ void hist_add(const LevelLaunch& a, unsigned* SH, uns
 // (store), joins the list at its field index (cz, cy, cx).  Returns (bits of
 // the reconstruction, code).  The bound and the extents are read again from
 // the launch: the rare call holds few of the caller's registers.
-__device__ __noinline__ uint2 qslow(const LevelLaunch& a, float x, float p, bool store, int cz,
+static __device__ __noinline__ uint2 qslow(const LevelLaunch& a, float x, float p, bool store, int cz,
                                     int cy, int cx) {
   uint16_t cd;
   float rr;
@@ -251,7 +251,7 @@ __device__ __forceinline__ void quant2(const LevelLaunch& a, const Ctx& c, float
 // Decompression of one point whose code is 0: the stored value from the
 // sorted unpredictable list (0 and a flag when it is missing; 0 for a halo
 // position outside the field, which no valid point reads).
-__device__ __noinline__ float dslow(const LevelLaunch& a, int cz, int cy, int cx) {
+static __device__ __noinline__ float dslow(const LevelLaunch& a, int cz, int cy, int cx) {
   if (cz < 0 || cz >= a.g[0] || cy < 0 || cy >= a.g[1] || cx < 0 || cx >= a.g[2]) return 0.0f;
   const long long xi = (long long)((unsigned long long)cz * a.xs[0] +
                                    (unsigned long long)cy * a.xs[1] +
@@ -755,6 +755,149 @@ __device__ __forceinline__ void compress_tiles(const LevelLaunch& a, unsigned ch
   __syncthreads();
   for (int k = threadIdx.x; k < kHistWin; k += kThr)
     if (SH[k]) atomicAdd(&a.hist[kHistLo + k], SH[k]);
+  if (threadIdx.x == 0) bulk_wait_read0();
+}
+
+// Level 1 of several 3-D fields in one launch (a batched plan): tile t of
+// the launch belongs to item map[t], as that item's tile t - tile_begin.
+// The CTAs walk the launch's tiles as above; a CTA whose next tile starts a
+// new item flushes its histogram window into the old item's histogram and
+// takes the new item's descriptor into shared memory.  The items' tensor
+// maps sit in device memory; the next tile's copies are issued with its own
+// item's maps.
+template <class G, int IP>
+__device__ __forceinline__ void compress_tiles_batch(const LevelItem* __restrict__ items,
+                                                     const uint16_t* __restrict__ map,
+                                                     const LevelTmaMaps* __restrict__ maps,
+                                                     int ntiles, unsigned char* smem_raw,
+                                                     uint64_t* mbar, LevelItem& it) {
+  unsigned char* sm = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  unsigned* SH = reinterpret_cast<unsigned*>(sm + G::oHist);
+  if (threadIdx.x == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[2], 1);
+    fence_mbar_init();
+  }
+  for (int i = threadIdx.x; i < kHistWin; i += kThr) SH[i] = 0;
+  __syncthreads();
+  if ((int)blockIdx.x >= ntiles) return;
+  {
+    // host fault injection (every level-1 item carries it): a barrier that
+    // expects bytes no copy brings, before any copy is issued
+    const LevelLaunch& f = items[map[blockIdx.x]].L;
+    if (f.extra_tx > 0) {
+      if (threadIdx.x == 0) mbar_expect_tx(&mbar[2], (unsigned)f.extra_tx);
+      const bool ok = wait_polls(&mbar[2], 0, f.wait_polls > 0 ? (unsigned)f.wait_polls : kPolls);
+      if (!__syncthreads_and(ok) && threadIdx.x == 0 && f.err) atomicOr(f.err, 2);
+      return;
+    }
+  }
+  auto issue = [&](int tile) {  // one thread
+    const int k = map[tile];
+    const LevelItem& q = items[k];
+    issue_tile<G>(sm, &mbar[0], tile - (int)q.tile_begin, q.nt1, q.nt2, &maps[k].x, &maps[k].rc,
+                  &maps[k].cc);
+  };
+  if (threadIdx.x == 0) issue((int)blockIdx.x);
+  float* S = reinterpret_cast<float*>(sm);
+  const float* CB = reinterpret_cast<const float*>(sm + G::oCB);
+  const uint16_t* CC = reinterpret_cast<const uint16_t*>(sm + G::oCC);
+  uint16_t* C16 = reinterpret_cast<uint16_t*>(sm + G::oC16);
+  Ctx c;
+  c.SH = SH;
+  c.full = false;
+  int cur = -1;
+  bool counting = false;
+  int i = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+    const int k = map[tile];
+    if (k != cur) {
+      __syncthreads();  // the CTA is done with the old item and its window
+      if (cur >= 0 && counting)
+        for (int j = threadIdx.x; j < kHistWin; j += kThr)
+          if (SH[j]) {
+            atomicAdd(&it.L.hist[kHistLo + j], SH[j]);
+            SH[j] = 0;
+          }
+      __syncthreads();
+      static_assert(sizeof(LevelItem) % 4 == 0 && sizeof(LevelItem) / 4 <= kThr, "item copy");
+      if (threadIdx.x < sizeof(LevelItem) / 4)
+        reinterpret_cast<unsigned*>(&it)[threadIdx.x] =
+            reinterpret_cast<const unsigned*>(items + k)[threadIdx.x];
+      __syncthreads();
+      cur = k;
+      c.g0 = (int)it.L.g[0];
+      c.g1 = (int)it.L.g[1];
+      c.g2 = (int)it.L.g[2];
+      c.el = it.L.bt->el[0];
+      c.two_e = it.L.bt->two_e[0];
+      c.inv = it.L.bt->inv[0];
+      counting = it.L.hist != nullptr;
+    }
+    const bool landed = wait_polls(&mbar[0], (unsigned)i & 1u, kPolls);
+    if (threadIdx.x == 0 && i >= 1) bulk_wait_read0();  // the last code store has read its buffer
+    if (!__syncthreads_and(landed)) {
+      // a copy never completed: report it and leave (after the code store)
+      if (threadIdx.x == 0) {
+        if (it.L.err) atomicOr(it.L.err, 2);
+        bulk_wait_read0();
+      }
+      return;
+    }
+    {
+      const int lt = tile - (int)it.tile_begin;
+      const int r = lt / it.nt2;
+      c.ox = (lt % it.nt2) * G::TX;
+      c.oy = (r % it.nt1) * G::TY;
+      c.oz = (r / it.nt1) * G::TZ;
+    }
+    const bool full = c.oz + G::TZ <= c.g0 && c.oy + G::TY <= c.g1 && c.ox + G::TX <= c.g2;
+    c.full = full && counting;
+    const bool want_rec = it.L.rout != nullptr;
+    run_tile<G, IP, false>(it.L, c, S, CB, CC, C16, want_rec);
+    fence_proxy_async_smem();  // code tile written: visible to the bulk store
+    __syncthreads();
+    if (want_rec) {
+      store_tile<G>(it.L, c, S);
+      __syncthreads();
+    }
+    if (maps[k].use_out) {
+      if (threadIdx.x == 0) {
+        tma_store_3d(&maps[k].out, c.ox, c.oy, c.oz, C16);
+        bulk_commit();
+      }
+    } else {
+      // the code array's rows are not on 16-byte boundaries: plain stores
+      for (int g = threadIdx.x; g < G::kC; g += kThr) {
+        const int lx = g % G::TX, t = g / G::TX;
+        const int cz = c.oz + t / G::TY, cy = c.oy + t % G::TY, cx = c.ox + lx;
+        if (cz < c.g0 && cy < c.g1 && cx < c.g2)
+          it.L.cout[(long long)cz * it.L.os[0] + (long long)cy * it.L.os[1] + cx] = C16[g];
+      }
+    }
+    if (threadIdx.x == 0) {
+      const int nt = tile + (int)gridDim.x;
+      if (nt < ntiles) issue(nt);
+    }
+    if (!full && counting) {
+      for (int g = threadIdx.x; g < G::kC / 8; g += kThr) {
+        const uint4 v = reinterpret_cast<const uint4*>(C16)[g];
+        const int lx = (g % (G::TX / 8)) * 8;
+        const int t = g / (G::TX / 8);
+        const int ly = t % G::TY, lz = t / G::TY;
+        const int cz = c.oz + lz, cy = c.oy + ly, cx = c.ox + lx;
+        const int nval = (cz < c.g0 && cy < c.g1) ? min(8, max(0, c.g2 - cx)) : 0;
+        const unsigned wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (q < nval) hist_add(it.L, SH, (wv[q >> 1] >> (16 * (q & 1))) & 0xffffu);
+      }
+    }
+  }
+  __syncthreads();
+  if (cur >= 0 && counting)
+    for (int j = threadIdx.x; j < kHistWin; j += kThr)
+      if (SH[j]) atomicAdd(&it.L.hist[kHistLo + j], SH[j]);
   if (threadIdx.x == 0) bulk_wait_read0();
 }
 

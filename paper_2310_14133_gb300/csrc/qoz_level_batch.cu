@@ -6,6 +6,7 @@
 // single-field compression.  Two row-copy tile shapes per instance are
 // compiled, and for level 1 the bulk-copy kernel; the batch plan times them
 // on its first run and keeps the fastest.
+#include "qoz_level1.cuh"
 #include "qoz_level_impl.cuh"
 
 namespace qoz {
@@ -47,12 +48,30 @@ __global__ void __launch_bounds__(THR, 1024 / THR)
       &mp->cc, mp->use_out ? &mp->out : nullptr);
 }
 
+// Level 1 of 3-D fields on the persistent bulk-copy kernel: grid-stride CTAs
+// over all the launch's tiles (ntiles), each tile's item from the map.  The
+// per-item state costs registers: three CTAs per SM (85 registers) keep the
+// kernel free of spills, where four (64) spilled.
+constexpr int kBatchL1CtasPerSm = 4;
+template <int A0, int A1, int A2, int IP>
+__global__ void __launch_bounds__(l1::kThr, kBatchL1CtasPerSm)
+    level1_batch_kernel(const LevelItem* __restrict__ items, const uint16_t* __restrict__ map,
+                        const LevelTmaMaps* __restrict__ maps, int ntiles) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mbar[3];
+  __shared__ __align__(16) LevelItem it;
+  constexpr l1::Tile3 t = l1::tile_for(A0);
+  l1::compress_tiles_batch<l1::Geo<A0, A1, A2, t.tz, t.ty, t.tx>, IP>(items, map, maps, ntiles,
+                                                                       smem, mbar, it);
+}
+
 struct Info {
   const void* fn;
   size_t smem;
   int t[3];
   int threads;
   unsigned long long* done;
+  bool persistent;  // grid-stride CTAs (one per resident slot) over the tiles
 };
 
 template <int A0, int A1, int A2, int TZ, int TY, int TX, bool HIST>
@@ -62,7 +81,7 @@ Info info_of() {
   constexpr size_t smem = G::smem_bytes(false, HIST);
   static_assert(smem + sizeof(LevelItem) <= 112 * 1024, "two CTAs per SM");
   return Info{(const void*)level_batch_kernel<A0, A1, A2, TZ, TY, TX, HIST>, smem, {TZ, TY, TX},
-              kThreads, &done};
+              kThreads, &done, false};
 }
 
 template <int A0, int A1, int A2, bool IS2D, int IP>
@@ -74,7 +93,31 @@ Info info_tma() {
   static_assert((smem + sizeof(LevelItem) + 1088) * (1024 / t.thr) <= 228 * 1024,
                 "tiles must fit the CTAs per SM");
   return Info{(const void*)level_tma_batch_kernel<A0, A1, A2, t.tz, t.ty, t.tx, t.thr, IP>, smem,
-              {t.tz, t.ty, t.tx}, t.thr, &done};
+              {t.tz, t.ty, t.tx}, t.thr, &done, false};
+}
+
+template <int A0, int A1, int A2, int IP>
+Info info_l1() {
+  constexpr l1::Tile3 t = l1::tile_for(A0);
+  using G = l1::Geo<A0, A1, A2, t.tz, t.ty, t.tx>;
+  static unsigned long long done = 0;
+  constexpr size_t smem = G::kSmem;
+  static_assert((smem + sizeof(LevelItem) + 1024 + 64) * kBatchL1CtasPerSm <= 228 * 1024,
+                "CTAs per SM");
+  return Info{(const void*)level1_batch_kernel<A0, A1, A2, IP>, smem, {t.tz, t.ty, t.tx},
+              l1::kThr, &done, true};
+}
+
+template <int IP>
+Info info_l1_ip(int order3) {
+  switch (order3) {
+    case 0: return info_l1<0, 1, 2, IP>();
+    case 1: return info_l1<0, 2, 1, IP>();
+    case 2: return info_l1<1, 0, 2, IP>();
+    case 3: return info_l1<1, 2, 0, IP>();
+    case 4: return info_l1<2, 0, 1, IP>();
+    default: return info_l1<2, 1, 0, IP>();
+  }
 }
 
 template <int IP>
@@ -113,7 +156,9 @@ Info info_h(int is2d, int order3, int v) {
 }
 
 Info get_info(const LevelKey& k) {
-  if (k.variant == kLevelVariantBulk)
+  if (k.variant == kLevelVariantPersist && !k.is2d)
+    return k.interp == 1 ? info_l1_ip<1>(k.order3) : info_l1_ip<0>(k.order3);
+  if (k.variant == kLevelVariantBulk || k.variant == kLevelVariantPersist)
     return k.interp == 1 ? info_tma_ip<1>(k.is2d, k.order3) : info_tma_ip<0>(k.is2d, k.order3);
   const int v = k.variant ? 1 : 0;
   return k.hist ? info_h<true>(k.is2d, k.order3, v) : info_h<false>(k.is2d, k.order3, v);
@@ -142,6 +187,19 @@ cudaError_t launch_level_batch(const LevelKey& k, const LevelItem* d_items, cons
                                const LevelTmaMaps* d_maps, unsigned nblocks, cudaStream_t s) {
   if (nblocks == 0) return cudaSuccess;
   const Info in = get_info(k);
+  if (in.persistent) {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      nsm = 1;
+    const unsigned slots = (unsigned)(kBatchL1CtasPerSm * (nsm > 0 ? nsm : 1));
+    int ntiles = (int)nblocks;
+    void* args[] = {(void*)&d_items, (void*)&d_map, (void*)&d_maps, (void*)&ntiles};
+    cudaError_t e = cudaLaunchKernel(in.fn, dim3(nblocks < slots ? nblocks : slots),
+                                     dim3(in.threads), args, in.smem, s);
+    note_launch(1);
+    return e;
+  }
   void* args[] = {(void*)&d_items, (void*)&d_map, (void*)&d_maps};
   cudaError_t e = cudaLaunchKernel(in.fn, dim3(nblocks), dim3(in.threads), args, in.smem, s);
   note_launch(1);
