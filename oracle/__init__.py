@@ -98,6 +98,7 @@ def lib():
             "orc_canonical_codes": (None, [P, i32, P]),
             "orc_huffman_encode": (i64, [P, i64, i32, P, P, P, P, i64]),
             "orc_huffman_decode": (i32, [P, P, i64, i32, P, P, i32, P]),
+            "orc_huffman_subruns": (i32, [P, i64, i32, P, P]),
             "orc_estimate_bits": (f64, [P, i64, i64]),
             "orc_max_abs_err": (f64, [P, P, i64]),
             "orc_mse": (f64, [P, P, i64]),
@@ -282,6 +283,22 @@ def huffman_encode(symbols, lengths, codes, chunk: int | None = None):
     if w < 0:
         raise ValueError(f"encode failed ({w})")
     return words[:w].copy(), offs
+
+
+def huffman_subruns(symbols, lengths, chunk: int | None = None):
+    """The stream's sub-run table (uint16, n_chunks x (S - 1) entries in chunk
+    order; empty when S = 1): the coded length in bits of each 512-code run
+    of a chunk but its last.  chunk None takes entropy_chunk."""
+    s = np.ascontiguousarray(symbols, dtype=np.uint16).ravel()
+    ln = np.ascontiguousarray(lengths, dtype=np.uint8)
+    chunk = entropy_chunk(s.size) if chunk is None else int(chunk)
+    S = chunk // 512 if chunk >= 1024 else 1
+    nch = (s.size + chunk - 1) // chunk
+    sub = np.zeros(max(nch * (S - 1), 1), dtype=np.uint16)
+    r = int(lib().orc_huffman_subruns(_ptr(s), s.size, chunk, _ptr(ln), _ptr(sub)))
+    if r < 0:
+        raise ValueError("a symbol without a code")
+    return sub[:nch * (S - 1)].copy()
 
 
 def huffman_decode(words, offs, n: int, lengths, codes, chunk: int | None = None):

@@ -99,6 +99,14 @@ int64_t orc_huffman_encode(const uint16_t* sym, int64_t n, int chunk, const uint
                            int64_t cap_words);
 int orc_huffman_decode(const uint32_t* words, const uint64_t* offs, int64_t n, int chunk,
                        const uint8_t* len, const uint64_t* code, int K, uint16_t* out);
+/* Sub-run table of the chunked stream: a chunk of `chunk` >= 1024 codes is
+ * cut into S = chunk / 512 runs of 512 codes, and the table holds, per chunk
+ * in order, the coded length in bits of its first S - 1 runs (runs past the
+ * end of the codes count 0); chunks of fewer than 1024 codes have none.
+ * Writes n_chunks * (S - 1) entries to sub (none when S == 1); returns S, or
+ * -1 for a symbol without a code. */
+int orc_huffman_subruns(const uint16_t* sym, int64_t n, int chunk, const uint8_t* len,
+                        uint16_t* sub);
 
 /* Rate estimate: Huffman bits of the codes + 32 bits per unpredictable value
  * + 32 bits per anchor. */

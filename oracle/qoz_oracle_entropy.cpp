@@ -22,7 +22,10 @@
  *   - stream: chunks of `chunk` symbols; each chunk starts on a fresh 32-bit
  *     word, its codes are written most significant bit first, and words fill
  *     from their most significant bit; the unused tail of a chunk's last word
- *     is zero; offs[c] is the word offset of chunk c (offs[n_chunks] = total).
+ *     is zero; offs[c] is the word offset of chunk c (offs[n_chunks] = total);
+ *   - sub-runs: a chunk of at least 1024 codes is cut into runs of 512, and
+ *     the stream records the coded length of each run but the last, so that
+ *     a decoder can start a thread at every run;
  *
  * Plain sequential code; the tree is built explicitly and walked for depths.
  */
@@ -131,6 +134,24 @@ int64_t orc_huffman_encode(const uint16_t* sym, int64_t n, int chunk, const uint
   }
   offs[nchunks] = (uint64_t)w;
   return w;
+}
+
+int orc_huffman_subruns(const uint16_t* sym, int64_t n, int chunk, const uint8_t* len,
+                        uint16_t* sub) {
+  const int S = chunk >= 1024 ? chunk / 512 : 1;
+  if (S == 1) return 1;
+  const int64_t nchunks = (n + chunk - 1) / chunk;
+  for (int64_t c = 0; c < nchunks; ++c)
+    for (int j = 0; j + 1 < S; ++j) {
+      uint32_t bits = 0;
+      for (int64_t i = c * chunk + (int64_t)j * 512; i < c * chunk + (int64_t)(j + 1) * 512 && i < n;
+           ++i) {
+        if (len[sym[i]] == 0) return -1;
+        bits += len[sym[i]];
+      }
+      sub[c * (S - 1) + j] = (uint16_t)bits;  // at most 512 * 58 bits
+    }
+  return S;
 }
 
 int orc_huffman_decode(const uint32_t* words, const uint64_t* offs, int64_t n, int chunk,

@@ -151,3 +151,64 @@ def test_chunk_size_rule(orc):
     words, offs = orc.huffman_encode(np.array([0, 1, 1, 0] * 100, np.uint16), ln,
                                      orc.canonical_codes(ln))
     assert offs.size == 400 // 256 + 2 and offs[-1] == words.size
+
+
+def test_subrun_table_hand_worked(orc):
+    """Chunks of 1024 codes hold two runs of 512; the table records the first
+    run's coded length.  Chunk 0: 512 codes of a 1-bit symbol, then 512 of a
+    2-bit one; chunk 1 (476 codes, all 2-bit): its first run is the 476 codes
+    there are, 952 bits."""
+    ln = np.array([1, 2, 2], dtype=np.uint8)
+    sym = np.array([0] * 512 + [1] * 512 + [2] * 476, dtype=np.uint16)
+    assert orc.huffman_subruns(sym, ln, chunk=1024).tolist() == [512, 952]
+    # chunks below 1024 codes carry no table
+    assert orc.huffman_subruns(sym, ln, chunk=512).size == 0
+    # four runs per chunk of 2048: three entries, the last two of the short
+    # second chunk past its end (0 bits)
+    sym2 = np.array([0] * 2048 + [1] * 600, dtype=np.uint16)
+    assert orc.huffman_subruns(sym2, ln, chunk=2048).tolist() == [512, 512, 512, 1024, 176, 0]
+
+
+def _decode_from(words, bitpos, count, ln, codes):
+    """Plain prefix decoding of `count` codes from bit `bitpos` of the words
+    (test side, independent of the oracle's decoder)."""
+    table = {(int(ln[s]), int(codes[s])): s for s in range(ln.size) if ln[s]}
+    out = []
+    for _ in range(count):
+        v, L = 0, 0
+        while True:
+            w = int(words[bitpos // 32])
+            v = (v << 1) | ((w >> (31 - bitpos % 32)) & 1)
+            bitpos += 1
+            L += 1
+            if (L, v) in table:
+                out.append(table[(L, v)])
+                break
+            assert L < 64
+    return out, bitpos
+
+
+def test_subrun_table_starts_decode_their_runs(orc):
+    """Every run starts at the bit the table says: decoding from the chunk
+    start plus the preceding runs' lengths yields exactly that run's codes
+    and ends where the next run starts (a skewed alphabet with long codes)."""
+    rng = np.random.default_rng(17)
+    n = 5000
+    sym = np.minimum(rng.geometric(0.35, n) - 1, 40).astype(np.uint16)
+    hist = np.bincount(sym, minlength=64).astype(np.uint64)
+    ln, _ = orc.huffman_lengths(hist)
+    cd = orc.canonical_codes(ln)
+    chunk = 2048
+    words, offs = orc.huffman_encode(sym, ln, cd, chunk=chunk)
+    sub = orc.huffman_subruns(sym, ln, chunk=chunk)
+    S = chunk // 512
+    for c in range(offs.size - 1):
+        start = 32 * int(offs[c])
+        for j in range(S):
+            b = c * chunk + j * 512
+            cnt = max(0, min(512, n - b))
+            got, end = _decode_from(words, start, cnt, ln, cd)
+            assert got == sym[b:b + cnt].tolist()
+            if j + 1 < S:
+                assert end - start == int(sub[c * (S - 1) + j])
+                start = end
