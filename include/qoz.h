@@ -183,14 +183,16 @@ qoz_status qoz_blob_copy_arrays(const qoz_blob* b, uint16_t* d_codes, int64_t* d
  * `stream` (NULL: the blob's stream), which it then synchronises. */
 qoz_status qoz_blob_histogram(const qoz_blob* b, uint32_t* h_hist, void* stream);
 
-/* Serialized form (format 2): a 160-byte header (magic, version, shape,
+/* Serialized form (format 3): a 160-byte header (magic, version, shape,
  * bound, params, counts, checksum), the anchors (float32), the unpredictable
  * indices (int64) and values (float32), then the code section: the codes of
  * all N points (anchors carry code 0) in canonical Huffman code, the entropy
  * stage the rate estimate of Sec. 6.1 stands for.  The code section holds a
  * 288-byte fixed part (used symbols, longest code, chunk size, chunk and
  * word counts, number of codes per length 0..63), the used symbols in
- * (length, symbol) order, the n_chunks + 1 word offsets (uint64) and the
+ * (length, symbol) order, the n_chunks + 1 word offsets (uint64), for chunks
+ * of 1024 codes or more the run table (per chunk, the coded length in bits
+ * of each 512-code run but the last, uint16, padded to 8 bytes) and the
  * stream (uint32 words; each chunk starts on a word, codes most significant
  * bit first from each word's most significant bit).  Code lengths follow
  * Huffman's construction with ties going to the leaf queue; codes are
@@ -218,7 +220,7 @@ qoz_status qoz_blob_serialize_async(const qoz_blob* b, void* h_buf, size_t cap, 
  * work): an optimal prefix code averages under 17 bits per symbol on a
  * 65536-symbol alphabet, and each chunk adds at most one partial word. */
 qoz_status qoz_blob_serialize_bound(const qoz_blob* b, size_t* bound);
-/* Parses a serialized stream (format 2) onto the device: checks the header,
+/* Parses a serialized stream (format 3) onto the device: checks the header,
  * the code section (a complete canonical code, consistent chunk offsets) and
  * the unpredictable list on the host, decodes the codes on the device and
  * verifies the checksum.  QOZ_ECORRUPT for any inconsistency.  Synchronises. */

@@ -44,9 +44,9 @@ constexpr int kTabThreads = 1024;
 constexpr int kHuffSmemSym = 4096;  // used symbols handled in shared memory
 constexpr int kLut = 12;            // bits of the decoder's lookup table
 constexpr int kDecSmemSym = 12288;  // symbols the decoder keeps in shared memory
-constexpr int kDecThreads = 128;    // decoder: one chunk per thread
-constexpr int kRingWords = 64;      // decoder: stream words staged per thread
-constexpr int kRingGroup = 16;      // decoder: words per asynchronous refill
+constexpr int kDecThreads = 256;    // decoder: one run of a chunk per thread
+constexpr int kRingWords = 32;      // decoder: stream words staged per thread
+constexpr int kRingGroup = 8;       // decoder: words per asynchronous refill
 
 // Workspace of the table kernel (device memory).
 struct HuffWork {
@@ -256,26 +256,38 @@ __device__ __forceinline__ void load8(const uint16_t* __restrict__ sym, long lon
 __global__ void __launch_bounds__(256)
     huff_count_kernel(const uint16_t* __restrict__ sym, long long n,
                       const unsigned char* __restrict__ len, long long nchunks, int chunk,
-                      unsigned long long* __restrict__ offs, int* err) {
+                      unsigned long long* __restrict__ offs, uint16_t* __restrict__ sub,
+                      int* err) {
   const long long c = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (c >= nchunks) return;
   const long long base = c * chunk;
-  unsigned bits = 0;
+  const int runs = entropy_runs(chunk);
+  unsigned bits = 0, rbits = 0;
   bool missing = false;  // a code the table has no entry for
+  // step j covers codes 256 j .. 256 j + 255 of the chunk: two steps per run
   for (int j = 0; j < chunk / 256; ++j) {
     const long long i = base + 8ll * (j * 32 + lane);
-    if (i >= n) break;
-    uint32_t v[4];
-    load8(sym, i, n, v);
+    if (i < n) {
+      uint32_t v[4];
+      load8(sym, i, n, v);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      if (i + k >= n) break;
-      const unsigned L = len[(v[k >> 1] >> (16 * (k & 1))) & 0xffffu];
-      missing |= L == 0u;
-      bits += L;
+      for (int k = 0; k < 8; ++k) {
+        if (i + k >= n) break;
+        const unsigned L = len[(v[k >> 1] >> (16 * (k & 1))) & 0xffffu];
+        missing |= L == 0u;
+        rbits += L;
+      }
+    }
+    if (runs > 1 && (j & 1)) {  // a run ends: its length into the table (all but the last)
+      unsigned r = rbits;
+      for (int off = 16; off > 0; off >>= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
+      if (lane == 0 && (j >> 1) + 1 < runs) sub[c * (runs - 1) + (j >> 1)] = (uint16_t)r;
+      bits += rbits;
+      rbits = 0;
     }
   }
+  bits += rbits;
   if (missing) atomicOr(err, 2);
   for (int off = 16; off > 0; off >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, off);
   if (lane == 0) offs[c] = (bits + 31) / 32;
@@ -479,8 +491,9 @@ __device__ __noinline__ int2 decode_long(const DecTables& T, uint32_t x, unsigne
 
 __global__ void __launch_bounds__(kDecThreads)
     huff_decode_kernel(const uint32_t* __restrict__ words,
-                       const unsigned long long* __restrict__ offs, long long nchunks,
-                       int chunk, long long n, const HuffFixed* __restrict__ fx,
+                       const unsigned long long* __restrict__ offs,
+                       const uint16_t* __restrict__ sub, long long nchunks, int chunk,
+                       int runs, long long n, const HuffFixed* __restrict__ fx,
                        const uint16_t* __restrict__ syms, unsigned nss,
                        uint16_t* __restrict__ out, int* err) {
   __shared__ DecTables T;
@@ -525,15 +538,26 @@ __global__ void __launch_bounds__(kDecThreads)
   // the first nss symbols (the long codes' among them) in shared memory
   for (unsigned k = t; k < nss; k += blockDim.x) ssym[k] = syms[k];
   __syncthreads();
-  const long long c = blockIdx.x * (long long)blockDim.x + t;
-  if (c >= nchunks) return;
+  // one thread per run of a chunk: its first bit is the sum of the lengths
+  // the table records for the runs before it
+  const long long item = blockIdx.x * (long long)blockDim.x + t;
+  if (item >= nchunks * runs) return;
+  const long long c = item / runs;
+  const int run = (int)(item - c * runs);
   const unsigned long long w0 = offs[c], w1 = offs[c + 1];
   if (w1 < w0 || w1 - w0 > 0xffffffffull) {
     atomicOr(err, 4);
     return;
   }
-  const unsigned nw = (unsigned)(w1 - w0);  // the chunk's words
-  const uint32_t* W = words + w0;
+  unsigned long long first = 0;  // the run's first bit in the chunk
+  for (int k = 0; k < run; ++k) first += sub[c * (runs - 1) + k];
+  const unsigned long long cbits = 32ull * (w1 - w0);
+  if (first > cbits) {
+    atomicOr(err, 4);
+    return;
+  }
+  const unsigned nw = (unsigned)(w1 - w0 - (first >> 5));  // words from the run's first on
+  const uint32_t* W = words + w0 + (first >> 5);
   // The chunk's words pass through this thread's ring of kRingWords words
   // in shared memory (four groups of kRingGroup), filled by asynchronous
   // copies a group at a time: when the window's second word enters group m,
@@ -562,7 +586,7 @@ __global__ void __launch_bounds__(kDecThreads)
   // the window: words wcur and wcur + 1 (w0r, w1r), sh bits of w0r consumed
   unsigned wcur = 0;
   uint32_t w0r = ring[0], w1r = ring[1];
-  int sh = 0;
+  int sh = (int)(first & 31);
   // the window moves on by one word when adv (without a branch but for the
   // rare refill)
   auto advance = [&](bool adv) {
@@ -618,8 +642,10 @@ __global__ void __launch_bounds__(kDecThreads)
     advance(adv);
     return true;
   };
-  const long long b = c * chunk;
-  const int cnt = (int)(b + chunk < n ? chunk : n - b);
+  const long long b = c * chunk + (long long)run * kEntropyRun;
+  const long long cend = c * chunk + chunk < n ? c * chunk + chunk : n;
+  const long long rend = runs > 1 && b + kEntropyRun < cend ? b + kEntropyRun : cend;
+  const int cnt = b < rend ? (int)(rend - b) : 0;
   uint16_t* o = out + b;
   int i = 0;
   for (; i + 8 <= cnt; i += 8) {  // chunks start on multiples of eight codes
@@ -645,8 +671,11 @@ __global__ void __launch_bounds__(kDecThreads)
     }
     o[i] = (uint16_t)sym;
   }
-  // the codes must end inside the chunk's words
-  if (32ull * wcur + (unsigned long long)sh > 32ull * nw) atomicOr(err, 4);
+  // the codes must end inside the chunk's words, and a run but the last
+  // exactly where the table puts the next one
+  const unsigned long long end = 32ull * ((first >> 5) + wcur) + (unsigned long long)sh;
+  if (end > cbits || (run + 1 < runs && end != first + sub[c * (runs - 1) + run]))
+    atomicOr(err, 4);
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
@@ -665,9 +694,12 @@ qoz_status huff_encode(const qoz_blob* b, cudaStream_t s, HuffEncoded* h, bool s
   memset(h, 0, sizeof(*h));
   h->chunk = entropy_chunk(b->N);
   h->n_chunks = (b->N + h->chunk - 1) / h->chunk;
-  // the section's fixed part and symbol list, then the chunk offsets
+  // the section's fixed part and symbol list, then the chunk offsets and
+  // the run table
   h->sym_bytes = pad8_bytes(sizeof(uint16_t) * kSymbols);
-  const size_t sec = sizeof(HuffFixed) + h->sym_bytes + sizeof(unsigned long long) * (h->n_chunks + 1);
+  h->sub_bytes = entropy_sub_bytes(h->n_chunks, h->chunk);
+  const size_t sec = sizeof(HuffFixed) + h->sym_bytes +
+                     sizeof(unsigned long long) * (h->n_chunks + 1) + h->sub_bytes;
   cudaError_t e = dev_alloc(&h->d_work, sizeof(HuffWork), s);
   if (e == cudaSuccess) e = dev_alloc(&h->d_section, sec, s);
   if (e != cudaSuccess) {
@@ -679,6 +711,7 @@ qoz_status huff_encode(const qoz_blob* b, cudaStream_t s, HuffEncoded* h, bool s
   uint16_t* syms = reinterpret_cast<uint16_t*>(static_cast<char*>(h->d_section) + sizeof(HuffFixed));
   unsigned long long* offs = reinterpret_cast<unsigned long long*>(
       static_cast<char*>(h->d_section) + sizeof(HuffFixed) + h->sym_bytes);
+  uint16_t* sub_tab = reinterpret_cast<uint16_t*>(offs + (h->n_chunks + 1));
   e = cudaMemsetAsync(h->d_section, 0, sec, s);
   constexpr size_t kTabSmem = (size_t)kHuffSmemSym * (8 + 8 + 8 + 1 + 1);
   static unsigned long long attr_done = 0;
@@ -693,7 +726,7 @@ qoz_status huff_encode(const qoz_blob* b, cudaStream_t s, HuffEncoded* h, bool s
   const unsigned grid = (unsigned)((nch * 32 + 255) / 256);
   if (e == cudaSuccess && nch > 0) {
     huff_count_kernel<<<grid, 256, 0, s>>>(b->d_codes, b->N, w->len, nch, h->chunk, offs,
-                                           &w->err);
+                                           sub_tab, &w->err);
     note_launch(1);
     e = launch_check(cudaGetLastError());
   }
@@ -765,6 +798,7 @@ qoz_status huff_encode(const qoz_blob* b, cudaStream_t s, HuffEncoded* h, bool s
 cudaError_t huff_decode(const void* d_section, const uint32_t* d_words, long long nchunks,
                         int chunk, unsigned n_sym, long long N, uint16_t* d_codes, int* d_err,
                         cudaStream_t s) {
+  const int runs = entropy_runs(chunk);
   if (nchunks <= 0) return cudaSuccess;
   const HuffFixed* fx = static_cast<const HuffFixed*>(d_section);
   const uint16_t* syms =
@@ -779,9 +813,10 @@ cudaError_t huff_decode(const void* d_section, const uint32_t* d_words, long lon
   cudaError_t e = ensure_smem_attr((const void*)huff_decode_kernel, &attr_done,
                                    kRingBytes + sizeof(uint16_t) * kDecSmemSym);
   if (e != cudaSuccess) return e;
-  const unsigned grid = (unsigned)((nchunks + kDecThreads - 1) / kDecThreads);
+  const uint16_t* sub = reinterpret_cast<const uint16_t*>(offs + (nchunks + 1));
+  const unsigned grid = (unsigned)((nchunks * runs + kDecThreads - 1) / kDecThreads);
   huff_decode_kernel<<<grid, kDecThreads, kRingBytes + sizeof(uint16_t) * nss, s>>>(
-      d_words, offs, nchunks, chunk, N, fx, syms, nss, d_codes, d_err);
+      d_words, offs, sub, nchunks, chunk, runs, N, fx, syms, nss, d_codes, d_err);
   note_launch(1);
   return cudaGetLastError();
 }

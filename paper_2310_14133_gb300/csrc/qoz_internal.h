@@ -195,6 +195,17 @@ inline int entropy_chunk(long long N) {
   while (c > kEntropyChunkMin && (N + c - 1) / c < 8192) c >>= 1;
   return c;
 }
+// Runs of a chunk: a chunk of 1024 codes or more is cut into runs of
+// kEntropyRun codes, and the section records the coded length of each run
+// but the last (n_chunks * (runs - 1) uint16 after the chunk offsets), so
+// that the decoder starts a thread at every run.
+constexpr int kEntropyRun = 512;
+__host__ __device__ inline int entropy_runs(int chunk) {
+  return chunk >= 2 * kEntropyRun ? chunk / kEntropyRun : 1;
+}
+inline size_t entropy_sub_bytes(long long n_chunks, int chunk) {
+  return ((size_t)2 * (size_t)n_chunks * (size_t)(entropy_runs(chunk) - 1) + 7) & ~(size_t)7;
+}
 constexpr int kMaxCodeLen = 58;      // longest code the coder handles
 
 // Fixed part of the serialized code section (288 bytes): counts, then the
@@ -216,6 +227,7 @@ struct HuffEncoded {
   int chunk;  // symbols per chunk
   long long n_chunks, n_words;
   size_t sym_bytes;
+  size_t sub_bytes;  // the run table after the chunk offsets (padded to 8)
   void* d_work;
   void* d_section;
   uint32_t* d_words;

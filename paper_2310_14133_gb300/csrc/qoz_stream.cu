@@ -30,7 +30,7 @@ namespace qoz {
 namespace {
 
 constexpr char kMagic[8] = {'Q', 'O', 'Z', 'G', 'B', '3', '0', '0'};
-constexpr uint32_t kVersion = 2;
+constexpr uint32_t kVersion = 3;
 constexpr int32_t kCodingHuffman = 1;
 
 struct Header {
@@ -107,12 +107,12 @@ uint64_t host_checksum(const unsigned char* p, size_t nbytes, uint64_t word0) {
 size_t pad8(size_t v) { return (v + 7) & ~(size_t)7; }
 
 struct Layout {
-  size_t anchors, uidx, uval, codes, sym, offs, words, total;
+  size_t anchors, uidx, uval, codes, sym, offs, sub, words, total;
 };
 
 // Offsets of every part; the code section's sizes come from its fixed part.
 Layout layout_of(long long na, long long nu, long long n_sym, long long n_chunks,
-                 long long n_words) {
+                 long long n_words, int chunk) {
   Layout L;
   L.anchors = sizeof(Header);
   L.uidx = L.anchors + pad8(sizeof(float) * na);
@@ -120,13 +120,14 @@ Layout layout_of(long long na, long long nu, long long n_sym, long long n_chunks
   L.codes = L.uval + pad8(sizeof(float) * nu);
   L.sym = L.codes + sizeof(HuffFixed);
   L.offs = L.sym + pad8(sizeof(uint16_t) * n_sym);
-  L.words = L.offs + sizeof(unsigned long long) * (n_chunks + 1);
+  L.sub = L.offs + sizeof(unsigned long long) * (n_chunks + 1);
+  L.words = L.sub + (chunk > 0 ? entropy_sub_bytes(n_chunks, chunk) : 0);
   L.total = L.words + pad8(sizeof(uint32_t) * n_words);
   return L;
 }
 
 Layout layout_of(const qoz_blob* b, const HuffEncoded& h) {
-  return layout_of(b->na, b->nu, h.fixed.n_sym, h.n_chunks, h.n_words);
+  return layout_of(b->na, b->nu, h.fixed.n_sym, h.n_chunks, h.n_words, h.chunk);
 }
 
 // The device-resident parts, each with its place in the stream.
@@ -143,8 +144,7 @@ int parts_of(const qoz_blob* b, const HuffEncoded& h, const Layout& L, Part* out
       {b->d_uval, sizeof(float) * b->nu, L.uval},
       {sec, sizeof(HuffFixed), L.codes},
       {sec + sizeof(HuffFixed), L.offs - L.sym, L.sym},  // zero-padded on the device
-      {sec + sizeof(HuffFixed) + h.sym_bytes, sizeof(unsigned long long) * (h.n_chunks + 1),
-       L.offs},
+      {sec + sizeof(HuffFixed) + h.sym_bytes, L.words - L.offs, L.offs},  // offsets, run table
       {h.d_words, sizeof(uint32_t) * h.n_words, L.words}};
   int k = 0;
   for (const Part& p : ps)
@@ -328,7 +328,7 @@ qoz_status qoz_blob_serialize_bound(const qoz_blob* b, size_t* bound) {
   // alphabet; each chunk adds at most one partly filled word
   const long long nch = (b->N + kEntropyChunkMin - 1) / kEntropyChunkMin;  // at most
   const long long words = (b->N * 17 + 31) / 32 + nch;
-  *bound = layout_of(b->na, b->nu, 65536, nch, words).total;
+  *bound = layout_of(b->na, b->nu, 65536, nch, words, kEntropyChunkMin).total;
   return QOZ_OK;
 }
 
@@ -397,14 +397,16 @@ qoz_status qoz_blob_deserialize(const void* h_buf, size_t size, void* stream, qo
     return fail(QOZ_ECORRUPT, "header: inconsistent counts or bound");
   const unsigned char* in = (const unsigned char*)h_buf;
   // the code section's fixed part gives the remaining sizes
-  const Layout L0 = layout_of(na, h.n_unpred, 0, 0, 0);
+  const Layout L0 = layout_of(na, h.n_unpred, 0, 0, 0, 0);
   if (size < L0.codes + sizeof(HuffFixed)) return fail(QOZ_ECORRUPT, "stream truncated");
   HuffFixed f;
   memcpy(&f, in + L0.codes, sizeof(f));
   if (f.n_sym > 65536 || (long long)f.n_chunks < 0 || f.n_chunks > (uint64_t)r.N + 1 ||
-      f.n_words > (uint64_t)(size / 4))
+      f.n_words > (uint64_t)(size / 4) || f.chunk < 8 || f.chunk > (uint32_t)kEntropyChunk ||
+      f.chunk % 8 != 0)
     return fail(QOZ_ECORRUPT, "code section: inconsistent sizes");
-  const Layout L = layout_of(na, h.n_unpred, f.n_sym, (long long)f.n_chunks, (long long)f.n_words);
+  const Layout L = layout_of(na, h.n_unpred, f.n_sym, (long long)f.n_chunks, (long long)f.n_words,
+                             (int)f.chunk);
   if (size < L.total || h.code_bytes != L.total - L.codes)
     return fail(QOZ_ECORRUPT, "stream truncated (%zu < %zu)", size, L.total);
   if (!code_section_ok(f, r.N, in + L.sym, L.offs - L.sym))
@@ -461,7 +463,8 @@ qoz_status qoz_blob_deserialize(const void* h_buf, size_t size, void* stream, qo
   };
   unsigned long long* d_acc = nullptr;
   cudaError_t e;
-  const size_t sec = sizeof(HuffFixed) + hc.sym_bytes + 8 * (hc.n_chunks + 1);
+  hc.sub_bytes = entropy_sub_bytes(hc.n_chunks, hc.chunk);
+  const size_t sec = sizeof(HuffFixed) + hc.sym_bytes + 8 * (hc.n_chunks + 1) + hc.sub_bytes;
   if ((e = dev_alloc((void**)&b->d_codes, sizeof(uint16_t) * b->N, s)) != cudaSuccess ||
       (e = dev_alloc((void**)&b->d_anchors, sizeof(float) * na, s)) != cudaSuccess ||
       (e = dev_alloc((void**)&b->d_uidx, sizeof(long long) * b->nu, s)) != cudaSuccess ||

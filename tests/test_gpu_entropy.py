@@ -43,7 +43,7 @@ def pad8(v):
 
 
 def parse(buf):
-    """Sections of a serialized stream (format 2) as numpy views."""
+    """Sections of a serialized stream (format 3) as numpy views."""
     b = bytes(buf.numpy()) if hasattr(buf, "numpy") else bytes(buf)
     n_anchors, n_unpred = struct.unpack_from("<qq", b, OFF_ANCHORS)
     off = HEADER + pad8(4 * n_anchors) + pad8(8 * n_unpred) + pad8(4 * n_unpred)
@@ -53,11 +53,14 @@ def parse(buf):
     syms = np.frombuffer(b, dtype=np.uint16, count=n_sym, offset=so)
     oo = so + pad8(2 * n_sym)
     offs = np.frombuffer(b, dtype=np.uint64, count=n_chunks + 1, offset=oo)
-    wo = oo + 8 * (n_chunks + 1)
+    runs = chunk // 512 if chunk >= 1024 else 1
+    ro = oo + 8 * (n_chunks + 1)
+    sub = np.frombuffer(b, dtype=np.uint16, count=n_chunks * (runs - 1), offset=ro)
+    wo = ro + pad8(2 * n_chunks * (runs - 1))
     words = np.frombuffer(b, dtype=np.uint32, count=n_words, offset=wo)
     return dict(code_off=off, n_sym=n_sym, max_len=max_len, chunk=chunk, flags=flags,
-                n_chunks=n_chunks, n_words=n_words, bl=bl, syms=syms, offs=offs, words=words,
-                total=wo + pad8(4 * n_words))
+                n_chunks=n_chunks, n_words=n_words, bl=bl, syms=syms, offs=offs, sub=sub,
+                sub_off=ro, words_off=wo, words=words, total=wo + pad8(4 * n_words))
 
 
 def expected(orc, codes, chunk=None):
@@ -67,11 +70,12 @@ def expected(orc, codes, chunk=None):
     ln, mx = orc.huffman_lengths(h)
     cd = orc.canonical_codes(ln)
     words, offs = orc.huffman_encode(codes.ravel(), ln, cd, chunk=chunk)
+    sub = orc.huffman_subruns(codes.ravel(), ln, chunk=chunk)
     used = np.nonzero(ln)[0]
     order = sorted(used, key=lambda s: (int(ln[s]), int(s)))
     bl = np.bincount(ln[used], minlength=64).astype(np.uint32)
-    return dict(ln=ln, cd=cd, mx=mx, words=words, offs=offs, syms=np.array(order, np.uint16),
-                bl=bl)
+    return dict(ln=ln, cd=cd, mx=mx, words=words, offs=offs, sub=sub,
+                syms=np.array(order, np.uint16), bl=bl)
 
 
 def check_section(orc, q, blob, buf):
@@ -83,6 +87,7 @@ def check_section(orc, q, blob, buf):
     assert np.array_equal(sec["bl"], ref["bl"]), "codes per length"
     assert np.array_equal(sec["syms"], ref["syms"]), "symbol order"
     assert np.array_equal(sec["offs"], ref["offs"]), "chunk word offsets"
+    assert np.array_equal(sec["sub"], ref["sub"]), "run table"
     assert np.array_equal(sec["words"], ref["words"]), "stream words"
     assert sec["total"] == buf.numel()
     # the stream's length is exactly the sum of the code lengths, per chunk
@@ -98,6 +103,8 @@ CASES = [
     ((7, 1, 9), 1e-2, 11),
     ((1, 1, 1), 1e-3, 12),       # one point: an anchor, one symbol
     ((64, 64, 64), 1e-2, 13),
+    ((128, 256, 256), 1e-3, 14),  # chunks of 1024: two runs each
+    ((201, 255, 333), 1e-4, 15),  # chunks of 2048: four runs, ragged tail
 ]
 
 
@@ -149,7 +156,7 @@ def _checksum(b):
         return int(np.sum(mix(w ^ mix(np.arange(w.size, dtype=np.uint64))), dtype=np.uint64))
 
 
-@pytest.mark.parametrize("chunk", [CHUNK, 512, 200])
+@pytest.mark.parametrize("chunk", [CHUNK, 2048, 512, 200])
 def test_gpu_decodes_oracle_stream(q, orc, chunk):
     # replace the GPU's code section by one the oracle wrote (layout as
     # specified; a reader takes any chunk size that is a multiple of 8 up to
@@ -165,7 +172,10 @@ def test_gpu_decodes_oracle_stream(q, orc, chunk):
                         ref["words"].size) + ref["bl"].tobytes()
     body = fixed + ref["syms"].tobytes()
     body += bytes(pad8(len(body)) - len(body))
-    body += ref["offs"].astype(np.uint64).tobytes() + ref["words"].tobytes()
+    body += ref["offs"].astype(np.uint64).tobytes()
+    body += ref["sub"].astype(np.uint16).tobytes()
+    body += bytes(pad8(len(body)) - len(body))
+    body += ref["words"].tobytes()
     body += bytes(pad8(len(body)) - len(body))
     out = bytearray(buf[:sec["code_off"]]) + body
     struct.pack_into("<Q", out, OFF_CODE_BYTES, len(body))
@@ -192,7 +202,7 @@ def test_corrupt_code_sections(q):
 
     # a flipped stream bit: caught by the checksum or the decoder
     b = bytearray(raw)
-    b[sec["code_off"] + FIXED + pad8(2 * sec["n_sym"]) + 8 * (sec["n_chunks"] + 1) + 5] ^= 0x40
+    b[sec["words_off"] + 5] ^= 0x40
     expect_corrupt(b)
     # an incomplete code (one length count changed)
     b = bytearray(raw)
@@ -232,3 +242,23 @@ def test_async_matches_sync_and_bound(q):
     # smaller than the raw 16-bit codes
     assert used < 2 * x.numel()
     blob.free()
+
+
+def test_corrupt_run_table(q):
+    """A run-table entry off by one (checksum made valid): the runs no longer
+    meet where the table says, and the decoder reports the stream corrupt."""
+    import synth
+    x = synth.grf((128, 256, 256), 5.0 / 3.0, seed=5, n_modes=32).cuda()
+    blob = q.compress(x, 1e-3)
+    buf = blob.serialize()
+    sec = parse(buf)
+    assert sec["chunk"] == 1024 and sec["sub"].size == sec["n_chunks"]
+    raw = bytearray(bytes(buf.numpy()))
+    k = sec["sub_off"] + 2 * (sec["n_chunks"] // 2)
+    struct.pack_into("<H", raw, k, struct.unpack_from("<H", raw, k)[0] + 1)
+    struct.pack_into("<Q", raw, OFF_CHECKSUM, _checksum(bytes(raw)))
+    with pytest.raises(q.QozError) as ei:
+        q.deserialize(torch.frombuffer(raw, dtype=torch.uint8))
+    assert ei.value.status == 4
+    blob.free()
+
