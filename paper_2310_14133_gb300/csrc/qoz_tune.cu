@@ -978,9 +978,14 @@ __device__ double e0_dev(const BoundTable& bt, const E0Spec& sp) {
 // The (alpha, beta) candidates of Sec. 6.3, built on the device once
 // Algorithm 1 has chosen every level: candidate k = (si * na + ia) * nb + ib
 // at bound scales[si] * e0.
+// The (alpha, beta) candidates of a tune: n_pairs distinct settings (index
+// pairs into alphas / betas) at n_scales bounds.  With alpha = 1 every level
+// bound is e (min(1, beta) = 1 for beta >= 1), so the pairs (1, beta) after
+// the first give the same trial and are not run; the host copies its result.
 struct AbSpec {
-  int n_alpha, n_beta, n_scales;
+  int n_alpha, n_beta, n_scales, n_pairs;
   double alphas[8], betas[8], scales[3];
+  unsigned char pa[64], pb[64];
 };
 
 // Bounds of the top-level Algorithm 1 candidates (alpha = beta = 1, every
@@ -1033,18 +1038,18 @@ __global__ void __launch_bounds__(32 * kAlg1MaxCand)
   __syncthreads();
   if (l == 1) {
     // every level chosen: the (alpha, beta) candidates, when asked for
-    const int nab = ab.n_alpha * ab.n_beta;
-    if (nab == 0) return;
+    const int np = ab.n_pairs;
+    if (np == 0) return;
     const double e0 = *e0p;
-    for (int k = threadIdx.x; k < ab.n_scales * nab; k += blockDim.x) {
+    for (int k = threadIdx.x; k < ab.n_scales * np; k += blockDim.x) {
       TrialCand t = base;
       for (int ll = 1; ll <= Ls; ++ll) {
         t.interp[ll - 1] = h.chi[ll - 1];
         set_axes_dev(&t, ll, ndims, h.cho[ll - 1]);
       }
-      const int si = k / nab, kk = k - si * nab;
-      fill_bounds_dev(&t, __dmul_rn(ab.scales[si], e0), ab.alphas[kk / ab.n_beta],
-                      ab.betas[kk % ab.n_beta], Ls);
+      const int si = k / np, kk = k - si * np;
+      fill_bounds_dev(&t, __dmul_rn(ab.scales[si], e0), ab.alphas[ab.pa[kk]], ab.betas[ab.pb[kk]],
+                      Ls);
       cands[k] = t;
     }
     return;
@@ -1238,7 +1243,7 @@ class Tuner {
     const int nc = (int)cl.size();
     if (nc == 0 || nc > kAlg1MaxCand) return fail(QOZ_EINVAL, "1..16 Algorithm 1 candidates");
     if (!d_range_) return fail(QOZ_EINVAL, "tuner value range not started");
-    const int nab = ab.n_alpha * ab.n_beta * ab.n_scales;
+    const int nab = ab.n_pairs * ab.n_scales;
     qoz_status st = ensure(nc > nab ? nc : nab);
     if (st != QOZ_OK) return st;
     Alg1Ctl h;
@@ -1684,12 +1689,31 @@ qoz_status tune_impl(const float* d_field, const qoz_shape& shape, double rel_eb
   ab.scales[0] = 1.0;
   ab.scales[1] = 0.8;
   ab.scales[2] = 1.2;
-  std::vector<TrialResult> res;
+  // distinct settings: every (1, beta) after the first repeats its trial
+  std::vector<int> pair_of(nab);
+  int first_unit = -1;
+  ab.n_pairs = 0;
+  for (int k = 0; k < nab; ++k) {
+    const int ai = k / o.n_beta, bi = k % o.n_beta;
+    if (o.alphas[ai] == 1.0 && first_unit >= 0) {
+      pair_of[k] = first_unit;
+      continue;
+    }
+    if (o.alphas[ai] == 1.0) first_unit = ab.n_pairs;
+    ab.pa[ab.n_pairs] = (unsigned char)ai;
+    ab.pb[ab.n_pairs] = (unsigned char)bi;
+    pair_of[k] = ab.n_pairs++;
+  }
+  std::vector<TrialResult> ures, res;
   Alg1Ctl ctl;
   BoundTable bt;
   if ((st = T.alg1_enqueue(base, cands, d, sp, ab)) != QOZ_OK) return st;
-  if ((st = T.launch(ab.n_scales * nab, 1, 0, true)) != QOZ_OK) return st;
-  if ((st = T.collect(ab.n_scales * nab, true, &res, &ctl, &bt)) != QOZ_OK) return st;
+  if ((st = T.launch(ab.n_scales * ab.n_pairs, 1, 0, true)) != QOZ_OK) return st;
+  if ((st = T.collect(ab.n_scales * ab.n_pairs, true, &ures, &ctl, &bt)) != QOZ_OK) return st;
+  res.resize((size_t)ab.n_scales * nab);
+  for (int si = 0; si < ab.n_scales; ++si)
+    for (int k = 0; k < nab; ++k)
+      res[(size_t)si * nab + k] = ures[(size_t)si * ab.n_pairs + pair_of[k]];
   for (int l = 1; l <= sm.Ls; ++l) {
     ch_interp[l - 1] = ctl.chi[l - 1];
     ch_order[l - 1] = ctl.cho[l - 1];
