@@ -994,9 +994,21 @@ def main():
         e2e_run(args.steps)
         barrier()
         e2e_s = (time.perf_counter() - t0) / args.steps
+        # the host link alone: one field copied in (the rate e2e cannot exceed)
+        link_ms = []
+        for _ in range(3):
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea.record(copy_stream)
+            with torch.cuda.stream(copy_stream):
+                bufs[0].copy_(hx, non_blocking=True)
+            eb.record(copy_stream)
+            eb.synchronize()
+            link_ms.append(ea.elapsed_time(eb))
+        link_gbs = 4.0 * N / (min(link_ms) * 1e-3) / 1e9
         e2e = {"value": 4.0 * N * world / e2e_s / 1e9, "unit": "GB/s",
                "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": ser_bytes,
                "ms_per_step": e2e_s * 1e3,
+               "h2d_link_gbs": link_gbs,
                "pipeline": "each step copies its field from pinned host memory (copy "
                            "stream) and reads its serialized stream (canonical Huffman code "
                            "section) back to pinned host memory (serialize on a read-back "
