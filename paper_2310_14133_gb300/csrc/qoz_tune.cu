@@ -168,7 +168,6 @@ __device__ __forceinline__ void trial_pass(const TrialPass& t, TrialAcc& acc) {
   float* S = t.S;
   const int nS = t.nS;
   (void)nS;
-  const int lane = threadIdx.x & 31;
   // a target's position, its field value and its prediction
   struct Tgt {
     int li;
@@ -240,17 +239,13 @@ __device__ __forceinline__ void trial_pass(const TrialPass& t, TrialAcc& acc) {
       if (ae != ae || ae > acc.mx) acc.mx = ae;
     }
     if (kFull && t.hist) {
-      // lanes with equal codes add once (smooth data puts most of a warp's
-      // codes in one or two bins)
-      const unsigned peers = __match_any_sync(__activemask(), code);
-      if (lane == __ffs(peers) - 1) {
-        const unsigned kk = code - (unsigned)kTHistLo;
-        const unsigned n = (unsigned)__popc(peers);
-        if (kk < (unsigned)kTHistWin)
-          atomicAdd(&t.SH[kk], n);
-        else
-          atomicAdd(&t.ghist[code], n);
-      }
+      // one shared atomic per code (the window around the zero bin), global
+      // beyond it
+      const unsigned kk = code - (unsigned)kTHistLo;
+      if (kk < (unsigned)kTHistWin)
+        atomicAdd(&t.SH[kk], 1u);
+      else
+        atomicAdd(&t.ghist[code], 1u);
     }
   };
   for (int it = threadIdx.x; it < items; it += THREADS) {
