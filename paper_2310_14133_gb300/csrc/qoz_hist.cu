@@ -10,8 +10,9 @@ namespace qoz {
 namespace {
 
 // Codes concentrate around the zero bin 32768; a shared-memory window covers
-// the bins near it, the rare far bins go straight to global memory.  Equal
-// codes within a warp are merged with one match before the shared atomic.
+// the bins near it, the rare far bins go straight to global memory.  One
+// atomic per code: merging a warp's equal codes with a match first measured
+// slower in the tuner's trials.
 constexpr int kWinLo = kRadius - 2048;
 constexpr int kWin = 4096;
 constexpr int kHistThreads = 512;
@@ -21,15 +22,12 @@ constexpr int kHistBlocks = 152 * 2;
 // without a code pass kNoCode.
 constexpr unsigned kNoCode = 0xffffffffu;
 __device__ __forceinline__ void hist_add(unsigned* sh, unsigned* gh, unsigned code) {
-  const unsigned peers = __match_any_sync(0xffffffffu, code);
-  const int lane = threadIdx.x & 31;
-  if (code != kNoCode && lane == __ffs(peers) - 1) {
-    const unsigned k = code - (unsigned)kWinLo;
-    if (k < (unsigned)kWin)
-      atomicAdd(&sh[k], (unsigned)__popc(peers));
-    else
-      atomicAdd(&gh[code], (unsigned)__popc(peers));
-  }
+  if (code == kNoCode) return;
+  const unsigned k = code - (unsigned)kWinLo;
+  if (k < (unsigned)kWin)
+    atomicAdd(&sh[k], 1u);
+  else
+    atomicAdd(&gh[code], 1u);
 }
 
 __global__ void __launch_bounds__(kHistThreads) hist_kernel(const uint16_t* __restrict__ codes,
