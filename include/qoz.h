@@ -11,7 +11,13 @@
  *     Eq. ssim2), and the Huffman rate estimate of the quantization bins
  *     (Sec. 6.1),
  *   - the sampled online tuner (Sec. 6.1 sampling, Algorithm 1, Sec. 6.3
- *     candidates and Table I comparisons).
+ *     candidates and Table I comparisons),
+ *   - the lag-k error autocorrelation (Eq. ac) and its tuning mode,
+ *   - a learned tuner (features, a small network and its training), which
+ *     the paper's conclusion leaves to future work,
+ *   - batched compression of many fields in one plan,
+ *   - serialization with canonical Huffman coding of the codes (the entropy
+ *     stage the rate estimate of Sec. 6.1 stands for).
  *
  * General conventions
  *   - Field dims are slowest-first: 2D {ny, nx}, 3D {nz, ny, nx}; the last
