@@ -267,8 +267,15 @@ qoz_status qoz_batch_create(const qoz_shape* shapes, int32_t nfields, const qoz_
  * bound eb[i]: relative to the field's value range when eb_relative != 0
  * (eb > 0), absolute otherwise (eb >= 0).  outs[i] receive blobs allocated
  * stream-ordered on `stream` (free each with qoz_blob_free).  Synchronises
- * `stream` once.  A plan serves one run at a time: calls on one plan must not
- * overlap. */
+ * `stream` after the run and again once the unpredictable lists are copied
+ * out (the plan reuses its list buffers).  A plan serves one run at a time:
+ * calls on one plan must not overlap.  A field whose unpredictable points
+ * overflow the plan's list is compressed again alone (qoz_compress_abs's
+ * path, same result).  Errors: QOZ_EINVAL (a NULL array, a misaligned field
+ * or a bad bound), QOZ_ENOMEM, QOZ_ECUDA, and QOZ_ETIMEOUT when a bounded
+ * wait for a tile's bulk copy gave up in any field, after which the plan
+ * serves the next call as before; on any failure no blob is returned
+ * (every outs[i] = NULL). */
 qoz_status qoz_batch_compress(qoz_batch* plan, const float* const* d_fields, const double* eb,
                               int32_t eb_relative, void* stream, qoz_blob** outs);
 
