@@ -305,8 +305,9 @@ qoz_status qoz_compress_batch(const float* const* d_fields, const qoz_shape* sha
 /* ---------------------------------------------------------------- metrics */
 
 typedef struct {
-  double max_abs_err;    /* max |a - b| (computed in double, exact) */
-  double mse;            /* mean of (a - b)^2 over all points, in double */
+  double max_abs_err;    /* max |a - b|, exact: the difference of the maximising pair in double */
+  double mse;            /* mean of (a - b)^2 over all points: compensated binary32 sums per
+                            thread, double across threads (1e-6 relative of the double sum) */
   double psnr;           /* Eq. psnr: 20 log10(vrange / sqrt(mse)); +inf if mse = 0 */
   double ssim;           /* Eq. ssim: mean over windows (NaN if not requested / none) */
   int64_t ssim_windows;

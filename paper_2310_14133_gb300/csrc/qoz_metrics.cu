@@ -3,10 +3,11 @@
 // fixed order, so every result is deterministic.
 //
 // Arithmetic.  The maximum error is exact: the binary32 difference |a - b| is
-// a monotone rounding of the exact one, so only elements whose rounded
-// difference reaches the running maximum are re-evaluated in double.  The
-// squared errors are summed in binary32 with compensation (Kahan), per
-// thread, then in double across threads.
+// a monotone rounding of the exact one, so each thread keeps the element that
+// leads by its rounded difference and, among ties, by the subtraction's
+// rounding error; the leader's difference is taken in double at the end.
+// The squared errors and the autocorrelation terms are summed in binary32
+// with compensation (Kahan), per thread, then in double across threads.
 //
 // SSIM.  For windows of edge 7 the moments are box sums taken separably:
 // along x in registers, along y in shared memory, along z through a ring of
