@@ -17,16 +17,21 @@
 //     from 256 to 4096 that gives at least 8192 chunks, recorded in the
 //     section's fixed part), each starting on a 32-bit
 //     word, codes most significant bit first, words filled from their most
-//     significant bit, the tail of a chunk's last word zero.
+//     significant bit, the tail of a chunk's last word zero;
+//   - run table: a chunk of 1024 symbols or more is cut into runs of
+//     kEntropyRun (512) symbols, and the coded length in bits of each run
+//     but the last is stored (uint16), so a decoder can start at every run.
 //
 // Kernels: one CTA builds the table (shared memory up to kHuffSmemSym used
-// symbols, a global workspace beyond); the encoder counts each chunk's words,
-// scans them into word offsets and writes the chunks (one warp per chunk,
-// each lane a run of consecutive symbols); the decoder walks one chunk per
-// thread with a 12-bit lookup table and, for longer codes, the canonical
-// codes' interval ends, checking every index against the stream it was
-// given.  Smaller fields get smaller chunks so that their decode still
-// spreads over thousands of threads.
+// symbols, a global workspace beyond); the encoder counts each chunk's words
+// and its runs' bits, scans the word counts into offsets and writes the
+// chunks (one warp per chunk, each lane a run of consecutive symbols); the
+// decoder gives each run its own thread, which starts at the bit the run
+// table gives and decodes with a 12-bit lookup table and, for longer codes,
+// the canonical codes' interval ends, checking every index against the
+// stream it was given and that the run ends where the next one starts.
+// Smaller fields get smaller chunks so that their decode still spreads over
+// thousands of threads.
 #include <cuda_runtime.h>
 
 #include <cstring>

@@ -7,8 +7,10 @@
 // each part padded to 8 bytes.  The code section is the entropy stage's
 // output: its 288-byte fixed part (symbol count, longest code, chunk size,
 // chunk and word counts, number of codes per length), the used symbols in
-// (length, symbol) order, the n_chunks + 1 word offsets (uint64) and the
-// stream words (uint32).  The header's checksum field holds a 64-bit sum over
+// (length, symbol) order, the n_chunks + 1 word offsets (uint64), for chunks
+// of 1024 codes or more the run table (the coded bits of each 512-code run
+// but a chunk's last, uint16) and the stream words (uint32).  The header's
+// checksum field holds a 64-bit sum over
 // every 8-byte word w_i of header and payload of mix(w_i ^ mix(i)), taken
 // with the field itself zero; being a sum, it is computed on the device for
 // the device-resident parts, in parallel, and on the host for the header.
