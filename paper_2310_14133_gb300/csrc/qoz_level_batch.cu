@@ -4,8 +4,10 @@
 // into shared memory and runs the same tile code as the single-field launch,
 // so every field's codes, reconstruction, list and histogram are those of a
 // single-field compression.  Two row-copy tile shapes per instance are
-// compiled, and for level 1 the bulk-copy kernel; the batch plan times them
-// on its first run and keeps the fastest.
+// compiled, and for level 1 the bulk-copy kernel (one tile per CTA) and, for
+// 3-D fields, the persistent bulk-copy kernel of qoz_level1.cuh, whose CTAs
+// walk the tiles of all the launch's fields; the batch plan can time them
+// on its first run and keep the fastest.
 #include "qoz_level1.cuh"
 #include "qoz_level_impl.cuh"
 

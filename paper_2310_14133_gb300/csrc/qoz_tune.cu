@@ -12,6 +12,8 @@
 // decisions; trials whose outcome does not depend on an earlier decision are
 // batched into one launch (all candidates of an Algorithm 1 level; all
 // (alpha, beta) at e and at the 0.8 e / 1.2 e that Table I may ask for).
+// Every (1, beta) gives e_l = e on all levels (beta >= 1), so of those only
+// the first setting runs and the others take its results.
 #include <cuda_runtime.h>
 
 #include <algorithm>
