@@ -258,9 +258,9 @@ ENTROPY_CHUNK = 4096
 
 
 def entropy_chunk(n: int) -> int:
-    """The stream's chunk size for n codes (reading A21 of the entropy
-    stage): the largest of 4096, 2048, 1024, 512 and 256 codes that still
-    gives at least 8192 chunks, else 256."""
+    """The stream's chunk size for n codes (a layout the paper leaves open;
+    this project's reading): the largest of 4096, 2048, 1024, 512 and 256
+    codes that still gives at least 8192 chunks, else 256."""
     c = ENTROPY_CHUNK
     while c > 256 and -(-n // c) < 8192:
         c //= 2

@@ -200,7 +200,8 @@ int orc_table1(double b1, double m1, double b2, double m2, double b2p, double m2
 }
 
 /* Candidate k of the (alpha, beta) search: alpha ascending in the outer
- * loop, beta in the inner one (reading A10's visiting order). */
+ * loop, beta in the inner one (the paper lists the candidates but not the
+ * order it visits them in; this is the order taken here). */
 void orc_ab_candidate(const orc_tune_opts* o, int k, double* alpha, double* beta) {
   *alpha = o->alphas[k / o->n_beta];
   *beta = o->betas[k % o->n_beta];
@@ -234,9 +235,9 @@ int orc_select_fixed(int n, const double* B, const double* M, int maxerr_mode,
   return best;
 }
 
-/* Target mode (reading A11): the second point of a candidate is taken at
- * 1.2 e0 when the first already meets the target (a larger bound lowers the
- * rate), else at 0.8 e0. */
+/* Target mode (this project's extension of Sec. 6.3): the second point of a
+ * candidate is taken at 1.2 e0 when the first already meets the target (a
+ * larger bound lowers the rate), else at 0.8 e0. */
 double orc_target_scale(double M, double target) { return M >= target ? 1.2 : 0.8; }
 
 /* Bit rate where the line through (B, M) and (B2, M2) reaches the target;

@@ -135,9 +135,10 @@ def test_round_trip(n, chunk, seed):
 
 
 def test_chunk_size_rule(orc):
-    """The writer's chunk size (reading A21): the largest of 4096 .. 256 codes
-    that still gives 8192 chunks, else 256; worked by hand at the sizes of
-    the workloads (48^3, 256^3, 512^3, 1024^3) and at the switch points."""
+    """The writer's chunk size (this project's layout; the paper fixes
+    none): the largest of 4096 .. 256 codes that still gives 8192 chunks,
+    else 256; worked by hand at the sizes of the workloads (48^3, 256^3,
+    512^3, 1024^3) and at the switch points."""
     assert orc.entropy_chunk(0) == 256
     assert orc.entropy_chunk(48 ** 3) == 256          # 432 chunks
     assert orc.entropy_chunk(256 * 8192) == 256       # exactly 8192 chunks of 256
